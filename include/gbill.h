@@ -1,0 +1,227 @@
+/*
+ * gbill.h -- C ABI of the GB300 (sm_103a) textured 2D-Gaussian-surfel
+ * rasterizer ("Gaussian Billboards", arXiv 2412.12734), forward and backward.
+ *
+ * The library renders oriented 2D Gaussian surfels (Sec. 3.1, Eq. 3-4), each
+ * carrying an N x N RGB colour grid sampled bilinearly in its uv plane
+ * (Sec. 3.2, Eq. 5, Alg. 2) plus one set of view-dependent SH coefficients
+ * added on top (Sec. 4.2), composited front to back (Sec. 3.1, Eq. 2,
+ * Alg. 1 fwd).  The backward pass (Alg. 1 bwd, Alg. 2 adj-bilinear) returns
+ * gradients for centres, quaternions, scales, opacities, SH coefficients and
+ * texels, with the uv adjoint receiving the colour-interpolation term.
+ *
+ * Conventions shared by every entry point:
+ *   - Every array argument is a DEVICE pointer (CUDA global memory) unless the
+ *     comment says "host".  The caller owns every input and output buffer; the
+ *     library never frees them and never keeps them after a call returns
+ *     (except the saved state described at gb_saved_create).
+ *   - Floats are IEEE binary32, little endian.  Arrays are dense, row-major,
+ *     with the shapes given in brackets.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All work is enqueued on it; calls return before the GPU
+ *     finishes unless a comment says the call synchronizes.
+ *   - Errors are returned as gb_status; no call aborts, throws or exits.  A
+ *     readable message for the last failing call on a context is available
+ *     from gb_last_error().  On a non-OK return no output is guaranteed.
+ *   - A context is not thread safe: use one context per host thread.
+ *
+ * Parameter meaning (activated values; logits/log-scales live above the ABI):
+ *   means      [K,3]  splat centre p_k in world space                 (Eq. 3)
+ *   quats      [K,4]  (w,x,y,z), any nonzero norm; normalised inside; the
+ *                     tangents t_u, t_v are the first two columns of its
+ *                     rotation matrix                                  (Sec. 3.1)
+ *   scales     [K,2]  (s_u, s_v) > 0, linear                           (Eq. 3)
+ *   opacities  [K]    o_k in (0,1); alpha = min(0.99, o_k G(u,v))      (Eq. 4)
+ *   sh         [K,(D+1)^2,3]  real SH coefficients, degree D <= 3, ordered
+ *                     l = 0..D, m = -l..l; colour term added to the grid colour
+ *                     (Sec. 4.2), no offset and no clamp
+ *   textures   [K,N,N,3] colour grid C_k[i_u][i_v][rgb] spanning
+ *                     [-sigma, sigma]^2 of the uv plane, corner aligned, border
+ *                     clamped                                        (Eq. 5, Alg. 2)
+ */
+#ifndef GBILL_H
+#define GBILL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GBILL_ABI_VERSION 1
+#define GBILL_MAX_CAMERAS 64
+#define GBILL_MAX_SCENES 16
+
+typedef enum {
+    GB_OK = 0,
+    GB_ERR_INVALID_ARG = 1, /* a pointer, size, count or option is out of range   */
+    GB_ERR_UNSUPPORTED = 2, /* valid request the build does not implement          */
+    GB_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has the reason)  */
+    GB_ERR_CAPACITY = 4,    /* a reserved buffer was too small (no-sync mode)       */
+    GB_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up                   */
+    GB_ERR_NONFINITE = 6    /* non-finite values were found where none may be       */
+} gb_status;
+
+typedef enum { GB_F32 = 0, GB_F16 = 1, GB_BF16 = 2 } gb_dtype;
+
+/* Forward option flags. */
+#define GB_FLAG_NO_SYNC 1u /* never synchronize: use the reserved capacity of the
+                              saved state, flag overflow on the device (checked by
+                              gb_saved_check); required inside CUDA graph capture */
+#define GB_FLAG_PERSISTENT 2u /* render with persistent blocks pulling tiles from
+                                 a device work counter instead of one block per tile */
+
+typedef struct gb_context gb_context;
+typedef struct gb_saved gb_saved;
+
+/* One pinhole camera (OpenCV axes: x right, y down, z forward).  Pixel (x,y)
+ * has its centre at (x+0.5, y+0.5); (cx, cy) is the principal point in those
+ * pixel units.  Host struct. */
+typedef struct {
+    int32_t width, height;  /* pixels, 1..16384                                 */
+    float fx, fy, cx, cy;   /* intrinsics                                        */
+    float world_to_cam[12]; /* row-major 3x4 [R | t]; R orthonormal              */
+    float near_plane;       /* splats with centre depth <= near are culled       */
+    int32_t scene;          /* index into the scenes array of the call           */
+} gb_camera;
+
+/* One scene: K splats sharing one texture size and storage type.  Host
+ * struct whose array members are device pointers. */
+typedef struct {
+    int64_t num_splats;       /* K >= 0                                          */
+    const float *means;       /* [K,3]                                           */
+    const float *quats;       /* [K,4]                                           */
+    const float *scales;      /* [K,2]                                           */
+    const float *opacities;   /* [K]                                             */
+    const void *sh;           /* [K,(D+1)^2,3] of sh_dtype                       */
+    const void *textures;     /* [K,N,N,3] of tex_dtype                          */
+    int32_t sh_degree;        /* D in 0..3                                       */
+    int32_t sh_dtype;         /* gb_dtype                                        */
+    int32_t tex_n;            /* N in {1,2,4,8}                                  */
+    int32_t tex_dtype;        /* gb_dtype                                        */
+    float sigma;              /* grid extent in uv units (paper default 0.5)     */
+    int32_t reserved;         /* must be 0                                       */
+} gb_scene;
+
+/* Gradient outputs of one scene, FP32 device arrays shaped like the inputs.
+ * gb_render_backward OVERWRITES them with the sum over that scene's cameras.
+ * A NULL member skips that output (its work is still done). */
+typedef struct {
+    float *d_means, *d_quats, *d_scales, *d_opacities, *d_sh, *d_textures;
+} gb_grads;
+
+/* Render options (host struct; NULL = defaults). */
+typedef struct {
+    int32_t tile_size;   /* 8, 16 (default 0 = 16)                               */
+    int32_t batch_depth; /* splats staged per shared-memory batch, 0 = automatic;
+                            otherwise a multiple of 32 up to the tile's pixels    */
+    uint32_t flags;      /* GB_FLAG_*                                             */
+    int32_t reserved;    /* must be 0                                             */
+    float background[3]; /* added as T_final * background (default black)        */
+} gb_options;
+
+/* Counters of the last forward on a saved state (gb_saved_stats). */
+typedef struct {
+    int64_t records;     /* (splat, camera) pairs projected                       */
+    int64_t visible;     /* records that survived culling                          */
+    int64_t instances;   /* (tile, splat) pairs after duplication                  */
+    int64_t tiles;       /* tiles over all cameras                                 */
+    int64_t pixels;      /* pixels over all cameras                                */
+    int64_t capacity;    /* reserved instance capacity                             */
+    int32_t overflow;    /* nonzero if a no-sync forward ran out of capacity       */
+    int32_t error_flags; /* device error bits (bit 0: bounded wait timed out)      */
+} gb_stats;
+
+/* ---------------------------------------------------------------- contexts -- */
+
+/* Creates a context bound to CUDA device `device` (made current on the calling
+ * thread).  The context owns the scratch memory of the sort (grown on demand
+ * with cudaMalloc).  *out receives the handle; GB_ERR_CUDA if the device is
+ * missing. */
+gb_status gb_context_create(int32_t device, gb_context **out);
+
+/* Frees the context and its scratch after synchronizing the device.  NULL is a
+ * no-op.  Saved states created from it must be destroyed first. */
+gb_status gb_context_destroy(gb_context *ctx);
+
+/* Message of the last failing call on `ctx` (static storage owned by the
+ * context; valid until the next call on it).  Never NULL. */
+const char *gb_last_error(const gb_context *ctx);
+
+/* Name of a status code.  Never NULL. */
+const char *gb_status_string(gb_status status);
+
+/* ------------------------------------------------------------- saved state -- */
+
+/* A saved state holds everything the backward pass needs from one forward:
+ * projected records, the depth permutation, the sorted (tile, splat) list,
+ * the tile ranges and per-pixel final transmittance and last-contributor
+ * index (the backward recomputes each pixel's transmittances from these,
+ * Alg. 1 bwd).  It is created empty and grows on demand with cudaMalloc in
+ * synchronizing forwards; it is overwritten by every forward that uses it.
+ * It must not be shared by two forwards in flight. */
+gb_status gb_saved_create(gb_context *ctx, gb_saved **out);
+gb_status gb_saved_destroy(gb_saved *saved);
+
+/* Pre-sizes a saved state so that GB_FLAG_NO_SYNC forwards (e.g. inside a CUDA
+ * graph capture) never allocate: `records` = sum over cameras of the scene's
+ * splat count, `instances` = (tile, splat) pairs, `pixels` and `tiles` over
+ * all cameras.  Synchronizes the device. */
+gb_status gb_saved_reserve(gb_saved *saved, int64_t records, int64_t instances, int64_t pixels,
+                           int64_t tiles);
+
+/* Copies the counters of the last forward into *out (host); synchronizes the
+ * saved state's last stream. */
+gb_status gb_saved_stats(gb_saved *saved, gb_stats *out);
+
+/* Synchronizes and returns GB_ERR_CAPACITY if the last no-sync forward ran out
+ * of instance capacity (its outputs are then invalid; reserve more and rerun),
+ * GB_ERR_TIMEOUT if a bounded device wait gave up, else GB_OK. */
+gb_status gb_saved_check(gb_saved *saved);
+
+/* Copies the sorted instance list of the last forward to HOST arrays: keys[i]
+ * = (global tile id << 32) | bits(FP32 centre depth), ids[i] = splat index
+ * within its scene, cams[i] = camera index.  Global tile ids number the tiles
+ * of camera 0 first (row-major, ceil(W/tile) per row), then camera 1, ...
+ * `cap` is the host capacity; *count receives the instance count (arrays are
+ * filled up to min(count, cap)).  Synchronizes.  Used by parity tests. */
+gb_status gb_saved_export_keys(gb_saved *saved, uint64_t *keys, int64_t *ids, int32_t *cams,
+                               int64_t cap, int64_t *count);
+
+/* ----------------------------------------------------------------- render -- */
+
+/* Forward render of all cameras (Alg. 1 fwd; Eq. 2-5).
+ *   scenes  host array [n_scenes] (1..GBILL_MAX_SCENES)
+ *   cams    host array [n_cams]   (1..GBILL_MAX_CAMERAS); cams[i].scene indexes scenes
+ *   rgb     [P,3]  P = sum over cameras of W*H; camera i's pixels start at
+ *                  sum_{j<i} W_j H_j, row-major within a camera
+ *   depth   [P]    sum_i z_i alpha_i T_i (z_i: plane-hit depth, or centre
+ *                  depth where the screen-space low-pass is the larger)
+ *   alpha   [P]    1 - T_final
+ * Steps on `stream`: preprocess (homography, FP32 tile rectangle, depth key),
+ * depth radix sort, tile-count scan, (tile, splat) duplication, tile radix
+ * sort, tile ranges, per-tile render.  Unless GB_FLAG_NO_SYNC is set the
+ * call synchronizes once (to size the instance list) and may grow `saved`.
+ * Returns GB_ERR_INVALID_ARG for bad sizes/pointers/options,
+ * GB_ERR_UNSUPPORTED for tex_n not in {1,2,4,8} or sh_degree > 3. */
+gb_status gb_render_forward(gb_context *ctx, gb_saved *saved, const gb_scene *scenes,
+                            int32_t n_scenes, const gb_camera *cams, int32_t n_cams,
+                            const gb_options *opt, float *rgb, float *depth, float *alpha,
+                            void *stream);
+
+/* Backward of the last forward on `saved` (Alg. 1 bwd, Alg. 2 adj-bilinear).
+ *   d_rgb   [P,3] dL/drgb (required); d_depth [P], d_alpha [P] (nullable)
+ *   grads   host array [n_scenes] of gb_grads (device pointers), overwritten
+ *           with the gradient summed over each scene's cameras.
+ * The scene parameter arrays passed to the forward must be unchanged.
+ * Enqueued on `stream`, never synchronizes. */
+gb_status gb_render_backward(gb_context *ctx, gb_saved *saved, const float *d_rgb,
+                             const float *d_depth, const float *d_alpha, const gb_grads *grads,
+                             int32_t n_scenes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBILL_H */

@@ -502,6 +502,10 @@ struct Ctx {
     std::vector<std::array<double, 4>> box; /* prefilter boxes       */
     bool prefilter;
     double bg[3];
+    /* prefilter bins: 16x16-pixel cells listing (in depth order) the splats
+       whose box touches the cell; the per-pixel box test stays exact */
+    int bins_x = 0, bins_y = 0;
+    std::vector<std::vector<int32_t>> bins;
 };
 
 /* Runs the front-to-back loop of one pixel; fills the contributor list. */
@@ -515,7 +519,15 @@ static void pixel_forward(const Ctx &cx, int px, int py, std::vector<Contrib> *c
     double mf = INFINITY, mg = INFINITY;
     int n = 0;
     if (contribs) contribs->clear();
-    for (size_t i = 0; i < cx.order.size(); ++i) {
+    const std::vector<int32_t> *bin = nullptr;
+    if (cx.prefilter) {
+        const int bx = std::min(std::max(px / 16, 0), cx.bins_x - 1);
+        const int by = std::min(std::max(py / 16, 0), cx.bins_y - 1);
+        bin = &cx.bins[size_t(by) * cx.bins_x + bx];
+    }
+    const size_t count = bin ? bin->size() : cx.order.size();
+    for (size_t ii = 0; ii < count; ++ii) {
+        const size_t i = bin ? size_t((*bin)[ii]) : ii;
         if (cx.prefilter) {
             const auto &b = cx.box[i];
             if (X < b[0] || X > b[2] || Y < b[1] || Y > b[3]) continue;
@@ -593,6 +605,21 @@ static void build_ctx(Ctx &cx, const orc_scene *sc, const orc_camera *cam, const
         }
     }
     for (int c = 0; c < 3; ++c) cx.bg[c] = bg ? bg[c] : 0.0;
+    if (cx.prefilter) {
+        cx.bins_x = (cam->width + 15) / 16;
+        cx.bins_y = (cam->height + 15) / 16;
+        cx.bins.assign(size_t(cx.bins_x) * cx.bins_y, {});
+        for (size_t i = 0; i < cx.order.size(); ++i) {
+            const auto &b = cx.box[i];
+            /* pixel centres x + 0.5 inside [b0, b2] */
+            const double lx = std::max(std::floor(b[0] - 0.5), 0.0), hx = std::min(std::ceil(b[2] - 0.5), double(cam->width - 1));
+            const double ly = std::max(std::floor(b[1] - 0.5), 0.0), hy = std::min(std::ceil(b[3] - 0.5), double(cam->height - 1));
+            if (!(lx <= hx) || !(ly <= hy)) continue;
+            for (int by = int(ly) / 16; by <= int(hy) / 16; ++by)
+                for (int bx = int(lx) / 16; bx <= int(hx) / 16; ++bx)
+                    cx.bins[size_t(by) * cx.bins_x + bx].push_back(int32_t(i));
+        }
+    }
 }
 
 int orc_num_threads(void) { return num_threads(); }

@@ -1,0 +1,537 @@
+// C ABI of the rasterizer (include/gbill.h): argument checking, the frame
+// descriptor, buffer management of saved states and the launch sequence of
+// the forward and backward passes.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "gbill_internal.cuh"
+#include "render_common.cuh"
+
+using namespace gbill;
+
+struct gb_context {
+    int device;
+    char err[512];
+};
+
+struct gb_saved {
+    gb_context *ctx;
+    int64_t cap_rec, cap_inst, cap_pix, cap_tiles;
+    Record *rec;
+    uint32_t *depth_key, *rec_id, *keys_tmp, *vals_tmp, *dkeys_sorted, *perm, *offsets;
+    uint2 *rect;
+    int32_t *inv;
+    float *rec_grad;
+    uint32_t *inst_tile, *inst_val, *inst_tile_tmp, *inst_val_tmp, *tiles_sorted, *vals_sorted;
+    uint2 *ranges;
+    float *t_final;
+    uint32_t *last;
+    Counters *cnt;
+    Counters *cnt_host;
+    void *scratch;
+    size_t scratch_bytes;
+    // last forward
+    Frame frame;
+    bool has_forward;
+    int64_t n_records, n_pixels, max_k, inst_max;
+    int tile_bits, batch_fwd, batch_bwd;
+    uint32_t flags;
+    cudaStream_t stream;
+};
+
+namespace {
+
+gb_status fail(gb_context *ctx, gb_status st, const char *fmt, ...) {
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+#define GB_CUDA(ctx, call)                                                                   \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail((ctx), GB_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                                 \
+    } while (0)
+
+cudaError_t alloc(void **p, size_t bytes) {
+    if (*p) {
+        cudaError_t e = cudaFree(*p);
+        if (e != cudaSuccess) return e;
+    }
+    *p = nullptr;
+    return cudaMalloc(p, std::max<size_t>(bytes, 16));
+}
+
+template <typename T>
+cudaError_t alloc_t(T **p, int64_t n) {
+    return alloc(reinterpret_cast<void **>(p), size_t(std::max<int64_t>(n, 1)) * sizeof(T));
+}
+
+gb_status reserve_records(gb_saved *s, int64_t n) {
+    if (n <= s->cap_rec) return GB_OK;
+    gb_context *ctx = s->ctx;
+    GB_CUDA(ctx, cudaDeviceSynchronize());
+    const int64_t c = n + n / 8 + 1024;
+    GB_CUDA(ctx, alloc_t(&s->rec, c));
+    GB_CUDA(ctx, alloc_t(&s->depth_key, c));
+    GB_CUDA(ctx, alloc_t(&s->rec_id, c));
+    GB_CUDA(ctx, alloc_t(&s->keys_tmp, c));
+    GB_CUDA(ctx, alloc_t(&s->vals_tmp, c));
+    GB_CUDA(ctx, alloc_t(&s->dkeys_sorted, c));
+    GB_CUDA(ctx, alloc_t(&s->perm, c));
+    GB_CUDA(ctx, alloc_t(&s->offsets, c));
+    GB_CUDA(ctx, alloc_t(&s->rect, c));
+    GB_CUDA(ctx, alloc_t(&s->inv, c));
+    GB_CUDA(ctx, alloc_t(&s->rec_grad, c * kRecGrad));
+    s->cap_rec = c;
+    return GB_OK;
+}
+
+gb_status reserve_instances(gb_saved *s, int64_t n) {
+    if (n <= s->cap_inst) return GB_OK;
+    gb_context *ctx = s->ctx;
+    if (n >= int64_t(0xF0000000u))
+        return fail(ctx, GB_ERR_CAPACITY, "%lld (tile, splat) instances exceed the 32-bit index range",
+                    (long long)n);
+    GB_CUDA(ctx, cudaDeviceSynchronize());
+    const int64_t c = std::min<int64_t>(n + n / 4 + 4096, int64_t(0xF0000000u));
+    GB_CUDA(ctx, alloc_t(&s->inst_tile, c));
+    GB_CUDA(ctx, alloc_t(&s->inst_val, c));
+    GB_CUDA(ctx, alloc_t(&s->inst_tile_tmp, c));
+    GB_CUDA(ctx, alloc_t(&s->inst_val_tmp, c));
+    GB_CUDA(ctx, alloc_t(&s->tiles_sorted, c));
+    GB_CUDA(ctx, alloc_t(&s->vals_sorted, c));
+    s->cap_inst = c;
+    return GB_OK;
+}
+
+gb_status reserve_pixels(gb_saved *s, int64_t n) {
+    if (n <= s->cap_pix) return GB_OK;
+    gb_context *ctx = s->ctx;
+    GB_CUDA(ctx, cudaDeviceSynchronize());
+    GB_CUDA(ctx, alloc_t(&s->t_final, n));
+    GB_CUDA(ctx, alloc_t(&s->last, n));
+    s->cap_pix = n;
+    return GB_OK;
+}
+
+gb_status reserve_tiles(gb_saved *s, int64_t n) {
+    if (n <= s->cap_tiles) return GB_OK;
+    gb_context *ctx = s->ctx;
+    GB_CUDA(ctx, cudaDeviceSynchronize());
+    GB_CUDA(ctx, alloc_t(&s->ranges, n));
+    s->cap_tiles = n;
+    return GB_OK;
+}
+
+gb_status reserve_scratch(gb_saved *s) {
+    const size_t need = std::max(radix_scratch_bytes(std::max(s->cap_rec, s->cap_inst)),
+                                 scan_scratch_bytes(s->cap_rec)) + 1024;
+    if (need <= s->scratch_bytes) return GB_OK;
+    gb_context *ctx = s->ctx;
+    GB_CUDA(ctx, cudaDeviceSynchronize());
+    GB_CUDA(ctx, alloc(&s->scratch, need));
+    s->scratch_bytes = need;
+    return GB_OK;
+}
+
+int default_batch(int N, bool bwd) {
+    const int per = int(72 + 12 * N * N + (bwd ? 64 + 12 * N * N : 0));
+    int b = (64 * 1024) / per;
+    b = std::min(b, 256);
+    b &= ~31;
+    return std::max(b, 32);
+}
+
+size_t batch_smem(int N, int batch, bool bwd) {
+    switch (N) {
+        case 1: return stage_bytes<1>(batch, bwd);
+        case 2: return stage_bytes<2>(batch, bwd);
+        case 4: return stage_bytes<4>(batch, bwd);
+        default: return stage_bytes<8>(batch, bwd);
+    }
+}
+
+__global__ void zero_rec_grad(float *g, const Counters *cnt, int64_t max_n) {
+    const int64_t n = std::min<int64_t>(int64_t(cnt->n_visible), max_n) * kRecGrad / 4;
+    float4 *g4 = reinterpret_cast<float4 *>(g);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        g4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+bool dtype_ok(int32_t d) { return d == GB_F32 || d == GB_F16 || d == GB_BF16; }
+
+gb_status build_frame(gb_context *ctx, const gb_scene *scenes, int32_t n_scenes, const gb_camera *cams,
+                      int32_t n_cams, int tile, const float bg[3], Frame &f, int64_t &max_k) {
+    if (!scenes || n_scenes < 1 || n_scenes > kMaxScenes)
+        return fail(ctx, GB_ERR_INVALID_ARG, "n_scenes must be in 1..%d", kMaxScenes);
+    if (!cams || n_cams < 1 || n_cams > kMaxCams)
+        return fail(ctx, GB_ERR_INVALID_ARG, "n_cams must be in 1..%d", kMaxCams);
+    memset(&f, 0, sizeof(f));
+    f.n_cams = n_cams;
+    f.n_scenes = n_scenes;
+    f.tile = tile;
+    for (int i = 0; i < 3; ++i) f.bg[i] = bg ? bg[i] : 0.0f;
+    max_k = 0;
+    for (int s = 0; s < n_scenes; ++s) {
+        const gb_scene &g = scenes[s];
+        SceneDev &d = f.scenes[s];
+        if (g.num_splats < 0 || g.num_splats > (int64_t(1) << 31))
+            return fail(ctx, GB_ERR_INVALID_ARG, "scene %d: num_splats %lld out of range", s, (long long)g.num_splats);
+        if (g.sh_degree < 0 || g.sh_degree > 3)
+            return fail(ctx, GB_ERR_UNSUPPORTED, "scene %d: sh_degree %d not in 0..3", s, g.sh_degree);
+        if (!(g.tex_n == 1 || g.tex_n == 2 || g.tex_n == 4 || g.tex_n == 8))
+            return fail(ctx, GB_ERR_UNSUPPORTED, "scene %d: tex_n %d not in {1,2,4,8}", s, g.tex_n);
+        if (!dtype_ok(g.sh_dtype) || !dtype_ok(g.tex_dtype))
+            return fail(ctx, GB_ERR_INVALID_ARG, "scene %d: bad storage dtype", s);
+        if (!(g.sigma > 0.0f) || !isfinite(g.sigma))
+            return fail(ctx, GB_ERR_INVALID_ARG, "scene %d: sigma must be positive", s);
+        if (g.reserved != 0) return fail(ctx, GB_ERR_INVALID_ARG, "scene %d: reserved field must be 0", s);
+        if (g.num_splats > 0 && (!g.means || !g.quats || !g.scales || !g.opacities || !g.sh || !g.textures))
+            return fail(ctx, GB_ERR_INVALID_ARG, "scene %d: null parameter pointer", s);
+        if (g.tex_n != scenes[0].tex_n || g.tex_dtype != scenes[0].tex_dtype)
+            return fail(ctx, GB_ERR_UNSUPPORTED, "scenes of one call must share tex_n and tex_dtype");
+        d.K = g.num_splats;
+        d.means = g.means;
+        d.quats = g.quats;
+        d.scales = g.scales;
+        d.opac = g.opacities;
+        d.sh = g.sh;
+        d.tex = g.textures;
+        d.D = g.sh_degree;
+        d.sh_dtype = g.sh_dtype;
+        d.N = g.tex_n;
+        d.tex_dtype = g.tex_dtype;
+        d.sigma = g.sigma;
+        max_k = std::max(max_k, g.num_splats);
+    }
+    int64_t tiles = 0, pix = 0, rec = 0;
+    for (int c = 0; c < n_cams; ++c) {
+        const gb_camera &g = cams[c];
+        CamDev &d = f.cams[c];
+        if (g.width < 1 || g.height < 1 || g.width > 16384 || g.height > 16384)
+            return fail(ctx, GB_ERR_INVALID_ARG, "camera %d: size %dx%d out of range", c, g.width, g.height);
+        if (g.scene < 0 || g.scene >= n_scenes)
+            return fail(ctx, GB_ERR_INVALID_ARG, "camera %d: scene %d out of range", c, g.scene);
+        bool fin = isfinite(g.fx) && isfinite(g.fy) && isfinite(g.cx) && isfinite(g.cy) && isfinite(g.near_plane);
+        for (int i = 0; i < 12; ++i) fin = fin && isfinite(g.world_to_cam[i]);
+        if (!fin) return fail(ctx, GB_ERR_NONFINITE, "camera %d has non-finite parameters", c);
+        d.width = g.width;
+        d.height = g.height;
+        d.tiles_x = int32_t(ceil_div(g.width, tile));
+        d.tiles_y = int32_t(ceil_div(g.height, tile));
+        d.fx = g.fx; d.fy = g.fy; d.cx = g.cx; d.cy = g.cy;
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) d.R[3 * i + j] = g.world_to_cam[4 * i + j];
+            d.t[i] = g.world_to_cam[4 * i + 3];
+        }
+        for (int i = 0; i < 3; ++i)
+            d.campos[i] = -(d.R[i] * d.t[0] + d.R[3 + i] * d.t[1] + d.R[6 + i] * d.t[2]);
+        d.near_plane = g.near_plane;
+        d.scene = g.scene;
+        d.tile_off = uint32_t(tiles);
+        d.pix_off = pix;
+        d.rec_off = rec;
+        tiles += int64_t(d.tiles_x) * d.tiles_y;
+        pix += int64_t(g.width) * g.height;
+        rec += scenes[g.scene].num_splats;
+    }
+    if (tiles >= (int64_t(1) << 31) || rec >= int64_t(0xF0000000u))
+        return fail(ctx, GB_ERR_INVALID_ARG, "frame too large (%lld tiles, %lld records)", (long long)tiles,
+                    (long long)rec);
+    f.n_tiles = uint32_t(tiles);
+    f.n_pixels = pix;
+    f.n_records = rec;
+    return GB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *gb_status_string(gb_status s) {
+    switch (s) {
+        case GB_OK: return "GB_OK";
+        case GB_ERR_INVALID_ARG: return "GB_ERR_INVALID_ARG";
+        case GB_ERR_UNSUPPORTED: return "GB_ERR_UNSUPPORTED";
+        case GB_ERR_CUDA: return "GB_ERR_CUDA";
+        case GB_ERR_CAPACITY: return "GB_ERR_CAPACITY";
+        case GB_ERR_TIMEOUT: return "GB_ERR_TIMEOUT";
+        case GB_ERR_NONFINITE: return "GB_ERR_NONFINITE";
+    }
+    return "GB_UNKNOWN_STATUS";
+}
+
+const char *gb_last_error(const gb_context *ctx) { return ctx ? ctx->err : "null context"; }
+
+gb_status gb_context_create(int32_t device, gb_context **out) {
+    if (!out) return GB_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return GB_ERR_CUDA;
+    if (cudaSetDevice(device) != cudaSuccess) return GB_ERR_CUDA;
+    gb_context *c = new (std::nothrow) gb_context();
+    if (!c) return GB_ERR_CUDA;
+    c->device = device;
+    c->err[0] = 0;
+    *out = c;
+    return GB_OK;
+}
+
+gb_status gb_context_destroy(gb_context *ctx) {
+    if (!ctx) return GB_OK;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    delete ctx;
+    return GB_OK;
+}
+
+gb_status gb_saved_create(gb_context *ctx, gb_saved **out) {
+    if (!ctx || !out) return fail(ctx, GB_ERR_INVALID_ARG, "null argument");
+    gb_saved *s = new (std::nothrow) gb_saved();
+    if (!s) return fail(ctx, GB_ERR_CUDA, "host allocation failed");
+    memset(s, 0, sizeof(*s));
+    s->ctx = ctx;
+    cudaError_t e = cudaMalloc(&s->cnt, sizeof(Counters));
+    if (e == cudaSuccess) e = cudaMallocHost(&s->cnt_host, sizeof(Counters));
+    if (e != cudaSuccess) {
+        if (s->cnt) cudaFree(s->cnt);
+        delete s;
+        return fail(ctx, GB_ERR_CUDA, "saved state allocation failed: %s", cudaGetErrorString(e));
+    }
+    memset(s->cnt_host, 0, sizeof(Counters));
+    cudaMemset(s->cnt, 0, sizeof(Counters));
+    *out = s;
+    return GB_OK;
+}
+
+gb_status gb_saved_destroy(gb_saved *s) {
+    if (!s) return GB_OK;
+    cudaDeviceSynchronize();
+    void *ptrs[] = {s->rec, s->depth_key, s->rec_id, s->keys_tmp, s->vals_tmp, s->dkeys_sorted, s->perm,
+                    s->offsets, s->rect, s->inv, s->rec_grad, s->inst_tile, s->inst_val, s->inst_tile_tmp,
+                    s->inst_val_tmp, s->tiles_sorted, s->vals_sorted, s->ranges, s->t_final, s->last,
+                    s->cnt, s->scratch};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (s->cnt_host) cudaFreeHost(s->cnt_host);
+    delete s;
+    return GB_OK;
+}
+
+gb_status gb_saved_reserve(gb_saved *s, int64_t records, int64_t instances, int64_t pixels, int64_t tiles) {
+    if (!s || records < 0 || instances < 0 || pixels < 0 || tiles < 0)
+        return fail(s ? s->ctx : nullptr, GB_ERR_INVALID_ARG, "bad reserve arguments");
+    gb_status st;
+    if ((st = reserve_records(s, records)) != GB_OK) return st;
+    if ((st = reserve_instances(s, instances)) != GB_OK) return st;
+    if ((st = reserve_pixels(s, pixels)) != GB_OK) return st;
+    if ((st = reserve_tiles(s, tiles)) != GB_OK) return st;
+    if ((st = reserve_scratch(s)) != GB_OK) return st;
+    GB_CUDA(s->ctx, cudaDeviceSynchronize());
+    return GB_OK;
+}
+
+gb_status gb_saved_stats(gb_saved *s, gb_stats *out) {
+    if (!s || !out) return fail(s ? s->ctx : nullptr, GB_ERR_INVALID_ARG, "null argument");
+    GB_CUDA(s->ctx, cudaMemcpyAsync(s->cnt_host, s->cnt, sizeof(Counters), cudaMemcpyDeviceToHost, s->stream));
+    GB_CUDA(s->ctx, cudaStreamSynchronize(s->stream));
+    out->records = s->n_records;
+    out->visible = s->cnt_host->n_visible;
+    out->instances = s->cnt_host->n_instances;
+    out->tiles = s->frame.n_tiles;
+    out->pixels = s->n_pixels;
+    out->capacity = s->cap_inst;
+    out->overflow = int32_t(s->cnt_host->overflow);
+    out->error_flags = int32_t(s->cnt_host->error_flags);
+    return GB_OK;
+}
+
+gb_status gb_saved_check(gb_saved *s) {
+    gb_stats st;
+    gb_status r = gb_saved_stats(s, &st);
+    if (r != GB_OK) return r;
+    if (st.overflow)
+        return fail(s->ctx, GB_ERR_CAPACITY, "instance capacity %lld exceeded (%lld needed)",
+                    (long long)st.capacity, (long long)st.instances);
+    if (st.error_flags & 1) return fail(s->ctx, GB_ERR_TIMEOUT, "a bounded device wait timed out");
+    return GB_OK;
+}
+
+gb_status gb_saved_export_keys(gb_saved *s, uint64_t *keys, int64_t *ids, int32_t *cams, int64_t cap,
+                               int64_t *count) {
+    if (!s || !count || cap < 0) return fail(s ? s->ctx : nullptr, GB_ERR_INVALID_ARG, "bad arguments");
+    if (!s->has_forward) return fail(s->ctx, GB_ERR_INVALID_ARG, "no forward recorded on this saved state");
+    gb_stats st;
+    gb_status r = gb_saved_stats(s, &st);
+    if (r != GB_OK) return r;
+    if (st.overflow) return fail(s->ctx, GB_ERR_CAPACITY, "last forward overflowed");
+    *count = st.instances;
+    const int64_t n = std::min<int64_t>(cap, st.instances);
+    if (n == 0) return GB_OK;
+    if (!keys || !ids || !cams) return fail(s->ctx, GB_ERR_INVALID_ARG, "null output array");
+    uint64_t *dk = nullptr;
+    int64_t *di = nullptr;
+    int32_t *dc = nullptr;
+    GB_CUDA(s->ctx, cudaMalloc(&dk, n * 8));
+    GB_CUDA(s->ctx, cudaMalloc(&di, n * 8));
+    GB_CUDA(s->ctx, cudaMalloc(&dc, n * 4));
+    GB_CUDA(s->ctx, launch_export_keys(s->frame, s->tiles_sorted, s->vals_sorted, s->perm, s->depth_key, n, dk,
+                                       di, dc, s->stream));
+    GB_CUDA(s->ctx, cudaMemcpyAsync(keys, dk, n * 8, cudaMemcpyDeviceToHost, s->stream));
+    GB_CUDA(s->ctx, cudaMemcpyAsync(ids, di, n * 8, cudaMemcpyDeviceToHost, s->stream));
+    GB_CUDA(s->ctx, cudaMemcpyAsync(cams, dc, n * 4, cudaMemcpyDeviceToHost, s->stream));
+    GB_CUDA(s->ctx, cudaStreamSynchronize(s->stream));
+    cudaFree(dk);
+    cudaFree(di);
+    cudaFree(dc);
+    return GB_OK;
+}
+
+gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int32_t n_scenes,
+                            const gb_camera *cams, int32_t n_cams, const gb_options *opt, float *rgb,
+                            float *depth, float *alpha, void *stream) {
+    if (!ctx) return GB_ERR_INVALID_ARG;
+    if (!s || s->ctx != ctx) return fail(ctx, GB_ERR_INVALID_ARG, "saved state missing or from another context");
+    if (!rgb) return fail(ctx, GB_ERR_INVALID_ARG, "rgb output is required");
+    gb_options o{};
+    if (opt) o = *opt;
+    if (o.reserved != 0) return fail(ctx, GB_ERR_INVALID_ARG, "options.reserved must be 0");
+    const int tile = o.tile_size ? o.tile_size : 16;
+    if (tile != 16) return fail(ctx, GB_ERR_UNSUPPORTED, "tile_size %d not built (16 only)", tile);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Frame f;
+    int64_t max_k = 0;
+    gb_status r = build_frame(ctx, scenes, n_scenes, cams, n_cams, tile, o.background, f, max_k);
+    if (r != GB_OK) return r;
+    const int N = scenes[0].tex_n;
+    const int nt = tile * tile;
+    int bf = o.batch_depth ? o.batch_depth : default_batch(N, false);
+    int bb = o.batch_depth ? o.batch_depth : default_batch(N, true);
+    if (bf < 32 || bf > nt || (bf & 31)) return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d invalid", bf);
+    if (batch_smem(N, bf, false) > 200 * 1024 || batch_smem(N, bb, true) > 200 * 1024)
+        return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d needs too much shared memory", bf);
+    const bool nosync = (o.flags & GB_FLAG_NO_SYNC) != 0;
+    if (nosync) {
+        if (f.n_records > s->cap_rec || f.n_pixels > s->cap_pix || int64_t(f.n_tiles) > s->cap_tiles ||
+            s->cap_inst == 0)
+            return fail(ctx, GB_ERR_CAPACITY, "saved state not reserved for this frame (no-sync mode)");
+    } else {
+        if ((r = reserve_records(s, f.n_records)) != GB_OK) return r;
+        if ((r = reserve_pixels(s, f.n_pixels)) != GB_OK) return r;
+        if ((r = reserve_tiles(s, f.n_tiles)) != GB_OK) return r;
+        if ((r = reserve_instances(s, std::max<int64_t>(s->cap_inst, 1 << 16))) != GB_OK) return r;
+        if ((r = reserve_scratch(s)) != GB_OK) return r;
+    }
+    const int64_t R = f.n_records;
+    int tile_bits = 1;
+    while ((int64_t(1) << tile_bits) < int64_t(f.n_tiles)) ++tile_bits;
+    s->frame = f;
+    s->n_records = R;
+    s->n_pixels = f.n_pixels;
+    s->max_k = max_k;
+    s->tile_bits = tile_bits;
+    s->batch_fwd = bf;
+    s->batch_bwd = bb;
+    s->flags = o.flags;
+    s->stream = st;
+    s->has_forward = false;
+
+    GB_CUDA(ctx, cudaMemsetAsync(s->cnt, 0, sizeof(Counters), st));
+    GB_CUDA(ctx, cudaMemsetAsync(s->ranges, 0, size_t(f.n_tiles) * sizeof(uint2), st));
+    GB_CUDA(ctx, launch_preprocess(f, max_k, s->depth_key, s->rec_id, s->rect, s->rec, s->cnt, st));
+    GB_CUDA(ctx, radix_sort_pairs(s->depth_key, s->rec_id, s->keys_tmp, s->vals_tmp, s->dkeys_sorted, s->perm, R,
+                                  nullptr, 0, 32, s->scratch, s->scratch_bytes, st));
+    GB_CUDA(ctx, tile_counts_scan(f, s->perm, s->rect, R, &s->cnt->n_visible, s->offsets, s->scratch,
+                                  s->scratch_bytes, s->cnt, s->cap_inst, st));
+    int64_t inst_max = s->cap_inst;
+    if (!nosync) {
+        GB_CUDA(ctx, cudaMemcpyAsync(s->cnt_host, s->cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+        GB_CUDA(ctx, cudaStreamSynchronize(st));
+        const int64_t need = s->cnt_host->n_instances;
+        if (need > s->cap_inst) {
+            if ((r = reserve_instances(s, need)) != GB_OK) return r;
+            if ((r = reserve_scratch(s)) != GB_OK) return r;
+            GB_CUDA(ctx, cudaMemsetAsync(&s->cnt->overflow, 0, sizeof(uint32_t), st));
+        }
+        inst_max = std::max<int64_t>(need, 1);
+    }
+    s->inst_max = inst_max;
+    GB_CUDA(ctx, launch_emit(f, s->perm, s->rect, s->offsets, R, s->cnt, s->cap_inst, s->inst_tile, s->inst_val, st));
+    GB_CUDA(ctx, radix_sort_pairs(s->inst_tile, s->inst_val, s->inst_tile_tmp, s->inst_val_tmp, s->tiles_sorted,
+                                  s->vals_sorted, inst_max, &s->cnt->n_instances, 0, tile_bits, s->scratch,
+                                  s->scratch_bytes, st));
+    GB_CUDA(ctx, launch_ranges(s->tiles_sorted, inst_max, s->cnt, s->ranges, st));
+    RenderBufs b;
+    b.rec = s->rec;
+    b.perm = s->perm;
+    b.inst_val = s->vals_sorted;
+    b.ranges = s->ranges;
+    b.rgb = rgb;
+    b.depth = depth;
+    b.alpha = alpha;
+    b.t_final = s->t_final;
+    b.last = s->last;
+    b.cnt = s->cnt;
+    GB_CUDA(ctx, launch_render_fwd(f, b, bf, st));
+    s->has_forward = true;
+    return GB_OK;
+}
+
+gb_status gb_render_backward(gb_context *ctx, gb_saved *s, const float *d_rgb, const float *d_depth,
+                             const float *d_alpha, const gb_grads *grads, int32_t n_scenes, void *stream) {
+    if (!ctx) return GB_ERR_INVALID_ARG;
+    if (!s || s->ctx != ctx) return fail(ctx, GB_ERR_INVALID_ARG, "saved state missing or from another context");
+    if (!s->has_forward) return fail(ctx, GB_ERR_INVALID_ARG, "no forward recorded on this saved state");
+    if (!d_rgb) return fail(ctx, GB_ERR_INVALID_ARG, "d_rgb is required");
+    if (!grads || n_scenes != s->frame.n_scenes)
+        return fail(ctx, GB_ERR_INVALID_ARG, "grads must hold one entry per scene (%d)", s->frame.n_scenes);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Frame f = s->frame;
+    for (int i = 0; i < n_scenes; ++i) {
+        SceneDev &d = f.scenes[i];
+        d.g_means = grads[i].d_means;
+        d.g_quats = grads[i].d_quats;
+        d.g_scales = grads[i].d_scales;
+        d.g_opac = grads[i].d_opacities;
+        d.g_sh = grads[i].d_sh;
+        d.g_tex = grads[i].d_textures;
+        if (d.g_tex && d.K > 0)
+            GB_CUDA(ctx, cudaMemsetAsync(d.g_tex, 0, size_t(d.K) * d.N * d.N * 3 * sizeof(float), st));
+    }
+    const int64_t R = s->n_records;
+    zero_rec_grad<<<unsigned(std::min<int64_t>(ceil_div(std::max<int64_t>(R, 1) * 4, 256), 65535)), 256, 0, st>>>(
+        s->rec_grad, s->cnt, R);
+    GB_CUDA(ctx, cudaGetLastError());
+    GB_CUDA(ctx, launch_inverse_perm(s->perm, R, s->cnt, s->inv, st));
+    RenderBwdBufs b;
+    b.fw.rec = s->rec;
+    b.fw.perm = s->perm;
+    b.fw.inst_val = s->vals_sorted;
+    b.fw.ranges = s->ranges;
+    b.fw.rgb = nullptr;
+    b.fw.depth = nullptr;
+    b.fw.alpha = nullptr;
+    b.fw.t_final = s->t_final;
+    b.fw.last = s->last;
+    b.fw.cnt = s->cnt;
+    b.d_rgb = d_rgb;
+    b.d_depth = d_depth;
+    b.d_alpha = d_alpha;
+    b.rec_grad = s->rec_grad;
+    GB_CUDA(ctx, launch_render_bwd(f, b, s->batch_bwd, st));
+    GB_CUDA(ctx, launch_preprocess_bwd(f, s->max_k, s->rec_grad, s->inv, st));
+    return GB_OK;
+}
+
+}  // extern "C"

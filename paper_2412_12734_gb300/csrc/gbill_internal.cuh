@@ -1,0 +1,174 @@
+// Internal declarations of the sm_103a rasterizer library.  Nothing here is
+// part of the C ABI (include/gbill.h).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gbill.h"
+
+namespace gbill {
+
+constexpr int kMaxCams = GBILL_MAX_CAMERAS;
+constexpr int kMaxScenes = GBILL_MAX_SCENES;
+
+// Constants of the method (Sec. 3.1 Eq. 4 with the 3DGS-lineage clamp and
+// cutoffs; the screen-space low-pass of the 2DGS lineage).
+constexpr float kAlphaMin = 1.0f / 255.0f;  // skip a splat below this alpha
+constexpr float kAlphaMax = 0.99f;          // alpha clamp
+constexpr float kTMin = 1e-4f;              // stop before T would drop below
+constexpr float kLowPass = 2.0f;            // rho_lp = 2 |x - c|^2 (sigma_lp = sqrt(2)/2 px)
+// 2 ln 255: u^2 + v^2 beyond this gives alpha < 1/255 for any o <= 1.
+constexpr float kRhoMax = 11.0825270903f;
+// sqrt(ln 255): radius of the low-pass disk where 2 r^2 = rho_max.
+constexpr float kLowPassRadius = 2.35398885833f;
+
+// Per-camera data, derived on the host from gb_camera.
+struct CamDev {
+    int32_t width, height, tiles_x, tiles_y;
+    float fx, fy, cx, cy;
+    float R[9];
+    float t[3];
+    float campos[3];
+    float near_plane;
+    int32_t scene;
+    uint32_t tile_off;  // first global tile id of this camera
+    int64_t pix_off;    // first pixel of this camera in the packed outputs
+    int64_t rec_off;    // first record (= tile_off-like offset over splats)
+};
+
+struct SceneDev {
+    int64_t K;
+    const float *means, *quats, *scales, *opac;
+    const void *sh;
+    const void *tex;
+    int32_t D, sh_dtype, N, tex_dtype;
+    float sigma;
+    int32_t pad;
+    float *g_means, *g_quats, *g_scales, *g_opac, *g_sh, *g_tex;
+};
+
+// Everything a launch needs about the frame, passed BY VALUE as a kernel
+// parameter (no host->device copy, safe under graph capture).
+struct Frame {
+    int32_t n_cams, n_scenes, tile, flags;
+    int64_t n_records;
+    int64_t n_pixels;
+    uint32_t n_tiles;
+    uint32_t pad;
+    float bg[3];
+    float pad2;
+    CamDev cams[kMaxCams];
+    SceneDev scenes[kMaxScenes];
+};
+
+// A projected (splat, camera) record, 64 bytes, written by preprocess and
+// read by both render passes.  With the projected centre c moved to the
+// origin the splat-to-screen homography T' is lower block triangular:
+//   T' = [[t00 t01 0], [t10 t11 0], [t20 t21 t22]],   t22 = centre depth z.
+// zeta = adj(T') (dx, dy, 1) / t22 gives the ray/plane hit u = zeta_x/zeta_z,
+// v = zeta_y/zeta_z for the pixel offset (dx, dy) = x - c, and the hit depth
+// J / zeta_z with J = t00 t11 - t01 t10 = m22 z.
+//   q0 = ( t11, -t01, -t10,  t00)           zeta_xy = [[q0.x q0.y][q0.z q0.w]] (dx,dy)
+//   q1 = ( m20,  m21,  m22,  z  )           zeta_z  = m20 dx + m21 dy + m22
+//   q2 = ( c_hi.x, c_hi.y, c_lo.x, c_lo.y ) c = c_hi + c_lo (double-float centre)
+//   q3 = ( o, r_sh, g_sh, b_sh )            opacity and SH colour
+struct __align__(16) Record {
+    float4 q0, q1, q2, q3;
+};
+
+// Gradient of one record (16 floats): d q0 (4), d m20, d m21, d m22, d z,
+// d c (2), d o, d rgb (3), 2 unused.
+constexpr int kRecGrad = 16;
+
+// Device-side counters of one forward.
+struct Counters {
+    uint32_t n_visible;    // records surviving culling
+    uint32_t n_instances;  // (tile, splat) pairs
+    uint32_t overflow;     // capacity exceeded
+    uint32_t error_flags;  // bit 0: bounded wait timed out
+    uint32_t work_next;    // persistent render work counter (forward)
+    uint32_t work_next_bwd;
+    uint32_t pad[2];
+};
+
+// ---------------------------------------------------------------- helpers --
+
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+template <typename T>
+__device__ __forceinline__ float load_as_float(const T *p, int64_t i);
+template <>
+__device__ __forceinline__ float load_as_float<float>(const float *p, int64_t i) { return p[i]; }
+template <>
+__device__ __forceinline__ float load_as_float<__half>(const __half *p, int64_t i) {
+    return __half2float(p[i]);
+}
+template <>
+__device__ __forceinline__ float load_as_float<__nv_bfloat16>(const __nv_bfloat16 *p, int64_t i) {
+    return __bfloat162float(p[i]);
+}
+
+// Binary search of the camera owning global tile id `tile`.
+__device__ __forceinline__ int camera_of_tile(const Frame &f, uint32_t tile) {
+    int lo = 0, hi = f.n_cams - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (f.cams[mid].tile_off <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ------------------------------------------------------- host-side launchers --
+
+// preprocess.cu
+cudaError_t launch_preprocess(const Frame &f, int64_t max_k, uint32_t *depth_key, uint32_t *rec_id,
+                              uint2 *rect, Record *rec, Counters *cnt, cudaStream_t s);
+cudaError_t launch_preprocess_bwd(const Frame &f, int64_t max_k, const float *rec_grad,
+                                  const int32_t *inv_perm, cudaStream_t s);
+
+// sort.cu
+size_t radix_scratch_bytes(int64_t n);
+cudaError_t radix_sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *keys_tmp,
+                             uint32_t *vals_tmp, uint32_t *keys_out, uint32_t *vals_out,
+                             int64_t max_n, const uint32_t *n_dev, int begin_bit, int end_bit,
+                             void *scratch, size_t scratch_bytes, cudaStream_t s);
+size_t scan_scratch_bytes(int64_t n);
+cudaError_t tile_counts_scan(const Frame &f, const uint32_t *perm, const uint2 *rect, int64_t max_n,
+                             const uint32_t *n_dev, uint32_t *offsets, void *scratch,
+                             size_t scratch_bytes, Counters *cnt, int64_t capacity, cudaStream_t s);
+cudaError_t launch_emit(const Frame &f, const uint32_t *perm, const uint2 *rect,
+                        const uint32_t *offsets, int64_t max_n, const Counters *cnt, int64_t capacity,
+                        uint32_t *inst_tile, uint32_t *inst_val, cudaStream_t s);
+cudaError_t launch_ranges(const uint32_t *tiles_sorted, int64_t max_n, const Counters *cnt,
+                          uint2 *ranges, cudaStream_t s);
+cudaError_t launch_inverse_perm(const uint32_t *perm, int64_t n_records, const Counters *cnt,
+                                int32_t *inv, cudaStream_t s);
+cudaError_t launch_export_keys(const Frame &f, const uint32_t *tiles_sorted,
+                               const uint32_t *vals_sorted, const uint32_t *perm,
+                               const uint32_t *depth_key_by_rec, int64_t n, uint64_t *keys,
+                               int64_t *ids, int32_t *cams, cudaStream_t s);
+
+// render_fwd.cu / render_bwd.cu
+struct RenderBufs {
+    const Record *rec;        // indexed by record id
+    const uint32_t *perm;     // depth-sorted position -> record id
+    const uint32_t *inst_val; // sorted instances -> depth-sorted position
+    const uint2 *ranges;      // [n_tiles] (begin, end)
+    float *rgb, *depth, *alpha;
+    float *t_final;           // [n_pixels]
+    uint32_t *last;           // [n_pixels] 1 + index in the tile range of the last blended splat
+    Counters *cnt;
+};
+cudaError_t launch_render_fwd(const Frame &f, const RenderBufs &b, int batch, cudaStream_t s);
+
+struct RenderBwdBufs {
+    RenderBufs fw;
+    const float *d_rgb, *d_depth, *d_alpha;
+    float *rec_grad;          // [n_visible, 16], indexed by depth-sorted position
+};
+cudaError_t launch_render_bwd(const Frame &f, const RenderBwdBufs &b, int batch, cudaStream_t s);
+
+}  // namespace gbill

@@ -1,0 +1,473 @@
+// Preprocess (forward and backward) of the textured 2D-Gaussian rasterizer.
+//
+// Forward, one thread per (splat, camera) record:
+//   1. FP32 tile rectangle and depth key (culling and rectangles are FP32
+//      decisions; the operation sequence is fixed and contraction-free, so the
+//      (tile, depth) key list is reproducible bit for bit).
+//   2. The render record: the splat-to-screen homography of Eq. 3 composed
+//      with the pinhole camera, expressed relative to the projected centre
+//      (so its upper-right block vanishes), its adjugate (ray/splat
+//      intersection, u = zeta_x / zeta_z), the centre as a double-float pair,
+//      and the view-dependent SH colour added to the grid colour (Sec. 4.2).
+//      Near edge-on splats (|det| tiny against its terms) redo the homography
+//      and its inverse in FP64.
+// Backward, one thread per splat: sums over the scene's cameras the chain from
+// the record gradients back to means, quaternions, scales, opacity and SH.
+#include <math.h>
+
+#include "gbill_internal.cuh"
+
+namespace gbill {
+namespace {
+
+// ------------------------------------------------------------------ FP32 ops --
+// Single-rounded IEEE operations that the compiler may not fuse or reorder.
+__device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fdv(float a, float b) { return __fdiv_rn(a, b); }
+
+// FP32 culling, pixel rectangle and depth of one record.
+__device__ bool key_rect(const float p[3], const float q[4], float su, float sv, float o,
+                         const CamDev &c, float &z_out, int rect[4]) {
+    const float qn2 = fa(fa(fa(fm(q[0], q[0]), fm(q[1], q[1])), fm(q[2], q[2])), fm(q[3], q[3]));
+    if (!(qn2 > 0.0f)) return false;
+    const float qinv = fdv(1.0f, __fsqrt_rn(qn2));
+    const float w = fm(q[0], qinv), x = fm(q[1], qinv), y = fm(q[2], qinv), z = fm(q[3], qinv);
+    const float tu0 = fs(1.0f, fm(2.0f, fa(fm(y, y), fm(z, z))));
+    const float tu1 = fm(2.0f, fa(fm(x, y), fm(w, z)));
+    const float tu2 = fm(2.0f, fs(fm(x, z), fm(w, y)));
+    const float tv0 = fm(2.0f, fs(fm(x, y), fm(w, z)));
+    const float tv1 = fs(1.0f, fm(2.0f, fa(fm(x, x), fm(z, z))));
+    const float tv2 = fm(2.0f, fa(fm(y, z), fm(w, x)));
+    const float a0 = fm(su, tu0), a1 = fm(su, tu1), a2 = fm(su, tu2);
+    const float b0 = fm(sv, tv0), b1 = fm(sv, tv1), b2 = fm(sv, tv2);
+    const float *R = c.R;
+    const float A0 = fa(fa(fm(R[0], a0), fm(R[1], a1)), fm(R[2], a2));
+    const float A1 = fa(fa(fm(R[3], a0), fm(R[4], a1)), fm(R[5], a2));
+    const float A2 = fa(fa(fm(R[6], a0), fm(R[7], a1)), fm(R[8], a2));
+    const float B0 = fa(fa(fm(R[0], b0), fm(R[1], b1)), fm(R[2], b2));
+    const float B1 = fa(fa(fm(R[3], b0), fm(R[4], b1)), fm(R[5], b2));
+    const float B2 = fa(fa(fm(R[6], b0), fm(R[7], b1)), fm(R[8], b2));
+    const float P0 = fa(fa(fa(fm(R[0], p[0]), fm(R[1], p[1])), fm(R[2], p[2])), c.t[0]);
+    const float P1 = fa(fa(fa(fm(R[3], p[0]), fm(R[4], p[1])), fm(R[5], p[2])), c.t[1]);
+    const float P2 = fa(fa(fa(fm(R[6], p[0]), fm(R[7], p[1])), fm(R[8], p[2])), c.t[2]);
+    if (!(P2 > c.near_plane)) return false;
+    if (!(o >= kAlphaMin)) return false;
+    const float xz = fdv(P0, P2), yz = fdv(P1, P2);
+    const float t00 = fm(c.fx, fs(A0, fm(A2, xz))), t01 = fm(c.fx, fs(B0, fm(B2, xz)));
+    const float t10 = fm(c.fy, fs(A1, fm(A2, yz))), t11 = fm(c.fy, fs(B1, fm(B2, yz)));
+    const float t20 = A2, t21 = B2;
+    const float d00 = fm(kRhoMax, fa(fm(t00, t00), fm(t01, t01)));
+    const float d11 = fm(kRhoMax, fa(fm(t10, t10), fm(t11, t11)));
+    const float d02 = fm(kRhoMax, fa(fm(t00, t20), fm(t01, t21)));
+    const float d12 = fm(kRhoMax, fa(fm(t10, t20), fm(t11, t21)));
+    const float d22 = fs(fm(kRhoMax, fa(fm(t20, t20), fm(t21, t21))), fm(P2, P2));
+    if (!(d22 < 0.0f)) return false;
+    const float nd = -d22;
+    const float ox = fdv(d02, d22), oy = fdv(d12, d22);
+    const float hx = fdv(__fsqrt_rn(fa(fm(d02, d02), fm(d00, nd))), nd);
+    const float hy = fdv(__fsqrt_rn(fa(fm(d12, d12), fm(d11, nd))), nd);
+    const float cx = fa(fm(c.fx, xz), c.cx), cy = fa(fm(c.fy, yz), c.cy);
+    float elx = fs(fa(cx, ox), hx), ehx = fa(fa(cx, ox), hx);
+    float ely = fs(fa(cy, oy), hy), ehy = fa(fa(cy, oy), hy);
+    if (!(elx == elx) || !(ehx == ehx)) { elx = -INFINITY; ehx = INFINITY; }
+    if (!(ely == ely) || !(ehy == ehy)) { ely = -INFINITY; ehy = INFINITY; }
+    const float lox = fminf(elx, fs(cx, kLowPassRadius)), hix = fmaxf(ehx, fa(cx, kLowPassRadius));
+    const float loy = fminf(ely, fs(cy, kLowPassRadius)), hiy = fmaxf(ehy, fa(cy, kLowPassRadius));
+    const float fx0 = fmaxf(ceilf(fs(lox, 0.5f)), 0.0f);
+    const float fx1 = fminf(floorf(fs(hix, 0.5f)), float(c.width - 1));
+    const float fy0 = fmaxf(ceilf(fs(loy, 0.5f)), 0.0f);
+    const float fy1 = fminf(floorf(fs(hiy, 0.5f)), float(c.height - 1));
+    if (!(fx0 <= fx1) || !(fy0 <= fy1)) return false;
+    rect[0] = int(fx0);
+    rect[1] = int(fy0);
+    rect[2] = int(fx1);
+    rect[3] = int(fy1);
+    z_out = P2;
+    return true;
+}
+
+// ------------------------------------------------------- double-float (FP32) --
+// Error-free transformations: Knuth's two-sum, Dekker's fast two-sum and the
+// FMA two-product; a double-float carries ~48 significant bits.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const DF s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ DF df_mul_f(DF a, float b) {
+    DF p = two_prod(a.hi, b);
+    return fast_two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
+}
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const DF p = df_mul_f(b, q1);
+    const DF r = df_add(a, DF{-p.hi, -p.lo});
+    const float q2 = __fdiv_rn(r.hi, b.hi);
+    return fast_two_sum(q1, q2);
+}
+// dot(row, p) + t in double-float
+__device__ __forceinline__ DF df_affine(const float *row, const float p[3], float t) {
+    DF acc = two_prod(row[0], p[0]);
+    acc = df_add(acc, two_prod(row[1], p[1]));
+    acc = df_add(acc, two_prod(row[2], p[2]));
+    return df_add(acc, DF{t, 0.0f});
+}
+// a d - b c with one rounding error (Kahan's FMA scheme).
+__device__ __forceinline__ float det2(float a, float b, float c, float d) {
+    const float w = b * c;
+    const float e = __fmaf_rn(-b, c, w);
+    const float f = __fmaf_rn(a, d, -w);
+    return f + e;
+}
+
+// ------------------------------------------------------------- SH colour --
+// Real SH basis up to degree 3 with the (-1)^m sign: polynomials in the unit
+// direction.  Normalisations sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) (times
+// sqrt(2) for m != 0) multiplied out with the Legendre coefficients.
+constexpr float kY0 = 0.28209479177387814f;   // 1 / (2 sqrt(pi))
+constexpr float kY1 = 0.48860251190291992f;   // sqrt(3 / (4 pi))
+constexpr float kY2a = 1.09254843059207907f;  // sqrt(15 / pi) / 2
+constexpr float kY2b = 0.31539156525252005f;  // sqrt(5 / pi) / 4
+constexpr float kY2c = 0.54627421529603959f;  // sqrt(15 / pi) / 4
+constexpr float kY3a = 0.59004358992664352f;  // sqrt(35 / (2 pi)) / 4
+constexpr float kY3b = 2.89061144264055405f;  // sqrt(105 / pi) / 2
+constexpr float kY3c = 0.45704579946446572f;  // sqrt(21 / (2 pi)) / 4
+constexpr float kY3d = 0.37317633259011546f;  // sqrt(7 / pi) / 4
+constexpr float kY3e = 1.44530572132027738f;  // sqrt(105 / pi) / 4
+
+__device__ __forceinline__ void sh_basis(int D, float x, float y, float z, float Y[16]) {
+    Y[0] = kY0;
+    if (D < 1) return;
+    Y[1] = -kY1 * y;
+    Y[2] = kY1 * z;
+    Y[3] = -kY1 * x;
+    if (D < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = kY2a * x * y;
+    Y[5] = -kY2a * y * z;
+    Y[6] = kY2b * (2.0f * zz - xx - yy);
+    Y[7] = -kY2a * x * z;
+    Y[8] = kY2c * (xx - yy);
+    if (D < 3) return;
+    Y[9] = -kY3a * y * (3.0f * xx - yy);
+    Y[10] = kY3b * x * y * z;
+    Y[11] = -kY3c * y * (4.0f * zz - xx - yy);
+    Y[12] = kY3d * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+    Y[13] = -kY3c * x * (4.0f * zz - xx - yy);
+    Y[14] = kY3e * z * (xx - yy);
+    Y[15] = -kY3a * x * (xx - 3.0f * yy);
+}
+
+// Gradient of each basis polynomial with respect to (x, y, z).
+__device__ __forceinline__ void sh_basis_grad(int D, float x, float y, float z, float G[16][3]) {
+    for (int i = 0; i < 16; ++i) G[i][0] = G[i][1] = G[i][2] = 0.0f;
+    if (D < 1) return;
+    G[1][1] = -kY1;
+    G[2][2] = kY1;
+    G[3][0] = -kY1;
+    if (D < 2) return;
+    G[4][0] = kY2a * y; G[4][1] = kY2a * x;
+    G[5][1] = -kY2a * z; G[5][2] = -kY2a * y;
+    G[6][0] = -2.0f * kY2b * x; G[6][1] = -2.0f * kY2b * y; G[6][2] = 4.0f * kY2b * z;
+    G[7][0] = -kY2a * z; G[7][2] = -kY2a * x;
+    G[8][0] = 2.0f * kY2c * x; G[8][1] = -2.0f * kY2c * y;
+    if (D < 3) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    G[9][0] = -kY3a * 6.0f * x * y; G[9][1] = -kY3a * (3.0f * xx - 3.0f * yy);
+    G[10][0] = kY3b * y * z; G[10][1] = kY3b * x * z; G[10][2] = kY3b * x * y;
+    G[11][0] = kY3c * 2.0f * x * y; G[11][1] = -kY3c * (4.0f * zz - xx - 3.0f * yy);
+    G[11][2] = -kY3c * 8.0f * y * z;
+    G[12][0] = -kY3d * 6.0f * x * z; G[12][1] = -kY3d * 6.0f * y * z;
+    G[12][2] = kY3d * (6.0f * zz - 3.0f * xx - 3.0f * yy);
+    G[13][0] = -kY3c * (4.0f * zz - 3.0f * xx - yy); G[13][1] = kY3c * 2.0f * x * y;
+    G[13][2] = -kY3c * 8.0f * x * z;
+    G[14][0] = kY3e * 2.0f * x * z; G[14][1] = -kY3e * 2.0f * y * z; G[14][2] = kY3e * (xx - yy);
+    G[15][0] = -kY3a * (3.0f * xx - 3.0f * yy); G[15][1] = kY3a * 6.0f * x * y;
+}
+
+__device__ __forceinline__ float load_sh(const SceneDev &s, int64_t i) {
+    switch (s.sh_dtype) {
+        case GB_F16: return load_as_float(static_cast<const __half *>(s.sh), i);
+        case GB_BF16: return load_as_float(static_cast<const __nv_bfloat16 *>(s.sh), i);
+        default: return load_as_float(static_cast<const float *>(s.sh), i);
+    }
+}
+
+// ------------------------------------------------------ rotation and frame --
+struct Frame3 {
+    float tu[3], tv[3];
+    float qn[4];
+    float qnorm;
+};
+__device__ __forceinline__ Frame3 tangent_frame(const float q[4]) {
+    Frame3 f;
+    f.qnorm = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    const float inv = 1.0f / f.qnorm;
+    for (int i = 0; i < 4; ++i) f.qn[i] = q[i] * inv;
+    const float w = f.qn[0], x = f.qn[1], y = f.qn[2], z = f.qn[3];
+    f.tu[0] = 1.0f - 2.0f * (y * y + z * z);
+    f.tu[1] = 2.0f * (x * y + w * z);
+    f.tu[2] = 2.0f * (x * z - w * y);
+    f.tv[0] = 2.0f * (x * y - w * z);
+    f.tv[1] = 1.0f - 2.0f * (x * x + z * z);
+    f.tv[2] = 2.0f * (y * z + w * x);
+    return f;
+}
+
+// FP64 homography block for near edge-on splats.
+__device__ void homography_fp64(const float p[3], const float q[4], float su, float sv,
+                                const CamDev &c, float t[6], float &J, float &m20z, float &m21z) {
+    const double qn = sqrt((double)q[0] * q[0] + (double)q[1] * q[1] + (double)q[2] * q[2] +
+                           (double)q[3] * q[3]);
+    const double w = q[0] / qn, x = q[1] / qn, y = q[2] / qn, z = q[3] / qn;
+    const double tu[3] = {1 - 2 * (y * y + z * z), 2 * (x * y + w * z), 2 * (x * z - w * y)};
+    const double tv[3] = {2 * (x * y - w * z), 1 - 2 * (x * x + z * z), 2 * (y * z + w * x)};
+    double A[3], B[3], P[3];
+    for (int i = 0; i < 3; ++i) {
+        const float *r = c.R + 3 * i;
+        A[i] = su * ((double)r[0] * tu[0] + (double)r[1] * tu[1] + (double)r[2] * tu[2]);
+        B[i] = sv * ((double)r[0] * tv[0] + (double)r[1] * tv[1] + (double)r[2] * tv[2]);
+        P[i] = (double)r[0] * p[0] + (double)r[1] * p[1] + (double)r[2] * p[2] + (double)c.t[i];
+    }
+    const double xz = P[0] / P[2], yz = P[1] / P[2];
+    const double t00 = c.fx * (A[0] - A[2] * xz), t01 = c.fx * (B[0] - B[2] * xz);
+    const double t10 = c.fy * (A[1] - A[2] * yz), t11 = c.fy * (B[1] - B[2] * yz);
+    const double t20 = A[2], t21 = B[2];
+    t[0] = (float)t00; t[1] = (float)t01; t[2] = (float)t10; t[3] = (float)t11;
+    t[4] = (float)t20; t[5] = (float)t21;
+    J = (float)(t00 * t11 - t01 * t10);
+    m20z = (float)(t10 * t21 - t11 * t20);
+    m21z = (float)(t01 * t20 - t00 * t21);
+}
+
+// --------------------------------------------------------- forward kernel --
+__global__ void __launch_bounds__(256) preprocess_kernel(Frame f, uint32_t *depth_key,
+                                                         uint32_t *rec_id, uint2 *rect_out,
+                                                         Record *rec_out, Counters *cnt) {
+    const int ci = blockIdx.y;
+    const CamDev &cam = f.cams[ci];
+    const SceneDev &sc = f.scenes[cam.scene];
+    const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    bool valid = false;
+    if (k < sc.K) {
+        const int64_t r = cam.rec_off + k;
+        float p[3], q[4];
+        for (int i = 0; i < 3; ++i) p[i] = sc.means[3 * k + i];
+        for (int i = 0; i < 4; ++i) q[i] = sc.quats[4 * k + i];
+        const float su = sc.scales[2 * k], sv = sc.scales[2 * k + 1];
+        const float o = sc.opac[k];
+        float zkey;
+        int pr[4];
+        valid = key_rect(p, q, su, sv, o, cam, zkey, pr);
+        rec_id[r] = uint32_t(r);
+        if (!valid) {
+            depth_key[r] = 0xFFFFFFFFu;
+            rect_out[r] = make_uint2(0u, 0u);
+        } else {
+            depth_key[r] = __float_as_uint(zkey);
+            const int T = f.tile;
+            rect_out[r] = make_uint2(uint32_t(pr[0] / T) | (uint32_t(pr[1] / T) << 16),
+                                     uint32_t(pr[2] / T) | (uint32_t(pr[3] / T) << 16));
+            // ---- render record ----
+            const Frame3 fr = tangent_frame(q);
+            float A[3], B[3];
+            for (int i = 0; i < 3; ++i) {
+                const float *row = cam.R + 3 * i;
+                A[i] = su * (row[0] * fr.tu[0] + row[1] * fr.tu[1] + row[2] * fr.tu[2]);
+                B[i] = sv * (row[0] * fr.tv[0] + row[1] * fr.tv[1] + row[2] * fr.tv[2]);
+            }
+            const DF Px = df_affine(cam.R + 0, p, cam.t[0]);
+            const DF Py = df_affine(cam.R + 3, p, cam.t[1]);
+            const DF Pz = df_affine(cam.R + 6, p, cam.t[2]);
+            const DF xz = df_div(Px, Pz), yz = df_div(Py, Pz);
+            const DF cxd = df_add(df_mul_f(xz, cam.fx), DF{cam.cx, 0.0f});
+            const DF cyd = df_add(df_mul_f(yz, cam.fy), DF{cam.cy, 0.0f});
+            const float z = Pz.hi;
+            float t00 = cam.fx * det2(A[0], A[2], Px.hi, z) / z;
+            float t01 = cam.fx * det2(B[0], B[2], Px.hi, z) / z;
+            float t10 = cam.fy * det2(A[1], A[2], Py.hi, z) / z;
+            float t11 = cam.fy * det2(B[1], B[2], Py.hi, z) / z;
+            float t20 = A[2], t21 = B[2];
+            float J = det2(t00, t01, t10, t11);
+            float m20z = det2(t10, t11, t20, t21);
+            float m21z = det2(t01, t00, t21, t20);
+            const float scale = fabsf(t00 * t11) + fabsf(t01 * t10);
+            if (!(fabsf(J) * 64.0f > scale)) {
+                float t[6];
+                homography_fp64(p, q, su, sv, cam, t, J, m20z, m21z);
+                t00 = t[0]; t01 = t[1]; t10 = t[2]; t11 = t[3]; t20 = t[4]; t21 = t[5];
+            }
+            const float iz = 1.0f / z;
+            // SH colour, d = (p - campos) / |p - campos|
+            float dx = p[0] - cam.campos[0], dy = p[1] - cam.campos[1], dz = p[2] - cam.campos[2];
+            const float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
+            dx *= dn; dy *= dn; dz *= dn;
+            float Y[16];
+            sh_basis(sc.D, dx, dy, dz, Y);
+            const int M = (sc.D + 1) * (sc.D + 1);
+            float rgb[3] = {0.0f, 0.0f, 0.0f};
+            for (int m = 0; m < M; ++m)
+                for (int ch = 0; ch < 3; ++ch) rgb[ch] += Y[m] * load_sh(sc, (k * M + m) * 3 + ch);
+            Record R;
+            R.q0 = make_float4(t11, -t01, -t10, t00);
+            R.q1 = make_float4(m20z * iz, m21z * iz, J * iz, z);
+            R.q2 = make_float4(cxd.hi, cyd.hi, cxd.lo, cyd.lo);
+            R.q3 = make_float4(o, rgb[0], rgb[1], rgb[2]);
+            rec_out[r] = R;
+        }
+    }
+    // warp-aggregated visible count
+    const unsigned m = __ballot_sync(0xffffffffu, valid);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&cnt->n_visible, uint32_t(__popc(m)));
+}
+
+// -------------------------------------------------------- backward kernel --
+__global__ void __launch_bounds__(128) preprocess_bwd_kernel(Frame f, const float *rec_grad,
+                                                             const int32_t *inv_perm) {
+    const SceneDev &sc = f.scenes[blockIdx.y];
+    const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (k >= sc.K) return;
+    float p[3], q[4];
+    for (int i = 0; i < 3; ++i) p[i] = sc.means[3 * k + i];
+    for (int i = 0; i < 4; ++i) q[i] = sc.quats[4 * k + i];
+    const float su = sc.scales[2 * k], sv = sc.scales[2 * k + 1];
+    const Frame3 fr = tangent_frame(q);
+    const int M = (sc.D + 1) * (sc.D + 1);
+    float g_p[3] = {0, 0, 0}, g_tu[3] = {0, 0, 0}, g_tv[3] = {0, 0, 0};
+    float g_su = 0.0f, g_sv = 0.0f, g_o = 0.0f;
+    float g_sh[16][3];
+    for (int m = 0; m < 16; ++m) g_sh[m][0] = g_sh[m][1] = g_sh[m][2] = 0.0f;
+    for (int ci = 0; ci < f.n_cams; ++ci) {
+        const CamDev &cam = f.cams[ci];
+        if (cam.scene != int(blockIdx.y)) continue;
+        const int32_t j = inv_perm[cam.rec_off + k];
+        if (j < 0) continue;
+        const float4 *gp = reinterpret_cast<const float4 *>(rec_grad + int64_t(j) * kRecGrad);
+        const float4 g0 = gp[0], g1 = gp[1], g2 = gp[2], g3 = gp[3];
+        // forward recompute (camera space)
+        float a[3], b[3], A[3], B[3], P[3];
+        for (int i = 0; i < 3; ++i) { a[i] = su * fr.tu[i]; b[i] = sv * fr.tv[i]; }
+        for (int i = 0; i < 3; ++i) {
+            const float *row = cam.R + 3 * i;
+            A[i] = row[0] * a[0] + row[1] * a[1] + row[2] * a[2];
+            B[i] = row[0] * b[0] + row[1] * b[1] + row[2] * b[2];
+            P[i] = row[0] * p[0] + row[1] * p[1] + row[2] * p[2] + cam.t[i];
+        }
+        const float z = P[2], iz = 1.0f / z;
+        const float xz = P[0] * iz, yz = P[1] * iz;
+        const float t00 = cam.fx * (A[0] - A[2] * xz), t01 = cam.fx * (B[0] - B[2] * xz);
+        const float t10 = cam.fy * (A[1] - A[2] * yz), t11 = cam.fy * (B[1] - B[2] * yz);
+        const float t20 = A[2], t21 = B[2];
+        const float m20 = (t10 * t21 - t11 * t20) * iz;
+        const float m21 = (t01 * t20 - t00 * t21) * iz;
+        const float m22 = (t00 * t11 - t01 * t10) * iz;
+        // record gradients
+        float h00 = g0.w, h01 = -g0.y, h10 = -g0.z, h11 = g0.x;  // d t00, d t01, d t10, d t11
+        float h20 = 0.0f, h21 = 0.0f;
+        const float gm20 = g1.x, gm21 = g1.y, gm22 = g1.z;
+        float gz = g1.w;
+        // m20 = (t10 t21 - t11 t20) / z
+        h10 += gm20 * t21 * iz; h21 += gm20 * t10 * iz; h11 -= gm20 * t20 * iz; h20 -= gm20 * t11 * iz;
+        gz -= gm20 * m20 * iz;
+        // m21 = (t01 t20 - t00 t21) / z
+        h01 += gm21 * t20 * iz; h20 += gm21 * t01 * iz; h00 -= gm21 * t21 * iz; h21 -= gm21 * t00 * iz;
+        gz -= gm21 * m21 * iz;
+        // m22 = (t00 t11 - t01 t10) / z
+        h00 += gm22 * t11 * iz; h11 += gm22 * t00 * iz; h01 -= gm22 * t10 * iz; h10 -= gm22 * t01 * iz;
+        gz -= gm22 * m22 * iz;
+        // centre c = (fx xz + cx, fy yz + cy)
+        float gxz = g2.x * cam.fx, gyz = g2.y * cam.fy;
+        // t00 = fx (A0 - A2 xz) ...
+        float gA[3] = {cam.fx * h00, cam.fy * h10, 0.0f}, gB[3] = {cam.fx * h01, cam.fy * h11, 0.0f};
+        gA[2] = -cam.fx * h00 * xz - cam.fy * h10 * yz + h20;
+        gB[2] = -cam.fx * h01 * xz - cam.fy * h11 * yz + h21;
+        gxz -= cam.fx * (h00 * A[2] + h01 * B[2]);
+        gyz -= cam.fy * (h10 * A[2] + h11 * B[2]);
+        float gP[3] = {gxz * iz, gyz * iz, gz - (gxz * xz + gyz * yz) * iz};
+        // back to world space (R^T)
+        for (int i = 0; i < 3; ++i) {
+            const float ga = cam.R[i] * gA[0] + cam.R[3 + i] * gA[1] + cam.R[6 + i] * gA[2];
+            const float gb = cam.R[i] * gB[0] + cam.R[3 + i] * gB[1] + cam.R[6 + i] * gB[2];
+            g_p[i] += cam.R[i] * gP[0] + cam.R[3 + i] * gP[1] + cam.R[6 + i] * gP[2];
+            g_su += ga * fr.tu[i];
+            g_sv += gb * fr.tv[i];
+            g_tu[i] += su * ga;
+            g_tv[i] += sv * gb;
+        }
+        g_o += g2.z;
+        // SH colour
+        const float grgb[3] = {g2.w, g3.x, g3.y};
+        float d[3] = {p[0] - cam.campos[0], p[1] - cam.campos[1], p[2] - cam.campos[2]};
+        const float dist = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        for (int i = 0; i < 3; ++i) d[i] /= dist;
+        float Y[16], G[16][3];
+        sh_basis(sc.D, d[0], d[1], d[2], Y);
+        sh_basis_grad(sc.D, d[0], d[1], d[2], G);
+        float gd[3] = {0, 0, 0};
+        for (int m = 0; m < M; ++m)
+            for (int ch = 0; ch < 3; ++ch) {
+                g_sh[m][ch] += Y[m] * grgb[ch];
+                const float kc = load_sh(sc, (k * M + m) * 3 + ch) * grgb[ch];
+                gd[0] += kc * G[m][0];
+                gd[1] += kc * G[m][1];
+                gd[2] += kc * G[m][2];
+            }
+        const float dd = gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2];
+        for (int i = 0; i < 3; ++i) g_p[i] += (gd[i] - d[i] * dd) / dist;
+    }
+    // tangents -> normalised quaternion -> raw quaternion
+    const float w = fr.qn[0], x = fr.qn[1], y = fr.qn[2], z = fr.qn[3];
+    float gq[4];
+    gq[0] = 2.0f * (g_tu[1] * z - g_tu[2] * y - g_tv[0] * z + g_tv[2] * x);
+    gq[1] = 2.0f * (g_tu[1] * y + g_tu[2] * z + g_tv[0] * y + g_tv[2] * w) - 4.0f * g_tv[1] * x;
+    gq[2] = 2.0f * (g_tu[1] * x - g_tu[2] * w + g_tv[0] * x + g_tv[2] * z) - 4.0f * g_tu[0] * y;
+    gq[3] = 2.0f * (g_tu[1] * w + g_tu[2] * x - g_tv[0] * w + g_tv[2] * y) - 4.0f * (g_tu[0] + g_tv[1]) * z;
+    const float qd = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * z;
+    if (sc.g_means)
+        for (int i = 0; i < 3; ++i) sc.g_means[3 * k + i] = g_p[i];
+    if (sc.g_quats)
+        for (int i = 0; i < 4; ++i) sc.g_quats[4 * k + i] = (gq[i] - fr.qn[i] * qd) / fr.qnorm;
+    if (sc.g_scales) { sc.g_scales[2 * k] = g_su; sc.g_scales[2 * k + 1] = g_sv; }
+    if (sc.g_opac) sc.g_opac[k] = g_o;
+    if (sc.g_sh)
+        for (int m = 0; m < M; ++m)
+            for (int ch = 0; ch < 3; ++ch) sc.g_sh[(k * M + m) * 3 + ch] = g_sh[m][ch];
+}
+
+}  // namespace
+
+cudaError_t launch_preprocess(const Frame &f, int64_t max_k, uint32_t *depth_key, uint32_t *rec_id,
+                              uint2 *rect, Record *rec, Counters *cnt, cudaStream_t s) {
+    if (max_k <= 0) return cudaSuccess;
+    dim3 grid(unsigned(ceil_div(max_k, 256)), unsigned(f.n_cams));
+    preprocess_kernel<<<grid, 256, 0, s>>>(f, depth_key, rec_id, rect, rec, cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess_bwd(const Frame &f, int64_t max_k, const float *rec_grad,
+                                  const int32_t *inv_perm, cudaStream_t s) {
+    if (max_k <= 0) return cudaSuccess;
+    dim3 grid(unsigned(ceil_div(max_k, 128)), unsigned(f.n_scenes));
+    preprocess_bwd_kernel<<<grid, 128, 0, s>>>(f, rec_grad, inv_perm);
+    return cudaGetLastError();
+}
+
+}  // namespace gbill

@@ -1,0 +1,263 @@
+// Backward per-tile render (Alg. 1 bwd with Alg. 2 adj-bilinear).
+//
+// One block per tile, one thread per pixel, batches walked back to front
+// from the last blended splat of the tile.  Each pixel recomputes alpha and
+// the colour of every splat it blended and its transmittance
+// T_i = T_{i+1} / (1 - alpha_i) from the saved final T, then forms:
+//   colour adjoint  c^ = alpha T dL/dC                       (-> SH colour, grid)
+//   (C^, u^, v^)    = adj-bilinear(u, v, C_k, c^)            (Alg. 2)
+//   alpha^          = dL/dC . (c T - S / (1 - alpha)) + depth and alpha terms
+//   Gaussian:  rho^ -> (u^, v^) on the uv branch, -> centre on the low-pass one
+//   intersection:   (u^, v^) -> zeta^ -> record (adj(T'), centre) gradients
+// Record gradients (14 floats) are reduced over the warp, summed per batch in
+// shared memory and added to global memory with one atomic per value per tile;
+// colour-grid gradients are summed per batch in shared memory and added to the
+// global texel gradient with one atomic per non-zero texel channel per tile.
+#include "render_common.cuh"
+
+namespace gbill {
+namespace {
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int TS, int N, typename TexT>
+__global__ void __launch_bounds__(TS * TS) render_bwd_kernel(Frame f, RenderBwdBufs b, int batch) {
+    constexpr int NT = TS * TS;
+    constexpr int TEXF = N * N * 3;
+    constexpr int NG = 14;  // record gradient values accumulated per splat
+    extern __shared__ float4 smem[];
+    float4 *s_rec = smem;
+    float *s_tex = reinterpret_cast<float *>(s_rec + 4 * batch);
+    int32_t *s_k = reinterpret_cast<int32_t *>(s_tex + batch * TEXF);
+    uint32_t *s_j = reinterpret_cast<uint32_t *>(s_k + batch);
+    float *s_g = reinterpret_cast<float *>(s_j + batch);  // [batch][16]
+    float *s_tg = s_g + batch * kRecGrad;                  // [batch][TEXF]
+    __shared__ uint32_t s_maxlast;
+
+    const uint32_t tile = blockIdx.x;
+    const int ci = camera_of_tile(f, tile);
+    const CamDev &cam = f.cams[ci];
+    const SceneDev &sc = f.scenes[cam.scene];
+    const uint32_t lt = tile - cam.tile_off;
+    const int tx = int(lt % uint32_t(cam.tiles_x)), ty = int(lt / uint32_t(cam.tiles_x));
+    int lx, ly;
+    tile_pixel<TS>(threadIdx.x, lx, ly);
+    const int px = tx * TS + lx, py = ty * TS + ly;
+    const bool inside = px < cam.width && py < cam.height;
+    const float xf = float(px) + 0.5f, yf = float(py) + 0.5f;
+    const uint2 range = b.fw.ranges[tile];
+    const float sigma = sc.sigma;
+    const float kN = float(N - 1) / (2.0f * sigma);
+
+    float T = 1.0f, T_final = 1.0f, dC0 = 0, dC1 = 0, dC2 = 0, dD = 0, dA = 0;
+    uint32_t last = 0;
+    if (threadIdx.x == 0) s_maxlast = 0;
+    __syncthreads();
+    if (inside) {
+        const int64_t pix = cam.pix_off + int64_t(py) * cam.width + px;
+        T = T_final = b.fw.t_final[pix];
+        last = b.fw.last[pix];
+        dC0 = b.d_rgb[3 * pix + 0];
+        dC1 = b.d_rgb[3 * pix + 1];
+        dC2 = b.d_rgb[3 * pix + 2];
+        if (b.d_depth) dD = b.d_depth[pix];
+        if (b.d_alpha) dA = b.d_alpha[pix];
+        if (last) atomicMax(&s_maxlast, last);
+    }
+    const float bgdot = dC0 * f.bg[0] + dC1 * f.bg[1] + dC2 * f.bg[2];
+    const float dTfin = (dA - bgdot) * T_final;  // times 1/(1-alpha) per splat
+    float S0 = 0, S1 = 0, S2 = 0, SD = 0;
+    __syncthreads();
+    const int max_last = int(s_maxlast);
+    float *g_tex = sc.g_tex;
+
+    for (int be = max_last; be > 0; be -= batch) {
+        const int bs = max(0, be - batch), nb = be - bs;
+        for (int e = threadIdx.x; e < nb * kRecGrad; e += NT) s_g[e] = 0.0f;
+        for (int e = threadIdx.x; e < nb * TEXF; e += NT) s_tg[e] = 0.0f;
+        stage_batch<N, NT, TexT>(b.fw, cam, sc, range.x + bs, nb, s_rec, s_tex, s_k, s_j);
+        __syncthreads();
+        for (int i = nb - 1; i >= 0; --i) {
+            float g[NG];
+#pragma unroll
+            for (int q = 0; q < NG; ++q) g[q] = 0.0f;
+            bool act = inside && uint32_t(bs + i) < last;
+            if (act) {
+                const float4 q0 = s_rec[4 * i + 0], q1 = s_rec[4 * i + 1], q2 = s_rec[4 * i + 2],
+                             q3 = s_rec[4 * i + 3];
+                const float dx = (xf - q2.x) - q2.z, dy = (yf - q2.y) - q2.w;
+                const float zz = fmaf(q1.x, dx, fmaf(q1.y, dy, q1.z));
+                act = zz != 0.0f;
+                if (act) {
+                    const float rz = __frcp_rn(zz);
+                    const float u = fmaf(q0.x, dx, q0.y * dy) * rz;
+                    const float v = fmaf(q0.z, dx, q0.w * dy) * rz;
+                    const float ruv = fmaf(u, u, v * v);
+                    const float rlp = kLowPass * fmaf(dx, dx, dy * dy);
+                    const bool uvb = ruv <= rlp;
+                    const float rho = uvb ? ruv : rlp;
+                    const float G = gauss(rho);
+                    const float ar = q3.x * G;
+                    const bool clamped = ar > kAlphaMax;
+                    const float alpha = clamped ? kAlphaMax : ar;
+                    act = alpha >= kAlphaMin;
+                    if (act) {
+                        const float om = 1.0f - alpha;
+                        const float iom = __frcp_rn(om);
+                        const float Ti = T * iom;
+                        const Cell<N> cell = grid_cell<N>(u, v, sigma, kN);
+                        const float *tg = s_tex + i * TEXF;
+                        float col[3];
+                        grid_colour<N>(tg, cell, col);
+                        col[0] += q3.y;
+                        col[1] += q3.z;
+                        col[2] += q3.w;
+                        const float w = alpha * Ti;
+                        const float ch0 = w * dC0, ch1 = w * dC1, ch2 = w * dC2;
+                        g[11] = ch0; g[12] = ch1; g[13] = ch2;
+                        // adj-bilinear: grid adjoint and uv adjoint
+                        float uh = 0.0f, vh = 0.0f;
+                        float *tgo = s_tg + i * TEXF;
+                        if (N == 1) {
+                            atomicAdd(tgo + 0, ch0);
+                            atomicAdd(tgo + 1, ch1);
+                            atomicAdd(tgo + 2, ch2);
+                        } else {
+                            const float fu = cell.fu, fv = cell.fv;
+                            const float w00 = (1.0f - fu) * (1.0f - fv), w10 = fu * (1.0f - fv);
+                            const float w01 = (1.0f - fu) * fv, w11 = fu * fv;
+                            const int o00 = cell.base, o10 = o00 + 3 * N, o01 = o00 + 3, o11 = o10 + 3;
+                            const float chv[3] = {ch0, ch1, ch2};
+                            float fuh = 0.0f, fvh = 0.0f;
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                const float c00 = tg[o00 + c], c10 = tg[o10 + c], c01 = tg[o01 + c],
+                                            c11 = tg[o11 + c];
+                                fuh += chv[c] * ((c10 - c00) * (1.0f - fv) + (c11 - c01) * fv);
+                                fvh += chv[c] * ((c01 - c00) * (1.0f - fu) + (c11 - c10) * fu);
+                                if (w00 != 0.0f) atomicAdd(tgo + o00 + c, chv[c] * w00);
+                                if (w10 != 0.0f) atomicAdd(tgo + o10 + c, chv[c] * w10);
+                                if (w01 != 0.0f) atomicAdd(tgo + o01 + c, chv[c] * w01);
+                                if (w11 != 0.0f) atomicAdd(tgo + o11 + c, chv[c] * w11);
+                            }
+                            if (u > -sigma && u < sigma) uh = kN * fuh;
+                            if (v > -sigma && v < sigma) vh = kN * fvh;
+                        }
+                        // alpha adjoint
+                        const float zi = uvb ? q1.z * q1.w * rz : q1.w;
+                        float ah = dC0 * (col[0] * Ti - S0 * iom) + dC1 * (col[1] * Ti - S1 * iom) +
+                                   dC2 * (col[2] * Ti - S2 * iom);
+                        ah += dD * (zi * Ti - SD * iom) + dTfin * iom;
+                        S0 = fmaf(col[0], w, S0);
+                        S1 = fmaf(col[1], w, S1);
+                        S2 = fmaf(col[2], w, S2);
+                        SD = fmaf(zi, w, SD);
+                        T = Ti;
+                        const float zih = dD * w;
+                        float rhoh = 0.0f;
+                        if (!clamped) {
+                            g[10] = ah * G;
+                            rhoh = -0.5f * alpha * ah;
+                        }
+                        float zzh = 0.0f, dxh = 0.0f, dyh = 0.0f;
+                        if (uvb) {
+                            uh = fmaf(2.0f * u, rhoh, uh);
+                            vh = fmaf(2.0f * v, rhoh, vh);
+                            // zi = m22 z / zeta_z
+                            g[6] += zih * q1.w * rz;
+                            g[7] += zih * q1.z * rz;
+                            zzh = -zih * zi * rz;
+                        } else {
+                            dxh = 2.0f * kLowPass * dx * rhoh;
+                            dyh = 2.0f * kLowPass * dy * rhoh;
+                            g[7] += zih;
+                        }
+                        const float zxh = uh * rz, zyh = vh * rz;
+                        zzh -= (uh * u + vh * v) * rz;
+                        g[0] = zxh * dx;
+                        g[1] = zxh * dy;
+                        g[2] = zyh * dx;
+                        g[3] = zyh * dy;
+                        g[4] = zzh * dx;
+                        g[5] = zzh * dy;
+                        g[6] += zzh;
+                        dxh += zxh * q0.x + zyh * q0.z + zzh * q1.x;
+                        dyh += zxh * q0.y + zyh * q0.w + zzh * q1.y;
+                        g[8] = -dxh;
+                        g[9] = -dyh;
+                    }
+                }
+            }
+            if (__any_sync(0xffffffffu, act)) {
+#pragma unroll
+                for (int q = 0; q < NG; ++q) g[q] = warp_sum(g[q]);
+                if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+                    for (int q = 0; q < NG; ++q)
+                        if (g[q] != 0.0f) atomicAdd(s_g + i * kRecGrad + q, g[q]);
+                }
+            }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < nb * kRecGrad; e += NT) {
+            const float v = s_g[e];
+            if (v != 0.0f) {
+                const int s = e / kRecGrad, q = e - s * kRecGrad;
+                atomicAdd(b.rec_grad + int64_t(s_j[s]) * kRecGrad + q, v);
+            }
+        }
+        if (g_tex)
+            for (int e = threadIdx.x; e < nb * TEXF; e += NT) {
+                const float v = s_tg[e];
+                if (v != 0.0f) {
+                    const int s = e / TEXF, o = e - s * TEXF;
+                    atomicAdd(g_tex + int64_t(s_k[s]) * TEXF + o, v);
+                }
+            }
+        __syncthreads();
+    }
+}
+
+template <int TS, int N, typename TexT>
+cudaError_t launch_t(const Frame &f, const RenderBwdBufs &b, int batch, cudaStream_t s) {
+    const size_t smem = stage_bytes<N>(batch, true);
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(render_bwd_kernel<TS, N, TexT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    render_bwd_kernel<TS, N, TexT><<<f.n_tiles, TS * TS, smem, s>>>(f, b, batch);
+    return cudaGetLastError();
+}
+
+template <int TS, typename TexT>
+cudaError_t launch_n(const Frame &f, const RenderBwdBufs &b, int N, int batch, cudaStream_t s) {
+    switch (N) {
+        case 1: return launch_t<TS, 1, TexT>(f, b, batch, s);
+        case 2: return launch_t<TS, 2, TexT>(f, b, batch, s);
+        case 4: return launch_t<TS, 4, TexT>(f, b, batch, s);
+        case 8: return launch_t<TS, 8, TexT>(f, b, batch, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_render_bwd(const Frame &f, const RenderBwdBufs &b, int batch, cudaStream_t s) {
+    if (f.n_tiles == 0) return cudaSuccess;
+    const SceneDev &sc = f.scenes[0];
+    if (f.tile != 16) return cudaErrorInvalidValue;
+    switch (sc.tex_dtype) {
+        case GB_F16: return launch_n<16, __half>(f, b, sc.N, batch, s);
+        case GB_BF16: return launch_n<16, __nv_bfloat16>(f, b, sc.N, batch, s);
+        default: return launch_n<16, float>(f, b, sc.N, batch, s);
+    }
+}
+
+}  // namespace gbill

@@ -1,0 +1,138 @@
+// Forward per-tile render (Alg. 1 fwd with the colour grid of Eq. 5).
+//
+// One block per TS x TS tile, one thread per pixel.  The tile's depth-sorted
+// splats are staged in batches (record + colour grid, converted to FP32) in
+// shared memory; every pixel walks them front to back:
+//   zeta = adj(T') (dx, dy, 1)                (ray/splat intersection)
+//   rho  = min(u^2 + v^2, 2 |x - c|^2)        (Eq. 4 plus screen low-pass)
+//   alpha = min(0.99, o exp(-rho/2)), skipped below 1/255
+//   stop before T (1 - alpha) < 1e-4
+//   c = bilinear(C_k, u, v) + SH colour       (Eq. 5, Alg. 2, Sec. 4.2)
+//   C += c alpha T, D += z alpha T, T *= 1 - alpha   (Eq. 2)
+// Saved for the backward: final T and 1 + index of the last blended splat.
+#include "render_common.cuh"
+
+namespace gbill {
+namespace {
+
+template <int TS, int N, typename TexT>
+__global__ void __launch_bounds__(TS * TS) render_fwd_kernel(Frame f, RenderBufs b, int batch) {
+    constexpr int NT = TS * TS;
+    constexpr int TEXF = N * N * 3;
+    extern __shared__ float4 smem[];
+    float4 *s_rec = smem;
+    float *s_tex = reinterpret_cast<float *>(s_rec + 4 * batch);
+    int32_t *s_k = reinterpret_cast<int32_t *>(s_tex + batch * TEXF);
+    uint32_t *s_j = reinterpret_cast<uint32_t *>(s_k + batch);
+
+    const uint32_t tile = blockIdx.x;
+    const int ci = camera_of_tile(f, tile);
+    const CamDev &cam = f.cams[ci];
+    const SceneDev &sc = f.scenes[cam.scene];
+    const uint32_t lt = tile - cam.tile_off;
+    const int tx = int(lt % uint32_t(cam.tiles_x)), ty = int(lt / uint32_t(cam.tiles_x));
+    int lx, ly;
+    tile_pixel<TS>(threadIdx.x, lx, ly);
+    const int px = tx * TS + lx, py = ty * TS + ly;
+    const bool inside = px < cam.width && py < cam.height;
+    const float xf = float(px) + 0.5f, yf = float(py) + 0.5f;
+    const uint2 range = b.ranges[tile];
+    const int n_inst = int(range.y - range.x);
+    const float sigma = sc.sigma;
+    const float kN = float(N - 1) / (2.0f * sigma);
+
+    float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, Dp = 0.0f;
+    uint32_t last = 0;
+    bool done = !inside;
+    for (int bs = 0; bs < n_inst; bs += batch) {
+        if (__syncthreads_count(done) == NT) break;
+        const int nb = min(batch, n_inst - bs);
+        stage_batch<N, NT, TexT>(b, cam, sc, range.x + bs, nb, s_rec, s_tex, s_k, s_j);
+        __syncthreads();
+        if (!done) {
+            for (int i = 0; i < nb; ++i) {
+                const float4 q0 = s_rec[4 * i + 0], q1 = s_rec[4 * i + 1], q2 = s_rec[4 * i + 2];
+                const float dx = (xf - q2.x) - q2.z, dy = (yf - q2.y) - q2.w;
+                const float zz = fmaf(q1.x, dx, fmaf(q1.y, dy, q1.z));
+                if (zz == 0.0f) continue;
+                const float rz = __frcp_rn(zz);
+                const float u = fmaf(q0.x, dx, q0.y * dy) * rz;
+                const float v = fmaf(q0.z, dx, q0.w * dy) * rz;
+                const float ruv = fmaf(u, u, v * v);
+                const float rlp = kLowPass * fmaf(dx, dx, dy * dy);
+                const bool uvb = ruv <= rlp;
+                const float rho = uvb ? ruv : rlp;
+                const float4 q3 = s_rec[4 * i + 3];
+                const float alpha = fminf(kAlphaMax, q3.x * gauss(rho));
+                if (alpha < kAlphaMin) continue;
+                const float tT = T * (1.0f - alpha);
+                if (tT < kTMin) {
+                    done = true;
+                    break;
+                }
+                const Cell<N> cell = grid_cell<N>(u, v, sigma, kN);
+                float col[3];
+                grid_colour<N>(s_tex + i * TEXF, cell, col);
+                const float w = alpha * T;
+                C0 = fmaf(col[0] + q3.y, w, C0);
+                C1 = fmaf(col[1] + q3.z, w, C1);
+                C2 = fmaf(col[2] + q3.w, w, C2);
+                const float zi = uvb ? q1.z * q1.w * rz : q1.w;
+                Dp = fmaf(zi, w, Dp);
+                T = tT;
+                last = uint32_t(bs + i + 1);
+            }
+        }
+    }
+    if (inside) {
+        const int64_t pix = cam.pix_off + int64_t(py) * cam.width + px;
+        b.rgb[3 * pix + 0] = C0 + T * f.bg[0];
+        b.rgb[3 * pix + 1] = C1 + T * f.bg[1];
+        b.rgb[3 * pix + 2] = C2 + T * f.bg[2];
+        if (b.depth) b.depth[pix] = Dp;
+        if (b.alpha) b.alpha[pix] = 1.0f - T;
+        b.t_final[pix] = T;
+        b.last[pix] = last;
+    }
+}
+
+template <int TS, int N, typename TexT>
+cudaError_t launch_t(const Frame &f, const RenderBufs &b, int batch, cudaStream_t s) {
+    const size_t smem = stage_bytes<N>(batch, false);
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(render_fwd_kernel<TS, N, TexT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    render_fwd_kernel<TS, N, TexT><<<f.n_tiles, TS * TS, smem, s>>>(f, b, batch);
+    return cudaGetLastError();
+}
+
+template <int TS, typename TexT>
+cudaError_t launch_n(const Frame &f, const RenderBufs &b, int N, int batch, cudaStream_t s) {
+    switch (N) {
+        case 1: return launch_t<TS, 1, TexT>(f, b, batch, s);
+        case 2: return launch_t<TS, 2, TexT>(f, b, batch, s);
+        case 4: return launch_t<TS, 4, TexT>(f, b, batch, s);
+        case 8: return launch_t<TS, 8, TexT>(f, b, batch, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_render_fwd(const Frame &f, const RenderBufs &b, int batch, cudaStream_t s) {
+    if (f.n_tiles == 0) return cudaSuccess;
+    // every scene of a launch shares tex_n and tex_dtype (checked by the caller)
+    const SceneDev &sc = f.scenes[0];
+    if (f.tile != 16) return cudaErrorInvalidValue;
+    switch (sc.tex_dtype) {
+        case GB_F16: return launch_n<16, __half>(f, b, sc.N, batch, s);
+        case GB_BF16: return launch_n<16, __nv_bfloat16>(f, b, sc.N, batch, s);
+        default: return launch_n<16, float>(f, b, sc.N, batch, s);
+    }
+}
+
+}  // namespace gbill

@@ -1,0 +1,369 @@
+// Sorting and bookkeeping kernels: stable LSD radix sort of (u32 key, u32
+// value) pairs, exclusive scan, (tile, splat) instance duplication, per-tile
+// ranges.  Element counts may live on the device (kernels are launched for a
+// capacity and read the true count), so no host round trip is needed between
+// preprocess and render.
+#include "gbill_internal.cuh"
+
+namespace gbill {
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortRounds = 16;  // 32-key rounds per warp
+constexpr int kWarpTile = 32 * kSortRounds;
+constexpr int kSortTile = kWarpTile * kSortWarps;  // 4096 keys per block
+constexpr int kRadix = 256;
+
+__device__ __forceinline__ uint32_t load_n(const uint32_t *n_dev, int64_t max_n) {
+    return n_dev ? uint32_t(min(int64_t(*n_dev), max_n)) : uint32_t(max_n);
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Per-block digit histogram, written digit-major: hist[d * nblocks + block].
+__global__ void __launch_bounds__(kSortThreads) radix_upsweep(const uint32_t *keys, int64_t max_n,
+                                                              const uint32_t *n_dev, int shift,
+                                                              uint32_t mask, uint32_t *hist) {
+    __shared__ uint32_t h[kRadix];
+    const uint32_t n = load_n(n_dev, max_n);
+    for (int i = threadIdx.x; i < kRadix; i += kSortThreads) h[i] = 0;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t base = int64_t(blockIdx.x) * kSortTile + int64_t(warp) * kWarpTile;
+    for (int r = 0; r < kSortRounds; ++r) {
+        const int64_t idx = base + r * 32 + lane;
+        const bool act = idx < n;
+        const uint32_t am = __ballot_sync(0xffffffffu, act);
+        if (act) {
+            const uint32_t d = (keys[idx] >> shift) & mask;
+            const uint32_t peers = __match_any_sync(am, d);
+            if ((peers & lanemask_lt()) == 0) atomicAdd(&h[d], uint32_t(__popc(peers)));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kRadix; i += kSortThreads) hist[int64_t(i) * gridDim.x + blockIdx.x] = h[i];
+}
+
+// Stable scatter: warp w owns keys [w*512, (w+1)*512) of the block tile and
+// ranks them in order with warp-match; per-digit warp counts are then
+// prefix-summed over warps so earlier warps come first.
+__global__ void __launch_bounds__(kSortThreads) radix_downsweep(
+    const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *keys_out, uint32_t *vals_out,
+    int64_t max_n, const uint32_t *n_dev, int shift, uint32_t mask, const uint32_t *offs) {
+    __shared__ uint32_t wcount[kSortWarps][kRadix];
+    __shared__ uint32_t goff[kRadix];
+    const uint32_t n = load_n(n_dev, max_n);
+    const int64_t blk_base = int64_t(blockIdx.x) * kSortTile;
+    if (blk_base >= n) return;  // uniform per block
+    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&wcount[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < kRadix; i += kSortThreads) goff[i] = offs[int64_t(i) * gridDim.x + blockIdx.x];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t base = blk_base + int64_t(warp) * kWarpTile;
+    uint32_t k_[kSortRounds], v_[kSortRounds], rank_[kSortRounds];
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r) {
+        const int64_t idx = base + r * 32 + lane;
+        const bool act = idx < n;
+        const uint32_t am = __ballot_sync(0xffffffffu, act);
+        rank_[r] = 0xffffffffu;
+        if (act) {
+            k_[r] = keys_in[idx];
+            v_[r] = vals_in[idx];
+            const uint32_t d = (k_[r] >> shift) & mask;
+            const uint32_t peers = __match_any_sync(am, d);
+            const uint32_t before = wcount[warp][d];
+            rank_[r] = before + __popc(peers & lt);
+            __syncwarp(am);
+            if ((peers & lt) == 0) wcount[warp][d] = before + __popc(peers);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // exclusive prefix over warps, per digit
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
+        uint32_t run = goff[d];
+        for (int w = 0; w < kSortWarps; ++w) {
+            const uint32_t c = wcount[w][d];
+            wcount[w][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r) {
+        if (rank_[r] != 0xffffffffu) {
+            const uint32_t d = (k_[r] >> shift) & mask;
+            const uint32_t pos = wcount[warp][d] + rank_[r];
+            keys_out[pos] = k_[r];
+            vals_out[pos] = v_[r];
+        }
+    }
+}
+
+// ----------------------------------------------------------------- scan --
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+struct LoadArray {
+    const uint32_t *a;
+    __device__ uint32_t operator()(int64_t i) const { return a[i]; }
+};
+
+// Tile count of the j-th depth-sorted record: rectangle area in tiles.
+struct LoadTileCount {
+    const uint32_t *perm;
+    const uint2 *rect;
+    __device__ uint32_t operator()(int64_t j) const {
+        const uint2 r = rect[perm[j]];
+        const uint32_t nx = (r.y & 0xffffu) - (r.x & 0xffffu) + 1u;
+        const uint32_t ny = (r.y >> 16) - (r.x >> 16) + 1u;
+        return nx * ny;
+    }
+};
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total) {
+    __shared__ uint32_t wsum[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t s = lane < kScanThreads / 32 ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < kScanThreads / 32) wsum[lane] = s;
+    }
+    __syncthreads();
+    const uint32_t before = warp ? wsum[warp - 1] : 0u;
+    *total = wsum[kScanThreads / 32 - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+template <class Load>
+__global__ void __launch_bounds__(kScanThreads) scan_reduce(Load ld, int64_t max_n, const uint32_t *n_dev,
+                                                            uint32_t *block_sums) {
+    const uint32_t n = load_n(n_dev, max_n);
+    const int64_t base = int64_t(blockIdx.x) * kScanTile + int64_t(threadIdx.x) * kScanItems;
+    uint32_t s = 0;
+    for (int i = 0; i < kScanItems; ++i)
+        if (base + i < n) s += ld(base + i);
+    uint32_t tot;
+    block_exclusive_scan(s, &tot);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+// Single block: exclusive scan of the block sums in place; total to *total.
+__global__ void __launch_bounds__(kScanThreads) scan_block_sums(uint32_t *sums, int64_t nb, uint32_t *total,
+                                                                Counters *cnt, int64_t capacity) {
+    uint32_t carry = 0;
+    for (int64_t base = 0; base < nb; base += kScanThreads) {
+        const int64_t i = base + threadIdx.x;
+        const uint32_t v = i < nb ? sums[i] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan(v, &tot);
+        if (i < nb) sums[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        if (total) *total = carry;
+        if (cnt) {
+            cnt->n_instances = carry;
+            if (int64_t(carry) > capacity) cnt->overflow = 1u;
+        }
+    }
+}
+
+template <class Load>
+__global__ void __launch_bounds__(kScanThreads) scan_downsweep(Load ld, int64_t max_n, const uint32_t *n_dev,
+                                                               const uint32_t *block_sums, uint32_t *out) {
+    const uint32_t n = load_n(n_dev, max_n);
+    const int64_t base = int64_t(blockIdx.x) * kScanTile + int64_t(threadIdx.x) * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t s = 0;
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = base + i < n ? ld(base + i) : 0u;
+        s += v[i];
+    }
+    uint32_t tot;
+    uint32_t run = block_sums[blockIdx.x] + block_exclusive_scan(s, &tot);
+    for (int i = 0; i < kScanItems; ++i) {
+        if (base + i < n) out[base + i] = run;
+        run += v[i];
+    }
+}
+
+template <class Load>
+cudaError_t exclusive_scan(Load ld, int64_t max_n, const uint32_t *n_dev, uint32_t *out, uint32_t *total,
+                           void *scratch, size_t scratch_bytes, Counters *cnt, int64_t capacity,
+                           cudaStream_t s) {
+    const int64_t nb = ceil_div(max_n, kScanTile);
+    if (nb <= 0) return cudaSuccess;
+    if (scratch_bytes < size_t(nb) * sizeof(uint32_t)) return cudaErrorInvalidValue;
+    uint32_t *sums = static_cast<uint32_t *>(scratch);
+    scan_reduce<<<unsigned(nb), kScanThreads, 0, s>>>(ld, max_n, n_dev, sums);
+    scan_block_sums<<<1, kScanThreads, 0, s>>>(sums, nb, total, cnt, capacity);
+    scan_downsweep<<<unsigned(nb), kScanThreads, 0, s>>>(ld, max_n, n_dev, sums, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------- duplication --
+__device__ __forceinline__ int camera_of_record(const Frame &f, int64_t r) {
+    int lo = 0, hi = f.n_cams - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (f.cams[mid].rec_off <= r) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) emit_kernel(Frame f, const uint32_t *perm, const uint2 *rect,
+                                                   const uint32_t *offsets, int64_t max_n,
+                                                   const Counters *cnt, int64_t capacity,
+                                                   uint32_t *inst_tile, uint32_t *inst_val) {
+    const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= min(int64_t(cnt->n_visible), max_n)) return;
+    const uint32_t r = perm[j];
+    const int ci = camera_of_record(f, r);
+    const CamDev &cam = f.cams[ci];
+    const uint2 rc = rect[r];
+    const uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16, x1 = rc.y & 0xffffu, y1 = rc.y >> 16;
+    int64_t o = offsets[j];
+    if (o + int64_t(x1 - x0 + 1) * (y1 - y0 + 1) > capacity) return;  // overflow flagged by the scan
+    for (uint32_t y = y0; y <= y1; ++y)
+        for (uint32_t x = x0; x <= x1; ++x) {
+            inst_tile[o] = cam.tile_off + y * uint32_t(cam.tiles_x) + x;
+            inst_val[o] = uint32_t(j);
+            ++o;
+        }
+}
+
+__global__ void ranges_kernel(const uint32_t *tiles, int64_t max_n, const Counters *cnt, uint2 *ranges) {
+    const int64_t n = min(int64_t(cnt->n_instances), max_n);
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t t = tiles[i];
+    if (i == 0 || tiles[i - 1] != t) ranges[t].x = uint32_t(i);
+    if (i == n - 1 || tiles[i + 1] != t) ranges[t].y = uint32_t(i + 1);
+}
+
+__global__ void inverse_perm_kernel(const uint32_t *perm, int64_t n_records, const Counters *cnt, int32_t *inv) {
+    const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= n_records) return;
+    inv[perm[j]] = j < int64_t(cnt->n_visible) ? int32_t(j) : -1;
+}
+
+__global__ void export_keys_kernel(Frame f, const uint32_t *tiles, const uint32_t *vals, const uint32_t *perm,
+                                   const uint32_t *depth_key, int64_t n, uint64_t *keys, int64_t *ids,
+                                   int32_t *cams) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t r = perm[vals[i]];
+    const int ci = camera_of_record(f, r);
+    keys[i] = (uint64_t(tiles[i]) << 32) | depth_key[r];
+    ids[i] = int64_t(r) - f.cams[ci].rec_off;
+    cams[i] = ci;
+}
+
+}  // namespace
+
+size_t radix_scratch_bytes(int64_t n) {
+    const int64_t nb = ceil_div(n, kSortTile);
+    const int64_t h = nb * kRadix;
+    return size_t(h) * sizeof(uint32_t) + size_t(ceil_div(h, kScanTile) + 1) * sizeof(uint32_t) + 256;
+}
+
+size_t scan_scratch_bytes(int64_t n) { return size_t(ceil_div(n, kScanTile) + 1) * sizeof(uint32_t); }
+
+cudaError_t radix_sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *keys_tmp,
+                             uint32_t *vals_tmp, uint32_t *keys_out, uint32_t *vals_out, int64_t max_n,
+                             const uint32_t *n_dev, int begin_bit, int end_bit, void *scratch,
+                             size_t scratch_bytes, cudaStream_t s) {
+    if (max_n <= 0) return cudaSuccess;
+    const int64_t nb = ceil_div(max_n, kSortTile);
+    const int64_t h = nb * kRadix;
+    if (scratch_bytes < radix_scratch_bytes(max_n)) return cudaErrorInvalidValue;
+    uint32_t *hist = static_cast<uint32_t *>(scratch);
+    uint32_t *scan_tmp = hist + h;
+    const size_t scan_bytes = scratch_bytes - size_t(h) * sizeof(uint32_t);
+    const int passes = (end_bit - begin_bit + 7) / 8;
+    if (passes <= 0) {
+        cudaMemcpyAsync(keys_out, keys_in, size_t(max_n) * 4, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(vals_out, vals_in, size_t(max_n) * 4, cudaMemcpyDeviceToDevice, s);
+        return cudaGetLastError();
+    }
+    const uint32_t *ki = keys_in, *vi = vals_in;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = begin_bit + 8 * p;
+        const int bits = min(8, end_bit - shift);
+        const uint32_t mask = (1u << bits) - 1u;
+        uint32_t *ko = ((passes - p) & 1) ? keys_out : keys_tmp;
+        uint32_t *vo = ((passes - p) & 1) ? vals_out : vals_tmp;
+        radix_upsweep<<<unsigned(nb), kSortThreads, 0, s>>>(ki, max_n, n_dev, shift, mask, hist);
+        cudaError_t e = exclusive_scan(LoadArray{hist}, h, nullptr, hist, nullptr, scan_tmp, scan_bytes,
+                                       nullptr, 0, s);
+        if (e != cudaSuccess) return e;
+        radix_downsweep<<<unsigned(nb), kSortThreads, 0, s>>>(ki, vi, ko, vo, max_n, n_dev, shift, mask, hist);
+        ki = ko;
+        vi = vo;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t tile_counts_scan(const Frame &f, const uint32_t *perm, const uint2 *rect, int64_t max_n,
+                             const uint32_t *n_dev, uint32_t *offsets, void *scratch, size_t scratch_bytes,
+                             Counters *cnt, int64_t capacity, cudaStream_t s) {
+    (void)f;
+    return exclusive_scan(LoadTileCount{perm, rect}, max_n, n_dev, offsets, nullptr, scratch, scratch_bytes,
+                          cnt, capacity, s);
+}
+
+cudaError_t launch_emit(const Frame &f, const uint32_t *perm, const uint2 *rect, const uint32_t *offsets,
+                        int64_t max_n, const Counters *cnt, int64_t capacity, uint32_t *inst_tile,
+                        uint32_t *inst_val, cudaStream_t s) {
+    if (max_n <= 0) return cudaSuccess;
+    emit_kernel<<<unsigned(ceil_div(max_n, 256)), 256, 0, s>>>(f, perm, rect, offsets, max_n, cnt, capacity,
+                                                              inst_tile, inst_val);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ranges(const uint32_t *tiles_sorted, int64_t max_n, const Counters *cnt, uint2 *ranges,
+                          cudaStream_t s) {
+    if (max_n <= 0) return cudaSuccess;
+    ranges_kernel<<<unsigned(ceil_div(max_n, 256)), 256, 0, s>>>(tiles_sorted, max_n, cnt, ranges);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inverse_perm(const uint32_t *perm, int64_t n_records, const Counters *cnt, int32_t *inv,
+                                cudaStream_t s) {
+    if (n_records <= 0) return cudaSuccess;
+    inverse_perm_kernel<<<unsigned(ceil_div(n_records, 256)), 256, 0, s>>>(perm, n_records, cnt, inv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export_keys(const Frame &f, const uint32_t *tiles_sorted, const uint32_t *vals_sorted,
+                               const uint32_t *perm, const uint32_t *depth_key_by_rec, int64_t n,
+                               uint64_t *keys, int64_t *ids, int32_t *cams, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    export_keys_kernel<<<unsigned(ceil_div(n, 256)), 256, 0, s>>>(f, tiles_sorted, vals_sorted, perm,
+                                                                  depth_key_by_rec, n, keys, ids, cams);
+    return cudaGetLastError();
+}
+
+}  // namespace gbill

@@ -1,0 +1,265 @@
+"""PyTorch front end of the GB300 textured 2D-Gaussian rasterizer.
+
+``Rasterizer`` owns a C-ABI context and converts torch CUDA tensors and camera
+dicts into the structs of include/gbill.h; ``render`` is the differentiable
+``torch.autograd.Function`` whose backward recomputes per-pixel
+transmittance from the saved final T and last-contributor index (no per-splat
+alphas are stored).  PyTorch provides device memory and streams only; every
+step of the forward and backward runs in ``libgbill.so``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+DTYPES = {torch.float32: L.GB_F32, torch.float16: L.GB_F16, torch.bfloat16: L.GB_BF16}
+STORAGE = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}
+PARAMS = ("means", "quats", "scales", "opacities", "sh", "textures")
+
+
+def camera_struct(cam: dict, scene: int = 0) -> L.gb_camera:
+    c = L.gb_camera()
+    c.width, c.height = int(cam["width"]), int(cam["height"])
+    c.fx, c.fy, c.cx, c.cy = (float(cam[k]) for k in ("fx", "fy", "cx", "cy"))
+    R = np.asarray(cam["R"], np.float32)
+    t = np.asarray(cam["t"], np.float32)
+    w2c = np.concatenate([R, t[:, None]], axis=1).reshape(-1)
+    for i in range(12):
+        c.world_to_cam[i] = float(w2c[i])
+    c.near_plane = float(cam.get("near", 0.01))
+    c.scene = int(scene)
+    return c
+
+
+def scene_to_device(scene: dict, device="cuda") -> dict:
+    """Copies a generator scene (numpy) to torch tensors in its storage types."""
+    out = {}
+    for k in ("means", "quats", "scales", "opacities"):
+        out[k] = torch.as_tensor(np.ascontiguousarray(scene[k]), dtype=torch.float32, device=device)
+    out["sh"] = torch.as_tensor(scene["sh"], device=device).to(STORAGE[scene.get("sh_dtype", "f32")]).contiguous()
+    out["textures"] = torch.as_tensor(scene["textures"], device=device).to(
+        STORAGE[scene.get("tex_dtype", "f32")]).contiguous()
+    out["sh_degree"] = int(scene["sh_degree"])
+    out["tex_n"] = int(scene["tex_n"])
+    out["sigma"] = float(scene.get("sigma", 0.5))
+    return out
+
+
+def _check_tensor(t: torch.Tensor, name: str, shape_tail, dtypes=(torch.float32,)):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype not in dtypes:
+        raise ValueError(f"{name}: dtype {t.dtype} not in {dtypes}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if tuple(t.shape[1:]) != tuple(shape_tail):
+        raise ValueError(f"{name}: shape {tuple(t.shape)} does not end in {shape_tail}")
+
+
+def scene_struct(sc: dict) -> L.gb_scene:
+    K = int(sc["means"].shape[0])
+    D, N = int(sc["sh_degree"]), int(sc["tex_n"])
+    _check_tensor(sc["means"], "means", (3,))
+    _check_tensor(sc["quats"], "quats", (4,))
+    _check_tensor(sc["scales"], "scales", (2,))
+    _check_tensor(sc["opacities"], "opacities", ())
+    _check_tensor(sc["sh"], "sh", ((D + 1) ** 2, 3), tuple(DTYPES))
+    _check_tensor(sc["textures"], "textures", (N, N, 3), tuple(DTYPES))
+    for k in PARAMS:
+        if sc[k].shape[0] != K:
+            raise ValueError(f"{k}: first dimension {sc[k].shape[0]} != {K}")
+    s = L.gb_scene()
+    s.num_splats = K
+    s.means, s.quats, s.scales = sc["means"].data_ptr(), sc["quats"].data_ptr(), sc["scales"].data_ptr()
+    s.opacities, s.sh, s.textures = sc["opacities"].data_ptr(), sc["sh"].data_ptr(), sc["textures"].data_ptr()
+    s.sh_degree, s.sh_dtype = D, DTYPES[sc["sh"].dtype]
+    s.tex_n, s.tex_dtype = N, DTYPES[sc["textures"].dtype]
+    s.sigma = float(sc.get("sigma", 0.5))
+    s.reserved = 0
+    return s
+
+
+class Saved:
+    """Owns one gb_saved handle (state kept between a forward and its backward)."""
+
+    def __init__(self, rast: "Rasterizer"):
+        self.rast = rast
+        h = C.c_void_p()
+        L.check(L.load().gb_saved_create(rast.ctx, C.byref(h)), rast.ctx)
+        self.handle = h
+        self.n_scenes = 0
+        self.shapes = []
+
+    def reserve(self, records: int, instances: int, pixels: int, tiles: int):
+        L.check(L.load().gb_saved_reserve(self.handle, records, instances, pixels, tiles), self.rast.ctx)
+
+    def stats(self) -> dict:
+        st = L.gb_stats()
+        L.check(L.load().gb_saved_stats(self.handle, C.byref(st)), self.rast.ctx)
+        return {f: getattr(st, f) for f, _ in L.gb_stats._fields_}
+
+    def check(self):
+        L.check(L.load().gb_saved_check(self.handle), self.rast.ctx)
+
+    def export_keys(self):
+        """Sorted (key, splat id, camera) instance list of the last forward."""
+        n = C.c_int64()
+        L.check(L.load().gb_saved_export_keys(self.handle, None, None, None, 0, C.byref(n)), self.rast.ctx)
+        cnt = n.value
+        keys = np.zeros(cnt, np.uint64)
+        ids = np.zeros(cnt, np.int64)
+        cams = np.zeros(cnt, np.int32)
+        if cnt:
+            L.check(L.load().gb_saved_export_keys(self.handle, keys.ctypes.data, ids.ctypes.data,
+                                                  cams.ctypes.data, cnt, C.byref(n)), self.rast.ctx)
+        return keys, ids, cams
+
+    def __del__(self):
+        try:
+            if self.handle:
+                L.load().gb_saved_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+class Rasterizer:
+    """A C-ABI context on one CUDA device."""
+
+    def __init__(self, device: int | None = None):
+        lib = L.load()
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = int(device)
+        h = C.c_void_p()
+        st = lib.gb_context_create(self.device, C.byref(h))
+        if st != L.GB_OK:
+            raise L.GbillError(st, f"cannot create a context on CUDA device {self.device}")
+        self.ctx = h
+
+    def __del__(self):
+        try:
+            if self.ctx:
+                L.load().gb_context_destroy(self.ctx)
+                self.ctx = None
+        except Exception:
+            pass
+
+    @staticmethod
+    def pixel_count(cams) -> int:
+        return sum(int(c["width"]) * int(c["height"]) for c in cams)
+
+    def forward(self, scenes: list, cams: list, cam_scene=None, saved: Saved | None = None,
+                tile: int = 16, batch: int = 0, flags: int = 0, background=None, stream=None,
+                out=None):
+        """Renders every camera; returns (rgb [P,3], depth [P], alpha [P], saved)."""
+        lib = L.load()
+        n_s, n_c = len(scenes), len(cams)
+        cam_scene = list(cam_scene) if cam_scene is not None else [0] * n_c
+        sarr = (L.gb_scene * n_s)(*[scene_struct(s) for s in scenes])
+        carr = (L.gb_camera * n_c)(*[camera_struct(c, cam_scene[i]) for i, c in enumerate(cams)])
+        opt = L.gb_options()
+        opt.tile_size, opt.batch_depth, opt.flags, opt.reserved = tile, batch, flags, 0
+        if background is not None:
+            for i in range(3):
+                opt.background[i] = float(background[i])
+        P = self.pixel_count(cams)
+        dev = scenes[0]["means"].device
+        if out is None:
+            rgb = torch.empty((P, 3), device=dev)
+            depth = torch.empty(P, device=dev)
+            alpha = torch.empty(P, device=dev)
+        else:
+            rgb, depth, alpha = out
+        if saved is None:
+            saved = Saved(self)
+        saved.n_scenes = n_s
+        saved.shapes = [(int(s["means"].shape[0]), int(s["sh_degree"]), int(s["tex_n"])) for s in scenes]
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        st = lib.gb_render_forward(self.ctx, saved.handle, sarr, n_s, carr, n_c, C.byref(opt),
+                                   rgb.data_ptr(), depth.data_ptr() if depth is not None else None,
+                                   alpha.data_ptr() if alpha is not None else None, C.c_void_p(s.cuda_stream))
+        L.check(st, self.ctx)
+        return rgb, depth, alpha, saved
+
+    def backward(self, saved: Saved, d_rgb: torch.Tensor, d_depth=None, d_alpha=None, grads=None,
+                 stream=None):
+        """Gradients of every scene (list of dicts), summed over its cameras."""
+        lib = L.load()
+        dev = d_rgb.device
+        if grads is None:
+            grads = []
+            for K, D, N in saved.shapes:
+                grads.append({
+                    "means": torch.empty((K, 3), device=dev), "quats": torch.empty((K, 4), device=dev),
+                    "scales": torch.empty((K, 2), device=dev), "opacities": torch.empty(K, device=dev),
+                    "sh": torch.empty((K, (D + 1) ** 2, 3), device=dev),
+                    "textures": torch.empty((K, N, N, 3), device=dev),
+                })
+        garr = (L.gb_grads * len(grads))()
+        for i, g in enumerate(grads):
+            for k in PARAMS:
+                t = g.get(k)
+                setattr(garr[i], "d_" + k, t.data_ptr() if t is not None else None)
+        for t, name in ((d_rgb, "d_rgb"), (d_depth, "d_depth"), (d_alpha, "d_alpha")):
+            if t is not None and (not t.is_contiguous() or t.dtype != torch.float32):
+                raise ValueError(f"{name} must be contiguous float32")
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        st = lib.gb_render_backward(self.ctx, saved.handle, d_rgb.data_ptr(),
+                                    d_depth.data_ptr() if d_depth is not None else None,
+                                    d_alpha.data_ptr() if d_alpha is not None else None,
+                                    garr, len(grads), C.c_void_p(s.cuda_stream))
+        L.check(st, self.ctx)
+        return grads
+
+
+_default = {}
+
+
+def default_rasterizer() -> Rasterizer:
+    dev = torch.cuda.current_device()
+    if dev not in _default:
+        _default[dev] = Rasterizer(dev)
+    return _default[dev]
+
+
+class _RenderFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, means, quats, scales, opacities, sh, textures, meta):
+        rast, cams, sh_degree, tex_n, sigma, background = meta
+        sc = {"means": means.contiguous(), "quats": quats.contiguous(), "scales": scales.contiguous(),
+              "opacities": opacities.contiguous(), "sh": sh.contiguous(), "textures": textures.contiguous(),
+              "sh_degree": sh_degree, "tex_n": tex_n, "sigma": sigma}
+        rgb, depth, alpha, saved = rast.forward([sc], cams, background=background)
+        ctx.saved_handle = saved
+        ctx.rast = rast
+        ctx.keep = sc  # parameters must stay alive and unchanged until backward
+        ctx.dtypes = (sh.dtype, textures.dtype)
+        return rgb, depth, alpha
+
+    @staticmethod
+    def backward(ctx, d_rgb, d_depth, d_alpha):
+        d_rgb = d_rgb.contiguous().float() if d_rgb is not None else None
+        if d_rgb is None:
+            d_rgb = torch.zeros_like(ctx.keep["means"][:0])
+        d_depth = d_depth.contiguous().float() if d_depth is not None else None
+        d_alpha = d_alpha.contiguous().float() if d_alpha is not None else None
+        g = ctx.rast.backward(ctx.saved_handle, d_rgb, d_depth, d_alpha)[0]
+        return (g["means"], g["quats"], g["scales"], g["opacities"], g["sh"].to(ctx.dtypes[0]),
+                g["textures"].to(ctx.dtypes[1]), None)
+
+
+def render(means, quats, scales, opacities, sh, textures, cams, sh_degree: int, tex_n: int,
+           sigma: float = 0.5, background=None, rasterizer: Rasterizer | None = None):
+    """Differentiable render of one scene into all ``cams``.
+
+    Returns (rgb [P,3], depth [P], alpha [P]) with the cameras' pixels packed
+    one after another (row-major per camera).
+    """
+    rast = rasterizer or default_rasterizer()
+    meta = (rast, list(cams), int(sh_degree), int(tex_n), float(sigma), background)
+    return _RenderFn.apply(means, quats, scales, opacities, sh, textures, meta)

@@ -1,0 +1,239 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Keys are compared bit for bit; rgb and alpha within 2e-5 max abs error;
+depth within 2e-5 relative to max(1, |depth|); gradients per tensor within
+1e-3 of max(|g*|, 1e-3 max|g*|).  Pixels whose decisions sit within the
+oracle's margin of a threshold are excluded from image errors (and counted)
+and get zero upstream gradient on both sides.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2412_12734_gb300 import scenes
+from tests.gpu_util import (GRAD_REL, IMG_TOL, compare_images, gpu_run, grad_errors, masked_upstream,
+                            oracle_run)
+
+pytestmark = pytest.mark.gpu
+
+
+def _tile_offsets(cams, tile=16):
+    offs, o = [], 0
+    for c in cams:
+        offs.append(o)
+        o += -(-int(c["width"]) // tile) * -(-int(c["height"]) // tile)
+    return offs
+
+
+def _check_keys(scene_list, cams, cam_scene, gpu):
+    keys, ids, cidx = gpu["keys"]
+    offs = _tile_offsets(cams)
+    exp_k, exp_i, exp_c = [], [], []
+    for ci, c in enumerate(cams):
+        k, i = oracle.tile_keys(scene_list[cam_scene[ci]], c, 16, offs[ci])
+        exp_k.append(k)
+        exp_i.append(i)
+        exp_c.append(np.full(len(k), ci))
+    ek, ei = np.concatenate(exp_k), np.concatenate(exp_i)
+    assert len(keys) == len(ek), (len(keys), len(ek))
+    assert np.array_equal(keys, ek)
+    assert np.array_equal(ids, ei)
+    assert np.array_equal(cidx, np.concatenate(exp_c))
+
+
+CASES = {
+    "plain_1k": lambda: (scenes.workload("plain_1k")["scenes"], scenes.workload("plain_1k")["cams"]),
+    "tiny_n1_d0": lambda: ([scenes.tiny_scene(1, K=6, tex_n=1, sh_degree=0)], [scenes.tiny_camera(40, 24)]),
+    "tiny_n2_d3": lambda: ([scenes.tiny_scene(2, K=6, tex_n=2, sh_degree=3)], [scenes.tiny_camera(37, 29)]),
+    "tiny_n4_d3": lambda: ([scenes.tiny_scene(3, K=8, tex_n=4, sh_degree=3)], [scenes.tiny_camera(48, 33)]),
+    "tiny_n8_d2": lambda: ([scenes.tiny_scene(4, K=8, tex_n=8, sh_degree=2)], [scenes.tiny_camera(50, 50)]),
+    "tiny_n4_sigma2": lambda: ([scenes.tiny_scene(5, K=8, tex_n=4, sh_degree=1, sigma=2.0)],
+                               [scenes.tiny_camera(33, 47)]),
+    "tiny_f16": lambda: ([scenes.tiny_scene(6, K=8, tex_n=4, sh_degree=3, sh_dtype="f16", tex_dtype="f16")],
+                         [scenes.tiny_camera(40, 40)]),
+    "tiny_bf16": lambda: ([scenes.tiny_scene(7, K=8, tex_n=8, sh_degree=3, sh_dtype="bf16", tex_dtype="bf16")],
+                          [scenes.tiny_camera(40, 40)]),
+    "planes_2k": lambda: ([scenes.planes_scene(8, K=2000, tex_n=4, log_scale=(-3.0, 0.6))],
+                          [scenes.look_at([0.5, 1.0, -8.0], [0, 0, 0], 160, 90)]),
+    "dense_many_tiles": lambda: ([scenes.cube_scene(9, K=3000, half=1.0, log_scale=(-2.3, 0.4), sh_degree=3,
+                                                    tex_n=4)],
+                                [scenes.look_at([0.0, 0.0, -3.5], [0, 0, 0], 200, 136)]),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_keys_bit_exact(case):
+    sc, cams = CASES[case]()
+    gpu = gpu_run(sc, cams, keys=True)
+    _check_keys(sc, cams, [0] * len(cams), gpu)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_image_parity(case):
+    sc, cams = CASES[case]()
+    bg = np.array([0.25, 0.5, 0.75], np.float32) if "tiny" in case else None
+    gpu = gpu_run(sc, cams, bg=bg)
+    ref = oracle_run(sc[0], cams[0], bg=bg)
+    e_rgb, excl = compare_images(gpu["rgb"][0], ref, "rgb")
+    e_a, _ = compare_images(gpu["alpha"][0], ref, "alpha")
+    e_d, _ = compare_images(gpu["depth"][0], ref, "depth", relative_to=ref["depth"])
+    n = ref["rgb"].shape[0] * ref["rgb"].shape[1]
+    assert excl <= max(2, 0.01 * n), f"{excl} of {n} pixels near a decision threshold"
+    assert e_rgb <= IMG_TOL, f"rgb max err {e_rgb:.3e}"
+    assert e_a <= IMG_TOL, f"alpha max err {e_a:.3e}"
+    assert e_d <= IMG_TOL, f"depth max rel err {e_d:.3e}"
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_gradient_parity(case):
+    sc, cams = CASES[case]()
+    rng = np.random.default_rng(11)
+    ref = oracle_run(sc[0], cams[0])
+    d_rgb = masked_upstream(ref, rng)
+    use_da = case in ("tiny_n4_d3", "tiny_n8_d2", "planes_2k")
+    d_dep = masked_upstream(ref, rng, 1, 0.3)[..., 0] if use_da else None
+    d_alp = masked_upstream(ref, rng, 1)[..., 0] if use_da else None
+    gpu = gpu_run(sc, cams, d_rgb=[d_rgb], d_depth=[d_dep] if use_da else None,
+                  d_alpha=[d_alp] if use_da else None)
+    og = oracle.backward(sc[0], cams[0], d_rgb, d_dep, d_alp)
+    errs = grad_errors(gpu["grads"][0], og)
+    bad = {k: v for k, v in errs.items() if v > 1.0}
+    assert not bad, f"gradient ratios over tolerance {GRAD_REL}: {errs}"
+
+
+def test_multi_view_multi_scene():
+    """Two scenes, four cameras of different sizes in one launch: per-camera
+    keys and images, and gradients summed over each scene's cameras."""
+    s0 = scenes.tiny_scene(21, K=7, tex_n=4, sh_degree=3)
+    s1 = scenes.tiny_scene(22, K=5, tex_n=4, sh_degree=1)
+    cams = [scenes.tiny_camera(40, 24), scenes.tiny_camera(17, 33, eye=(0.5, 0.2, -4.0)),
+            scenes.tiny_camera(64, 48, focal=45.0, eye=(-0.7, 0.4, -4.5)), scenes.tiny_camera(16, 16)]
+    cam_scene = [0, 1, 0, 1]
+    sl = [s0, s1]
+    rng = np.random.default_rng(5)
+    refs = [oracle_run(sl[cam_scene[i]], c) for i, c in enumerate(cams)]
+    d_rgb = [masked_upstream(r, rng) for r in refs]
+    gpu = gpu_run(sl, cams, cam_scene=cam_scene, d_rgb=d_rgb, keys=True)
+    _check_keys(sl, cams, cam_scene, gpu)
+    for i, r in enumerate(refs):
+        e, _ = compare_images(gpu["rgb"][i], r, "rgb")
+        assert e <= IMG_TOL, (i, e)
+    for s in range(2):
+        og = None
+        for i, c in enumerate(cams):
+            if cam_scene[i] == s:
+                og = oracle.backward(sl[s], c, d_rgb[i], grads=og)
+        errs = grad_errors(gpu["grads"][s], og)
+        assert all(v <= 1.0 for v in errs.values()), (s, errs)
+
+
+def test_plain_100k_full_frame():
+    """100,000 planar + clutter splats, SH degree 3, 8x8 FP32 textures, one
+    1280x720 camera: full-frame keys, image and gradients against the oracle
+    (bbox-prefiltered mode, identical to brute force)."""
+    w = scenes.workload("plain_100k")
+    sc, cam = w["scenes"][0], w["cams"][0]
+    ref = oracle_run(sc, cam, prefilter=True)
+    rng = np.random.default_rng(3)
+    d_rgb = masked_upstream(ref, rng)
+    gpu = gpu_run([sc], [cam], d_rgb=[d_rgb], keys=True)
+    _check_keys([sc], [cam], [0], gpu)
+    e_rgb, excl = compare_images(gpu["rgb"][0], ref, "rgb")
+    assert excl <= 0.001 * 921600, excl
+    assert e_rgb <= IMG_TOL, e_rgb
+    og = oracle.backward(sc, cam, d_rgb, prefilter=True)
+    errs = grad_errors(gpu["grads"][0], og)
+    assert all(v <= 1.0 for v in errs.values()), errs
+
+
+# ------------------------------------------------------------------ edge cases --
+
+def test_empty_and_culled_scenes():
+    """K = 0, and every splat behind the camera: images equal the background,
+    no instances, zero gradients."""
+    bg = np.array([0.1, 0.2, 0.3], np.float32)
+    cam = scenes.tiny_camera(20, 12)
+    empty = scenes.subset(scenes.tiny_scene(1, K=3), np.arange(0))
+    behind = scenes.tiny_scene(2, K=4)
+    behind["means"][:, 2] = -6.0  # camera at z = -4 looking at +z
+    for sc in (empty, behind):
+        d_rgb = np.ones((12, 20, 3))
+        gpu = gpu_run([sc], [cam], bg=bg, d_rgb=[d_rgb])
+        assert gpu["stats"]["instances"] == 0
+        np.testing.assert_array_equal(gpu["rgb"][0], np.broadcast_to(bg, (12, 20, 3)))
+        np.testing.assert_array_equal(gpu["alpha"][0], 0.0)
+        for v in gpu["grads"][0].values():
+            assert np.all(v == 0)
+
+
+def test_one_pixel_and_degenerate_quaternion():
+    sc = scenes.tiny_scene(4, K=5)
+    sc["quats"][2] = 0.0  # zero quaternion: culled on both sides
+    for cam in (scenes.tiny_camera(1, 1, focal=2.0), scenes.tiny_camera(7, 3)):
+        gpu = gpu_run([sc], [cam], keys=True)
+        _check_keys([sc], [cam], [0], gpu)
+        ref = oracle_run(sc, cam)
+        e, _ = compare_images(gpu["rgb"][0], ref, "rgb")
+        assert e <= IMG_TOL
+
+
+def test_batch_depth_does_not_change_results():
+    sc, cams = CASES["dense_many_tiles"]()
+    a = gpu_run(sc, cams, batch=32)
+    b = gpu_run(sc, cams, batch=0)
+    np.testing.assert_array_equal(a["rgb"][0], b["rgb"][0])
+    np.testing.assert_array_equal(a["depth"][0], b["depth"][0])
+
+
+def test_invalid_arguments_are_rejected():
+    import torch
+
+    from paper_2412_12734_gb300 import _lib as L
+    from paper_2412_12734_gb300 import render as R
+    rast = R.Rasterizer(0)
+    dev = R.scene_to_device(scenes.tiny_scene(1, K=3, tex_n=4))
+    cam = scenes.tiny_camera(8, 8)
+    bad = dict(dev)
+    bad["tex_n"] = 3
+    bad["textures"] = torch.zeros((3, 3, 3, 3), device="cuda")
+    with pytest.raises(L.GbillError) as ei:
+        rast.forward([bad], [cam])
+    assert ei.value.status == 2
+    bad_cam = dict(cam)
+    bad_cam["width"] = 0
+    with pytest.raises(L.GbillError) as ei:
+        rast.forward([dev], [bad_cam])
+    assert ei.value.status == 1
+    nan_cam = dict(cam)
+    nan_cam["fx"] = float("nan")
+    with pytest.raises(L.GbillError) as ei:
+        rast.forward([dev], [nan_cam])
+    assert ei.value.status == 6
+    with pytest.raises(L.GbillError) as ei:
+        rast.forward([dev], [cam], batch=48)
+    assert ei.value.status == 1
+
+
+def test_no_sync_capacity_overflow_is_reported():
+    """No-sync mode never allocates: too small a reservation is flagged on the
+    device and reported by gb_saved_check; a large enough one matches eager."""
+    from paper_2412_12734_gb300 import _lib as L
+    from paper_2412_12734_gb300 import render as R
+    sc, cams = CASES["dense_many_tiles"]()
+    rast = R.Rasterizer(0)
+    dev = [R.scene_to_device(s) for s in sc]
+    ref_rgb, _, _, saved0 = rast.forward(dev, cams)
+    need = saved0.stats()["instances"]
+    P = rast.pixel_count(cams)
+    tiles = -(-cams[0]["width"] // 16) * -(-cams[0]["height"] // 16)
+    small = R.Saved(rast)
+    small.reserve(3000, max(16, need // 4), P, tiles)
+    rast.forward(dev, cams, saved=small, flags=L.GB_FLAG_NO_SYNC)
+    with pytest.raises(L.GbillError) as ei:
+        small.check()
+    assert ei.value.status == 4
+    big = R.Saved(rast)
+    big.reserve(3000, need, P, tiles)
+    rgb, _, _, _ = rast.forward(dev, cams, saved=big, flags=L.GB_FLAG_NO_SYNC)
+    big.check()
+    assert np.array_equal(rgb.cpu().numpy(), ref_rgb.cpu().numpy())
