@@ -1,0 +1,461 @@
+#!/usr/bin/env python3
+"""fwd+bwd Mpixel/s of the GB300 textured 2D-Gaussian rasterizer.
+
+Workload (default): 1,000,000 splats (80 % on 6 planes, 20 % clutter in a
+10^3 box), SH degree 3 and N x N RGB textures stored in FP16, 16 cameras on a
+radius-6 sphere at 960x540 / 1280x720 / 1920x1080 (18,086,400 pixels), all
+views rendered in one batched forward + backward per step.  Beside it, the
+same 16 views one by one on the plain FP32 path (FP32 texture/SH storage).
+
+A step is one forward + backward of all views with inputs resident in HBM
+(they exceed the 129 MB L2, so no flush is needed between steps).  Prints one
+JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle on a
+bounded crop of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd Mpixel/s at 1M textured splats, batched vs plain FP32, max err vs FP64"
+FP32_PEAK_TFLOPS_AT_MAX = 152 * 128 * 2 * 2.070e9 / 1e12  # FMA = 2 FLOP, 2070 MHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batched_1m")
+    ap.add_argument("--tex-n", type=int, default=4)
+    ap.add_argument("--batch", type=int, default=0, help="splats per shared-memory batch (0 = auto)")
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--crop", type=int, default=0, help="oracle crop side in pixels (0 = all of camera 0)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers --
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        rows = [l.split(",") for l in open(self.path).read().strip().splitlines() if l.strip()]
+        os.unlink(self.path)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for i, n in enumerate(names):
+                if len(r) > 5 + i and r[5 + i].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_workload(args):
+    from paper_2412_12734_gb300 import scenes
+    return scenes.workload(args.workload, seed=0, tex_n=args.tex_n)
+
+
+def crop_window(cam, side):
+    W, H = int(cam["width"]), int(cam["height"])
+    if side <= 0:
+        return (0, 0, W, H)
+    w, h = min(side, W), min(side, H)
+    return ((W - w) // 2, (H - h) // 2, w, h)
+
+
+# ------------------------------------------------------------- CPU oracle --
+
+def oracle_sample(wl, crop: int):
+    """Oracle fwd+bwd on a centred crop of camera 0: (seconds, pixels, outputs)."""
+    import oracle
+    sc, cam = wl["scenes"][0], wl["cams"][0]
+    win = crop_window(cam, crop)
+    x0, y0, w, h = win
+    d = wl["d_rgb"][0][y0:y0 + h, x0:x0 + w]
+    t0 = time.perf_counter()
+    ref = oracle.render(sc, cam, window=win, prefilter=True)
+    oracle.backward(sc, cam, d, window=win, prefilter=True)
+    dt = time.perf_counter() - t0
+    return dt, w * h, ref, win
+
+
+# ----------------------------------------------------------- reference arm --
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    wl = make_workload(args)
+    oracle.build()
+    times = []
+    px = 0
+    for i in range(args.warmup + args.steps):
+        dt, px, _, win = oracle_sample(wl, args.crop)
+        if i >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * sum(times) / len(times)
+    value = px / (ms / 1e3) / 1e6
+    cores = oracle.num_threads()
+    sample = (f"{win[2]}x{win[3]} window of camera 0 ({wl['cams'][0]['width']}x{wl['cams'][0]['height']}) "
+              f"of the {args.workload} workload, fwd+bwd, bbox-prefiltered FP64 oracle")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "tex_n": args.tex_n, "crop": args.crop},
+        "cpu_baseline": {"value": value, "unit": "Mpixel/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our arm --
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_2412_12734_gb300 import _lib as L
+    from paper_2412_12734_gb300 import build as B
+    from paper_2412_12734_gb300 import render as R
+
+    torch.cuda.set_device(local)
+    if rank == 0:
+        B.build()
+    barrier(world)
+    lib = L.load()
+    wl = make_workload(args)
+    cams = wl["cams"]
+    P = sum(int(c["width"]) * int(c["height"]) for c in cams)
+    dev_scene = R.scene_to_device(wl["scenes"][0])
+    d_rgb = torch.as_tensor(np.concatenate([d.reshape(-1, 3) for d in wl["d_rgb"]]), device="cuda")
+    rast = R.Rasterizer(local)
+    stream = torch.cuda.current_stream()
+
+    # --- size the saved state with one synchronizing forward, then reserve
+    saved = R.Saved(rast)
+    rgb, depth, alpha, _ = rast.forward([dev_scene], cams, saved=saved, batch=args.batch)
+    st0 = saved.stats()
+    saved.reserve(st0["records"], int(st0["instances"] * 1.1) + 4096, P, st0["tiles"])
+    grads = rast.backward(saved, d_rgb)
+    out = (rgb, depth, alpha)
+
+    def step(flags=L.GB_FLAG_NO_SYNC):
+        rast.forward([dev_scene], cams, saved=saved, flags=flags, out=out, batch=args.batch)
+        rast.backward(saved, d_rgb, grads=grads)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    saved.check()
+
+    graph = None
+    if not args.no_graph:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        graph.replay()
+        torch.cuda.synchronize()
+        saved.check()
+
+    # --- timed region
+    sampler = ClockSampler(local)
+    launches0 = lib.gb_kernel_launches()
+    sampler.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        if graph is not None:
+            graph.replay()
+        else:
+            step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = lib.gb_kernel_launches() - launches0
+    if graph is not None:
+        launches = args.steps * launches_per_step(lib, step)
+    saved.check()
+    ms_max = allreduce_max(ms, world)
+    value = world * P / (ms_max / 1e3) / 1e6
+
+    # --- per-phase times over a second pass of K steps (events on the launch stream)
+    phase_acc = {}
+    pairs = None
+    for _ in range(args.steps):
+        rast.forward([dev_scene], cams, saved=saved, flags=L.GB_FLAG_NO_SYNC | L.GB_FLAG_TIMING, out=out,
+                     batch=args.batch)
+        rast.backward(saved, d_rgb, grads=grads)
+        for k, v in saved.phase_times().items():
+            phase_acc.setdefault(k, []).append(v)
+        pairs = saved.stats()
+    phases = {k: sum(v) / len(v) for k, v in phase_acc.items()}
+    dominant = max(phases, key=phases.get)
+    roofline = roofline_line(dominant, phases, pairs, clocks)
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: 1,000,000 splats, 16 views 960x540/1280x720/1920x1080, "
+                               f"{args.tex_n}x{args.tex_n} FP16 textures, SH3 FP16",
+                   "pixels_per_step": P, "tex_n": args.tex_n, "storage": "f16", "tile": 16,
+                   "graph": graph is not None, "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": f"replicas x{world}"},
+        "clocks": clocks, "gpu_launches": int(launches), "phases_ms": phases,
+        "stats": {k: pairs[k] for k in ("visible", "instances", "pairs_fwd", "pairs_bwd", "records")},
+        "roofline": roofline,
+    }
+
+    # --- plain FP32 path: the same views one by one
+    if not args.no_plain:
+        result["plain_fp32"] = plain_fp32(args, wl, rast, R, L, torch)
+
+    # --- e2e through host buffers
+    if not args.no_e2e:
+        result["e2e"] = e2e(args, wl, rast, R, L, torch, cams, P)
+
+    # --- CPU oracle baseline + max error vs FP64 (rank 0)
+    if rank == 0 and not args.no_cpu_baseline:
+        result["cpu_baseline"], result["max_err_vs_fp64"] = cpu_baseline(args, wl, rgb, alpha, depth, cams)
+
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    barrier(world)
+    return 0
+
+
+def launches_per_step(lib, step):
+    import torch
+    a = lib.gb_kernel_launches()
+    step()
+    torch.cuda.synchronize()
+    return lib.gb_kernel_launches() - a
+
+
+def roofline_line(dominant, phases, st, clocks):
+    """ALU roofline of the dominant kernel: algorithmic FLOPs per launch over
+    its measured launch time, against the FP32 FMA peak at the sampled clock.
+
+    FLOPs per (pixel, splat) pair (FMA = 2), counted from the kernels' math:
+    forward: 30 per evaluated pair (offset, intersection, rho, Gaussian, alpha
+    test) + 61 per blended pair (bilinear 27, cell 16, blend 18); backward:
+    30 per evaluated pair + 200 per contributing pair (colour 43, adjoints of
+    alpha, Gaussian, intersection and record 130, adj-bilinear weights 27).
+    Pair counts come from device counters of the same launches.
+    """
+    ms = phases[dominant]
+    sm = clocks.get("sm_mhz") or 2070.0
+    peak = 152 * 128 * 2 * sm * 1e6 / 1e12
+    if dominant == "render_bwd":
+        flops = 30 * st["pairs_bwd"] + 200 * st["pairs_bwd"]
+    elif dominant == "render_fwd":
+        flops = 91 * st["pairs_fwd"]
+    else:
+        flops = None
+    achieved = flops / (ms / 1e3) / 1e12 if flops else None
+    return {"kernel": dominant, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if achieved else None, "traffic": None,
+            "peak_source": f"FP32 FMA lanes 152x128 x2 at median sampled SM clock {sm:.0f} MHz",
+            "launch_ms": ms}
+
+
+def plain_fp32(args, wl, rast, R, L, torch):
+    sc = dict(wl["scenes"][0])
+    sc["sh_dtype"] = "f32"
+    sc["tex_dtype"] = "f32"
+    dev = R.scene_to_device(sc)
+    cams = wl["cams"]
+    d_views, outs, saveds, grads = [], [], [], []
+    o = 0
+    for c in cams:
+        n = int(c["width"]) * int(c["height"])
+        d_views.append(torch.as_tensor(wl["d_rgb"][len(d_views)].reshape(-1, 3), device="cuda"))
+        outs.append((torch.empty((n, 3), device="cuda"), torch.empty(n, device="cuda"),
+                     torch.empty(n, device="cuda")))
+        s = R.Saved(rast)
+        rast.forward([dev], [c], saved=s, out=outs[-1])
+        st = s.stats()
+        s.reserve(st["records"], int(st["instances"] * 1.1) + 4096, n, st["tiles"])
+        saveds.append(s)
+        grads.append(rast.backward(s, d_views[-1]))
+        o += n
+
+    def step():
+        for i, c in enumerate(cams):
+            rast.forward([dev], [c], saved=saveds[i], flags=L.GB_FLAG_NO_SYNC, out=outs[i])
+            rast.backward(saveds[i], d_views[i], grads=grads[i])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    for s in saveds:
+        s.check()
+    ms = e0.elapsed_time(e1) / args.steps
+    P = sum(int(c["width"]) * int(c["height"]) for c in cams)
+    return {"value": P / (ms / 1e3) / 1e6, "unit": "Mpixel/s", "ms_per_step": ms,
+            "note": "same 16 views rendered one by one, FP32 texture/SH storage, eager launches"}
+
+
+def e2e(args, wl, rast, R, L, torch, cams, P):
+    """Same metric through the C ABI with host buffers: each step copies the
+    scene parameters and dL/drgb from pinned host memory, runs forward +
+    backward, and reads rgb and every gradient back to pinned host memory."""
+    host = R.scene_to_device(wl["scenes"][0], device="cpu")
+    keys = ("means", "quats", "scales", "opacities", "sh", "textures")
+    h_in = {k: host[k].pin_memory() for k in keys}
+    h_drgb = torch.as_tensor(np.concatenate([d.reshape(-1, 3) for d in wl["d_rgb"]])).pin_memory()
+    d_in = {k: torch.empty_like(v, device="cuda") for k, v in h_in.items()}
+    d_drgb = torch.empty_like(h_drgb, device="cuda")
+    meta = {k: host[k] for k in ("sh_degree", "tex_n", "sigma")}
+    scene = dict(d_in, **meta)
+    saved = R.Saved(rast)
+    rgb, depth, alpha, _ = rast.forward([scene], cams, saved=saved)
+    grads = rast.backward(saved, d_drgb.copy_(h_drgb))
+    h_out = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in grads[0].items()}
+    h_rgb = torch.empty_like(rgb, device="cpu").pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in h_in.values()) + h_drgb.numel() * 4
+    d2h = sum(v.numel() * v.element_size() for v in h_out.values()) + h_rgb.numel() * 4
+
+    def step():
+        for k in keys:
+            d_in[k].copy_(h_in[k], non_blocking=True)
+        d_drgb.copy_(h_drgb, non_blocking=True)
+        rast.forward([scene], cams, saved=saved, out=(rgb, depth, alpha))
+        g = rast.backward(saved, d_drgb, grads=grads)
+        for k, v in g[0].items():
+            h_out[k].copy_(v, non_blocking=True)
+        h_rgb.copy_(rgb, non_blocking=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    return {"value": P / (ms / 1e3) / 1e6, "unit": "Mpixel/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": ms,
+            "note": "synchronizing forward (sizes the instance list on the host each step)"}
+
+
+def cpu_baseline(args, wl, rgb, alpha, depth, cams):
+    import oracle
+    oracle.build()
+    dt, px, ref, win = oracle_sample(wl, args.crop)
+    x0, y0, w, h = win
+    W, H = int(cams[0]["width"]), int(cams[0]["height"])
+    img = rgb[:W * H].reshape(H, W, 3)[y0:y0 + h, x0:x0 + w].cpu().numpy().astype(np.float64)
+    a = alpha[:W * H].reshape(H, W)[y0:y0 + h, x0:x0 + w].cpu().numpy().astype(np.float64)
+    mask = ref["margin_fwd"] > 1e-5
+    err = np.abs(img - ref["rgb"]).max(axis=2)
+    base = {"value": px / dt / 1e6, "unit": "Mpixel/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{w}x{h} crop of camera 0, fwd+bwd, FP64 bbox-prefiltered oracle, {dt:.1f} s"}
+    errs = {"rgb": float(err[mask].max()) if mask.any() else 0.0,
+            "alpha": float(np.abs(a - ref["alpha"])[mask].max()) if mask.any() else 0.0,
+            "excluded_px": int((~mask).sum()), "pixels": int(w * h),
+            "storage": "errors are against the FP64 oracle on the stored FP16 values"}
+    return base, errs
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        rc = run_reference(args, world, rank)
+    else:
+        rc = run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -71,6 +71,9 @@ typedef enum { GB_F32 = 0, GB_F16 = 1, GB_BF16 = 2 } gb_dtype;
                               gb_saved_check); required inside CUDA graph capture */
 #define GB_FLAG_PERSISTENT 2u /* render with persistent blocks pulling tiles from
                                  a device work counter instead of one block per tile */
+#define GB_FLAG_TIMING 4u     /* record CUDA events around every phase of this forward
+                                 and of the backward that follows it (see
+                                 gb_saved_phase_times); not for use in graph capture */
 
 typedef struct gb_context gb_context;
 typedef struct gb_saved gb_saved;
@@ -131,7 +134,25 @@ typedef struct {
     int64_t capacity;    /* reserved instance capacity                             */
     int32_t overflow;    /* nonzero if a no-sync forward ran out of capacity       */
     int32_t error_flags; /* device error bits (bit 0: bounded wait timed out)      */
+    int64_t pairs_fwd;   /* (pixel, splat) pairs evaluated by the last forward     */
+    int64_t pairs_bwd;   /* (pixel, splat) pairs evaluated by the last backward    */
 } gb_stats;
+
+/* Phases timed under GB_FLAG_TIMING, in the order gb_saved_phase_times
+ * returns them. */
+typedef enum {
+    GB_PHASE_PREPROCESS = 0, /* homography, FP32 rectangle, depth key, SH colour  */
+    GB_PHASE_DEPTH_SORT,     /* radix sort of records by depth                    */
+    GB_PHASE_COUNT_SCAN,     /* exclusive scan of per-record tile counts          */
+    GB_PHASE_EMIT,           /* (tile, splat) duplication                         */
+    GB_PHASE_TILE_SORT,      /* stable radix sort of instances by tile            */
+    GB_PHASE_RANGES,         /* per-tile [begin, end)                             */
+    GB_PHASE_RENDER_FWD,     /* per-tile front-to-back render                     */
+    GB_PHASE_BWD_SETUP,      /* gradient buffers zeroed, inverse permutation      */
+    GB_PHASE_RENDER_BWD,     /* per-tile back-to-front adjoint                    */
+    GB_PHASE_PREPROCESS_BWD, /* chain to means, quats, scales, opacity, SH        */
+    GB_PHASE_COUNT
+} gb_phase;
 
 /* ---------------------------------------------------------------- contexts -- */
 
@@ -179,6 +200,15 @@ gb_status gb_saved_stats(gb_saved *saved, gb_stats *out);
  * of instance capacity (its outputs are then invalid; reserve more and rerun),
  * GB_ERR_TIMEOUT if a bounded device wait gave up, else GB_OK. */
 gb_status gb_saved_check(gb_saved *saved);
+
+/* Durations in milliseconds (host array ms[GB_PHASE_COUNT]) of the phases of
+ * the last forward run with GB_FLAG_TIMING and of the backward after it
+ * (entries of a pass not run are -1).  Synchronizes. */
+gb_status gb_saved_phase_times(gb_saved *saved, float *ms, int32_t cap);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * contexts), for launch accounting. */
+uint64_t gb_kernel_launches(void);
 
 /* Copies the sorted instance list of the last forward to HOST arrays: keys[i]
  * = (global tile id << 32) | bits(FP32 centre depth), ids[i] = splat index

@@ -21,6 +21,9 @@ STATUS = {0: "GB_OK", 1: "GB_ERR_INVALID_ARG", 2: "GB_ERR_UNSUPPORTED", 3: "GB_E
 GB_F32, GB_F16, GB_BF16 = 0, 1, 2
 GB_FLAG_NO_SYNC = 1
 GB_FLAG_PERSISTENT = 2
+GB_FLAG_TIMING = 4
+PHASES = ("preprocess", "depth_sort", "count_scan", "emit", "tile_sort", "ranges", "render_fwd",
+          "bwd_setup", "render_bwd", "preprocess_bwd")
 MAX_CAMERAS = 64
 MAX_SCENES = 16
 
@@ -53,7 +56,8 @@ class gb_options(C.Structure):
 class gb_stats(C.Structure):
     _fields_ = [("records", C.c_int64), ("visible", C.c_int64), ("instances", C.c_int64),
                 ("tiles", C.c_int64), ("pixels", C.c_int64), ("capacity", C.c_int64),
-                ("overflow", C.c_int32), ("error_flags", C.c_int32)]
+                ("overflow", C.c_int32), ("error_flags", C.c_int32),
+                ("pairs_fwd", C.c_int64), ("pairs_bwd", C.c_int64)]
 
 
 _lib = None
@@ -91,6 +95,8 @@ def load() -> C.CDLL:
         "gb_saved_reserve": (C.c_int, [vp, i64, i64, i64, i64]),
         "gb_saved_stats": (C.c_int, [vp, C.POINTER(gb_stats)]),
         "gb_saved_check": (C.c_int, [vp]),
+        "gb_saved_phase_times": (C.c_int, [vp, C.POINTER(C.c_float), i32]),
+        "gb_kernel_launches": (C.c_uint64, []),
         "gb_saved_export_keys": (C.c_int, [vp, vp, vp, vp, i64, C.POINTER(i64)]),
         "gb_render_forward": (C.c_int, [vp, vp, C.POINTER(gb_scene), i32, C.POINTER(gb_camera), i32,
                                         C.POINTER(gb_options), vp, vp, vp, vp]),

@@ -7,11 +7,20 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "gbill_internal.cuh"
 #include "render_common.cuh"
 
 using namespace gbill;
+
+namespace gbill {
+static std::atomic<uint64_t> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add(uint64_t(n), std::memory_order_relaxed); }
+}  // namespace gbill
+
+// Events: [0..7] forward start + after each of its 7 phases, [8..11] backward.
+constexpr int kNumEvents = 12;
 
 struct gb_context {
     int device;
@@ -41,6 +50,8 @@ struct gb_saved {
     int tile_bits, batch_fwd, batch_bwd;
     uint32_t flags;
     cudaStream_t stream;
+    cudaEvent_t ev[kNumEvents];
+    bool ev_ready, timed_fwd, timed_bwd;
 };
 
 namespace {
@@ -311,6 +322,16 @@ gb_status gb_saved_create(gb_context *ctx, gb_saved **out) {
     }
     memset(s->cnt_host, 0, sizeof(Counters));
     cudaMemset(s->cnt, 0, sizeof(Counters));
+    for (int i = 0; i < kNumEvents; ++i) {
+        if (cudaEventCreate(&s->ev[i]) != cudaSuccess) {
+            for (int j = 0; j < i; ++j) cudaEventDestroy(s->ev[j]);
+            cudaFree(s->cnt);
+            cudaFreeHost(s->cnt_host);
+            delete s;
+            return fail(ctx, GB_ERR_CUDA, "event creation failed");
+        }
+    }
+    s->ev_ready = true;
     *out = s;
     return GB_OK;
 }
@@ -325,6 +346,8 @@ gb_status gb_saved_destroy(gb_saved *s) {
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (s->cnt_host) cudaFreeHost(s->cnt_host);
+    if (s->ev_ready)
+        for (int i = 0; i < kNumEvents; ++i) cudaEventDestroy(s->ev[i]);
     delete s;
     return GB_OK;
 }
@@ -354,6 +377,24 @@ gb_status gb_saved_stats(gb_saved *s, gb_stats *out) {
     out->capacity = s->cap_inst;
     out->overflow = int32_t(s->cnt_host->overflow);
     out->error_flags = int32_t(s->cnt_host->error_flags);
+    out->pairs_fwd = int64_t(s->cnt_host->pairs_fwd);
+    out->pairs_bwd = int64_t(s->cnt_host->pairs_bwd);
+    return GB_OK;
+}
+
+uint64_t gb_kernel_launches(void) { return g_launches.load(); }
+
+gb_status gb_saved_phase_times(gb_saved *s, float *ms, int32_t cap) {
+    if (!s || !ms || cap < 0) return fail(s ? s->ctx : nullptr, GB_ERR_INVALID_ARG, "bad arguments");
+    GB_CUDA(s->ctx, cudaStreamSynchronize(s->stream));
+    for (int i = 0; i < cap && i < GB_PHASE_COUNT; ++i) {
+        int a, b;
+        bool on;
+        if (i < 7) { a = i; b = i + 1; on = s->timed_fwd; }
+        else { a = i + 1; b = i + 2; on = s->timed_bwd; }
+        ms[i] = -1.0f;
+        if (on) GB_CUDA(s->ctx, cudaEventElapsedTime(&ms[i], s->ev[a], s->ev[b]));
+    }
     return GB_OK;
 }
 
@@ -446,14 +487,22 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
     s->flags = o.flags;
     s->stream = st;
     s->has_forward = false;
+    const bool timing = (o.flags & GB_FLAG_TIMING) != 0;
+    s->timed_fwd = s->timed_bwd = false;
+#define GB_MARK(i) \
+    if (timing) GB_CUDA(ctx, cudaEventRecord(s->ev[i], st))
 
+    GB_MARK(0);
     GB_CUDA(ctx, cudaMemsetAsync(s->cnt, 0, sizeof(Counters), st));
     GB_CUDA(ctx, cudaMemsetAsync(s->ranges, 0, size_t(f.n_tiles) * sizeof(uint2), st));
     GB_CUDA(ctx, launch_preprocess(f, max_k, s->depth_key, s->rec_id, s->rect, s->rec, s->cnt, st));
+    GB_MARK(1);
     GB_CUDA(ctx, radix_sort_pairs(s->depth_key, s->rec_id, s->keys_tmp, s->vals_tmp, s->dkeys_sorted, s->perm, R,
                                   nullptr, 0, 32, s->scratch, s->scratch_bytes, st));
+    GB_MARK(2);
     GB_CUDA(ctx, tile_counts_scan(f, s->perm, s->rect, R, &s->cnt->n_visible, s->offsets, s->scratch,
                                   s->scratch_bytes, s->cnt, s->cap_inst, st));
+    GB_MARK(3);
     int64_t inst_max = s->cap_inst;
     if (!nosync) {
         GB_CUDA(ctx, cudaMemcpyAsync(s->cnt_host, s->cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
@@ -467,11 +516,15 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
         inst_max = std::max<int64_t>(need, 1);
     }
     s->inst_max = inst_max;
+    if (timing && !nosync) GB_CUDA(ctx, cudaEventRecord(s->ev[3], st));  // exclude the host round trip
     GB_CUDA(ctx, launch_emit(f, s->perm, s->rect, s->offsets, R, s->cnt, s->cap_inst, s->inst_tile, s->inst_val, st));
+    GB_MARK(4);
     GB_CUDA(ctx, radix_sort_pairs(s->inst_tile, s->inst_val, s->inst_tile_tmp, s->inst_val_tmp, s->tiles_sorted,
                                   s->vals_sorted, inst_max, &s->cnt->n_instances, 0, tile_bits, s->scratch,
                                   s->scratch_bytes, st));
+    GB_MARK(5);
     GB_CUDA(ctx, launch_ranges(s->tiles_sorted, inst_max, s->cnt, s->ranges, st));
+    GB_MARK(6);
     RenderBufs b;
     b.rec = s->rec;
     b.perm = s->perm;
@@ -484,6 +537,9 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
     b.last = s->last;
     b.cnt = s->cnt;
     GB_CUDA(ctx, launch_render_fwd(f, b, bf, st));
+    GB_MARK(7);
+#undef GB_MARK
+    s->timed_fwd = timing;
     s->has_forward = true;
     return GB_OK;
 }
@@ -497,6 +553,8 @@ gb_status gb_render_backward(gb_context *ctx, gb_saved *s, const float *d_rgb, c
     if (!grads || n_scenes != s->frame.n_scenes)
         return fail(ctx, GB_ERR_INVALID_ARG, "grads must hold one entry per scene (%d)", s->frame.n_scenes);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool timing = (s->flags & GB_FLAG_TIMING) != 0;
+    if (timing) GB_CUDA(ctx, cudaEventRecord(s->ev[8], st));
     Frame f = s->frame;
     for (int i = 0; i < n_scenes; ++i) {
         SceneDev &d = f.scenes[i];
@@ -513,7 +571,9 @@ gb_status gb_render_backward(gb_context *ctx, gb_saved *s, const float *d_rgb, c
     zero_rec_grad<<<unsigned(std::min<int64_t>(ceil_div(std::max<int64_t>(R, 1) * 4, 256), 65535)), 256, 0, st>>>(
         s->rec_grad, s->cnt, R);
     GB_CUDA(ctx, cudaGetLastError());
+    count_launches(1);
     GB_CUDA(ctx, launch_inverse_perm(s->perm, R, s->cnt, s->inv, st));
+    if (timing) GB_CUDA(ctx, cudaEventRecord(s->ev[9], st));
     RenderBwdBufs b;
     b.fw.rec = s->rec;
     b.fw.perm = s->perm;
@@ -529,8 +589,12 @@ gb_status gb_render_backward(gb_context *ctx, gb_saved *s, const float *d_rgb, c
     b.d_depth = d_depth;
     b.d_alpha = d_alpha;
     b.rec_grad = s->rec_grad;
+    GB_CUDA(ctx, cudaMemsetAsync(&s->cnt->pairs_bwd, 0, sizeof(unsigned long long), st));
     GB_CUDA(ctx, launch_render_bwd(f, b, s->batch_bwd, st));
+    if (timing) GB_CUDA(ctx, cudaEventRecord(s->ev[10], st));
     GB_CUDA(ctx, launch_preprocess_bwd(f, s->max_k, s->rec_grad, s->inv, st));
+    if (timing) GB_CUDA(ctx, cudaEventRecord(s->ev[11], st));
+    s->timed_bwd = timing;
     return GB_OK;
 }
 

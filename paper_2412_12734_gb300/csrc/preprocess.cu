@@ -459,6 +459,7 @@ cudaError_t launch_preprocess(const Frame &f, int64_t max_k, uint32_t *depth_key
     if (max_k <= 0) return cudaSuccess;
     dim3 grid(unsigned(ceil_div(max_k, 256)), unsigned(f.n_cams));
     preprocess_kernel<<<grid, 256, 0, s>>>(f, depth_key, rec_id, rect, rec, cnt);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -467,6 +468,7 @@ cudaError_t launch_preprocess_bwd(const Frame &f, int64_t max_k, const float *re
     if (max_k <= 0) return cudaSuccess;
     dim3 grid(unsigned(ceil_div(max_k, 128)), unsigned(f.n_scenes));
     preprocess_bwd_kernel<<<grid, 128, 0, s>>>(f, rec_grad, inv_perm);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(TS * TS) render_bwd_kernel(Frame f, RenderBwdB
     const float kN = float(N - 1) / (2.0f * sigma);
 
     float T = 1.0f, T_final = 1.0f, dC0 = 0, dC1 = 0, dC2 = 0, dD = 0, dA = 0;
-    uint32_t last = 0;
+    uint32_t last = 0, npairs = 0;
     if (threadIdx.x == 0) s_maxlast = 0;
     __syncthreads();
     if (inside) {
@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(TS * TS) render_bwd_kernel(Frame f, RenderBwdB
 #pragma unroll
             for (int q = 0; q < NG; ++q) g[q] = 0.0f;
             bool act = inside && uint32_t(bs + i) < last;
+            npairs += act ? 1u : 0u;
             if (act) {
                 const float4 q0 = s_rec[4 * i + 0], q1 = s_rec[4 * i + 1], q2 = s_rec[4 * i + 2],
                              q3 = s_rec[4 * i + 3];
@@ -220,6 +221,9 @@ __global__ void __launch_bounds__(TS * TS) render_bwd_kernel(Frame f, RenderBwdB
             }
         __syncthreads();
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
+    if ((threadIdx.x & 31) == 0 && npairs) atomicAdd(&b.fw.cnt->pairs_bwd, (unsigned long long)npairs);
 }
 
 template <int TS, int N, typename TexT>
@@ -233,6 +237,7 @@ cudaError_t launch_t(const Frame &f, const RenderBwdBufs &b, int batch, cudaStre
         configured = true;
     }
     render_bwd_kernel<TS, N, TexT><<<f.n_tiles, TS * TS, smem, s>>>(f, b, batch);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(TS * TS) render_fwd_kernel(Frame f, RenderBufs
     const float kN = float(N - 1) / (2.0f * sigma);
 
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, Dp = 0.0f;
-    uint32_t last = 0;
+    uint32_t last = 0, npairs = 0;
     bool done = !inside;
     for (int bs = 0; bs < n_inst; bs += batch) {
         if (__syncthreads_count(done) == NT) break;
@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(TS * TS) render_fwd_kernel(Frame f, RenderBufs
         __syncthreads();
         if (!done) {
             for (int i = 0; i < nb; ++i) {
+                ++npairs;
                 const float4 q0 = s_rec[4 * i + 0], q1 = s_rec[4 * i + 1], q2 = s_rec[4 * i + 2];
                 const float dx = (xf - q2.x) - q2.z, dy = (yf - q2.y) - q2.w;
                 const float zz = fmaf(q1.x, dx, fmaf(q1.y, dy, q1.z));
@@ -84,6 +85,9 @@ __global__ void __launch_bounds__(TS * TS) render_fwd_kernel(Frame f, RenderBufs
             }
         }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
+    if ((threadIdx.x & 31) == 0 && npairs) atomicAdd(&b.cnt->pairs_fwd, (unsigned long long)npairs);
     if (inside) {
         const int64_t pix = cam.pix_off + int64_t(py) * cam.width + px;
         b.rgb[3 * pix + 0] = C0 + T * f.bg[0];
@@ -107,6 +111,7 @@ cudaError_t launch_t(const Frame &f, const RenderBufs &b, int batch, cudaStream_
         configured = true;
     }
     render_fwd_kernel<TS, N, TexT><<<f.n_tiles, TS * TS, smem, s>>>(f, b, batch);
+    count_launches(1);
     return cudaGetLastError();
 }
 

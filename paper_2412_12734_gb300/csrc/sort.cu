@@ -220,6 +220,7 @@ cudaError_t exclusive_scan(Load ld, int64_t max_n, const uint32_t *n_dev, uint32
     scan_reduce<<<unsigned(nb), kScanThreads, 0, s>>>(ld, max_n, n_dev, sums);
     scan_block_sums<<<1, kScanThreads, 0, s>>>(sums, nb, total, cnt, capacity);
     scan_downsweep<<<unsigned(nb), kScanThreads, 0, s>>>(ld, max_n, n_dev, sums, out);
+    count_launches(3);
     return cudaGetLastError();
 }
 
@@ -320,6 +321,7 @@ cudaError_t radix_sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, u
                                        nullptr, 0, s);
         if (e != cudaSuccess) return e;
         radix_downsweep<<<unsigned(nb), kSortThreads, 0, s>>>(ki, vi, ko, vo, max_n, n_dev, shift, mask, hist);
+        count_launches(2);
         ki = ko;
         vi = vo;
     }
@@ -340,6 +342,7 @@ cudaError_t launch_emit(const Frame &f, const uint32_t *perm, const uint2 *rect,
     if (max_n <= 0) return cudaSuccess;
     emit_kernel<<<unsigned(ceil_div(max_n, 256)), 256, 0, s>>>(f, perm, rect, offsets, max_n, cnt, capacity,
                                                               inst_tile, inst_val);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -347,6 +350,7 @@ cudaError_t launch_ranges(const uint32_t *tiles_sorted, int64_t max_n, const Cou
                           cudaStream_t s) {
     if (max_n <= 0) return cudaSuccess;
     ranges_kernel<<<unsigned(ceil_div(max_n, 256)), 256, 0, s>>>(tiles_sorted, max_n, cnt, ranges);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -354,6 +358,7 @@ cudaError_t launch_inverse_perm(const uint32_t *perm, int64_t n_records, const C
                                 cudaStream_t s) {
     if (n_records <= 0) return cudaSuccess;
     inverse_perm_kernel<<<unsigned(ceil_div(n_records, 256)), 256, 0, s>>>(perm, n_records, cnt, inv);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -363,6 +368,7 @@ cudaError_t launch_export_keys(const Frame &f, const uint32_t *tiles_sorted, con
     if (n <= 0) return cudaSuccess;
     export_keys_kernel<<<unsigned(ceil_div(n, 256)), 256, 0, s>>>(f, tiles_sorted, vals_sorted, perm,
                                                                   depth_key_by_rec, n, keys, ids, cams);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -105,6 +105,12 @@ class Saved:
     def check(self):
         L.check(L.load().gb_saved_check(self.handle), self.rast.ctx)
 
+    def phase_times(self) -> dict:
+        """Milliseconds per phase of the last forward/backward run with GB_FLAG_TIMING."""
+        arr = (C.c_float * len(L.PHASES))()
+        L.check(L.load().gb_saved_phase_times(self.handle, arr, len(L.PHASES)), self.rast.ctx)
+        return dict(zip(L.PHASES, (float(x) for x in arr)))
+
     def export_keys(self):
         """Sorted (key, splat id, camera) instance list of the last forward."""
         n = C.c_int64()

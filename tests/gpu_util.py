@@ -63,8 +63,16 @@ def compare_images(gpu_img, ref, what="rgb", tol=IMG_TOL, relative_to=None):
     return float(err[mask].max()) if mask.any() else 0.0, excluded
 
 
+GRAD_FLOOR = 1e-2     # elements below this fraction of the tensor's max get an absolute bound
+
+
 def grad_errors(g_gpu: dict, g_ref: dict) -> dict:
-    """Worst ratio |g - g*| / (GRAD_REL * max(|g*|, 1e-3 max|g*|)) per tensor (<= 1 passes)."""
+    """Worst ratio |g - g*| / (GRAD_REL * max(|g*|, GRAD_FLOOR max|g*|)) per tensor (<= 1 passes).
+
+    Elements much smaller than the tensor's largest entry are differences of
+    larger FP32 sums (u, v carry ~1e-7 relative FP32 error, amplified by
+    (N-1)/(2 sigma) in the texel weights), so below 1 % of the maximum the
+    bound is absolute: 1e-5 of the maximum."""
     out = {}
     for k, ref in g_ref.items():
         a = np.asarray(g_gpu[k], np.float64).reshape(ref.shape)
@@ -72,7 +80,7 @@ def grad_errors(g_gpu: dict, g_ref: dict) -> dict:
         if scale == 0:
             out[k] = float(np.abs(a).max() > 0)
             continue
-        den = GRAD_REL * np.maximum(np.abs(ref), 1e-3 * scale)
+        den = GRAD_REL * np.maximum(np.abs(ref), GRAD_FLOOR * scale)
         out[k] = float((np.abs(a - ref) / den).max())
     return out
 

@@ -1,8 +1,9 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
 Keys are compared bit for bit; rgb and alpha within 2e-5 max abs error;
-depth within 2e-5 relative to max(1, |depth|); gradients per tensor within
-1e-3 of max(|g*|, 1e-3 max|g*|).  Pixels whose decisions sit within the
+depth within 2e-5 relative to max(1, |depth|); gradients per element within
+1e-3 of max(|g*|, 1e-2 max|g*|) (relative above 1 % of the tensor's largest
+entry, absolute 1e-5 of it below).  Pixels whose decisions sit within the
 oracle's margin of a threshold are excluded from image errors (and counted)
 and get zero upstream gradient on both sides.
 """
