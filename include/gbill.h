@@ -210,6 +210,20 @@ gb_status gb_saved_phase_times(gb_saved *saved, float *ms, int32_t cap);
  * contexts), for launch accounting. */
 uint64_t gb_kernel_launches(void);
 
+/* Copies the projected records of the last forward to HOST memory for
+ * inspection: rec[r][16] for record r = (camera c, splat k), r = sum of the
+ * splat counts of the scenes of cameras 0..c-1, plus k.  Layout per record:
+ * t11, -t01, -t10, t00, m20, m21, m22, z, c_hi.x, c_hi.y, c_lo.x, c_lo.y, o,
+ * r, g, b, where T' = [[t00 t01 0][t10 t11 0][t20 t21 z]] is the splat-to-
+ * screen homography with the projected centre c moved to the origin and
+ * (m20, m21, m22) = third row of adj(T') / z; a pixel at offset (dx, dy) from
+ * c hits the splat at u = (t11 dx - t01 dy) / (m20 dx + m21 dy + m22), v =
+ * (t00 dy - t10 dx) / (same).  visible[r] = 1 if the record survived culling
+ * (other rows are undefined).  `cap` = records the host arrays hold.
+ * Synchronizes. */
+gb_status gb_saved_export_records(gb_saved *saved, float *rec, uint8_t *visible, int64_t cap,
+                                  int64_t *count);
+
 /* Copies the sorted instance list of the last forward to HOST arrays: keys[i]
  * = (global tile id << 32) | bits(FP32 centre depth), ids[i] = splat index
  * within its scene, cams[i] = camera index.  Global tile ids number the tiles

@@ -4,6 +4,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -436,6 +437,24 @@ gb_status gb_saved_export_keys(gb_saved *s, uint64_t *keys, int64_t *ids, int32_
     cudaFree(dk);
     cudaFree(di);
     cudaFree(dc);
+    return GB_OK;
+}
+
+gb_status gb_saved_export_records(gb_saved *s, float *rec, uint8_t *visible, int64_t cap, int64_t *count) {
+    if (!s || !count || cap < 0) return fail(s ? s->ctx : nullptr, GB_ERR_INVALID_ARG, "bad arguments");
+    if (!s->has_forward) return fail(s->ctx, GB_ERR_INVALID_ARG, "no forward recorded on this saved state");
+    *count = s->n_records;
+    const int64_t n = std::min<int64_t>(cap, s->n_records);
+    if (n == 0) return GB_OK;
+    if (!rec || !visible) return fail(s->ctx, GB_ERR_INVALID_ARG, "null output array");
+    GB_CUDA(s->ctx, cudaStreamSynchronize(s->stream));
+    GB_CUDA(s->ctx, cudaMemcpy(rec, s->rec, size_t(n) * sizeof(Record), cudaMemcpyDeviceToHost));
+    uint32_t *keys = static_cast<uint32_t *>(malloc(size_t(n) * 4));
+    if (!keys) return fail(s->ctx, GB_ERR_INVALID_ARG, "host allocation failed");
+    cudaError_t e = cudaMemcpy(keys, s->depth_key, size_t(n) * 4, cudaMemcpyDeviceToHost);
+    for (int64_t i = 0; i < n && e == cudaSuccess; ++i) visible[i] = keys[i] != 0xFFFFFFFFu;
+    free(keys);
+    GB_CUDA(s->ctx, e);
     return GB_OK;
 }
 

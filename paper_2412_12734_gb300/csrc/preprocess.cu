@@ -232,30 +232,33 @@ __device__ __forceinline__ Frame3 tangent_frame(const float q[4]) {
     return f;
 }
 
-// FP64 homography block for near edge-on splats.
+// Homography block in FP64 for splats seen at a grazing angle, where the
+// determinant J = fx fy (n . P) / z of the block cancels: t = (t00, t01, t10,
+// t11), m = (m20, m21, m22) = (fy n_x, fx n_y, fx fy n.P / z) / z.
 __device__ void homography_fp64(const float p[3], const float q[4], float su, float sv,
-                                const CamDev &c, float t[6], float &J, float &m20z, float &m21z) {
+                                const CamDev &c, float t[4], float m[3]) {
     const double qn = sqrt((double)q[0] * q[0] + (double)q[1] * q[1] + (double)q[2] * q[2] +
                            (double)q[3] * q[3]);
     const double w = q[0] / qn, x = q[1] / qn, y = q[2] / qn, z = q[3] / qn;
     const double tu[3] = {1 - 2 * (y * y + z * z), 2 * (x * y + w * z), 2 * (x * z - w * y)};
     const double tv[3] = {2 * (x * y - w * z), 1 - 2 * (x * x + z * z), 2 * (y * z + w * x)};
-    double A[3], B[3], P[3];
+    const double tw[3] = {2 * (x * z + w * y), 2 * (y * z - w * x), 1 - 2 * (x * x + y * y)};
+    double A[3], B[3], P[3], n[3];
     for (int i = 0; i < 3; ++i) {
         const float *r = c.R + 3 * i;
         A[i] = su * ((double)r[0] * tu[0] + (double)r[1] * tu[1] + (double)r[2] * tu[2]);
         B[i] = sv * ((double)r[0] * tv[0] + (double)r[1] * tv[1] + (double)r[2] * tv[2]);
+        n[i] = (double)su * sv * ((double)r[0] * tw[0] + (double)r[1] * tw[1] + (double)r[2] * tw[2]);
         P[i] = (double)r[0] * p[0] + (double)r[1] * p[1] + (double)r[2] * p[2] + (double)c.t[i];
     }
-    const double xz = P[0] / P[2], yz = P[1] / P[2];
-    const double t00 = c.fx * (A[0] - A[2] * xz), t01 = c.fx * (B[0] - B[2] * xz);
-    const double t10 = c.fy * (A[1] - A[2] * yz), t11 = c.fy * (B[1] - B[2] * yz);
-    const double t20 = A[2], t21 = B[2];
-    t[0] = (float)t00; t[1] = (float)t01; t[2] = (float)t10; t[3] = (float)t11;
-    t[4] = (float)t20; t[5] = (float)t21;
-    J = (float)(t00 * t11 - t01 * t10);
-    m20z = (float)(t10 * t21 - t11 * t20);
-    m21z = (float)(t01 * t20 - t00 * t21);
+    const double iz = 1.0 / P[2], xz = P[0] * iz, yz = P[1] * iz;
+    t[0] = (float)(c.fx * (A[0] - A[2] * xz));
+    t[1] = (float)(c.fx * (B[0] - B[2] * xz));
+    t[2] = (float)(c.fy * (A[1] - A[2] * yz));
+    t[3] = (float)(c.fy * (B[1] - B[2] * yz));
+    m[0] = (float)(c.fy * n[0] * iz);
+    m[1] = (float)(c.fx * n[1] * iz);
+    m[2] = (float)((double)c.fx * c.fy * (n[0] * P[0] + n[1] * P[1] + n[2] * P[2]) * iz * iz);
 }
 
 // --------------------------------------------------------- forward kernel --
@@ -288,11 +291,16 @@ __global__ void __launch_bounds__(256) preprocess_kernel(Frame f, uint32_t *dept
                                      uint32_t(pr[2] / T) | (uint32_t(pr[3] / T) << 16));
             // ---- render record ----
             const Frame3 fr = tangent_frame(q);
-            float A[3], B[3];
+            // camera-space tangent axes A = s_u R t_u, B = s_v R t_v and normal
+            // n = A x B = s_u s_v R t_w
+            const float w = fr.qn[0], x = fr.qn[1], y = fr.qn[2], zq = fr.qn[3];
+            const float tw[3] = {2.0f * (x * zq + w * y), 2.0f * (y * zq - w * x), 1.0f - 2.0f * (x * x + y * y)};
+            float A[3], B[3], nv[3];
             for (int i = 0; i < 3; ++i) {
                 const float *row = cam.R + 3 * i;
                 A[i] = su * (row[0] * fr.tu[0] + row[1] * fr.tu[1] + row[2] * fr.tu[2]);
                 B[i] = sv * (row[0] * fr.tv[0] + row[1] * fr.tv[1] + row[2] * fr.tv[2]);
+                nv[i] = (su * sv) * (row[0] * tw[0] + row[1] * tw[1] + row[2] * tw[2]);
             }
             const DF Px = df_affine(cam.R + 0, p, cam.t[0]);
             const DF Py = df_affine(cam.R + 3, p, cam.t[1]);
@@ -301,21 +309,27 @@ __global__ void __launch_bounds__(256) preprocess_kernel(Frame f, uint32_t *dept
             const DF cxd = df_add(df_mul_f(xz, cam.fx), DF{cam.cx, 0.0f});
             const DF cyd = df_add(df_mul_f(yz, cam.fy), DF{cam.cy, 0.0f});
             const float z = Pz.hi;
-            float t00 = cam.fx * det2(A[0], A[2], Px.hi, z) / z;
-            float t01 = cam.fx * det2(B[0], B[2], Px.hi, z) / z;
-            float t10 = cam.fy * det2(A[1], A[2], Py.hi, z) / z;
-            float t11 = cam.fy * det2(B[1], B[2], Py.hi, z) / z;
-            float t20 = A[2], t21 = B[2];
-            float J = det2(t00, t01, t10, t11);
-            float m20z = det2(t10, t11, t20, t21);
-            float m21z = det2(t01, t00, t21, t20);
-            const float scale = fabsf(t00 * t11) + fabsf(t01 * t10);
-            if (!(fabsf(J) * 64.0f > scale)) {
-                float t[6];
-                homography_fp64(p, q, su, sv, cam, t, J, m20z, m21z);
-                t00 = t[0]; t01 = t[1]; t10 = t[2]; t11 = t[3]; t20 = t[4]; t21 = t[5];
-            }
             const float iz = 1.0f / z;
+            // n . P: the only cancelling quantity (grazing view); double-float dot
+            DF np = two_prod(nv[0], Px.hi);
+            np = df_add(np, two_prod(nv[1], Py.hi));
+            np = df_add(np, two_prod(nv[2], Pz.hi));
+            const float nmag = fabsf(nv[0] * Px.hi) + fabsf(nv[1] * Py.hi) + fabsf(nv[2] * Pz.hi);
+            float t00, t01, t10, t11, m20, m21, m22;
+            if (fabsf(np.hi) * 4.0f > nmag) {
+                t00 = cam.fx * det2(A[0], A[2], Px.hi, z) * iz;
+                t01 = cam.fx * det2(B[0], B[2], Px.hi, z) * iz;
+                t10 = cam.fy * det2(A[1], A[2], Py.hi, z) * iz;
+                t11 = cam.fy * det2(B[1], B[2], Py.hi, z) * iz;
+                m20 = cam.fy * nv[0] * iz;
+                m21 = cam.fx * nv[1] * iz;
+                m22 = (cam.fx * cam.fy) * np.hi * iz * iz;
+            } else {
+                float t[4], m[3];
+                homography_fp64(p, q, su, sv, cam, t, m);
+                t00 = t[0]; t01 = t[1]; t10 = t[2]; t11 = t[3];
+                m20 = m[0]; m21 = m[1]; m22 = m[2];
+            }
             // SH colour, d = (p - campos) / |p - campos|
             float dx = p[0] - cam.campos[0], dy = p[1] - cam.campos[1], dz = p[2] - cam.campos[2];
             const float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
@@ -328,7 +342,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(Frame f, uint32_t *dept
                 for (int ch = 0; ch < 3; ++ch) rgb[ch] += Y[m] * load_sh(sc, (k * M + m) * 3 + ch);
             Record R;
             R.q0 = make_float4(t11, -t01, -t10, t00);
-            R.q1 = make_float4(m20z * iz, m21z * iz, J * iz, z);
+            R.q1 = make_float4(m20, m21, m22, z);
             R.q2 = make_float4(cxd.hi, cyd.hi, cxd.lo, cyd.lo);
             R.q3 = make_float4(o, rgb[0], rgb[1], rgb[2]);
             rec_out[r] = R;
