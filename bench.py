@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched_1m")
     ap.add_argument("--tex-n", type=int, default=4)
+    ap.add_argument("--views", type=int, default=0, help="use only the first V cameras (0 = all; profiling)")
     ap.add_argument("--batch", type=int, default=0, help="splats per shared-memory batch (0 = auto)")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -124,7 +125,11 @@ def allreduce_max(x: float, world: int) -> float:
 
 def make_workload(args):
     from paper_2412_12734_gb300 import scenes
-    return scenes.workload(args.workload, seed=0, tex_n=args.tex_n)
+    wl = scenes.workload(args.workload, seed=0, tex_n=args.tex_n)
+    if args.views:
+        for k in ("cams", "cam_scene", "d_rgb"):
+            wl[k] = wl[k][:args.views]
+    return wl
 
 
 def crop_window(cam, side):
@@ -274,7 +279,7 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: 1,000,000 splats, 16 views 960x540/1280x720/1920x1080, "
+        "config": {"workload": f"{args.workload}: 1,000,000 splats, {len(cams)} views 960x540/1280x720/1920x1080, "
                                f"{args.tex_n}x{args.tex_n} FP16 textures, SH3 FP16",
                    "pixels_per_step": P, "tex_n": args.tex_n, "storage": "f16", "tile": 16,
                    "graph": graph is not None, "l2": "inputs larger than L2 (no flush)",
