@@ -157,8 +157,12 @@ gb_status reserve_scratch(gb_saved *s) {
     return GB_OK;
 }
 
+size_t batch_smem(int N, int batch, bool bwd);
+
+// Batch depth giving ~64 KB of staged shared memory per 256-thread block
+// (three to four resident blocks per SM).
 int default_batch(int N, bool bwd) {
-    const int per = int(72 + 12 * N * N + (bwd ? 64 + 12 * N * N : 0));
+    const int per = int(batch_smem(N, 1, bwd));
     int b = (64 * 1024) / per;
     b = std::min(b, 256);
     b &= ~31;

@@ -18,21 +18,49 @@
 namespace gbill {
 namespace {
 
-__device__ __forceinline__ float warp_sum(float v) {
+// Reduce-scatter of 16 values over the warp: after five exchange steps (16
+// shuffles) lane l holds the warp total of value index
+// 8 b4 + 4 b3 + 2 b2 + b1 (b_i = bit i of l); lanes l and l^1 hold the same.
+__device__ __forceinline__ float warp_reduce_scatter16(float v[16], int lane) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int i = 0; i < 8; ++i) {
+        const bool up = lane & 16;
+        const float send = up ? v[i] : v[i + 8], keep = up ? v[i + 8] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool up = lane & 8;
+        const float send = up ? v[i] : v[i + 4], keep = up ? v[i + 4] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool up = lane & 4;
+        const float send = up ? v[i] : v[i + 2], keep = up ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    {
+        const bool up = lane & 2;
+        const float send = up ? v[0] : v[1], keep = up ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+__device__ __forceinline__ int scatter_index(int lane) {
+    return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
 }
 
 template <int TS, int N, typename TexT>
 __global__ void __launch_bounds__(TS * TS) render_bwd_kernel(Frame f, RenderBwdBufs b, int batch) {
     constexpr int NT = TS * TS;
-    constexpr int TEXF = N * N * 3;
-    constexpr int NG = 14;  // record gradient values accumulated per splat
+    constexpr int NN = N * N;
+    constexpr int TEXF = NN * 3;
     extern __shared__ float4 smem[];
     float4 *s_rec = smem;
-    float *s_tex = reinterpret_cast<float *>(s_rec + 4 * batch);
-    int32_t *s_k = reinterpret_cast<int32_t *>(s_tex + batch * TEXF);
+    float4 *s_tex = s_rec + 4 * batch;
+    int32_t *s_k = reinterpret_cast<int32_t *>(s_tex + batch * NN);
     uint32_t *s_j = reinterpret_cast<uint32_t *>(s_k + batch);
     float *s_g = reinterpret_cast<float *>(s_j + batch);  // [batch][16]
     float *s_tg = s_g + batch * kRecGrad;                  // [batch][TEXF]
@@ -46,6 +74,7 @@ __global__ void __launch_bounds__(TS * TS) render_bwd_kernel(Frame f, RenderBwdB
     const int tx = int(lt % uint32_t(cam.tiles_x)), ty = int(lt / uint32_t(cam.tiles_x));
     int lx, ly;
     tile_pixel<TS>(threadIdx.x, lx, ly);
+    const int lane = threadIdx.x & 31;
     const int px = tx * TS + lx, py = ty * TS + ly;
     const bool inside = px < cam.width && py < cam.height;
     const float xf = float(px) + 0.5f, yf = float(py) + 0.5f;
@@ -66,14 +95,16 @@ __global__ void __launch_bounds__(TS * TS) render_bwd_kernel(Frame f, RenderBwdB
         dC2 = b.d_rgb[3 * pix + 2];
         if (b.d_depth) dD = b.d_depth[pix];
         if (b.d_alpha) dA = b.d_alpha[pix];
-        if (last) atomicMax(&s_maxlast, last);
     }
+    const uint32_t wlast = __reduce_max_sync(0xffffffffu, last);
+    if (lane == 0 && wlast) atomicMax(&s_maxlast, wlast);
     const float bgdot = dC0 * f.bg[0] + dC1 * f.bg[1] + dC2 * f.bg[2];
     const float dTfin = (dA - bgdot) * T_final;  // times 1/(1-alpha) per splat
     float S0 = 0, S1 = 0, S2 = 0, SD = 0;
     __syncthreads();
     const int max_last = int(s_maxlast);
     float *g_tex = sc.g_tex;
+    const int my_q = scatter_index(lane);
 
     for (int be = max_last; be > 0; be -= batch) {
         const int bs = max(0, be - batch), nb = be - bs;
@@ -81,10 +112,12 @@ __global__ void __launch_bounds__(TS * TS) render_bwd_kernel(Frame f, RenderBwdB
         for (int e = threadIdx.x; e < nb * TEXF; e += NT) s_tg[e] = 0.0f;
         stage_batch<N, NT, TexT>(b.fw, cam, sc, range.x + bs, nb, s_rec, s_tex, s_k, s_j);
         __syncthreads();
-        for (int i = nb - 1; i >= 0; --i) {
-            float g[NG];
+        // splats at or beyond the warp's last contributor are skipped warp-wide
+        const int i_hi = min(nb, int(wlast) - bs);
+        for (int i = i_hi - 1; i >= 0; --i) {
+            float g[16];
 #pragma unroll
-            for (int q = 0; q < NG; ++q) g[q] = 0.0f;
+            for (int q = 0; q < 16; ++q) g[q] = 0.0f;
             bool act = inside && uint32_t(bs + i) < last;
             npairs += act ? 1u : 0u;
             if (act) {
@@ -94,7 +127,7 @@ __global__ void __launch_bounds__(TS * TS) render_bwd_kernel(Frame f, RenderBwdB
                 const float zz = fmaf(q1.x, dx, fmaf(q1.y, dy, q1.z));
                 act = zz != 0.0f;
                 if (act) {
-                    const float rz = __frcp_rn(zz);
+                    const float rz = fast_rcp(zz);
                     const float u = fmaf(q0.x, dx, q0.y * dy) * rz;
                     const float v = fmaf(q0.z, dx, q0.w * dy) * rz;
                     const float ruv = fmaf(u, u, v * v);
@@ -107,13 +140,12 @@ __global__ void __launch_bounds__(TS * TS) render_bwd_kernel(Frame f, RenderBwdB
                     const float alpha = clamped ? kAlphaMax : ar;
                     act = alpha >= kAlphaMin;
                     if (act) {
-                        const float om = 1.0f - alpha;
-                        const float iom = __frcp_rn(om);
+                        const float iom = fast_rcp(1.0f - alpha);
                         const float Ti = T * iom;
                         const Cell<N> cell = grid_cell<N>(u, v, sigma, kN);
-                        const float *tg = s_tex + i * TEXF;
+                        const Quad qd = grid_quad<N>(s_tex + i * NN, cell);
                         float col[3];
-                        grid_colour<N>(tg, cell, col);
+                        grid_colour<N>(qd, cell, col);
                         col[0] += q3.y;
                         col[1] += q3.z;
                         col[2] += q3.w;
@@ -131,19 +163,33 @@ __global__ void __launch_bounds__(TS * TS) render_bwd_kernel(Frame f, RenderBwdB
                             const float fu = cell.fu, fv = cell.fv;
                             const float w00 = (1.0f - fu) * (1.0f - fv), w10 = fu * (1.0f - fv);
                             const float w01 = (1.0f - fu) * fv, w11 = fu * fv;
-                            const int o00 = cell.base, o10 = o00 + 3 * N, o01 = o00 + 3, o11 = o10 + 3;
-                            const float chv[3] = {ch0, ch1, ch2};
-                            float fuh = 0.0f, fvh = 0.0f;
-#pragma unroll
-                            for (int c = 0; c < 3; ++c) {
-                                const float c00 = tg[o00 + c], c10 = tg[o10 + c], c01 = tg[o01 + c],
-                                            c11 = tg[o11 + c];
-                                fuh += chv[c] * ((c10 - c00) * (1.0f - fv) + (c11 - c01) * fv);
-                                fvh += chv[c] * ((c01 - c00) * (1.0f - fu) + (c11 - c10) * fu);
-                                if (w00 != 0.0f) atomicAdd(tgo + o00 + c, chv[c] * w00);
-                                if (w10 != 0.0f) atomicAdd(tgo + o10 + c, chv[c] * w10);
-                                if (w01 != 0.0f) atomicAdd(tgo + o01 + c, chv[c] * w01);
-                                if (w11 != 0.0f) atomicAdd(tgo + o11 + c, chv[c] * w11);
+                            const int o00 = 3 * cell.base, o10 = o00 + 3 * N, o01 = o00 + 3, o11 = o10 + 3;
+                            // d colour / d f_u and d f_v, dotted with the colour adjoint
+                            const float fuh = ch0 * ((qd.c10.x - qd.c00.x) * (1.0f - fv) + (qd.c11.x - qd.c01.x) * fv) +
+                                              ch1 * ((qd.c10.y - qd.c00.y) * (1.0f - fv) + (qd.c11.y - qd.c01.y) * fv) +
+                                              ch2 * ((qd.c10.z - qd.c00.z) * (1.0f - fv) + (qd.c11.z - qd.c01.z) * fv);
+                            const float fvh = ch0 * ((qd.c01.x - qd.c00.x) * (1.0f - fu) + (qd.c11.x - qd.c10.x) * fu) +
+                                              ch1 * ((qd.c01.y - qd.c00.y) * (1.0f - fu) + (qd.c11.y - qd.c10.y) * fu) +
+                                              ch2 * ((qd.c01.z - qd.c00.z) * (1.0f - fu) + (qd.c11.z - qd.c10.z) * fu);
+                            if (w00 != 0.0f) {
+                                atomicAdd(tgo + o00 + 0, ch0 * w00);
+                                atomicAdd(tgo + o00 + 1, ch1 * w00);
+                                atomicAdd(tgo + o00 + 2, ch2 * w00);
+                            }
+                            if (w10 != 0.0f) {
+                                atomicAdd(tgo + o10 + 0, ch0 * w10);
+                                atomicAdd(tgo + o10 + 1, ch1 * w10);
+                                atomicAdd(tgo + o10 + 2, ch2 * w10);
+                            }
+                            if (w01 != 0.0f) {
+                                atomicAdd(tgo + o01 + 0, ch0 * w01);
+                                atomicAdd(tgo + o01 + 1, ch1 * w01);
+                                atomicAdd(tgo + o01 + 2, ch2 * w01);
+                            }
+                            if (w11 != 0.0f) {
+                                atomicAdd(tgo + o11 + 0, ch0 * w11);
+                                atomicAdd(tgo + o11 + 1, ch1 * w11);
+                                atomicAdd(tgo + o11 + 2, ch2 * w11);
                             }
                             if (u > -sigma && u < sigma) uh = kN * fuh;
                             if (v > -sigma && v < sigma) vh = kN * fvh;
@@ -194,13 +240,8 @@ __global__ void __launch_bounds__(TS * TS) render_bwd_kernel(Frame f, RenderBwdB
                 }
             }
             if (__any_sync(0xffffffffu, act)) {
-#pragma unroll
-                for (int q = 0; q < NG; ++q) g[q] = warp_sum(g[q]);
-                if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-                    for (int q = 0; q < NG; ++q)
-                        if (g[q] != 0.0f) atomicAdd(s_g + i * kRecGrad + q, g[q]);
-                }
+                const float tot = warp_reduce_scatter16(g, lane);
+                if (!(lane & 1) && my_q < 14 && tot != 0.0f) atomicAdd(s_g + i * kRecGrad + my_q, tot);
             }
         }
         __syncthreads();
@@ -223,7 +264,7 @@ __global__ void __launch_bounds__(TS * TS) render_bwd_kernel(Frame f, RenderBwdB
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
-    if ((threadIdx.x & 31) == 0 && npairs) atomicAdd(&b.fw.cnt->pairs_bwd, (unsigned long long)npairs);
+    if (lane == 0 && npairs) atomicAdd(&b.fw.cnt->pairs_bwd, (unsigned long long)npairs);
 }
 
 template <int TS, int N, typename TexT>

@@ -16,21 +16,30 @@ __device__ __forceinline__ void tile_pixel(int tid, int &lx, int &ly) {
 
 // Bytes of dynamic shared memory for one staged batch: records, colour
 // grids, splat indices and (backward) record/grid gradient accumulators.
+// Colour grids are staged as RGBA float4 texels (16 bytes, alpha unused) so a
+// texel is one 128-bit shared load.
 template <int N>
 __host__ __device__ inline size_t stage_bytes(int batch, bool bwd) {
     const int texf = N * N * 3;
-    size_t b = size_t(batch) * (64 + 4 * texf + 8);
+    size_t b = size_t(batch) * (64 + 16 * N * N + 8);
     if (bwd) b += size_t(batch) * (4 * kRecGrad + 4 * texf);
     return b;
+}
+
+// 1 / x through the SFU (max error 1 ulp; flush-to-zero).
+__device__ __forceinline__ float fast_rcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
 
 // Loads the records and colour grids of instances [first, first + nb) of a
 // tile range into shared memory.  Caller synchronizes before and after.
 template <int N, int NT, typename TexT>
 __device__ __forceinline__ void stage_batch(const RenderBufs &b, const CamDev &cam, const SceneDev &sc,
-                                            uint32_t first, int nb, float4 *s_rec, float *s_tex,
+                                            uint32_t first, int nb, float4 *s_rec, float4 *s_tex,
                                             int32_t *s_k, uint32_t *s_j) {
-    constexpr int TEXF = N * N * 3;
+    constexpr int NN = N * N;
     const int t = threadIdx.x;
     if (t < nb) {
         const uint32_t j = b.inst_val[first + t];
@@ -45,9 +54,10 @@ __device__ __forceinline__ void stage_batch(const RenderBufs &b, const CamDev &c
     }
     __syncthreads();
     const TexT *tex = static_cast<const TexT *>(sc.tex);
-    for (int e = t; e < nb * TEXF; e += NT) {
-        const int s = e / TEXF, o = e - s * TEXF;
-        s_tex[e] = load_as_float(tex, int64_t(s_k[s]) * TEXF + o);
+    for (int e = t; e < nb * NN; e += NT) {
+        const int s = e / NN, o = e - s * NN;
+        const int64_t g = (int64_t(s_k[s]) * NN + o) * 3;
+        s_tex[e] = make_float4(load_as_float(tex, g), load_as_float(tex, g + 1), load_as_float(tex, g + 2), 0.0f);
     }
 }
 
@@ -55,7 +65,7 @@ __device__ __forceinline__ void stage_batch(const RenderBufs &b, const CamDev &c
 // cell index min(floor(u'), N-2) and fraction u' - index.
 template <int N>
 struct Cell {
-    int base;    // offset of texel (i_u, i_v) in floats
+    int base;    // index of texel (i_u, i_v) in the N x N grid
     float fu, fv;
 };
 
@@ -72,23 +82,44 @@ __device__ __forceinline__ Cell<N> grid_cell(float u, float v, float sigma, floa
     const int iu = min(int(up), N - 2), iv = min(int(vp), N - 2);
     c.fu = up - float(iu);
     c.fv = vp - float(iv);
-    c.base = (iu * N + iv) * 3;
+    c.base = iu * N + iv;
     return c;
 }
 
+// The four texels of a cell: (i_u, i_v), (i_u+1, i_v), (i_u, i_v+1), (i_u+1, i_v+1).
+struct Quad {
+    float4 c00, c10, c01, c11;
+};
+
 template <int N>
-__device__ __forceinline__ void grid_colour(const float *g, const Cell<N> &c, float col[3]) {
+__device__ __forceinline__ Quad grid_quad(const float4 *g, const Cell<N> &c) {
+    Quad q;
+    q.c00 = g[c.base];
     if (N == 1) {
-        col[0] = g[0]; col[1] = g[1]; col[2] = g[2];
+        q.c10 = q.c01 = q.c11 = q.c00;
+    } else {
+        q.c10 = g[c.base + N];
+        q.c01 = g[c.base + 1];
+        q.c11 = g[c.base + N + 1];
+    }
+    return q;
+}
+
+__device__ __forceinline__ float lerp2(float a00, float a10, float a01, float a11, float fu, float fv) {
+    const float a = fmaf(fu, a10 - a00, a00);
+    const float b = fmaf(fu, a11 - a01, a01);
+    return fmaf(fv, b - a, a);
+}
+
+template <int N>
+__device__ __forceinline__ void grid_colour(const Quad &q, const Cell<N> &c, float col[3]) {
+    if (N == 1) {
+        col[0] = q.c00.x; col[1] = q.c00.y; col[2] = q.c00.z;
         return;
     }
-    const float *p00 = g + c.base, *p10 = p00 + 3 * N, *p01 = p00 + 3, *p11 = p10 + 3;
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-        const float a = fmaf(c.fu, p10[ch] - p00[ch], p00[ch]);
-        const float bb = fmaf(c.fu, p11[ch] - p01[ch], p01[ch]);
-        col[ch] = fmaf(c.fv, bb - a, a);
-    }
+    col[0] = lerp2(q.c00.x, q.c10.x, q.c01.x, q.c11.x, c.fu, c.fv);
+    col[1] = lerp2(q.c00.y, q.c10.y, q.c01.y, q.c11.y, c.fu, c.fv);
+    col[2] = lerp2(q.c00.z, q.c10.z, q.c01.z, q.c11.z, c.fu, c.fv);
 }
 
 // exp(-rho / 2) through the SFU exponential.

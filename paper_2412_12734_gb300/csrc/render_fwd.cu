@@ -18,11 +18,11 @@ namespace {
 template <int TS, int N, typename TexT>
 __global__ void __launch_bounds__(TS * TS) render_fwd_kernel(Frame f, RenderBufs b, int batch) {
     constexpr int NT = TS * TS;
-    constexpr int TEXF = N * N * 3;
+    constexpr int NN = N * N;
     extern __shared__ float4 smem[];
     float4 *s_rec = smem;
-    float *s_tex = reinterpret_cast<float *>(s_rec + 4 * batch);
-    int32_t *s_k = reinterpret_cast<int32_t *>(s_tex + batch * TEXF);
+    float4 *s_tex = s_rec + 4 * batch;
+    int32_t *s_k = reinterpret_cast<int32_t *>(s_tex + batch * NN);
     uint32_t *s_j = reinterpret_cast<uint32_t *>(s_k + batch);
 
     const uint32_t tile = blockIdx.x;
@@ -51,12 +51,14 @@ __global__ void __launch_bounds__(TS * TS) render_fwd_kernel(Frame f, RenderBufs
         __syncthreads();
         if (!done) {
             for (int i = 0; i < nb; ++i) {
+                if (__all_sync(__activemask(), done)) break;
+                if (done) continue;
                 ++npairs;
                 const float4 q0 = s_rec[4 * i + 0], q1 = s_rec[4 * i + 1], q2 = s_rec[4 * i + 2];
                 const float dx = (xf - q2.x) - q2.z, dy = (yf - q2.y) - q2.w;
                 const float zz = fmaf(q1.x, dx, fmaf(q1.y, dy, q1.z));
                 if (zz == 0.0f) continue;
-                const float rz = __frcp_rn(zz);
+                const float rz = fast_rcp(zz);
                 const float u = fmaf(q0.x, dx, q0.y * dy) * rz;
                 const float v = fmaf(q0.z, dx, q0.w * dy) * rz;
                 const float ruv = fmaf(u, u, v * v);
@@ -69,11 +71,11 @@ __global__ void __launch_bounds__(TS * TS) render_fwd_kernel(Frame f, RenderBufs
                 const float tT = T * (1.0f - alpha);
                 if (tT < kTMin) {
                     done = true;
-                    break;
+                    continue;
                 }
                 const Cell<N> cell = grid_cell<N>(u, v, sigma, kN);
                 float col[3];
-                grid_colour<N>(s_tex + i * TEXF, cell, col);
+                grid_colour<N>(grid_quad<N>(s_tex + i * NN, cell), cell, col);
                 const float w = alpha * T;
                 C0 = fmaf(col[0] + q3.y, w, C0);
                 C1 = fmaf(col[1] + q3.z, w, C1);
