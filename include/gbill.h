@@ -116,7 +116,7 @@ typedef struct {
 
 /* Render options (host struct; NULL = defaults). */
 typedef struct {
-    int32_t tile_size;   /* 8, 16 (default 0 = 16)                               */
+    int32_t tile_size;   /* tile edge in pixels: 8 or 16 (0 = 16)                 */
     int32_t batch_depth; /* splats staged per shared-memory batch, 0 = automatic;
                             otherwise a multiple of 32 up to the tile's pixels    */
     uint32_t flags;      /* GB_FLAG_*                                             */
@@ -263,6 +263,24 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *saved, const gb_scene *sc
 gb_status gb_render_backward(gb_context *ctx, gb_saved *saved, const float *d_rgb,
                              const float *d_depth, const float *d_alpha, const gb_grads *grads,
                              int32_t n_scenes, void *stream);
+
+/* ---------------------------------------------------------------- tuning -- */
+
+/* Autotuner: times forward + backward of this frame for every candidate
+ * (tile_size 8 and 16; batch_depth 32, 64, 128, 256 where it fits the tile and
+ * the shared-memory budget) and writes the fastest options to *best (flags and
+ * background are copied from *base, which may be NULL).  Each candidate runs
+ * once untimed (which may grow `saved`) and then `reps` timed repetitions
+ * (1..100) with dL/drgb = 1 for every pixel.  The call allocates its own
+ * output, upstream-gradient and parameter-gradient buffers with cudaMalloc and
+ * frees them before returning; it synchronizes the device.  ms (host array of
+ * `cap` floats, nullable) receives the mean time per candidate in the order
+ * tried, tiles/batches (host, nullable) the candidate's options;
+ * *n_candidates (nullable) the number tried. */
+gb_status gb_autotune(gb_context *ctx, gb_saved *saved, const gb_scene *scenes, int32_t n_scenes,
+                      const gb_camera *cams, int32_t n_cams, const gb_options *base, int32_t reps,
+                      gb_options *best, float *ms, int32_t *tiles, int32_t *batches, int32_t cap,
+                      int32_t *n_candidates);
 
 #ifdef __cplusplus
 }

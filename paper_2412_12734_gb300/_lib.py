@@ -102,6 +102,9 @@ def load() -> C.CDLL:
         "gb_render_forward": (C.c_int, [vp, vp, C.POINTER(gb_scene), i32, C.POINTER(gb_camera), i32,
                                         C.POINTER(gb_options), vp, vp, vp, vp]),
         "gb_render_backward": (C.c_int, [vp, vp, vp, vp, vp, C.POINTER(gb_grads), i32, vp]),
+        "gb_autotune": (C.c_int, [vp, vp, C.POINTER(gb_scene), i32, C.POINTER(gb_camera), i32,
+                                  C.POINTER(gb_options), i32, C.POINTER(gb_options), vp, vp, vp, i32,
+                                  C.POINTER(i32)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

@@ -472,7 +472,7 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
     if (opt) o = *opt;
     if (o.reserved != 0) return fail(ctx, GB_ERR_INVALID_ARG, "options.reserved must be 0");
     const int tile = o.tile_size ? o.tile_size : 16;
-    if (tile != 16) return fail(ctx, GB_ERR_UNSUPPORTED, "tile_size %d not built (16 only)", tile);
+    if (tile != 8 && tile != 16) return fail(ctx, GB_ERR_UNSUPPORTED, "tile_size %d not built (8 or 16)", tile);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Frame f;
     int64_t max_k = 0;
@@ -480,8 +480,8 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
     if (r != GB_OK) return r;
     const int N = scenes[0].tex_n;
     const int nt = tile * tile;
-    int bf = o.batch_depth ? o.batch_depth : default_batch(N, false);
-    int bb = o.batch_depth ? o.batch_depth : default_batch(N, true);
+    int bf = o.batch_depth ? o.batch_depth : std::min(default_batch(N, false), nt);
+    int bb = o.batch_depth ? o.batch_depth : std::min(default_batch(N, true), nt);
     if (bf < 32 || bf > nt || (bf & 31)) return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d invalid", bf);
     if (batch_smem(N, bf, false) > 200 * 1024 || batch_smem(N, bb, true) > 200 * 1024)
         return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d needs too much shared memory", bf);
@@ -619,6 +619,114 @@ gb_status gb_render_backward(gb_context *ctx, gb_saved *s, const float *d_rgb, c
     if (timing) GB_CUDA(ctx, cudaEventRecord(s->ev[11], st));
     s->timed_bwd = timing;
     return GB_OK;
+}
+
+__global__ void fill_kernel(float *p, int64_t n, float v) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        p[i] = v;
+}
+
+gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int32_t n_scenes,
+                      const gb_camera *cams, int32_t n_cams, const gb_options *base, int32_t reps,
+                      gb_options *best, float *ms, int32_t *tiles, int32_t *batches, int32_t cap,
+                      int32_t *n_candidates) {
+    if (!ctx) return GB_ERR_INVALID_ARG;
+    if (!s || s->ctx != ctx || !best) return fail(ctx, GB_ERR_INVALID_ARG, "bad autotune arguments");
+    if (reps < 1 || reps > 100) return fail(ctx, GB_ERR_INVALID_ARG, "reps must be in 1..100");
+    Frame f;
+    int64_t max_k = 0;
+    gb_status r = build_frame(ctx, scenes, n_scenes, cams, n_cams, 16, nullptr, f, max_k);
+    if (r != GB_OK) return r;
+    const int N = scenes[0].tex_n;
+    // scratch buffers owned by this call
+    float *rgb = nullptr, *dep = nullptr, *alp = nullptr, *drgb = nullptr, *gbuf = nullptr;
+    size_t gtot = 0;
+    for (int i = 0; i < n_scenes; ++i) {
+        const int64_t K = scenes[i].num_splats, M = (scenes[i].sh_degree + 1) * (scenes[i].sh_degree + 1);
+        gtot += size_t(K) * (3 + 4 + 2 + 1 + 3 * M + 3 * N * N);
+    }
+    cudaError_t e = cudaMalloc(&rgb, size_t(f.n_pixels) * 12 + 16);
+    if (e == cudaSuccess) e = cudaMalloc(&dep, size_t(f.n_pixels) * 4 + 16);
+    if (e == cudaSuccess) e = cudaMalloc(&alp, size_t(f.n_pixels) * 4 + 16);
+    if (e == cudaSuccess) e = cudaMalloc(&drgb, size_t(f.n_pixels) * 12 + 16);
+    if (e == cudaSuccess) e = cudaMalloc(&gbuf, gtot * 4 + 16);
+    gb_grads g[kMaxScenes];
+    gb_status st = GB_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        st = fail(ctx, GB_ERR_CUDA, "autotune allocation failed: %s", cudaGetErrorString(e));
+    } else {
+        fill_kernel<<<1024, 256>>>(drgb, f.n_pixels * 3, 1.0f);
+        count_launches(1);
+        float *p = gbuf;
+        for (int i = 0; i < n_scenes; ++i) {
+            const int64_t K = scenes[i].num_splats, M = (scenes[i].sh_degree + 1) * (scenes[i].sh_degree + 1);
+            g[i].d_means = p; p += K * 3;
+            g[i].d_quats = p; p += K * 4;
+            g[i].d_scales = p; p += K * 2;
+            g[i].d_opacities = p; p += K;
+            g[i].d_sh = p; p += K * 3 * M;
+            g[i].d_textures = p; p += K * 3 * N * N;
+        }
+        gb_options o{};
+        if (base) o = *base;
+        o.flags &= ~(GB_FLAG_NO_SYNC | GB_FLAG_TIMING);
+        float best_ms = INFINITY;
+        int n = 0;
+        const int tile_c[2] = {16, 8};
+        const int batch_c[4] = {32, 64, 128, 256};
+        for (int ti = 0; ti < 2 && st == GB_OK; ++ti)
+            for (int bi = 0; bi < 4 && st == GB_OK; ++bi) {
+                const int T = tile_c[ti], B = batch_c[bi];
+                if (B > T * T) continue;
+                if (batch_smem(N, B, false) > 160 * 1024 || batch_smem(N, B, true) > 160 * 1024) continue;
+                o.tile_size = T;
+                o.batch_depth = B;
+                o.flags &= ~GB_FLAG_NO_SYNC;
+                st = gb_render_forward(ctx, s, scenes, n_scenes, cams, n_cams, &o, rgb, dep, alp, nullptr);
+                if (st == GB_OK) st = gb_render_backward(ctx, s, drgb, nullptr, nullptr, g, n_scenes, nullptr);
+                if (st != GB_OK) break;
+                o.flags |= GB_FLAG_NO_SYNC;
+                cudaEventRecord(e0, nullptr);
+                for (int k = 0; k < reps && st == GB_OK; ++k) {
+                    st = gb_render_forward(ctx, s, scenes, n_scenes, cams, n_cams, &o, rgb, dep, alp, nullptr);
+                    if (st == GB_OK) st = gb_render_backward(ctx, s, drgb, nullptr, nullptr, g, n_scenes, nullptr);
+                }
+                cudaEventRecord(e1, nullptr);
+                if (st != GB_OK) break;
+                e = cudaEventSynchronize(e1);
+                float t = 0.0f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+                if (e != cudaSuccess) {
+                    st = fail(ctx, GB_ERR_CUDA, "autotune timing failed: %s", cudaGetErrorString(e));
+                    break;
+                }
+                const gb_status chk = gb_saved_check(s);
+                if (chk != GB_OK) { st = chk; break; }
+                t /= float(reps);
+                if (n < cap) {
+                    if (ms) ms[n] = t;
+                    if (tiles) tiles[n] = T;
+                    if (batches) batches[n] = B;
+                }
+                ++n;
+                if (t < best_ms) {
+                    best_ms = t;
+                    *best = o;
+                    best->flags &= ~GB_FLAG_NO_SYNC;
+                    if (base) best->flags |= (base->flags & GB_FLAG_NO_SYNC);
+                }
+            }
+        if (n_candidates) *n_candidates = n;
+        if (st == GB_OK && n == 0) st = fail(ctx, GB_ERR_UNSUPPORTED, "no autotune candidate fits");
+    }
+    cudaDeviceSynchronize();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(rgb); cudaFree(dep); cudaFree(alp); cudaFree(drgb); cudaFree(gbuf);
+    return st;
 }
 
 }  // extern "C"

@@ -134,6 +134,13 @@ cudaError_t launch_render_fwd(const Frame &f, const RenderBufs &b, int batch, cu
     if (f.n_tiles == 0) return cudaSuccess;
     // every scene of a launch shares tex_n and tex_dtype (checked by the caller)
     const SceneDev &sc = f.scenes[0];
+    if (f.tile == 8) {
+        switch (sc.tex_dtype) {
+            case GB_F16: return launch_n<8, __half>(f, b, sc.N, batch, s);
+            case GB_BF16: return launch_n<8, __nv_bfloat16>(f, b, sc.N, batch, s);
+            default: return launch_n<8, float>(f, b, sc.N, batch, s);
+        }
+    }
     if (f.tile != 16) return cudaErrorInvalidValue;
     switch (sc.tex_dtype) {
         case GB_F16: return launch_n<16, __half>(f, b, sc.N, batch, s);

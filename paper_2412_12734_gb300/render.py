@@ -234,6 +234,51 @@ class Rasterizer:
         return grads
 
 
+    def autotune(self, scenes: list, cams: list, cam_scene=None, reps: int = 3, saved: Saved | None = None,
+                 cache: str | None = None) -> dict:
+        """Picks (tile, batch_depth) with the library's autotuner; results are
+        cached in a JSON file keyed by texture size, storage types, SH degree,
+        splat count and pixel count (rounded to powers of two)."""
+        import json
+        import os
+        key = "|".join(str(x) for x in (
+            int(scenes[0]["tex_n"]), str(scenes[0]["textures"].dtype), str(scenes[0]["sh"].dtype),
+            int(scenes[0]["sh_degree"]), sum(int(s["means"].shape[0]) for s in scenes).bit_length(),
+            self.pixel_count(cams).bit_length(), len(cams)))
+        path = cache or os.path.join(os.path.expanduser("~"), ".cache", "gbill", "autotune.json")
+        table = {}
+        if os.path.exists(path):
+            try:
+                table = json.load(open(path))
+            except (OSError, ValueError):
+                table = {}
+        if key in table:
+            return table[key]
+        lib = L.load()
+        n_s, n_c = len(scenes), len(cams)
+        cam_scene = list(cam_scene) if cam_scene is not None else [0] * n_c
+        sarr = (L.gb_scene * n_s)(*[scene_struct(s) for s in scenes])
+        carr = (L.gb_camera * n_c)(*[camera_struct(c, cam_scene[i]) for i, c in enumerate(cams)])
+        best = L.gb_options()
+        ms = (C.c_float * 16)()
+        tiles = (C.c_int32 * 16)()
+        batches = (C.c_int32 * 16)()
+        n = C.c_int32()
+        saved = saved or Saved(self)
+        L.check(lib.gb_autotune(self.ctx, saved.handle, sarr, n_s, carr, n_c, None, reps, C.byref(best),
+                                C.addressof(ms), C.addressof(tiles), C.addressof(batches), 16, C.byref(n)),
+                self.ctx)
+        res = {"tile": best.tile_size, "batch": best.batch_depth,
+               "candidates": [{"tile": tiles[i], "batch": batches[i], "ms": ms[i]} for i in range(n.value)]}
+        table[key] = res
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            json.dump(table, open(path, "w"), indent=1)
+        except OSError:
+            pass
+        return res
+
+
 _default = {}
 
 

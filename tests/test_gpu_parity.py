@@ -26,12 +26,12 @@ def _tile_offsets(cams, tile=16):
     return offs
 
 
-def _check_keys(scene_list, cams, cam_scene, gpu):
+def _check_keys(scene_list, cams, cam_scene, gpu, tile=16):
     keys, ids, cidx = gpu["keys"]
-    offs = _tile_offsets(cams)
+    offs = _tile_offsets(cams, tile)
     exp_k, exp_i, exp_c = [], [], []
     for ci, c in enumerate(cams):
-        k, i = oracle.tile_keys(scene_list[cam_scene[ci]], c, 16, offs[ci])
+        k, i = oracle.tile_keys(scene_list[cam_scene[ci]], c, tile, offs[ci])
         exp_k.append(k)
         exp_i.append(i)
         exp_c.append(np.full(len(k), ci))
@@ -100,6 +100,39 @@ def test_gradient_parity(case):
     errs = grad_errors(gpu["grads"][0], og)
     bad = {k: v for k, v in errs.items() if v > 1.0}
     assert not bad, f"gradient ratios over tolerance {GRAD_REL}: {errs}"
+
+
+@pytest.mark.parametrize("case", ["plain_1k", "tiny_n4_d3", "tiny_bf16", "dense_many_tiles"])
+def test_tile8_keys_image_gradients(case):
+    """8 x 8 tiles: same keys formula with tile = 8, same image and gradients."""
+    sc, cams = CASES[case]()
+    rng = np.random.default_rng(17)
+    ref = oracle_run(sc[0], cams[0])
+    d_rgb = masked_upstream(ref, rng)
+    gpu = gpu_run(sc, cams, d_rgb=[d_rgb], keys=True, tile=8)
+    _check_keys(sc, cams, [0], gpu, tile=8)
+    e, _ = compare_images(gpu["rgb"][0], ref, "rgb")
+    assert e <= IMG_TOL, e
+    errs = grad_errors(gpu["grads"][0], oracle.backward(sc[0], cams[0], d_rgb))
+    assert all(v <= 1.0 for v in errs.values()), errs
+
+
+def test_autotune_picks_a_valid_candidate(tmp_path):
+    from paper_2412_12734_gb300 import render as R
+    sc, cams = CASES["dense_many_tiles"]()
+    rast = R.Rasterizer(0)
+    dev = [R.scene_to_device(s) for s in sc]
+    res = rast.autotune(dev, cams, reps=2, cache=str(tmp_path / "tune.json"))
+    assert res["tile"] in (8, 16) and res["batch"] in (32, 64, 128, 256)
+    assert len(res["candidates"]) >= 4
+    best = min(res["candidates"], key=lambda c: c["ms"])
+    assert (best["tile"], best["batch"]) == (res["tile"], res["batch"])
+    again = rast.autotune(dev, cams, reps=2, cache=str(tmp_path / "tune.json"))
+    assert again == res  # served from the cache
+    rgb, _, _, _ = rast.forward(dev, cams, tile=res["tile"], batch=res["batch"])
+    ref = oracle_run(sc[0], cams[0])
+    e, _ = compare_images(rgb.cpu().numpy().reshape(ref["rgb"].shape), ref, "rgb")
+    assert e <= IMG_TOL
 
 
 def test_multi_view_multi_scene():
