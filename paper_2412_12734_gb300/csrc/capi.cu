@@ -33,7 +33,7 @@ struct gb_saved {
     int64_t cap_rec, cap_inst, cap_pix, cap_tiles;
     Record *rec;
     uint32_t *depth_key, *rec_id, *keys_tmp, *vals_tmp, *dkeys_sorted, *perm, *offsets;
-    uint2 *rect;
+    uint2 *rect, *pbox;
     int32_t *inv;
     float *rec_grad;
     uint32_t *inst_tile, *inst_val, *inst_tile_tmp, *inst_val_tmp, *tiles_sorted, *vals_sorted;
@@ -103,6 +103,7 @@ gb_status reserve_records(gb_saved *s, int64_t n) {
     GB_CUDA(ctx, alloc_t(&s->perm, c));
     GB_CUDA(ctx, alloc_t(&s->offsets, c));
     GB_CUDA(ctx, alloc_t(&s->rect, c));
+    GB_CUDA(ctx, alloc_t(&s->pbox, c));
     GB_CUDA(ctx, alloc_t(&s->inv, c));
     GB_CUDA(ctx, alloc_t(&s->rec_grad, c * kRecGrad));
     s->cap_rec = c;
@@ -345,7 +346,7 @@ gb_status gb_saved_destroy(gb_saved *s) {
     if (!s) return GB_OK;
     cudaDeviceSynchronize();
     void *ptrs[] = {s->rec, s->depth_key, s->rec_id, s->keys_tmp, s->vals_tmp, s->dkeys_sorted, s->perm,
-                    s->offsets, s->rect, s->inv, s->rec_grad, s->inst_tile, s->inst_val, s->inst_tile_tmp,
+                    s->offsets, s->rect, s->pbox, s->inv, s->rec_grad, s->inst_tile, s->inst_val, s->inst_tile_tmp,
                     s->inst_val_tmp, s->tiles_sorted, s->vals_sorted, s->ranges, s->t_final, s->last,
                     s->cnt, s->scratch};
     for (void *p : ptrs)
@@ -518,7 +519,7 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
     GB_MARK(0);
     GB_CUDA(ctx, cudaMemsetAsync(s->cnt, 0, sizeof(Counters), st));
     GB_CUDA(ctx, cudaMemsetAsync(s->ranges, 0, size_t(f.n_tiles) * sizeof(uint2), st));
-    GB_CUDA(ctx, launch_preprocess(f, max_k, s->depth_key, s->rec_id, s->rect, s->rec, s->cnt, st));
+    GB_CUDA(ctx, launch_preprocess(f, max_k, s->depth_key, s->rec_id, s->rect, s->pbox, s->rec, s->cnt, st));
     GB_MARK(1);
     GB_CUDA(ctx, radix_sort_pairs(s->depth_key, s->rec_id, s->keys_tmp, s->vals_tmp, s->dkeys_sorted, s->perm, R,
                                   nullptr, 0, 32, s->scratch, s->scratch_bytes, st));
@@ -553,6 +554,7 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
     b.perm = s->perm;
     b.inst_val = s->vals_sorted;
     b.ranges = s->ranges;
+    b.pbox = s->pbox;
     b.rgb = rgb;
     b.depth = depth;
     b.alpha = alpha;
@@ -602,6 +604,7 @@ gb_status gb_render_backward(gb_context *ctx, gb_saved *s, const float *d_rgb, c
     b.fw.perm = s->perm;
     b.fw.inst_val = s->vals_sorted;
     b.fw.ranges = s->ranges;
+    b.fw.pbox = s->pbox;
     b.fw.rgb = nullptr;
     b.fw.depth = nullptr;
     b.fw.alpha = nullptr;

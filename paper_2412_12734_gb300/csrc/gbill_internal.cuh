@@ -130,7 +130,7 @@ __device__ __forceinline__ int camera_of_tile(const Frame &f, uint32_t tile) {
 
 // preprocess.cu
 cudaError_t launch_preprocess(const Frame &f, int64_t max_k, uint32_t *depth_key, uint32_t *rec_id,
-                              uint2 *rect, Record *rec, Counters *cnt, cudaStream_t s);
+                              uint2 *rect, uint2 *pbox, Record *rec, Counters *cnt, cudaStream_t s);
 cudaError_t launch_preprocess_bwd(const Frame &f, int64_t max_k, const float *rec_grad,
                                   const int32_t *inv_perm, cudaStream_t s);
 
@@ -162,6 +162,7 @@ struct RenderBufs {
     const uint32_t *perm;     // depth-sorted position -> record id
     const uint32_t *inst_val; // sorted instances -> depth-sorted position
     const uint2 *ranges;      // [n_tiles] (begin, end)
+    const uint2 *pbox;        // [records] inclusive pixel rectangle (x0 | y0 << 16, x1 | y1 << 16)
     float *rgb, *depth, *alpha;
     float *t_final;           // [n_pixels]
     uint32_t *last;           // [n_pixels] 1 + index in the tile range of the last blended splat

@@ -263,7 +263,7 @@ __device__ void homography_fp64(const float p[3], const float q[4], float su, fl
 
 // --------------------------------------------------------- forward kernel --
 __global__ void __launch_bounds__(256) preprocess_kernel(Frame f, uint32_t *depth_key,
-                                                         uint32_t *rec_id, uint2 *rect_out,
+                                                         uint32_t *rec_id, uint2 *rect_out, uint2 *pbox,
                                                          Record *rec_out, Counters *cnt) {
     const int ci = blockIdx.y;
     const CamDev &cam = f.cams[ci];
@@ -289,6 +289,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(Frame f, uint32_t *dept
             const int T = f.tile;
             rect_out[r] = make_uint2(uint32_t(pr[0] / T) | (uint32_t(pr[1] / T) << 16),
                                      uint32_t(pr[2] / T) | (uint32_t(pr[3] / T) << 16));
+            pbox[r] = make_uint2(uint32_t(pr[0]) | (uint32_t(pr[1]) << 16), uint32_t(pr[2]) | (uint32_t(pr[3]) << 16));
             // ---- render record ----
             const Frame3 fr = tangent_frame(q);
             // camera-space tangent axes A = s_u R t_u, B = s_v R t_v and normal
@@ -469,10 +470,10 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(Frame f, const floa
 }  // namespace
 
 cudaError_t launch_preprocess(const Frame &f, int64_t max_k, uint32_t *depth_key, uint32_t *rec_id,
-                              uint2 *rect, Record *rec, Counters *cnt, cudaStream_t s) {
+                              uint2 *rect, uint2 *pbox, Record *rec, Counters *cnt, cudaStream_t s) {
     if (max_k <= 0) return cudaSuccess;
     dim3 grid(unsigned(ceil_div(max_k, 256)), unsigned(f.n_cams));
-    preprocess_kernel<<<grid, 256, 0, s>>>(f, depth_key, rec_id, rect, rec, cnt);
+    preprocess_kernel<<<grid, 256, 0, s>>>(f, depth_key, rec_id, rect, pbox, rec, cnt);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -62,7 +62,8 @@ __global__ void __launch_bounds__(TS * TS) render_bwd_kernel(Frame f, RenderBwdB
     float4 *s_tex = s_rec + 4 * batch;
     int32_t *s_k = reinterpret_cast<int32_t *>(s_tex + batch * NN);
     uint32_t *s_j = reinterpret_cast<uint32_t *>(s_k + batch);
-    float *s_g = reinterpret_cast<float *>(s_j + batch);  // [batch][16]
+    uint2 *s_box = reinterpret_cast<uint2 *>(s_j + batch);
+    float *s_g = reinterpret_cast<float *>(s_box + batch);  // [batch][16]
     float *s_tg = s_g + batch * kRecGrad;                  // [batch][TEXF]
     __shared__ uint32_t s_maxlast;
 
@@ -81,6 +82,7 @@ __global__ void __launch_bounds__(TS * TS) render_bwd_kernel(Frame f, RenderBwdB
     const uint2 range = b.fw.ranges[tile];
     const float sigma = sc.sigma;
     const float kN = float(N - 1) / (2.0f * sigma);
+    const WarpBox wb = warp_box<TS>(tx, ty, threadIdx.x);
 
     float T = 1.0f, T_final = 1.0f, dC0 = 0, dC1 = 0, dC2 = 0, dD = 0, dA = 0;
     uint32_t last = 0, npairs = 0;
@@ -110,11 +112,12 @@ __global__ void __launch_bounds__(TS * TS) render_bwd_kernel(Frame f, RenderBwdB
         const int bs = max(0, be - batch), nb = be - bs;
         for (int e = threadIdx.x; e < nb * kRecGrad; e += NT) s_g[e] = 0.0f;
         for (int e = threadIdx.x; e < nb * TEXF; e += NT) s_tg[e] = 0.0f;
-        stage_batch<N, NT, TexT>(b.fw, cam, sc, range.x + bs, nb, s_rec, s_tex, s_k, s_j);
+        stage_batch<N, NT, TexT>(b.fw, cam, sc, range.x + bs, nb, s_rec, s_tex, s_k, s_j, s_box);
         __syncthreads();
         // splats at or beyond the warp's last contributor are skipped warp-wide
         const int i_hi = min(nb, int(wlast) - bs);
         for (int i = i_hi - 1; i >= 0; --i) {
+            if (wb.misses(s_box[i])) continue;
             float g[16];
 #pragma unroll
             for (int q = 0; q < 16; ++q) g[q] = 0.0f;

@@ -14,6 +14,27 @@ __device__ __forceinline__ void tile_pixel(int tid, int &lx, int &ly) {
     ly = (warp / (TS / 8)) * 4 + (lane >> 3);
 }
 
+// The 8 x 4 pixel block of a warp misses a splat's inclusive pixel rectangle:
+// every pixel of the block has alpha < 1/255 for that splat, so the whole
+// warp skips it (the same rectangle decides tile membership).
+struct WarpBox {
+    int x0, y0, x1, y1;
+    __device__ __forceinline__ bool misses(uint2 b) const {
+        return int(b.x & 0xffffu) > x1 || int(b.y & 0xffffu) < x0 || int(b.x >> 16) > y1 || int(b.y >> 16) < y0;
+    }
+};
+
+template <int TS>
+__device__ __forceinline__ WarpBox warp_box(int tx, int ty, int tid) {
+    const int warp = tid >> 5;
+    WarpBox w;
+    w.x0 = tx * TS + (warp % (TS / 8)) * 8;
+    w.y0 = ty * TS + (warp / (TS / 8)) * 4;
+    w.x1 = w.x0 + 7;
+    w.y1 = w.y0 + 3;
+    return w;
+}
+
 // Bytes of dynamic shared memory for one staged batch: records, colour
 // grids, splat indices and (backward) record/grid gradient accumulators.
 // Colour grids are staged as RGBA float4 texels (16 bytes, alpha unused) so a
@@ -21,7 +42,7 @@ __device__ __forceinline__ void tile_pixel(int tid, int &lx, int &ly) {
 template <int N>
 __host__ __device__ inline size_t stage_bytes(int batch, bool bwd) {
     const int texf = N * N * 3;
-    size_t b = size_t(batch) * (64 + 16 * N * N + 8);
+    size_t b = size_t(batch) * (64 + 16 * N * N + 16);
     if (bwd) b += size_t(batch) * (4 * kRecGrad + 4 * texf);
     return b;
 }
@@ -38,12 +59,13 @@ __device__ __forceinline__ float fast_rcp(float x) {
 template <int N, int NT, typename TexT>
 __device__ __forceinline__ void stage_batch(const RenderBufs &b, const CamDev &cam, const SceneDev &sc,
                                             uint32_t first, int nb, float4 *s_rec, float4 *s_tex,
-                                            int32_t *s_k, uint32_t *s_j) {
+                                            int32_t *s_k, uint32_t *s_j, uint2 *s_box) {
     constexpr int NN = N * N;
     const int t = threadIdx.x;
     if (t < nb) {
         const uint32_t j = b.inst_val[first + t];
         const uint32_t r = b.perm[j];
+        s_box[t] = b.pbox[r];
         const float4 *rp = reinterpret_cast<const float4 *>(b.rec + r);
         s_rec[4 * t + 0] = rp[0];
         s_rec[4 * t + 1] = rp[1];

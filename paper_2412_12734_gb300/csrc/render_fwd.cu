@@ -24,6 +24,7 @@ __global__ void __launch_bounds__(TS * TS) render_fwd_kernel(Frame f, RenderBufs
     float4 *s_tex = s_rec + 4 * batch;
     int32_t *s_k = reinterpret_cast<int32_t *>(s_tex + batch * NN);
     uint32_t *s_j = reinterpret_cast<uint32_t *>(s_k + batch);
+    uint2 *s_box = reinterpret_cast<uint2 *>(s_j + batch);
 
     const uint32_t tile = blockIdx.x;
     const int ci = camera_of_tile(f, tile);
@@ -38,6 +39,7 @@ __global__ void __launch_bounds__(TS * TS) render_fwd_kernel(Frame f, RenderBufs
     const float xf = float(px) + 0.5f, yf = float(py) + 0.5f;
     const uint2 range = b.ranges[tile];
     const int n_inst = int(range.y - range.x);
+    const WarpBox wb = warp_box<TS>(tx, ty, threadIdx.x);
     const float sigma = sc.sigma;
     const float kN = float(N - 1) / (2.0f * sigma);
 
@@ -47,12 +49,12 @@ __global__ void __launch_bounds__(TS * TS) render_fwd_kernel(Frame f, RenderBufs
     for (int bs = 0; bs < n_inst; bs += batch) {
         if (__syncthreads_count(done) == NT) break;
         const int nb = min(batch, n_inst - bs);
-        stage_batch<N, NT, TexT>(b, cam, sc, range.x + bs, nb, s_rec, s_tex, s_k, s_j);
+        stage_batch<N, NT, TexT>(b, cam, sc, range.x + bs, nb, s_rec, s_tex, s_k, s_j, s_box);
         __syncthreads();
         if (!done) {
             for (int i = 0; i < nb; ++i) {
                 if (__all_sync(__activemask(), done)) break;
-                if (done) continue;
+                if (done || wb.misses(s_box[i])) continue;
                 ++npairs;
                 const float4 q0 = s_rec[4 * i + 0], q1 = s_rec[4 * i + 1], q2 = s_rec[4 * i + 2];
                 const float dx = (xf - q2.x) - q2.z, dy = (yf - q2.y) - q2.w;
