@@ -53,7 +53,7 @@ __device__ __forceinline__ int scatter_index(int lane) {
 }
 
 template <int TS, int N, typename TexT>
-__global__ void __launch_bounds__(TS * TS) render_bwd_kernel(Frame f, RenderBwdBufs b, int batch) {
+__global__ void __launch_bounds__(TS * TS, 1024 / (TS * TS)) render_bwd_kernel(Frame f, RenderBwdBufs b, int batch) {
     constexpr int NT = TS * TS;
     constexpr int NN = N * N;
     constexpr int TEXF = NN * 3;

@@ -16,7 +16,7 @@ namespace gbill {
 namespace {
 
 template <int TS, int N, typename TexT>
-__global__ void __launch_bounds__(TS * TS) render_fwd_kernel(Frame f, RenderBufs b, int batch) {
+__global__ void __launch_bounds__(TS * TS, 1536 / (TS * TS)) render_fwd_kernel(Frame f, RenderBufs b, int batch) {
     constexpr int NT = TS * TS;
     constexpr int NN = N * N;
     extern __shared__ float4 smem[];
