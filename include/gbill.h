@@ -264,6 +264,38 @@ gb_status gb_render_backward(gb_context *ctx, gb_saved *saved, const float *d_rg
                              const float *d_depth, const float *d_alpha, const gb_grads *grads,
                              int32_t n_scenes, void *stream);
 
+/* ------------------------------------------------------------------ adam -- */
+
+/* One tensor of a fused Adam step (the optimiser of Sec. 3.3).  All pointers
+ * are device pointers of n elements; param, m and v are FP32 and updated in
+ * place; grad is read.  shadow (nullable) receives the updated parameter in
+ * shadow_dtype (FP16/BF16 storage read by the renderer, or FP32). */
+typedef struct {
+    float *param;
+    const float *grad;
+    float *m, *v;
+    void *shadow;
+    int32_t shadow_dtype; /* gb_dtype */
+    int32_t reserved;     /* must be 0 */
+    int64_t n;
+} gb_adam_tensor;
+
+/* Adam hyper-parameters; step is the 1-based iteration used for the bias
+ * corrections 1 - beta^step. */
+typedef struct {
+    float lr, beta1, beta2, eps;
+    int32_t step;
+    int32_t reserved; /* must be 0 */
+} gb_adam_config;
+
+/* m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps), in FP32, for every
+ * element of up to 16 tensors in one launch on `stream` (host array `tensors`).
+ * GB_ERR_INVALID_ARG for bad counts, null pointers, beta outside [0,1),
+ * step < 1. */
+gb_status gb_adam_step(gb_context *ctx, const gb_adam_tensor *tensors, int32_t n_tensors,
+                       const gb_adam_config *cfg, void *stream);
+
 /* ---------------------------------------------------------------- tuning -- */
 
 /* Autotuner: times forward + backward of this frame for every candidate

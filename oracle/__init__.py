@@ -311,3 +311,16 @@ def pixel_trace(scene: dict, cam: dict, px: int, py: int, cap: int = 4096) -> di
                               C.c_int32(cap), _p(ids), _p(a), _p(tr), _p(tf))
     n = min(n, cap)
     return {"ids": ids[:n], "alpha": a[:n], "trans": tr[:n], "t_final": float(tf[0])}
+
+
+def adam_step(param, grad, m, v, step: int, lr: float, beta1: float, beta2: float, eps: float):
+    """Adam (Kingma & Ba, Algorithm 1; the optimiser of Sec. 3.3) in FP64.
+
+    Returns the new (param, m, v); inputs are not modified."""
+    p = np.asarray(param, np.float64)
+    g = np.asarray(grad, np.float64)
+    m = beta1 * np.asarray(m, np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, np.float64) + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** step)
+    v_hat = v / (1.0 - beta2 ** step)
+    return p - lr * m_hat / (np.sqrt(v_hat) + eps), m, v

@@ -53,6 +53,16 @@ class gb_options(C.Structure):
                 ("reserved", C.c_int32), ("background", C.c_float * 3)]
 
 
+class gb_adam_tensor(C.Structure):
+    _fields_ = [("param", C.c_void_p), ("grad", C.c_void_p), ("m", C.c_void_p), ("v", C.c_void_p),
+                ("shadow", C.c_void_p), ("shadow_dtype", C.c_int32), ("reserved", C.c_int32), ("n", C.c_int64)]
+
+
+class gb_adam_config(C.Structure):
+    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("step", C.c_int32), ("reserved", C.c_int32)]
+
+
 class gb_stats(C.Structure):
     _fields_ = [("records", C.c_int64), ("visible", C.c_int64), ("instances", C.c_int64),
                 ("tiles", C.c_int64), ("pixels", C.c_int64), ("capacity", C.c_int64),
@@ -102,6 +112,7 @@ def load() -> C.CDLL:
         "gb_render_forward": (C.c_int, [vp, vp, C.POINTER(gb_scene), i32, C.POINTER(gb_camera), i32,
                                         C.POINTER(gb_options), vp, vp, vp, vp]),
         "gb_render_backward": (C.c_int, [vp, vp, vp, vp, vp, C.POINTER(gb_grads), i32, vp]),
+        "gb_adam_step": (C.c_int, [vp, C.POINTER(gb_adam_tensor), i32, C.POINTER(gb_adam_config), vp]),
         "gb_autotune": (C.c_int, [vp, vp, C.POINTER(gb_scene), i32, C.POINTER(gb_camera), i32,
                                   C.POINTER(gb_options), i32, C.POINTER(gb_options), vp, vp, vp, i32,
                                   C.POINTER(i32)]),

@@ -624,6 +624,29 @@ gb_status gb_render_backward(gb_context *ctx, gb_saved *s, const float *d_rgb, c
     return GB_OK;
 }
 
+gb_status gb_adam_step(gb_context *ctx, const gb_adam_tensor *tensors, int32_t n_tensors,
+                       const gb_adam_config *cfg, void *stream) {
+    if (!ctx) return GB_ERR_INVALID_ARG;
+    if (!tensors || !cfg || n_tensors < 1 || n_tensors > 16)
+        return fail(ctx, GB_ERR_INVALID_ARG, "n_tensors must be in 1..16 with a config");
+    if (cfg->step < 1 || !(cfg->beta1 >= 0.0f && cfg->beta1 < 1.0f) || !(cfg->beta2 >= 0.0f && cfg->beta2 < 1.0f) ||
+        !(cfg->eps >= 0.0f) || !isfinite(cfg->lr) || cfg->reserved != 0)
+        return fail(ctx, GB_ERR_INVALID_ARG, "bad Adam hyper-parameters");
+    int64_t biggest = 0;
+    for (int i = 0; i < n_tensors; ++i) {
+        const gb_adam_tensor &t = tensors[i];
+        if (t.n < 0 || t.reserved != 0 || (t.n > 0 && (!t.param || !t.grad || !t.m || !t.v)))
+            return fail(ctx, GB_ERR_INVALID_ARG, "adam tensor %d: bad pointer or size", i);
+        if (t.shadow && !dtype_ok(t.shadow_dtype))
+            return fail(ctx, GB_ERR_INVALID_ARG, "adam tensor %d: bad shadow dtype", i);
+        biggest = std::max(biggest, t.n);
+    }
+    // enough blocks to fill the GPU (152 SMs x 8 resident 256-thread blocks) per tensor
+    const int grid_x = int(std::max<int64_t>(1, std::min<int64_t>(ceil_div(biggest, 4 * 256), 152 * 8)));
+    GB_CUDA(ctx, launch_adam(tensors, n_tensors, *cfg, grid_x, static_cast<cudaStream_t>(stream)));
+    return GB_OK;
+}
+
 __global__ void fill_kernel(float *p, int64_t n, float v) {
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
         p[i] = v;

@@ -156,6 +156,9 @@ cudaError_t launch_export_keys(const Frame &f, const uint32_t *tiles_sorted,
                                const uint32_t *depth_key_by_rec, int64_t n, uint64_t *keys,
                                int64_t *ids, int32_t *cams, cudaStream_t s);
 
+// adam.cu
+cudaError_t launch_adam(const gb_adam_tensor *ts, int n, const gb_adam_config &c, int grid_x, cudaStream_t s);
+
 // render_fwd.cu / render_bwd.cu
 struct RenderBufs {
     const Record *rec;        // indexed by record id

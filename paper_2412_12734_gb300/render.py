@@ -325,3 +325,27 @@ def render(means, quats, scales, opacities, sh, textures, cams, sh_degree: int, 
     rast = rasterizer or default_rasterizer()
     meta = (rast, list(cams), int(sh_degree), int(tex_n), float(sigma), background)
     return _RenderFn.apply(means, quats, scales, opacities, sh, textures, meta)
+
+
+def adam_step(rast: Rasterizer, params: list, grads: list, ms: list, vs: list, step: int, lr: float = 1e-3,
+              betas=(0.9, 0.999), eps: float = 1e-15, shadows=None, stream=None):
+    """Fused Adam over up to 16 FP32 tensors in one launch (gb_adam_step).
+
+    shadows[i] (optional) receives the updated params[i] in its own dtype
+    (e.g. the BF16 textures the renderer reads)."""
+    n = len(params)
+    arr = (L.gb_adam_tensor * n)()
+    for i in range(n):
+        p, g, m, v = params[i], grads[i], ms[i], vs[i]
+        for t in (p, g, m, v):
+            if t.dtype != torch.float32 or not t.is_contiguous() or t.numel() != p.numel():
+                raise ValueError("adam tensors must be contiguous float32 of equal size")
+        arr[i].param, arr[i].grad, arr[i].m, arr[i].v = p.data_ptr(), g.data_ptr(), m.data_ptr(), v.data_ptr()
+        sh = shadows[i] if shadows is not None else None
+        arr[i].shadow = sh.data_ptr() if sh is not None else None
+        arr[i].shadow_dtype = DTYPES[sh.dtype] if sh is not None else 0
+        arr[i].reserved = 0
+        arr[i].n = p.numel()
+    cfg = L.gb_adam_config(float(lr), float(betas[0]), float(betas[1]), float(eps), int(step), 0)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    L.check(L.load().gb_adam_step(rast.ctx, arr, n, C.byref(cfg), C.c_void_p(s.cuda_stream)), rast.ctx)
