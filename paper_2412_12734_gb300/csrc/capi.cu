@@ -38,6 +38,9 @@ struct gb_saved {
     float *rec_grad;
     uint32_t *inst_tile, *inst_val, *inst_tile_tmp, *inst_val_tmp, *tiles_sorted, *vals_sorted;
     uint2 *ranges;
+    uint32_t *tl_keys, *tl_vals, *tl_keys_tmp, *tl_vals_tmp, *tl_keys_out, *tile_list;
+    uint32_t *work;  // [2 * kMaxGroups] persistent-render work counters (forward, backward)
+    bool use_list;
     float *t_final;
     uint32_t *last;
     Counters *cnt;
@@ -143,12 +146,19 @@ gb_status reserve_tiles(gb_saved *s, int64_t n) {
     gb_context *ctx = s->ctx;
     GB_CUDA(ctx, cudaDeviceSynchronize());
     GB_CUDA(ctx, alloc_t(&s->ranges, n));
+    GB_CUDA(ctx, alloc_t(&s->tl_keys, n));
+    GB_CUDA(ctx, alloc_t(&s->tl_vals, n));
+    GB_CUDA(ctx, alloc_t(&s->tl_keys_tmp, n));
+    GB_CUDA(ctx, alloc_t(&s->tl_vals_tmp, n));
+    GB_CUDA(ctx, alloc_t(&s->tl_keys_out, n));
+    GB_CUDA(ctx, alloc_t(&s->tile_list, n));
+    if (!s->work) GB_CUDA(ctx, alloc_t(&s->work, 2 * kMaxGroups));
     s->cap_tiles = n;
     return GB_OK;
 }
 
 gb_status reserve_scratch(gb_saved *s) {
-    const size_t need = std::max(radix_scratch_bytes(std::max(s->cap_rec, s->cap_inst)),
+    const size_t need = std::max(radix_scratch_bytes(std::max(std::max(s->cap_rec, s->cap_inst), s->cap_tiles)),
                                  scan_scratch_bytes(s->cap_rec)) + 1024;
     if (need <= s->scratch_bytes) return GB_OK;
     gb_context *ctx = s->ctx;
@@ -216,8 +226,6 @@ gb_status build_frame(gb_context *ctx, const gb_scene *scenes, int32_t n_scenes,
         if (g.reserved != 0) return fail(ctx, GB_ERR_INVALID_ARG, "scene %d: reserved field must be 0", s);
         if (g.num_splats > 0 && (!g.means || !g.quats || !g.scales || !g.opacities || !g.sh || !g.textures))
             return fail(ctx, GB_ERR_INVALID_ARG, "scene %d: null parameter pointer", s);
-        if (g.tex_n != scenes[0].tex_n || g.tex_dtype != scenes[0].tex_dtype)
-            return fail(ctx, GB_ERR_UNSUPPORTED, "scenes of one call must share tex_n and tex_dtype");
         d.K = g.num_splats;
         d.means = g.means;
         d.quats = g.quats;
@@ -231,6 +239,19 @@ gb_status build_frame(gb_context *ctx, const gb_scene *scenes, int32_t n_scenes,
         d.tex_dtype = g.tex_dtype;
         d.sigma = g.sigma;
         max_k = std::max(max_k, g.num_splats);
+    }
+    // render groups: one per distinct (tex_n, tex_dtype) among the cameras' scenes
+    int scene_group[kMaxScenes];
+    for (int sidx = 0; sidx < n_scenes; ++sidx) {
+        int g = -1;
+        for (int k = 0; k < f.n_groups; ++k)
+            if (f.group_N[k] == scenes[sidx].tex_n && f.group_dtype[k] == scenes[sidx].tex_dtype) g = k;
+        if (g < 0) {
+            g = f.n_groups++;
+            f.group_N[g] = scenes[sidx].tex_n;
+            f.group_dtype[g] = scenes[sidx].tex_dtype;
+        }
+        scene_group[sidx] = g;
     }
     int64_t tiles = 0, pix = 0, rec = 0;
     for (int c = 0; c < n_cams; ++c) {
@@ -256,6 +277,8 @@ gb_status build_frame(gb_context *ctx, const gb_scene *scenes, int32_t n_scenes,
             d.campos[i] = -(d.R[i] * d.t[0] + d.R[3 + i] * d.t[1] + d.R[6 + i] * d.t[2]);
         d.near_plane = g.near_plane;
         d.scene = g.scene;
+        d.group = scene_group[g.scene];
+        f.group_count[d.group] += uint32_t(int64_t(d.tiles_x) * d.tiles_y);
         d.tile_off = uint32_t(tiles);
         d.pix_off = pix;
         d.rec_off = rec;
@@ -269,6 +292,11 @@ gb_status build_frame(gb_context *ctx, const gb_scene *scenes, int32_t n_scenes,
     f.n_tiles = uint32_t(tiles);
     f.n_pixels = pix;
     f.n_records = rec;
+    uint32_t off = 0;
+    for (int k = 0; k < f.n_groups; ++k) {
+        f.group_off[k] = off;
+        off += f.group_count[k];
+    }
     return GB_OK;
 }
 
@@ -347,7 +375,8 @@ gb_status gb_saved_destroy(gb_saved *s) {
     cudaDeviceSynchronize();
     void *ptrs[] = {s->rec, s->depth_key, s->rec_id, s->keys_tmp, s->vals_tmp, s->dkeys_sorted, s->perm,
                     s->offsets, s->rect, s->pbox, s->inv, s->rec_grad, s->inst_tile, s->inst_val, s->inst_tile_tmp,
-                    s->inst_val_tmp, s->tiles_sorted, s->vals_sorted, s->ranges, s->t_final, s->last,
+                    s->inst_val_tmp, s->tiles_sorted, s->vals_sorted, s->ranges, s->tl_keys, s->tl_vals,
+                    s->tl_keys_tmp, s->tl_vals_tmp, s->tl_keys_out, s->tile_list, s->work, s->t_final, s->last,
                     s->cnt, s->scratch};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -479,7 +508,8 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
     int64_t max_k = 0;
     gb_status r = build_frame(ctx, scenes, n_scenes, cams, n_cams, tile, o.background, f, max_k);
     if (r != GB_OK) return r;
-    const int N = scenes[0].tex_n;
+    int N = 1;
+    for (int k = 0; k < f.n_groups; ++k) N = std::max(N, f.group_N[k]);
     const int nt = tile * tile;
     int bf = o.batch_depth ? o.batch_depth : std::min(default_batch(N, false), nt);
     int bb = o.batch_depth ? o.batch_depth : std::min(default_batch(N, true), nt);
@@ -549,6 +579,16 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
     GB_MARK(5);
     GB_CUDA(ctx, launch_ranges(s->tiles_sorted, inst_max, s->cnt, s->ranges, st));
     GB_MARK(6);
+    const bool persistent = (o.flags & GB_FLAG_PERSISTENT) != 0;
+    s->use_list = persistent || f.n_groups > 1;
+    if (s->use_list) {
+        int kbits = 24;
+        while ((1 << (kbits - 24)) < f.n_groups) ++kbits;
+        GB_CUDA(ctx, launch_tile_list(f, s->ranges, s->tl_keys, s->tl_vals, st));
+        GB_CUDA(ctx, radix_sort_pairs(s->tl_keys, s->tl_vals, s->tl_keys_tmp, s->tl_vals_tmp, s->tl_keys_out,
+                                      s->tile_list, f.n_tiles, nullptr, 0, kbits, s->scratch, s->scratch_bytes, st));
+        GB_CUDA(ctx, cudaMemsetAsync(s->work, 0, 2 * kMaxGroups * sizeof(uint32_t), st));
+    }
     RenderBufs b;
     b.rec = s->rec;
     b.perm = s->perm;
@@ -561,7 +601,8 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
     b.t_final = s->t_final;
     b.last = s->last;
     b.cnt = s->cnt;
-    GB_CUDA(ctx, launch_render_fwd(f, b, bf, st));
+    GB_CUDA(ctx, launch_render_fwd(f, b, bf, s->use_list ? s->tile_list : nullptr, persistent ? s->work : nullptr,
+                                   persistent, st));
     GB_MARK(7);
 #undef GB_MARK
     s->timed_fwd = timing;
@@ -616,7 +657,9 @@ gb_status gb_render_backward(gb_context *ctx, gb_saved *s, const float *d_rgb, c
     b.d_alpha = d_alpha;
     b.rec_grad = s->rec_grad;
     GB_CUDA(ctx, cudaMemsetAsync(&s->cnt->pairs_bwd, 0, sizeof(unsigned long long), st));
-    GB_CUDA(ctx, launch_render_bwd(f, b, s->batch_bwd, st));
+    const bool persistent = (s->flags & GB_FLAG_PERSISTENT) != 0;
+    GB_CUDA(ctx, launch_render_bwd(f, b, s->batch_bwd, s->use_list ? s->tile_list : nullptr,
+                                   persistent ? s->work + kMaxGroups : nullptr, persistent, st));
     if (timing) GB_CUDA(ctx, cudaEventRecord(s->ev[10], st));
     GB_CUDA(ctx, launch_preprocess_bwd(f, s->max_k, s->rec_grad, s->inv, st));
     if (timing) GB_CUDA(ctx, cudaEventRecord(s->ev[11], st));
@@ -663,7 +706,8 @@ gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int3
     int64_t max_k = 0;
     gb_status r = build_frame(ctx, scenes, n_scenes, cams, n_cams, 16, nullptr, f, max_k);
     if (r != GB_OK) return r;
-    const int N = scenes[0].tex_n;
+    int N = 1;
+    for (int k = 0; k < f.n_groups; ++k) N = std::max(N, f.group_N[k]);
     // scratch buffers owned by this call
     float *rgb = nullptr, *dep = nullptr, *alp = nullptr, *drgb = nullptr, *gbuf = nullptr;
     size_t gtot = 0;

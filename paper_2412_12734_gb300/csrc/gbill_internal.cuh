@@ -13,6 +13,7 @@ namespace gbill {
 
 constexpr int kMaxCams = GBILL_MAX_CAMERAS;
 constexpr int kMaxScenes = GBILL_MAX_SCENES;
+constexpr int kMaxGroups = 12;  // distinct (texture size, storage type) pairs of a frame
 
 // Constants of the method (Sec. 3.1 Eq. 4 with the 3DGS-lineage clamp and
 // cutoffs; the screen-space low-pass of the 2DGS lineage).
@@ -34,6 +35,7 @@ struct CamDev {
     float campos[3];
     float near_plane;
     int32_t scene;
+    int32_t group;      // render group: cameras whose scenes share (tex_n, tex_dtype)
     uint32_t tile_off;  // first global tile id of this camera
     int64_t pix_off;    // first pixel of this camera in the packed outputs
     int64_t rec_off;    // first record (= tile_off-like offset over splats)
@@ -57,9 +59,11 @@ struct Frame {
     int64_t n_records;
     int64_t n_pixels;
     uint32_t n_tiles;
-    uint32_t pad;
+    int32_t n_groups;
     float bg[3];
     float pad2;
+    int32_t group_N[kMaxGroups], group_dtype[kMaxGroups];
+    uint32_t group_off[kMaxGroups], group_count[kMaxGroups];  // segments of the tile list
     CamDev cams[kMaxCams];
     SceneDev scenes[kMaxScenes];
 };
@@ -171,13 +175,24 @@ struct RenderBufs {
     uint32_t *last;           // [n_pixels] 1 + index in the tile range of the last blended splat
     Counters *cnt;
 };
-cudaError_t launch_render_fwd(const Frame &f, const RenderBufs &b, int batch, cudaStream_t s);
+// Which tiles a render launch processes: tile = list[off + i] (or off + i when
+// list is null) for i < count; with `work` set, blocks are persistent and pull
+// i from that device counter.
+struct TileSched {
+    const uint32_t *list;
+    uint32_t off, count;
+    uint32_t *work;
+};
+cudaError_t launch_render_fwd(const Frame &f, const RenderBufs &b, int batch, const uint32_t *tile_list,
+                              uint32_t *work, bool persistent, cudaStream_t s);
+cudaError_t launch_tile_list(const Frame &f, const uint2 *ranges, uint32_t *keys, uint32_t *vals, cudaStream_t s);
 
 struct RenderBwdBufs {
     RenderBufs fw;
     const float *d_rgb, *d_depth, *d_alpha;
     float *rec_grad;          // [n_visible, 16], indexed by depth-sorted position
 };
-cudaError_t launch_render_bwd(const Frame &f, const RenderBwdBufs &b, int batch, cudaStream_t s);
+cudaError_t launch_render_bwd(const Frame &f, const RenderBwdBufs &b, int batch, const uint32_t *tile_list,
+                              uint32_t *work, bool persistent, cudaStream_t s);
 
 }  // namespace gbill

@@ -13,6 +13,8 @@
 // shared memory and added to global memory with one atomic per value per tile;
 // colour-grid gradients are summed per batch in shared memory and added to the
 // global texel gradient with one atomic per non-zero texel channel per tile.
+#include <algorithm>
+
 #include "render_common.cuh"
 
 namespace gbill {
@@ -53,7 +55,7 @@ __device__ __forceinline__ int scatter_index(int lane) {
 }
 
 template <int TS, int N, typename TexT>
-__global__ void __launch_bounds__(TS * TS, 1024 / (TS * TS)) render_bwd_kernel(Frame f, RenderBwdBufs b, int batch) {
+__device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b, int batch, uint32_t tile) {
     constexpr int NT = TS * TS;
     constexpr int NN = N * N;
     constexpr int TEXF = NN * 3;
@@ -67,7 +69,6 @@ __global__ void __launch_bounds__(TS * TS, 1024 / (TS * TS)) render_bwd_kernel(F
     float *s_tg = s_g + batch * kRecGrad;                  // [batch][TEXF]
     __shared__ uint32_t s_maxlast;
 
-    const uint32_t tile = blockIdx.x;
     const int ci = camera_of_tile(f, tile);
     const CamDev &cam = f.cams[ci];
     const SceneDev &sc = f.scenes[cam.scene];
@@ -271,7 +272,28 @@ __global__ void __launch_bounds__(TS * TS, 1024 / (TS * TS)) render_bwd_kernel(F
 }
 
 template <int TS, int N, typename TexT>
-cudaError_t launch_t(const Frame &f, const RenderBwdBufs &b, int batch, cudaStream_t s) {
+__global__ void __launch_bounds__(TS * TS, 1024 / (TS * TS)) render_bwd_kernel(Frame f, RenderBwdBufs b, int batch, TileSched ts) {
+    __shared__ uint32_t s_next;
+    for (int round = 0;; ++round) {
+        uint32_t idx;
+        if (ts.work) {
+            __syncthreads();
+            if (threadIdx.x == 0) s_next = atomicAdd(ts.work, 1u);
+            __syncthreads();
+            idx = s_next;
+        } else {
+            if (round) break;
+            idx = blockIdx.x;
+        }
+        if (idx >= ts.count) break;
+        const uint32_t tile = ts.list ? ts.list[ts.off + idx] : ts.off + idx;
+        bwd_tile<TS, N, TexT>(f, b, batch, tile);
+    }
+}
+
+template <int TS, int N, typename TexT>
+cudaError_t launch_t(const Frame &f, const RenderBwdBufs &b, int batch, TileSched ts, bool persistent,
+                     cudaStream_t s) {
     const size_t smem = stage_bytes<N>(batch, true);
     static bool configured = false;
     if (!configured) {
@@ -280,40 +302,71 @@ cudaError_t launch_t(const Frame &f, const RenderBwdBufs &b, int batch, cudaStre
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    render_bwd_kernel<TS, N, TexT><<<f.n_tiles, TS * TS, smem, s>>>(f, b, batch);
+    unsigned grid = ts.count;
+    if (persistent) {
+        static int per_sm = 0, sms = 0;
+        static size_t smem_seen = 0;
+        if (!per_sm || smem_seen != smem) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_bwd_kernel<TS, N, TexT>, TS * TS, smem);
+            smem_seen = smem;
+            if (per_sm < 1) per_sm = 1;
+        }
+        grid = std::min<unsigned>(grid, unsigned(per_sm * sms));
+    } else {
+        ts.work = nullptr;
+    }
+    if (grid == 0) return cudaSuccess;
+    render_bwd_kernel<TS, N, TexT><<<grid, TS * TS, smem, s>>>(f, b, batch, ts);
     count_launches(1);
     return cudaGetLastError();
 }
 
 template <int TS, typename TexT>
-cudaError_t launch_n(const Frame &f, const RenderBwdBufs &b, int N, int batch, cudaStream_t s) {
+cudaError_t launch_n(const Frame &f, const RenderBwdBufs &b, int N, int batch, TileSched ts, bool persistent,
+                     cudaStream_t s) {
     switch (N) {
-        case 1: return launch_t<TS, 1, TexT>(f, b, batch, s);
-        case 2: return launch_t<TS, 2, TexT>(f, b, batch, s);
-        case 4: return launch_t<TS, 4, TexT>(f, b, batch, s);
-        case 8: return launch_t<TS, 8, TexT>(f, b, batch, s);
+        case 1: return launch_t<TS, 1, TexT>(f, b, batch, ts, persistent, s);
+        case 2: return launch_t<TS, 2, TexT>(f, b, batch, ts, persistent, s);
+        case 4: return launch_t<TS, 4, TexT>(f, b, batch, ts, persistent, s);
+        case 8: return launch_t<TS, 8, TexT>(f, b, batch, ts, persistent, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
 }  // namespace
 
-cudaError_t launch_render_bwd(const Frame &f, const RenderBwdBufs &b, int batch, cudaStream_t s) {
+cudaError_t launch_render_bwd(const Frame &f, const RenderBwdBufs &b, int batch, const uint32_t *tile_list,
+                              uint32_t *work, bool persistent, cudaStream_t s) {
     if (f.n_tiles == 0) return cudaSuccess;
-    const SceneDev &sc = f.scenes[0];
-    if (f.tile == 8) {
-        switch (sc.tex_dtype) {
-            case GB_F16: return launch_n<8, __half>(f, b, sc.N, batch, s);
-            case GB_BF16: return launch_n<8, __nv_bfloat16>(f, b, sc.N, batch, s);
-            default: return launch_n<8, float>(f, b, sc.N, batch, s);
+    for (int g = 0; g < f.n_groups; ++g) {
+        TileSched ts;
+        ts.list = tile_list;
+        ts.off = tile_list ? f.group_off[g] : 0;
+        ts.count = tile_list ? f.group_count[g] : f.n_tiles;
+        ts.work = work ? work + g : nullptr;
+        const int N = f.group_N[g];
+        cudaError_t e;
+        if (f.tile == 8) {
+            switch (f.group_dtype[g]) {
+                case GB_F16: e = launch_n<8, __half>(f, b, N, batch, ts, persistent, s); break;
+                case GB_BF16: e = launch_n<8, __nv_bfloat16>(f, b, N, batch, ts, persistent, s); break;
+                default: e = launch_n<8, float>(f, b, N, batch, ts, persistent, s); break;
+            }
+        } else if (f.tile == 16) {
+            switch (f.group_dtype[g]) {
+                case GB_F16: e = launch_n<16, __half>(f, b, N, batch, ts, persistent, s); break;
+                case GB_BF16: e = launch_n<16, __nv_bfloat16>(f, b, N, batch, ts, persistent, s); break;
+                default: e = launch_n<16, float>(f, b, N, batch, ts, persistent, s); break;
+            }
+        } else {
+            return cudaErrorInvalidValue;
         }
+        if (e != cudaSuccess) return e;
     }
-    if (f.tile != 16) return cudaErrorInvalidValue;
-    switch (sc.tex_dtype) {
-        case GB_F16: return launch_n<16, __half>(f, b, sc.N, batch, s);
-        case GB_BF16: return launch_n<16, __nv_bfloat16>(f, b, sc.N, batch, s);
-        default: return launch_n<16, float>(f, b, sc.N, batch, s);
-    }
+    return cudaSuccess;
 }
 
 }  // namespace gbill

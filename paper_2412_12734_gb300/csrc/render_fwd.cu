@@ -10,13 +10,15 @@
 //   c = bilinear(C_k, u, v) + SH colour       (Eq. 5, Alg. 2, Sec. 4.2)
 //   C += c alpha T, D += z alpha T, T *= 1 - alpha   (Eq. 2)
 // Saved for the backward: final T and 1 + index of the last blended splat.
+#include <algorithm>
+
 #include "render_common.cuh"
 
 namespace gbill {
 namespace {
 
 template <int TS, int N, typename TexT>
-__global__ void __launch_bounds__(TS * TS, 1536 / (TS * TS)) render_fwd_kernel(Frame f, RenderBufs b, int batch) {
+__device__ __forceinline__ void fwd_tile(const Frame &f, const RenderBufs &b, int batch, uint32_t tile) {
     constexpr int NT = TS * TS;
     constexpr int NN = N * N;
     extern __shared__ float4 smem[];
@@ -26,7 +28,6 @@ __global__ void __launch_bounds__(TS * TS, 1536 / (TS * TS)) render_fwd_kernel(F
     uint32_t *s_j = reinterpret_cast<uint32_t *>(s_k + batch);
     uint2 *s_box = reinterpret_cast<uint2 *>(s_j + batch);
 
-    const uint32_t tile = blockIdx.x;
     const int ci = camera_of_tile(f, tile);
     const CamDev &cam = f.cams[ci];
     const SceneDev &sc = f.scenes[cam.scene];
@@ -105,7 +106,28 @@ __global__ void __launch_bounds__(TS * TS, 1536 / (TS * TS)) render_fwd_kernel(F
 }
 
 template <int TS, int N, typename TexT>
-cudaError_t launch_t(const Frame &f, const RenderBufs &b, int batch, cudaStream_t s) {
+__global__ void __launch_bounds__(TS * TS, 1536 / (TS * TS)) render_fwd_kernel(Frame f, RenderBufs b, int batch, TileSched ts) {
+    __shared__ uint32_t s_next;
+    for (int round = 0;; ++round) {
+        uint32_t idx;
+        if (ts.work) {
+            __syncthreads();
+            if (threadIdx.x == 0) s_next = atomicAdd(ts.work, 1u);
+            __syncthreads();
+            idx = s_next;
+        } else {
+            if (round) break;
+            idx = blockIdx.x;
+        }
+        if (idx >= ts.count) break;
+        const uint32_t tile = ts.list ? ts.list[ts.off + idx] : ts.off + idx;
+        fwd_tile<TS, N, TexT>(f, b, batch, tile);
+    }
+}
+
+template <int TS, int N, typename TexT>
+cudaError_t launch_t(const Frame &f, const RenderBufs &b, int batch, TileSched ts, bool persistent,
+                     cudaStream_t s) {
     const size_t smem = stage_bytes<N>(batch, false);
     static bool configured = false;
     if (!configured) {
@@ -114,41 +136,71 @@ cudaError_t launch_t(const Frame &f, const RenderBufs &b, int batch, cudaStream_
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    render_fwd_kernel<TS, N, TexT><<<f.n_tiles, TS * TS, smem, s>>>(f, b, batch);
+    unsigned grid = ts.count;
+    if (persistent) {
+        static int per_sm = 0, sms = 0;
+        static size_t smem_seen = 0;
+        if (!per_sm || smem_seen != smem) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_fwd_kernel<TS, N, TexT>, TS * TS, smem);
+            smem_seen = smem;
+            if (per_sm < 1) per_sm = 1;
+        }
+        grid = std::min<unsigned>(grid, unsigned(per_sm * sms));
+    } else {
+        ts.work = nullptr;
+    }
+    if (grid == 0) return cudaSuccess;
+    render_fwd_kernel<TS, N, TexT><<<grid, TS * TS, smem, s>>>(f, b, batch, ts);
     count_launches(1);
     return cudaGetLastError();
 }
 
 template <int TS, typename TexT>
-cudaError_t launch_n(const Frame &f, const RenderBufs &b, int N, int batch, cudaStream_t s) {
+cudaError_t launch_n(const Frame &f, const RenderBufs &b, int N, int batch, TileSched ts, bool persistent,
+                     cudaStream_t s) {
     switch (N) {
-        case 1: return launch_t<TS, 1, TexT>(f, b, batch, s);
-        case 2: return launch_t<TS, 2, TexT>(f, b, batch, s);
-        case 4: return launch_t<TS, 4, TexT>(f, b, batch, s);
-        case 8: return launch_t<TS, 8, TexT>(f, b, batch, s);
+        case 1: return launch_t<TS, 1, TexT>(f, b, batch, ts, persistent, s);
+        case 2: return launch_t<TS, 2, TexT>(f, b, batch, ts, persistent, s);
+        case 4: return launch_t<TS, 4, TexT>(f, b, batch, ts, persistent, s);
+        case 8: return launch_t<TS, 8, TexT>(f, b, batch, ts, persistent, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
 }  // namespace
 
-cudaError_t launch_render_fwd(const Frame &f, const RenderBufs &b, int batch, cudaStream_t s) {
+cudaError_t launch_render_fwd(const Frame &f, const RenderBufs &b, int batch, const uint32_t *tile_list,
+                              uint32_t *work, bool persistent, cudaStream_t s) {
     if (f.n_tiles == 0) return cudaSuccess;
-    // every scene of a launch shares tex_n and tex_dtype (checked by the caller)
-    const SceneDev &sc = f.scenes[0];
-    if (f.tile == 8) {
-        switch (sc.tex_dtype) {
-            case GB_F16: return launch_n<8, __half>(f, b, sc.N, batch, s);
-            case GB_BF16: return launch_n<8, __nv_bfloat16>(f, b, sc.N, batch, s);
-            default: return launch_n<8, float>(f, b, sc.N, batch, s);
+    for (int g = 0; g < f.n_groups; ++g) {
+        TileSched ts;
+        ts.list = tile_list;
+        ts.off = tile_list ? f.group_off[g] : 0;
+        ts.count = tile_list ? f.group_count[g] : f.n_tiles;
+        ts.work = work ? work + g : nullptr;
+        const int N = f.group_N[g];
+        cudaError_t e;
+        if (f.tile == 8) {
+            switch (f.group_dtype[g]) {
+                case GB_F16: e = launch_n<8, __half>(f, b, N, batch, ts, persistent, s); break;
+                case GB_BF16: e = launch_n<8, __nv_bfloat16>(f, b, N, batch, ts, persistent, s); break;
+                default: e = launch_n<8, float>(f, b, N, batch, ts, persistent, s); break;
+            }
+        } else if (f.tile == 16) {
+            switch (f.group_dtype[g]) {
+                case GB_F16: e = launch_n<16, __half>(f, b, N, batch, ts, persistent, s); break;
+                case GB_BF16: e = launch_n<16, __nv_bfloat16>(f, b, N, batch, ts, persistent, s); break;
+                default: e = launch_n<16, float>(f, b, N, batch, ts, persistent, s); break;
+            }
+        } else {
+            return cudaErrorInvalidValue;
         }
+        if (e != cudaSuccess) return e;
     }
-    if (f.tile != 16) return cudaErrorInvalidValue;
-    switch (sc.tex_dtype) {
-        case GB_F16: return launch_n<16, __half>(f, b, sc.N, batch, s);
-        case GB_BF16: return launch_n<16, __nv_bfloat16>(f, b, sc.N, batch, s);
-        default: return launch_n<16, float>(f, b, sc.N, batch, s);
-    }
+    return cudaSuccess;
 }
 
 }  // namespace gbill

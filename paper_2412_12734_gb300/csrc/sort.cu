@@ -282,7 +282,25 @@ __global__ void export_keys_kernel(Frame f, const uint32_t *tiles, const uint32_
     cams[i] = ci;
 }
 
+// Sort key of a tile: its render group, then instance count, largest first.
+__global__ void tile_key_kernel(Frame f, const uint2 *ranges, uint32_t *keys, uint32_t *vals) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= f.n_tiles) return;
+    const int ci = camera_of_tile(f, t);
+    const uint2 r = ranges[t];
+    const uint32_t cost = min(r.y - r.x, 0xFFFFFFu);
+    keys[t] = (uint32_t(f.cams[ci].group) << 24) | (0xFFFFFFu - cost);
+    vals[t] = t;
+}
+
 }  // namespace
+
+cudaError_t launch_tile_list(const Frame &f, const uint2 *ranges, uint32_t *keys, uint32_t *vals, cudaStream_t s) {
+    if (f.n_tiles == 0) return cudaSuccess;
+    tile_key_kernel<<<unsigned(ceil_div(f.n_tiles, 256)), 256, 0, s>>>(f, ranges, keys, vals);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 size_t radix_scratch_bytes(int64_t n) {
     const int64_t nb = ceil_div(n, kSortTile);
