@@ -54,7 +54,8 @@ def test_gpu_adam_matches_oracle():
         shadows.append(torch.empty(n, device="cuda", dtype=[torch.float16, torch.bfloat16, None, torch.bfloat16,
                                                               torch.float16][i] or torch.float32))
         host.append([p0.astype(np.float64), np.zeros(n), np.zeros(n)])
-    lr, b1, b2, eps = 1e-3, 0.9, 0.999, 1e-15
+    # the kernel receives FP32 hyper-parameters; the oracle gets the same values
+    lr, b1, b2, eps = (float(np.float32(x)) for x in (1e-3, 0.9, 0.999, 1e-15))
     for step in range(1, 4):
         gs = [rng.standard_normal(n).astype(np.float32) for n in sizes]
         grads = [torch.as_tensor(g, device="cuda") for g in gs]
