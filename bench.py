@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--views", type=int, default=0, help="use only the first V cameras (0 = all; profiling)")
     ap.add_argument("--batch", type=int, default=0, help="splats per shared-memory batch (0 = auto)")
     ap.add_argument("--tile", type=int, default=0, help="tile edge 8 or 16 (0 = autotune)")
+    ap.add_argument("--ppt", type=int, default=1, help="backward pixels per thread, 1 or 2")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -215,18 +216,18 @@ def run_ours(args, world, rank, local):
     if args.tile == 0:
         tune = rast.autotune([dev_scene], cams, reps=2,
                              cache=os.path.join(tempfile.gettempdir(), f"gbill_tune_{os.getpid()}.json"))
-        args.tile, args.batch = tune["tile"], tune["batch"]
+        args.tile, args.batch, args.ppt = tune["tile"], tune["batch"], tune["ppt"]
 
     # --- size the saved state with one synchronizing forward, then reserve
     saved = R.Saved(rast)
-    rgb, depth, alpha, _ = rast.forward([dev_scene], cams, saved=saved, batch=args.batch, tile=args.tile)
+    rgb, depth, alpha, _ = rast.forward([dev_scene], cams, saved=saved, batch=args.batch, tile=args.tile, ppt=args.ppt)
     st0 = saved.stats()
     saved.reserve(st0["records"], int(st0["instances"] * 1.1) + 4096, P, st0["tiles"])
     grads = rast.backward(saved, d_rgb)
     out = (rgb, depth, alpha)
 
     def step(flags=L.GB_FLAG_NO_SYNC):
-        rast.forward([dev_scene], cams, saved=saved, flags=flags, out=out, batch=args.batch, tile=args.tile)
+        rast.forward([dev_scene], cams, saved=saved, flags=flags, out=out, batch=args.batch, tile=args.tile, ppt=args.ppt)
         rast.backward(saved, d_rgb, grads=grads)
 
     for _ in range(args.warmup):
@@ -274,7 +275,7 @@ def run_ours(args, world, rank, local):
     pairs = None
     for _ in range(args.steps):
         rast.forward([dev_scene], cams, saved=saved, flags=L.GB_FLAG_NO_SYNC | L.GB_FLAG_TIMING, out=out,
-                     batch=args.batch, tile=args.tile)
+                     batch=args.batch, tile=args.tile, ppt=args.ppt)
         rast.backward(saved, d_rgb, grads=grads)
         for k, v in saved.phase_times().items():
             phase_acc.setdefault(k, []).append(v)
@@ -290,7 +291,7 @@ def run_ours(args, world, rank, local):
         "config": {"workload": f"{args.workload}: 1,000,000 splats, {len(cams)} views 960x540/1280x720/1920x1080, "
                                f"{args.tex_n}x{args.tex_n} FP16 textures, SH3 FP16",
                    "pixels_per_step": P, "tex_n": args.tex_n, "storage": "f16", "tile": args.tile,
-                   "batch_depth": args.batch, "autotune": tune,
+                   "batch_depth": args.batch, "pixels_per_thread": args.ppt, "autotune": tune,
                    "graph": graph is not None, "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{world}"},
         "clocks": clocks, "gpu_launches": int(launches), "phases_ms": phases,

@@ -120,7 +120,9 @@ typedef struct {
     int32_t batch_depth; /* splats staged per shared-memory batch, 0 = automatic;
                             otherwise a multiple of 32 up to the tile's pixels    */
     uint32_t flags;      /* GB_FLAG_*                                             */
-    int32_t reserved;    /* must be 0                                             */
+    int32_t pixels_per_thread; /* backward: 1, or 2 (two pixels of a column per
+                                  thread on the packed FP32x2 pipe); 0 = 1. With 2,
+                                  batch_depth is at most tile_size^2 / 2        */
     float background[3]; /* added as T_final * background (default black)        */
 } gb_options;
 
@@ -300,7 +302,8 @@ gb_status gb_adam_step(gb_context *ctx, const gb_adam_tensor *tensors, int32_t n
 
 /* Autotuner: times forward + backward of this frame for every candidate
  * (tile_size 8 and 16; batch_depth 32, 64, 128, 256 where it fits the tile and
- * the shared-memory budget) and writes the fastest options to *best (flags and
+ * the shared-memory budget; pixels_per_thread 1 and 2) and writes the fastest
+ * options to *best (flags and
  * background are copied from *base, which may be NULL).  Each candidate runs
  * once untimed (which may grow `saved`) and then `reps` timed repetitions
  * (1..100) with dL/drgb = 1 for every pixel.  The call allocates its own
@@ -311,8 +314,8 @@ gb_status gb_adam_step(gb_context *ctx, const gb_adam_tensor *tensors, int32_t n
  * *n_candidates (nullable) the number tried. */
 gb_status gb_autotune(gb_context *ctx, gb_saved *saved, const gb_scene *scenes, int32_t n_scenes,
                       const gb_camera *cams, int32_t n_cams, const gb_options *base, int32_t reps,
-                      gb_options *best, float *ms, int32_t *tiles, int32_t *batches, int32_t cap,
-                      int32_t *n_candidates);
+                      gb_options *best, float *ms, int32_t *tiles, int32_t *batches, int32_t *ppts,
+                      int32_t cap, int32_t *n_candidates);
 
 #ifdef __cplusplus
 }

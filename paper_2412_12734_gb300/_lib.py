@@ -50,7 +50,7 @@ class gb_grads(C.Structure):
 
 class gb_options(C.Structure):
     _fields_ = [("tile_size", C.c_int32), ("batch_depth", C.c_int32), ("flags", C.c_uint32),
-                ("reserved", C.c_int32), ("background", C.c_float * 3)]
+                ("pixels_per_thread", C.c_int32), ("background", C.c_float * 3)]
 
 
 class gb_adam_tensor(C.Structure):
@@ -114,7 +114,7 @@ def load() -> C.CDLL:
         "gb_render_backward": (C.c_int, [vp, vp, vp, vp, vp, C.POINTER(gb_grads), i32, vp]),
         "gb_adam_step": (C.c_int, [vp, C.POINTER(gb_adam_tensor), i32, C.POINTER(gb_adam_config), vp]),
         "gb_autotune": (C.c_int, [vp, vp, C.POINTER(gb_scene), i32, C.POINTER(gb_camera), i32,
-                                  C.POINTER(gb_options), i32, C.POINTER(gb_options), vp, vp, vp, i32,
+                                  C.POINTER(gb_options), i32, C.POINTER(gb_options), vp, vp, vp, vp, i32,
                                   C.POINTER(i32)]),
     }
     for name, (res, args) in sig.items():

@@ -51,7 +51,7 @@ struct gb_saved {
     Frame frame;
     bool has_forward;
     int64_t n_records, n_pixels, max_k, inst_max;
-    int tile_bits, batch_fwd, batch_bwd;
+    int tile_bits, batch_fwd, batch_bwd, ppt;
     uint32_t flags;
     cudaStream_t stream;
     cudaEvent_t ev[kNumEvents];
@@ -500,7 +500,8 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
     if (!rgb) return fail(ctx, GB_ERR_INVALID_ARG, "rgb output is required");
     gb_options o{};
     if (opt) o = *opt;
-    if (o.reserved != 0) return fail(ctx, GB_ERR_INVALID_ARG, "options.reserved must be 0");
+    const int ppt = o.pixels_per_thread ? o.pixels_per_thread : 1;
+    if (ppt != 1 && ppt != 2) return fail(ctx, GB_ERR_INVALID_ARG, "pixels_per_thread must be 1 or 2");
     const int tile = o.tile_size ? o.tile_size : 16;
     if (tile != 8 && tile != 16) return fail(ctx, GB_ERR_UNSUPPORTED, "tile_size %d not built (8 or 16)", tile);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -512,8 +513,9 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
     for (int k = 0; k < f.n_groups; ++k) N = std::max(N, f.group_N[k]);
     const int nt = tile * tile;
     int bf = o.batch_depth ? o.batch_depth : std::min(default_batch(N, false), nt);
-    int bb = o.batch_depth ? o.batch_depth : std::min(default_batch(N, true), nt);
+    int bb = o.batch_depth ? o.batch_depth : std::min(default_batch(N, true), nt / ppt);
     if (bf < 32 || bf > nt || (bf & 31)) return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d invalid", bf);
+    if (bb > nt / ppt) return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d exceeds the backward's %d threads", bb, nt / ppt);
     if (batch_smem(N, bf, false) > 200 * 1024 || batch_smem(N, bb, true) > 200 * 1024)
         return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d needs too much shared memory", bf);
     const bool nosync = (o.flags & GB_FLAG_NO_SYNC) != 0;
@@ -538,6 +540,7 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
     s->tile_bits = tile_bits;
     s->batch_fwd = bf;
     s->batch_bwd = bb;
+    s->ppt = ppt;
     s->flags = o.flags;
     s->stream = st;
     s->has_forward = false;
@@ -658,8 +661,12 @@ gb_status gb_render_backward(gb_context *ctx, gb_saved *s, const float *d_rgb, c
     b.rec_grad = s->rec_grad;
     GB_CUDA(ctx, cudaMemsetAsync(&s->cnt->pairs_bwd, 0, sizeof(unsigned long long), st));
     const bool persistent = (s->flags & GB_FLAG_PERSISTENT) != 0;
-    GB_CUDA(ctx, launch_render_bwd(f, b, s->batch_bwd, s->use_list ? s->tile_list : nullptr,
-                                   persistent ? s->work + kMaxGroups : nullptr, persistent, st));
+    if (s->ppt == 2)
+        GB_CUDA(ctx, launch_render_bwd2(f, b, s->batch_bwd, s->use_list ? s->tile_list : nullptr,
+                                        persistent ? s->work + kMaxGroups : nullptr, persistent, st));
+    else
+        GB_CUDA(ctx, launch_render_bwd(f, b, s->batch_bwd, s->use_list ? s->tile_list : nullptr,
+                                       persistent ? s->work + kMaxGroups : nullptr, persistent, st));
     if (timing) GB_CUDA(ctx, cudaEventRecord(s->ev[10], st));
     GB_CUDA(ctx, launch_preprocess_bwd(f, s->max_k, s->rec_grad, s->inv, st));
     if (timing) GB_CUDA(ctx, cudaEventRecord(s->ev[11], st));
@@ -697,8 +704,8 @@ __global__ void fill_kernel(float *p, int64_t n, float v) {
 
 gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int32_t n_scenes,
                       const gb_camera *cams, int32_t n_cams, const gb_options *base, int32_t reps,
-                      gb_options *best, float *ms, int32_t *tiles, int32_t *batches, int32_t cap,
-                      int32_t *n_candidates) {
+                      gb_options *best, float *ms, int32_t *tiles, int32_t *batches, int32_t *ppts,
+                      int32_t cap, int32_t *n_candidates) {
     if (!ctx) return GB_ERR_INVALID_ARG;
     if (!s || s->ctx != ctx || !best) return fail(ctx, GB_ERR_INVALID_ARG, "bad autotune arguments");
     if (reps < 1 || reps > 100) return fail(ctx, GB_ERR_INVALID_ARG, "reps must be in 1..100");
@@ -747,13 +754,15 @@ gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int3
         int n = 0;
         const int tile_c[2] = {16, 8};
         const int batch_c[4] = {32, 64, 128, 256};
+        for (int pi = 1; pi <= 2 && st == GB_OK; ++pi)
         for (int ti = 0; ti < 2 && st == GB_OK; ++ti)
             for (int bi = 0; bi < 4 && st == GB_OK; ++bi) {
                 const int T = tile_c[ti], B = batch_c[bi];
-                if (B > T * T) continue;
+                if (B > T * T / pi) continue;
                 if (batch_smem(N, B, false) > 160 * 1024 || batch_smem(N, B, true) > 160 * 1024) continue;
                 o.tile_size = T;
                 o.batch_depth = B;
+                o.pixels_per_thread = pi;
                 o.flags &= ~GB_FLAG_NO_SYNC;
                 st = gb_render_forward(ctx, s, scenes, n_scenes, cams, n_cams, &o, rgb, dep, alp, nullptr);
                 if (st == GB_OK) st = gb_render_backward(ctx, s, drgb, nullptr, nullptr, g, n_scenes, nullptr);
@@ -780,6 +789,7 @@ gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int3
                     if (ms) ms[n] = t;
                     if (tiles) tiles[n] = T;
                     if (batches) batches[n] = B;
+                    if (ppts) ppts[n] = pi;
                 }
                 ++n;
                 if (t < best_ms) {

@@ -194,5 +194,8 @@ struct RenderBwdBufs {
 };
 cudaError_t launch_render_bwd(const Frame &f, const RenderBwdBufs &b, int batch, const uint32_t *tile_list,
                               uint32_t *work, bool persistent, cudaStream_t s);
+// two pixels per thread (render_bwd2.cu)
+cudaError_t launch_render_bwd2(const Frame &f, const RenderBwdBufs &b, int batch, const uint32_t *tile_list,
+                               uint32_t *work, bool persistent, cudaStream_t s);
 
 }  // namespace gbill

@@ -172,7 +172,7 @@ class Rasterizer:
 
     def forward(self, scenes: list, cams: list, cam_scene=None, saved: Saved | None = None,
                 tile: int = 16, batch: int = 0, flags: int = 0, background=None, stream=None,
-                out=None):
+                out=None, ppt: int = 1):
         """Renders every camera; returns (rgb [P,3], depth [P], alpha [P], saved)."""
         lib = L.load()
         n_s, n_c = len(scenes), len(cams)
@@ -180,7 +180,7 @@ class Rasterizer:
         sarr = (L.gb_scene * n_s)(*[scene_struct(s) for s in scenes])
         carr = (L.gb_camera * n_c)(*[camera_struct(c, cam_scene[i]) for i, c in enumerate(cams)])
         opt = L.gb_options()
-        opt.tile_size, opt.batch_depth, opt.flags, opt.reserved = tile, batch, flags, 0
+        opt.tile_size, opt.batch_depth, opt.flags, opt.pixels_per_thread = tile, batch, flags, ppt
         if background is not None:
             for i in range(3):
                 opt.background[i] = float(background[i])
@@ -260,16 +260,18 @@ class Rasterizer:
         sarr = (L.gb_scene * n_s)(*[scene_struct(s) for s in scenes])
         carr = (L.gb_camera * n_c)(*[camera_struct(c, cam_scene[i]) for i, c in enumerate(cams)])
         best = L.gb_options()
-        ms = (C.c_float * 16)()
-        tiles = (C.c_int32 * 16)()
-        batches = (C.c_int32 * 16)()
+        ms = (C.c_float * 32)()
+        tiles = (C.c_int32 * 32)()
+        batches = (C.c_int32 * 32)()
+        ppts = (C.c_int32 * 32)()
         n = C.c_int32()
         saved = saved or Saved(self)
         L.check(lib.gb_autotune(self.ctx, saved.handle, sarr, n_s, carr, n_c, None, reps, C.byref(best),
-                                C.addressof(ms), C.addressof(tiles), C.addressof(batches), 16, C.byref(n)),
-                self.ctx)
-        res = {"tile": best.tile_size, "batch": best.batch_depth,
-               "candidates": [{"tile": tiles[i], "batch": batches[i], "ms": ms[i]} for i in range(n.value)]}
+                                C.addressof(ms), C.addressof(tiles), C.addressof(batches), C.addressof(ppts), 32,
+                                C.byref(n)), self.ctx)
+        res = {"tile": best.tile_size, "batch": best.batch_depth, "ppt": best.pixels_per_thread,
+               "candidates": [{"tile": tiles[i], "batch": batches[i], "ppt": ppts[i], "ms": ms[i]}
+                              for i in range(n.value)]}
         table[key] = res
         try:
             os.makedirs(os.path.dirname(path), exist_ok=True)

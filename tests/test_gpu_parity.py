@@ -102,6 +102,23 @@ def test_gradient_parity(case):
     assert not bad, f"gradient ratios over tolerance {GRAD_REL}: {errs}"
 
 
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("tile", [16, 8])
+def test_gradient_parity_two_pixels_per_thread(case, tile):
+    """Backward with two pixels of a column per thread (packed FP32x2 pipe)."""
+    sc, cams = CASES[case]()
+    rng = np.random.default_rng(23)
+    ref = oracle_run(sc[0], cams[0])
+    d_rgb = masked_upstream(ref, rng)
+    d_dep = masked_upstream(ref, rng, 1, 0.3)[..., 0]
+    d_alp = masked_upstream(ref, rng, 1)[..., 0]
+    gpu = gpu_run(sc, cams, d_rgb=[d_rgb], d_depth=[d_dep], d_alpha=[d_alp], tile=tile, ppt=2,
+                  bg=np.array([0.2, 0.1, 0.4], np.float32))
+    og = oracle.backward(sc[0], cams[0], d_rgb, d_dep, d_alp, bg=np.array([0.2, 0.1, 0.4], np.float32))
+    errs = grad_errors(gpu["grads"][0], og)
+    assert all(v <= 1.0 for v in errs.values()), errs
+
+
 @pytest.mark.parametrize("case", ["plain_1k", "tiny_n4_d3", "tiny_bf16", "dense_many_tiles"])
 def test_tile8_keys_image_gradients(case):
     """8 x 8 tiles: same keys formula with tile = 8, same image and gradients."""
