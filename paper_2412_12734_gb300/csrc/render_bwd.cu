@@ -20,39 +20,42 @@
 namespace gbill {
 namespace {
 
-// Reduce-scatter of 16 values over the warp: after five exchange steps (16
-// shuffles) lane l holds the warp total of value index
-// 8 b4 + 4 b3 + 2 b2 + b1 (b_i = bit i of l); lanes l and l^1 hold the same.
-__device__ __forceinline__ float warp_reduce_scatter16(float v[16], int lane) {
+// Reduce-scatter of 32 values over the warp (31 shuffles): lane l ends with
+// the warp total of value index l (bits of l select the kept half at each
+// exchange step, most significant first).
+__device__ __forceinline__ float warp_reduce_scatter32(float v[32], int lane) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < 16; ++i) {
         const bool up = lane & 16;
-        const float send = up ? v[i] : v[i + 8], keep = up ? v[i + 8] : v[i];
+        const float send = up ? v[i] : v[i + 16], keep = up ? v[i + 16] : v[i];
         v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 8; ++i) {
         const bool up = lane & 8;
-        const float send = up ? v[i] : v[i + 4], keep = up ? v[i + 4] : v[i];
+        const float send = up ? v[i] : v[i + 8], keep = up ? v[i + 8] : v[i];
         v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
     }
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 4; ++i) {
         const bool up = lane & 4;
-        const float send = up ? v[i] : v[i + 2], keep = up ? v[i + 2] : v[i];
+        const float send = up ? v[i] : v[i + 4], keep = up ? v[i + 4] : v[i];
         v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
     }
-    {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
         const bool up = lane & 2;
-        const float send = up ? v[0] : v[1], keep = up ? v[1] : v[0];
-        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+        const float send = up ? v[i] : v[i + 2], keep = up ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
     }
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+    const bool up = lane & 1;
+    const float send = up ? v[0] : v[1], keep = up ? v[1] : v[0];
+    return keep + __shfl_xor_sync(0xffffffffu, send, 1);
 }
 
-__device__ __forceinline__ int scatter_index(int lane) {
-    return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
-}
+// Warp-reduced values: 0..13 record gradients, 14..25 the RGB gradient of the
+// grid's four corner texels (0,0), (0,N-1), (N-1,0), (N-1,N-1).
+constexpr int kCornerSlot = 14;
 
 template <int TS, int N, typename TexT>
 __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b, int batch, uint32_t tile) {
@@ -107,7 +110,11 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
     __syncthreads();
     const int max_last = int(s_maxlast);
     float *g_tex = sc.g_tex;
-    const int my_q = scatter_index(lane);
+    // flat index (i_u N + i_v) of the corner texel this lane's reduced value feeds
+    const int my_corner = lane >= kCornerSlot && lane < kCornerSlot + 12 ? (lane - kCornerSlot) / 3 : -1;
+    const int my_corner_off = my_corner < 0 ? 0
+                              : 3 * ((my_corner & 2 ? (N - 1) * N : 0) + (my_corner & 1 ? N - 1 : 0)) +
+                                    (lane - kCornerSlot) % 3;
 
     for (int be = max_last; be > 0; be -= batch) {
         const int bs = max(0, be - batch), nb = be - bs;
@@ -119,9 +126,9 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
         const int i_hi = min(nb, int(wlast) - bs);
         for (int i = i_hi - 1; i >= 0; --i) {
             if (wb.misses(s_box[i])) continue;
-            float g[16];
+            float g[32];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) g[q] = 0.0f;
+            for (int q = 0; q < 32; ++q) g[q] = 0.0f;
             bool act = inside && uint32_t(bs + i) < last;
             npairs += act ? 1u : 0u;
             if (act) {
@@ -160,9 +167,10 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
                         float uh = 0.0f, vh = 0.0f;
                         float *tgo = s_tg + i * TEXF;
                         if (N == 1) {
-                            atomicAdd(tgo + 0, ch0);
-                            atomicAdd(tgo + 1, ch1);
-                            atomicAdd(tgo + 2, ch2);
+                            // the single texel is corner 0: reduced over the warp
+                            g[kCornerSlot + 0] = ch0;
+                            g[kCornerSlot + 1] = ch1;
+                            g[kCornerSlot + 2] = ch2;
                         } else {
                             const float fu = cell.fu, fv = cell.fv;
                             const float w00 = (1.0f - fu) * (1.0f - fv), w10 = fu * (1.0f - fv);
@@ -175,6 +183,21 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
                             const float fvh = ch0 * ((qd.c01.x - qd.c00.x) * (1.0f - fu) + (qd.c11.x - qd.c10.x) * fu) +
                                               ch1 * ((qd.c01.y - qd.c00.y) * (1.0f - fu) + (qd.c11.y - qd.c10.y) * fu) +
                                               ch2 * ((qd.c01.z - qd.c00.z) * (1.0f - fu) + (qd.c11.z - qd.c10.z) * fu);
+                            // a pixel whose whole bilinear weight sits on one grid-corner texel
+                            // (clamped in u and v) is reduced over the warp, not atomically added
+                            const int tsel = w00 == 1.0f ? cell.base : w10 == 1.0f ? cell.base + N
+                                             : w01 == 1.0f ? cell.base + 1 : w11 == 1.0f ? cell.base + N + 1 : -1;
+                            const int corner = tsel == 0 ? 0 : tsel == N - 1 ? 1 : tsel == (N - 1) * N ? 2
+                                               : tsel == N * N - 1 ? 3 : -1;
+                            if (corner >= 0) {
+#pragma unroll
+                                for (int q = 0; q < 4; ++q)
+                                    if (corner == q) {  // static indices keep g[] in registers
+                                        g[kCornerSlot + 3 * q + 0] = ch0;
+                                        g[kCornerSlot + 3 * q + 1] = ch1;
+                                        g[kCornerSlot + 3 * q + 2] = ch2;
+                                    }
+                            } else {
                             if (w00 != 0.0f) {
                                 atomicAdd(tgo + o00 + 0, ch0 * w00);
                                 atomicAdd(tgo + o00 + 1, ch1 * w00);
@@ -194,6 +217,7 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
                                 atomicAdd(tgo + o11 + 0, ch0 * w11);
                                 atomicAdd(tgo + o11 + 1, ch1 * w11);
                                 atomicAdd(tgo + o11 + 2, ch2 * w11);
+                            }
                             }
                             if (u > -sigma && u < sigma) uh = kN * fuh;
                             if (v > -sigma && v < sigma) vh = kN * fvh;
@@ -244,8 +268,11 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
                 }
             }
             if (__any_sync(0xffffffffu, act)) {
-                const float tot = warp_reduce_scatter16(g, lane);
-                if (!(lane & 1) && my_q < 14 && tot != 0.0f) atomicAdd(s_g + i * kRecGrad + my_q, tot);
+                const float tot = warp_reduce_scatter32(g, lane);
+                if (tot != 0.0f) {
+                    if (lane < kCornerSlot) atomicAdd(s_g + i * kRecGrad + lane, tot);
+                    else if (my_corner >= 0) atomicAdd(s_tg + i * TEXF + my_corner_off, tot);
+                }
             }
         }
         __syncthreads();
