@@ -20,6 +20,34 @@
 namespace gbill {
 namespace {
 
+// Reduce-scatter of 16 values over the warp (16 shuffles): lane l ends with the
+// warp total of value index 8 b4 + 4 b3 + 2 b2 + b1 (b_i = bit i of l); lanes
+// l and l^1 hold the same total.
+__device__ __forceinline__ float warp_reduce_scatter16(float v[16], int lane) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const bool up = lane & 16;
+        const float send = up ? v[i] : v[i + 8], keep = up ? v[i + 8] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool up = lane & 8;
+        const float send = up ? v[i] : v[i + 4], keep = up ? v[i + 4] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool up = lane & 4;
+        const float send = up ? v[i] : v[i + 2], keep = up ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    const bool up = lane & 2;
+    const float send = up ? v[0] : v[1], keep = up ? v[1] : v[0];
+    const float t = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    return t + __shfl_xor_sync(0xffffffffu, t, 1);
+}
+
 // Reduce-scatter of 32 values over the warp (31 shuffles): lane l ends with
 // the warp total of value index l (bits of l select the kept half at each
 // exchange step, most significant first).
@@ -110,6 +138,7 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
     __syncthreads();
     const int max_last = int(s_maxlast);
     float *g_tex = sc.g_tex;
+    const int my_q16 = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
     // flat index (i_u N + i_v) of the corner texel this lane's reduced value feeds
     const int my_corner = lane >= kCornerSlot && lane < kCornerSlot + 12 ? (lane - kCornerSlot) / 3 : -1;
     const int my_corner_off = my_corner < 0 ? 0
@@ -131,6 +160,9 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
             for (int q = 0; q < 32; ++q) g[q] = 0.0f;
             bool act = inside && uint32_t(bs + i) < last;
             npairs += act ? 1u : 0u;
+            // texel weights not reduced through the corner slots, and their cell
+            float rw00 = 0.0f, rw10 = 0.0f, rw01 = 0.0f, rw11 = 0.0f, rch0 = 0.0f, rch1 = 0.0f, rch2 = 0.0f;
+            int rbase = 0;
             if (act) {
                 const float4 q0 = s_rec[4 * i + 0], q1 = s_rec[4 * i + 1], q2 = s_rec[4 * i + 2],
                              q3 = s_rec[4 * i + 3];
@@ -183,42 +215,23 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
                             const float fvh = ch0 * ((qd.c01.x - qd.c00.x) * (1.0f - fu) + (qd.c11.x - qd.c10.x) * fu) +
                                               ch1 * ((qd.c01.y - qd.c00.y) * (1.0f - fu) + (qd.c11.y - qd.c10.y) * fu) +
                                               ch2 * ((qd.c01.z - qd.c00.z) * (1.0f - fu) + (qd.c11.z - qd.c10.z) * fu);
-                            // a pixel whose whole bilinear weight sits on one grid-corner texel
-                            // (clamped in u and v) is reduced over the warp, not atomically added
-                            const int tsel = w00 == 1.0f ? cell.base : w10 == 1.0f ? cell.base + N
-                                             : w01 == 1.0f ? cell.base + 1 : w11 == 1.0f ? cell.base + N + 1 : -1;
-                            const int corner = tsel == 0 ? 0 : tsel == N - 1 ? 1 : tsel == (N - 1) * N ? 2
-                                               : tsel == N * N - 1 ? 3 : -1;
-                            if (corner >= 0) {
-#pragma unroll
-                                for (int q = 0; q < 4; ++q)
-                                    if (corner == q) {  // static indices keep g[] in registers
-                                        g[kCornerSlot + 3 * q + 0] = ch0;
-                                        g[kCornerSlot + 3 * q + 1] = ch1;
-                                        g[kCornerSlot + 3 * q + 2] = ch2;
-                                    }
-                            } else {
-                            if (w00 != 0.0f) {
-                                atomicAdd(tgo + o00 + 0, ch0 * w00);
-                                atomicAdd(tgo + o00 + 1, ch1 * w00);
-                                atomicAdd(tgo + o00 + 2, ch2 * w00);
-                            }
-                            if (w10 != 0.0f) {
-                                atomicAdd(tgo + o10 + 0, ch0 * w10);
-                                atomicAdd(tgo + o10 + 1, ch1 * w10);
-                                atomicAdd(tgo + o10 + 2, ch2 * w10);
-                            }
-                            if (w01 != 0.0f) {
-                                atomicAdd(tgo + o01 + 0, ch0 * w01);
-                                atomicAdd(tgo + o01 + 1, ch1 * w01);
-                                atomicAdd(tgo + o01 + 2, ch2 * w01);
-                            }
-                            if (w11 != 0.0f) {
-                                atomicAdd(tgo + o11 + 0, ch0 * w11);
-                                atomicAdd(tgo + o11 + 1, ch1 * w11);
-                                atomicAdd(tgo + o11 + 2, ch2 * w11);
-                            }
-                            }
+                            // weights landing on a grid-corner texel go to the warp-reduced corner
+                            // slots; the rest (edge and interior texels) to the cell-group pass below
+                            const int iu = cell.base / N, iv = cell.base - iu * N;
+                            const float wc0 = (iu == 0 && iv == 0) ? w00 : 0.0f;
+                            const float wc1 = (iu == 0 && iv == N - 2) ? w01 : 0.0f;
+                            const float wc2 = (iu == N - 2 && iv == 0) ? w10 : 0.0f;
+                            const float wc3 = (iu == N - 2 && iv == N - 2) ? w11 : 0.0f;
+                            g[kCornerSlot + 0] = wc0 * ch0; g[kCornerSlot + 1] = wc0 * ch1; g[kCornerSlot + 2] = wc0 * ch2;
+                            g[kCornerSlot + 3] = wc1 * ch0; g[kCornerSlot + 4] = wc1 * ch1; g[kCornerSlot + 5] = wc1 * ch2;
+                            g[kCornerSlot + 6] = wc2 * ch0; g[kCornerSlot + 7] = wc2 * ch1; g[kCornerSlot + 8] = wc2 * ch2;
+                            g[kCornerSlot + 9] = wc3 * ch0; g[kCornerSlot + 10] = wc3 * ch1; g[kCornerSlot + 11] = wc3 * ch2;
+                            rw00 = w00 - wc0;
+                            rw10 = w10 - wc2;
+                            rw01 = w01 - wc1;
+                            rw11 = w11 - wc3;
+                            rbase = cell.base;
+                            rch0 = ch0; rch1 = ch1; rch2 = ch2;
                             if (u > -sigma && u < sigma) uh = kN * fuh;
                             if (v > -sigma && v < sigma) vh = kN * fvh;
                         }
@@ -272,6 +285,31 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
                 if (tot != 0.0f) {
                     if (lane < kCornerSlot) atomicAdd(s_g + i * kRecGrad + lane, tot);
                     else if (my_corner >= 0) atomicAdd(s_tg + i * TEXF + my_corner_off, tot);
+                }
+                // edge / interior texels: lanes sharing a cell touch the same four
+                // texels; each group is one reduce-scatter and one conflict-free atomic
+                if (N > 2) {
+                    unsigned pending = __ballot_sync(0xffffffffu, (rw00 != 0.0f) | (rw10 != 0.0f) | (rw01 != 0.0f) |
+                                                                     (rw11 != 0.0f));
+                    while (pending) {
+                        const int leader = __ffs(pending) - 1;
+                        const int key = __shfl_sync(0xffffffffu, rbase, leader);
+                        const bool mine = ((pending >> lane) & 1u) && rbase == key;
+                        pending &= ~__ballot_sync(0xffffffffu, mine);
+                        float h[16];
+                        h[0] = mine ? rw00 * rch0 : 0.0f; h[1] = mine ? rw00 * rch1 : 0.0f; h[2] = mine ? rw00 * rch2 : 0.0f;
+                        h[3] = mine ? rw10 * rch0 : 0.0f; h[4] = mine ? rw10 * rch1 : 0.0f; h[5] = mine ? rw10 * rch2 : 0.0f;
+                        h[6] = mine ? rw01 * rch0 : 0.0f; h[7] = mine ? rw01 * rch1 : 0.0f; h[8] = mine ? rw01 * rch2 : 0.0f;
+                        h[9] = mine ? rw11 * rch0 : 0.0f; h[10] = mine ? rw11 * rch1 : 0.0f; h[11] = mine ? rw11 * rch2 : 0.0f;
+                        h[12] = h[13] = h[14] = h[15] = 0.0f;
+                        const float t = warp_reduce_scatter16(h, lane);
+                        if (!(lane & 1) && my_q16 < 12 && t != 0.0f) {
+                            const int k = my_q16 / 3, c = my_q16 - 3 * k;
+                            // k: 0 -> (iu, iv), 1 -> (iu+1, iv), 2 -> (iu, iv+1), 3 -> (iu+1, iv+1)
+                            const int off = 3 * (key + ((k & 1) ? N : 0) + ((k & 2) ? 1 : 0)) + c;
+                            atomicAdd(s_tg + i * TEXF + off, t);
+                        }
+                    }
                 }
             }
         }
