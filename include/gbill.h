@@ -298,6 +298,32 @@ typedef struct {
 gb_status gb_adam_step(gb_context *ctx, const gb_adam_tensor *tensors, int32_t n_tensors,
                        const gb_adam_config *cfg, void *stream);
 
+/* ------------------------------------------------------ no allocation -- */
+
+/* Forward render for callers that cannot allocate device memory: code that
+ * runs where cudaMalloc is unavailable or forbidden (a host with a fixed
+ * device-memory budget handed out by someone else, a plug-in that must not
+ * touch the allocator, a caller that owns all memory it uses).  There is no
+ * counterpart in the paper; it is the forward of gb_render_forward (same
+ * arguments and outputs, no saved state, so no backward after it) with every
+ * scratch buffer taken from one fixed device array of about 36 MB compiled
+ * into the library; every GPU that loads the library holds that array until
+ * the process exits.
+ * Limits per call: 131,072 records (splats x cameras), 524,288 (tile, splat)
+ * instances, 1,048,576 pixels, 8,192 tiles; beyond them the call returns
+ * GB_ERR_CAPACITY with a message and renders nothing.  GB_FLAG_TIMING and
+ * GB_FLAG_PERSISTENT are rejected (GB_ERR_UNSUPPORTED).
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture.
+ * The call synchronizes `stream` once to check the instance count.  Every
+ * call shares the one array, which keeps the previous call's contents: calls
+ * that overlap on the GPU (other streams, other host threads) race and must
+ * be serialized by the caller. */
+gb_status gb_render_forward_noalloc(gb_context *ctx, const gb_scene *scenes, int32_t n_scenes,
+                                    const gb_camera *cams, int32_t n_cams, const gb_options *opt,
+                                    float *rgb, float *depth, float *alpha, void *stream);
+
 /* ---------------------------------------------------------------- tuning -- */
 
 /* Autotuner: times forward + backward of this frame for every candidate

@@ -113,6 +113,8 @@ def load() -> C.CDLL:
                                         C.POINTER(gb_options), vp, vp, vp, vp]),
         "gb_render_backward": (C.c_int, [vp, vp, vp, vp, vp, C.POINTER(gb_grads), i32, vp]),
         "gb_adam_step": (C.c_int, [vp, C.POINTER(gb_adam_tensor), i32, C.POINTER(gb_adam_config), vp]),
+        "gb_render_forward_noalloc": (C.c_int, [vp, C.POINTER(gb_scene), i32, C.POINTER(gb_camera), i32,
+                                                C.POINTER(gb_options), vp, vp, vp, vp]),
         "gb_autotune": (C.c_int, [vp, vp, C.POINTER(gb_scene), i32, C.POINTER(gb_camera), i32,
                                   C.POINTER(gb_options), i32, C.POINTER(gb_options), vp, vp, vp, vp, i32,
                                   C.POINTER(i32)]),

@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 
 #include "gbill_internal.cuh"
 #include "render_common.cuh"
@@ -694,6 +695,155 @@ gb_status gb_adam_step(gb_context *ctx, const gb_adam_tensor *tensors, int32_t n
     // enough blocks to fill the GPU (152 SMs x 8 resident 256-thread blocks) per tensor
     const int grid_x = int(std::max<int64_t>(1, std::min<int64_t>(ceil_div(biggest, 4 * 256), 152 * 8)));
     GB_CUDA(ctx, launch_adam(tensors, n_tensors, *cfg, grid_x, static_cast<cudaStream_t>(stream)));
+    return GB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Forward without allocation.  Every scratch buffer of the forward pipeline is
+// carved from this one file-scope device array, so the call never allocates.
+// Limits per call: records (splats x cameras), (tile, splat) instances,
+// pixels and tiles below; the array is 256-byte aligned and each carved
+// buffer starts on a 256-byte boundary.
+constexpr int64_t kNaMaxRecords = int64_t(1) << 17;
+constexpr int64_t kNaMaxInstances = int64_t(1) << 19;
+constexpr int64_t kNaMaxPixels = int64_t(1) << 20;
+constexpr int64_t kNaMaxTiles = int64_t(1) << 13;
+constexpr size_t na_round(size_t b) { return (b + 255) & ~size_t(255); }
+constexpr size_t kNaRadixBytes = size_t(kNaMaxInstances / 4096) * 256 * 4 + 64 * 1024;
+constexpr size_t kNaScratchBytes =
+    na_round(sizeof(Counters)) + na_round(2 * kMaxGroups * 4) +
+    na_round(kNaMaxRecords * sizeof(Record)) + 7 * na_round(kNaMaxRecords * 4) + 2 * na_round(kNaMaxRecords * 8) +
+    6 * na_round(kNaMaxInstances * 4) + 2 * na_round(kNaMaxPixels * 4) + na_round(kNaMaxTiles * 8) +
+    6 * na_round(kNaMaxTiles * 4) + na_round(kNaRadixBytes);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaScratchBytes];
+
+// Device address of g_noalloc_scratch, looked up once per device with that
+// device current (the host-side symbol is only a stand-in, not an address).
+static void *g_noalloc_addr[64] = {nullptr};
+static std::mutex g_noalloc_mu;
+
+gb_status gb_render_forward_noalloc(gb_context *ctx, const gb_scene *scenes, int32_t n_scenes,
+                                    const gb_camera *cams, int32_t n_cams, const gb_options *opt, float *rgb,
+                                    float *depth, float *alpha, void *stream) {
+    if (!ctx) return GB_ERR_INVALID_ARG;
+    if (!rgb) return fail(ctx, GB_ERR_INVALID_ARG, "rgb output is required");
+    gb_options o{};
+    if (opt) o = *opt;
+    const int tile = o.tile_size ? o.tile_size : 16;
+    if (tile != 8 && tile != 16) return fail(ctx, GB_ERR_UNSUPPORTED, "tile_size %d not built (8 or 16)", tile);
+    if (o.flags & (GB_FLAG_TIMING | GB_FLAG_PERSISTENT))
+        return fail(ctx, GB_ERR_UNSUPPORTED, "the no-allocation forward takes no timing or persistent flag");
+    Frame f;
+    int64_t max_k = 0;
+    gb_status r = build_frame(ctx, scenes, n_scenes, cams, n_cams, tile, o.background, f, max_k);
+    if (r != GB_OK) return r;
+    if (f.n_records > kNaMaxRecords || f.n_pixels > kNaMaxPixels || int64_t(f.n_tiles) > kNaMaxTiles)
+        return fail(ctx, GB_ERR_CAPACITY,
+                    "no-allocation forward limits: %lld records (max %lld), %lld pixels (max %lld), %u tiles (max %lld)",
+                    (long long)f.n_records, (long long)kNaMaxRecords, (long long)f.n_pixels,
+                    (long long)kNaMaxPixels, f.n_tiles, (long long)kNaMaxTiles);
+    int N = 1;
+    for (int k = 0; k < f.n_groups; ++k) N = std::max(N, f.group_N[k]);
+    const int nt = tile * tile;
+    const int bf = o.batch_depth ? o.batch_depth : std::min(default_batch(N, false), nt);
+    if (bf < 32 || bf > nt || (bf & 31) || batch_smem(N, bf, false) > 200 * 1024)
+        return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d invalid", bf);
+    int dev = 0;
+    GB_CUDA(ctx, cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(ctx, GB_ERR_UNSUPPORTED, "device index %d beyond 63", dev);
+    unsigned char *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void *ptr = nullptr;
+            GB_CUDA(ctx, cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+            g_noalloc_addr[dev] = ptr;
+        }
+        base = static_cast<unsigned char *>(g_noalloc_addr[dev]);
+    }
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        void *p = base + off;
+        off += na_round(bytes);
+        return p;
+    };
+    Counters *cnt = static_cast<Counters *>(carve(sizeof(Counters)));
+    carve(2 * kMaxGroups * 4);  // work counters (persistent mode is not offered here)
+    Record *rec = static_cast<Record *>(carve(kNaMaxRecords * sizeof(Record)));
+    uint32_t *depth_key = static_cast<uint32_t *>(carve(kNaMaxRecords * 4));
+    uint32_t *rec_id = static_cast<uint32_t *>(carve(kNaMaxRecords * 4));
+    uint32_t *keys_tmp = static_cast<uint32_t *>(carve(kNaMaxRecords * 4));
+    uint32_t *vals_tmp = static_cast<uint32_t *>(carve(kNaMaxRecords * 4));
+    uint32_t *dkeys_sorted = static_cast<uint32_t *>(carve(kNaMaxRecords * 4));
+    uint32_t *perm = static_cast<uint32_t *>(carve(kNaMaxRecords * 4));
+    uint32_t *offsets = static_cast<uint32_t *>(carve(kNaMaxRecords * 4));
+    uint2 *rect = static_cast<uint2 *>(carve(kNaMaxRecords * 8));
+    uint2 *pbox = static_cast<uint2 *>(carve(kNaMaxRecords * 8));
+    uint32_t *inst_tile = static_cast<uint32_t *>(carve(kNaMaxInstances * 4));
+    uint32_t *inst_val = static_cast<uint32_t *>(carve(kNaMaxInstances * 4));
+    uint32_t *inst_tile_tmp = static_cast<uint32_t *>(carve(kNaMaxInstances * 4));
+    uint32_t *inst_val_tmp = static_cast<uint32_t *>(carve(kNaMaxInstances * 4));
+    uint32_t *tiles_sorted = static_cast<uint32_t *>(carve(kNaMaxInstances * 4));
+    uint32_t *vals_sorted = static_cast<uint32_t *>(carve(kNaMaxInstances * 4));
+    float *t_final = static_cast<float *>(carve(kNaMaxPixels * 4));
+    uint32_t *last = static_cast<uint32_t *>(carve(kNaMaxPixels * 4));
+    uint2 *ranges = static_cast<uint2 *>(carve(kNaMaxTiles * 8));
+    uint32_t *tl_keys = static_cast<uint32_t *>(carve(kNaMaxTiles * 4));
+    uint32_t *tl_vals = static_cast<uint32_t *>(carve(kNaMaxTiles * 4));
+    uint32_t *tl_keys_tmp = static_cast<uint32_t *>(carve(kNaMaxTiles * 4));
+    uint32_t *tl_vals_tmp = static_cast<uint32_t *>(carve(kNaMaxTiles * 4));
+    uint32_t *tl_keys_out = static_cast<uint32_t *>(carve(kNaMaxTiles * 4));
+    uint32_t *tile_list = static_cast<uint32_t *>(carve(kNaMaxTiles * 4));
+    void *scratch = carve(kNaRadixBytes);
+    if (off > kNaScratchBytes) return fail(ctx, GB_ERR_CUDA, "internal: no-allocation scratch layout overflow");
+    if (radix_scratch_bytes(kNaMaxInstances) > kNaRadixBytes || scan_scratch_bytes(kNaMaxRecords) > kNaRadixBytes)
+        return fail(ctx, GB_ERR_CUDA, "internal: no-allocation sort scratch too small");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t R = f.n_records;
+    int tile_bits = 1;
+    while ((int64_t(1) << tile_bits) < int64_t(f.n_tiles)) ++tile_bits;
+    // the array keeps the previous call's contents: clear what must start at zero
+    GB_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(Counters), st));
+    GB_CUDA(ctx, cudaMemsetAsync(ranges, 0, size_t(f.n_tiles) * sizeof(uint2), st));
+    GB_CUDA(ctx, launch_preprocess(f, max_k, depth_key, rec_id, rect, pbox, rec, cnt, st));
+    GB_CUDA(ctx, radix_sort_pairs(depth_key, rec_id, keys_tmp, vals_tmp, dkeys_sorted, perm, R, nullptr, 0, 32,
+                                  scratch, kNaRadixBytes, st));
+    GB_CUDA(ctx, tile_counts_scan(f, perm, rect, R, &cnt->n_visible, offsets, scratch, kNaRadixBytes, cnt,
+                                  kNaMaxInstances, st));
+    // the instance count decides whether the list fits: read it (no allocation)
+    Counters host_cnt;
+    GB_CUDA(ctx, cudaMemcpyAsync(&host_cnt, cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    GB_CUDA(ctx, cudaStreamSynchronize(st));
+    if (int64_t(host_cnt.n_instances) > kNaMaxInstances)
+        return fail(ctx, GB_ERR_CAPACITY, "no-allocation forward: %u (tile, splat) instances (max %lld)",
+                    host_cnt.n_instances, (long long)kNaMaxInstances);
+    const int64_t inst_max = std::max<int64_t>(host_cnt.n_instances, 1);
+    GB_CUDA(ctx, launch_emit(f, perm, rect, offsets, R, cnt, kNaMaxInstances, inst_tile, inst_val, st));
+    GB_CUDA(ctx, radix_sort_pairs(inst_tile, inst_val, inst_tile_tmp, inst_val_tmp, tiles_sorted, vals_sorted,
+                                  inst_max, &cnt->n_instances, 0, tile_bits, scratch, kNaRadixBytes, st));
+    GB_CUDA(ctx, launch_ranges(tiles_sorted, inst_max, cnt, ranges, st));
+    const bool use_list = f.n_groups > 1;
+    if (use_list) {
+        int kbits = 24;
+        while ((1 << (kbits - 24)) < f.n_groups) ++kbits;
+        GB_CUDA(ctx, launch_tile_list(f, ranges, tl_keys, tl_vals, st));
+        GB_CUDA(ctx, radix_sort_pairs(tl_keys, tl_vals, tl_keys_tmp, tl_vals_tmp, tl_keys_out, tile_list, f.n_tiles,
+                                      nullptr, 0, kbits, scratch, kNaRadixBytes, st));
+    }
+    RenderBufs b;
+    b.rec = rec;
+    b.perm = perm;
+    b.inst_val = vals_sorted;
+    b.ranges = ranges;
+    b.pbox = pbox;
+    b.rgb = rgb;
+    b.depth = depth;
+    b.alpha = alpha;
+    b.t_final = t_final;
+    b.last = last;
+    b.cnt = cnt;
+    GB_CUDA(ctx, launch_render_fwd(f, b, bf, use_list ? tile_list : nullptr, nullptr, false, st));
     return GB_OK;
 }
 
