@@ -295,7 +295,8 @@ def run_ours(args, world, rank, local):
                    "graph": graph is not None, "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{world}"},
         "clocks": clocks, "gpu_launches": int(launches), "phases_ms": phases,
-        "stats": {k: pairs[k] for k in ("visible", "instances", "pairs_fwd", "pairs_bwd", "records")},
+        "stats": {k: pairs[k] for k in ("visible", "instances", "pairs_fwd", "pairs_bwd", "blended_fwd",
+                                        "contributing_bwd", "records")},
         "roofline": roofline,
     }
 
@@ -340,9 +341,9 @@ def roofline_line(dominant, phases, st, clocks):
     sm = clocks.get("sm_mhz") or 2070.0
     peak = 152 * 128 * 2 * sm * 1e6 / 1e12
     if dominant == "render_bwd":
-        flops = 30 * st["pairs_bwd"] + 200 * st["pairs_bwd"]
+        flops = 30 * st["pairs_bwd"] + 200 * st["contributing_bwd"]
     elif dominant == "render_fwd":
-        flops = 91 * st["pairs_fwd"]
+        flops = 30 * st["pairs_fwd"] + 61 * st["blended_fwd"]
     else:
         flops = None
     achieved = flops / (ms / 1e3) / 1e12 if flops else None

@@ -67,7 +67,8 @@ class gb_stats(C.Structure):
     _fields_ = [("records", C.c_int64), ("visible", C.c_int64), ("instances", C.c_int64),
                 ("tiles", C.c_int64), ("pixels", C.c_int64), ("capacity", C.c_int64),
                 ("overflow", C.c_int32), ("error_flags", C.c_int32),
-                ("pairs_fwd", C.c_int64), ("pairs_bwd", C.c_int64)]
+                ("pairs_fwd", C.c_int64), ("pairs_bwd", C.c_int64),
+                ("blended_fwd", C.c_int64), ("contributing_bwd", C.c_int64)]
 
 
 _lib = None

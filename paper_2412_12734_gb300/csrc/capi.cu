@@ -415,6 +415,8 @@ gb_status gb_saved_stats(gb_saved *s, gb_stats *out) {
     out->error_flags = int32_t(s->cnt_host->error_flags);
     out->pairs_fwd = int64_t(s->cnt_host->pairs_fwd);
     out->pairs_bwd = int64_t(s->cnt_host->pairs_bwd);
+    out->blended_fwd = int64_t(s->cnt_host->blend_fwd);
+    out->contributing_bwd = int64_t(s->cnt_host->contrib_bwd);
     return GB_OK;
 }
 
@@ -661,6 +663,7 @@ gb_status gb_render_backward(gb_context *ctx, gb_saved *s, const float *d_rgb, c
     b.d_alpha = d_alpha;
     b.rec_grad = s->rec_grad;
     GB_CUDA(ctx, cudaMemsetAsync(&s->cnt->pairs_bwd, 0, sizeof(unsigned long long), st));
+    GB_CUDA(ctx, cudaMemsetAsync(&s->cnt->contrib_bwd, 0, sizeof(unsigned long long), st));
     const bool persistent = (s->flags & GB_FLAG_PERSISTENT) != 0;
     if (s->ppt == 2)
         GB_CUDA(ctx, launch_render_bwd2(f, b, s->batch_bwd, s->use_list ? s->tile_list : nullptr,

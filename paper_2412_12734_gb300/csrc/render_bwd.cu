@@ -117,7 +117,7 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
     const WarpBox wb = warp_box<TS>(tx, ty, threadIdx.x);
 
     float T = 1.0f, T_final = 1.0f, dC0 = 0, dC1 = 0, dC2 = 0, dD = 0, dA = 0;
-    uint32_t last = 0, npairs = 0;
+    uint32_t last = 0, npairs = 0, ncontrib = 0;
     if (threadIdx.x == 0) s_maxlast = 0;
     __syncthreads();
     if (inside) {
@@ -183,6 +183,7 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
                     const float alpha = clamped ? kAlphaMax : ar;
                     act = alpha >= kAlphaMin;
                     if (act) {
+                        ++ncontrib;
                         const float iom = fast_rcp(1.0f - alpha);
                         const float Ti = T * iom;
                         const Cell<N> cell = grid_cell<N>(u, v, sigma, kN);
@@ -197,7 +198,6 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
                         g[11] = ch0; g[12] = ch1; g[13] = ch2;
                         // adj-bilinear: grid adjoint and uv adjoint
                         float uh = 0.0f, vh = 0.0f;
-                        float *tgo = s_tg + i * TEXF;
                         if (N == 1) {
                             // the single texel is corner 0: reduced over the warp
                             g[kCornerSlot + 0] = ch0;
@@ -207,7 +207,6 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
                             const float fu = cell.fu, fv = cell.fv;
                             const float w00 = (1.0f - fu) * (1.0f - fv), w10 = fu * (1.0f - fv);
                             const float w01 = (1.0f - fu) * fv, w11 = fu * fv;
-                            const int o00 = 3 * cell.base, o10 = o00 + 3 * N, o01 = o00 + 3, o11 = o10 + 3;
                             // d colour / d f_u and d f_v, dotted with the colour adjoint
                             const float fuh = ch0 * ((qd.c10.x - qd.c00.x) * (1.0f - fv) + (qd.c11.x - qd.c01.x) * fv) +
                                               ch1 * ((qd.c10.y - qd.c00.y) * (1.0f - fv) + (qd.c11.y - qd.c01.y) * fv) +
@@ -332,8 +331,12 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
         __syncthreads();
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
+        ncontrib += __shfl_xor_sync(0xffffffffu, ncontrib, o);
+    }
     if (lane == 0 && npairs) atomicAdd(&b.fw.cnt->pairs_bwd, (unsigned long long)npairs);
+    if (lane == 0 && ncontrib) atomicAdd(&b.fw.cnt->contrib_bwd, (unsigned long long)ncontrib);
 }
 
 template <int TS, int N, typename TexT>

@@ -189,7 +189,6 @@ __device__ __forceinline__ void bwd2_tile(const Frame &f, const RenderBwdBufs &b
             const uint32_t idx = uint32_t(bs + i);
             bool a0 = in0 && idx < last0, a1 = in1 && idx < last1;
             if (!__any_sync(0xffffffffu, a0 || a1)) continue;
-            npairs += uint32_t(a0) + uint32_t(a1);
             const float4 q0 = s_rec[4 * i + 0], q1 = s_rec[4 * i + 1], q2 = s_rec[4 * i + 2], q3 = s_rec[4 * i + 3];
             const float dx = (xf - q2.x) - q2.z;
             const float2 dy = sub2(sub2(yf, bc(q2.y)), bc(q2.w));
@@ -210,6 +209,7 @@ __device__ __forceinline__ void bwd2_tile(const Frame &f, const RenderBwdBufs &b
             a0 = a0 && alpha.x >= kAlphaMin;
             a1 = a1 && alpha.y >= kAlphaMin;
             if (!__any_sync(0xffffffffu, a0 || a1)) continue;
+            npairs += uint32_t(a0) + uint32_t(a1);
             // from here on every quantity of an inactive pixel is zero
             rz = sel2(a0, a1, rz, bc(0.0f));
             u = sel2(a0, a1, u, bc(0.0f));
@@ -294,7 +294,7 @@ __device__ __forceinline__ void bwd2_tile(const Frame &f, const RenderBwdBufs &b
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
-    if (lane == 0 && npairs) atomicAdd(&b.fw.cnt->pairs_bwd, (unsigned long long)npairs);
+    if (lane == 0 && npairs) atomicAdd(&b.fw.cnt->contrib_bwd, (unsigned long long)npairs);
 }
 
 template <int TS, int N, typename TexT>

@@ -45,7 +45,7 @@ __device__ __forceinline__ void fwd_tile(const Frame &f, const RenderBufs &b, in
     const float kN = float(N - 1) / (2.0f * sigma);
 
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, Dp = 0.0f;
-    uint32_t last = 0, npairs = 0;
+    uint32_t last = 0, npairs = 0, nblend = 0;
     bool done = !inside;
     for (int bs = 0; bs < n_inst; bs += batch) {
         if (__syncthreads_count(done) == NT) break;
@@ -87,12 +87,17 @@ __device__ __forceinline__ void fwd_tile(const Frame &f, const RenderBufs &b, in
                 Dp = fmaf(zi, w, Dp);
                 T = tT;
                 last = uint32_t(bs + i + 1);
+                ++nblend;
             }
         }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
+        nblend += __shfl_xor_sync(0xffffffffu, nblend, o);
+    }
     if ((threadIdx.x & 31) == 0 && npairs) atomicAdd(&b.cnt->pairs_fwd, (unsigned long long)npairs);
+    if ((threadIdx.x & 31) == 0 && nblend) atomicAdd(&b.cnt->blend_fwd, (unsigned long long)nblend);
     if (inside) {
         const int64_t pix = cam.pix_off + int64_t(py) * cam.width + px;
         b.rgb[3 * pix + 0] = C0 + T * f.bg[0];
