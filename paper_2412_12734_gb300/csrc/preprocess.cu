@@ -123,6 +123,29 @@ __device__ __forceinline__ DF df_div(DF a, DF b) {
     const float q2 = __fdiv_rn(r.hi, b.hi);
     return fast_two_sum(q1, q2);
 }
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    DF p = two_prod(a.hi, b.hi);
+    return fast_two_sum(p.hi, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo)));
+}
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ DF df_sqrt(DF a) {
+    const float x = sqrtf(a.hi);
+    const DF p = two_prod(x, x);
+    const DF r = df_add(a, df_neg(p));
+    return fast_two_sum(x, r.hi / (2.0f * x));
+}
+// 2 a in double-float (exact)
+__device__ __forceinline__ DF df_twice(DF a) { return DF{2.0f * a.hi, 2.0f * a.lo}; }
+// 1 - 2 a
+__device__ __forceinline__ DF df_one_minus_twice(DF a) { return df_add(DF{1.0f, 0.0f}, df_neg(df_twice(a))); }
+// dot of an FP32 row with a double-float vector
+__device__ __forceinline__ DF df_dot_fd(const float *row, const DF v[3]) {
+    DF acc = df_mul_f(v[0], row[0]);
+    acc = df_add(acc, df_mul_f(v[1], row[1]));
+    return df_add(acc, df_mul_f(v[2], row[2]));
+}
+
 // dot(row, p) + t in double-float
 __device__ __forceinline__ DF df_affine(const float *row, const float p[3], float t) {
     DF acc = two_prod(row[0], p[0]);
@@ -291,17 +314,28 @@ __global__ void __launch_bounds__(256) preprocess_kernel(Frame f, uint32_t *dept
                                      uint32_t(pr[2] / T) | (uint32_t(pr[3] / T) << 16));
             pbox[r] = make_uint2(uint32_t(pr[0]) | (uint32_t(pr[1]) << 16), uint32_t(pr[2]) | (uint32_t(pr[3]) << 16));
             // ---- render record ----
-            const Frame3 fr = tangent_frame(q);
-            // camera-space tangent axes A = s_u R t_u, B = s_v R t_v and normal
-            // n = A x B = s_u s_v R t_w
-            const float w = fr.qn[0], x = fr.qn[1], y = fr.qn[2], zq = fr.qn[3];
-            const float tw[3] = {2.0f * (x * zq + w * y), 2.0f * (y * zq - w * x), 1.0f - 2.0f * (x * x + y * y)};
-            float A[3], B[3], nv[3];
+            // The whole record chain in double-float (~48 bits): unit quaternion,
+            // tangent frame, camera-space axes A = s_u R t_u, B = s_v R t_v,
+            // normal n = A x B = s_u s_v R t_w, centre P, centre-relative block t
+            // and m = (fy n_x, fx n_y, fx fy n.P / z) / z.  Only n.P cancels (grazing
+            // view); below cos = 1/256 the block is redone in FP64.
+            DF qn2 = two_prod(q[0], q[0]);
+            for (int i = 1; i < 4; ++i) qn2 = df_add(qn2, two_prod(q[i], q[i]));
+            const DF qinv = df_div(DF{1.0f, 0.0f}, df_sqrt(qn2));
+            const DF w = df_mul_f(qinv, q[0]), x = df_mul_f(qinv, q[1]), y = df_mul_f(qinv, q[2]),
+                     zq = df_mul_f(qinv, q[3]);
+            const DF xx = df_mul(x, x), yy = df_mul(y, y), zz = df_mul(zq, zq), xy = df_mul(x, y), xzq = df_mul(x, zq),
+                     yzq = df_mul(y, zq), wx = df_mul(w, x), wy = df_mul(w, y), wz = df_mul(w, zq);
+            const DF tu[3] = {df_one_minus_twice(df_add(yy, zz)), df_twice(df_add(xy, wz)), df_twice(df_sub(xzq, wy))};
+            const DF tv[3] = {df_twice(df_sub(xy, wz)), df_one_minus_twice(df_add(xx, zz)), df_twice(df_add(yzq, wx))};
+            const DF tw[3] = {df_twice(df_add(xzq, wy)), df_twice(df_sub(yzq, wx)), df_one_minus_twice(df_add(xx, yy))};
+            const DF suv = two_prod(su, sv);
+            DF A[3], B[3], nv[3];
             for (int i = 0; i < 3; ++i) {
                 const float *row = cam.R + 3 * i;
-                A[i] = su * (row[0] * fr.tu[0] + row[1] * fr.tu[1] + row[2] * fr.tu[2]);
-                B[i] = sv * (row[0] * fr.tv[0] + row[1] * fr.tv[1] + row[2] * fr.tv[2]);
-                nv[i] = (su * sv) * (row[0] * tw[0] + row[1] * tw[1] + row[2] * tw[2]);
+                A[i] = df_mul_f(df_dot_fd(row, tu), su);
+                B[i] = df_mul_f(df_dot_fd(row, tv), sv);
+                nv[i] = df_mul(df_dot_fd(row, tw), suv);
             }
             const DF Px = df_affine(cam.R + 0, p, cam.t[0]);
             const DF Py = df_affine(cam.R + 3, p, cam.t[1]);
@@ -310,21 +344,19 @@ __global__ void __launch_bounds__(256) preprocess_kernel(Frame f, uint32_t *dept
             const DF cxd = df_add(df_mul_f(xz, cam.fx), DF{cam.cx, 0.0f});
             const DF cyd = df_add(df_mul_f(yz, cam.fy), DF{cam.cy, 0.0f});
             const float z = Pz.hi;
-            const float iz = 1.0f / z;
-            // n . P: the only cancelling quantity (grazing view); double-float dot
-            DF np = two_prod(nv[0], Px.hi);
-            np = df_add(np, two_prod(nv[1], Py.hi));
-            np = df_add(np, two_prod(nv[2], Pz.hi));
-            const float nmag = fabsf(nv[0] * Px.hi) + fabsf(nv[1] * Py.hi) + fabsf(nv[2] * Pz.hi);
+            DF np = df_mul(nv[0], Px);
+            np = df_add(np, df_mul(nv[1], Py));
+            np = df_add(np, df_mul(nv[2], Pz));
+            const float nmag = fabsf(nv[0].hi * Px.hi) + fabsf(nv[1].hi * Py.hi) + fabsf(nv[2].hi * Pz.hi);
             float t00, t01, t10, t11, m20, m21, m22;
-            if (fabsf(np.hi) * 4.0f > nmag) {
-                t00 = cam.fx * det2(A[0], A[2], Px.hi, z) * iz;
-                t01 = cam.fx * det2(B[0], B[2], Px.hi, z) * iz;
-                t10 = cam.fy * det2(A[1], A[2], Py.hi, z) * iz;
-                t11 = cam.fy * det2(B[1], B[2], Py.hi, z) * iz;
-                m20 = cam.fy * nv[0] * iz;
-                m21 = cam.fx * nv[1] * iz;
-                m22 = (cam.fx * cam.fy) * np.hi * iz * iz;
+            if (fabsf(np.hi) * 256.0f > nmag) {
+                t00 = df_mul_f(df_sub(A[0], df_mul(A[2], xz)), cam.fx).hi;
+                t01 = df_mul_f(df_sub(B[0], df_mul(B[2], xz)), cam.fx).hi;
+                t10 = df_mul_f(df_sub(A[1], df_mul(A[2], yz)), cam.fy).hi;
+                t11 = df_mul_f(df_sub(B[1], df_mul(B[2], yz)), cam.fy).hi;
+                m20 = df_div(df_mul_f(nv[0], cam.fy), Pz).hi;
+                m21 = df_div(df_mul_f(nv[1], cam.fx), Pz).hi;
+                m22 = df_div(df_div(df_mul(np, two_prod(cam.fx, cam.fy)), Pz), Pz).hi;
             } else {
                 float t[4], m[3];
                 homography_fp64(p, q, su, sv, cam, t, m);
