@@ -451,12 +451,21 @@ def cpu_baseline(args, wl, rgb, alpha, depth, cams):
     a = alpha[:W * H].reshape(H, W)[y0:y0 + h, x0:x0 + w].cpu().numpy().astype(np.float64)
     mask = ref["margin_fwd"] > 1e-5
     err = np.abs(img - ref["rgb"]).max(axis=2)
+    aerr = np.abs(a - ref["alpha"])
+    cond = ref["cond"]
+    well = mask & (cond <= 10.0)
     base = {"value": px / dt / 1e6, "unit": "Mpixel/s", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{w}x{h} crop of camera 0, fwd+bwd, FP64 bbox-prefiltered oracle, {dt:.1f} s"}
-    errs = {"rgb": float(err[mask].max()) if mask.any() else 0.0,
-            "alpha": float(np.abs(a - ref["alpha"])[mask].max()) if mask.any() else 0.0,
+
+    def mx(x, m):
+        return float(x[m].max()) if m.any() else 0.0
+    errs = {"rgb": mx(err, mask), "alpha": mx(aerr, mask),
+            "rgb_cond_le_10": mx(err, well), "alpha_cond_le_10": mx(aerr, well),
+            "rgb_per_cond": mx(err / np.maximum(cond, 1.0), mask),
+            "cond_gt_10_px": int((mask & (cond > 10.0)).sum()),
             "excluded_px": int((~mask).sum()), "pixels": int(w * h),
-            "storage": "errors are against the FP64 oracle on the stored FP16 values"}
+            "storage": "errors are against the FP64 oracle on the stored FP16 values; cond is the "
+                       "oracle's per-pixel conditioning of the FP32 plane-hit evaluation"}
     return base, errs
 
 

@@ -95,8 +95,9 @@ typedef struct {
                           /*       discontinuous decision to its threshold  */
     double *margin_grad;  /* [h*w] same over every decision with a kink      */
     double *cond;         /* [h*w] sum over blended splats of alpha T kappa,  */
-                          /*       kappa = condition number of the plane-hit */
-                          /*       denominator about the projected centre    */
+                          /*       kappa = first-order sensitivity of the    */
+                          /*       plane hit (u, v) about the projected      */
+                          /*       centre to relative rounding of its terms  */
     int64_t *n_pairs;     /* [1]   pairs evaluated                           */
 } orc_fwd_out;
 
@@ -582,9 +583,20 @@ static void pixel_forward(const Ctx &cx, int px, int py, std::vector<Contrib> *c
         cb.zi = e.uv_branch ? (pr.T[6] * e.u + pr.T[7] * e.v + pr.T[8]) : pr.T[8];
         const double w = e.alpha * T;
         if (e.uv_branch) {
+            /* first-order sensitivity of (u, v) to relative perturbations of
+               the centre-relative offsets and coefficients, over (1+|u|+|v|):
+               the denominator's cancellation times |u|+|v|, plus the
+               numerators' cancellation (a sub-pixel-thin splat seen from far
+               along its long axis) */
             const double a0 = std::fabs(pr.m[0] * e.dx), a1 = std::fabs(pr.m[1] * e.dy), a2 = std::fabs(pr.m[2]);
             const double den = std::fabs(pr.m[0] * e.dx + pr.m[1] * e.dy + pr.m[2]);
-            kap_sum += w * ((a0 + a1 + a2) / std::max(den, 1e-300));
+            const double kz = (a0 + a1 + a2) / std::max(den, 1e-300);
+            const double *A = pr.adj;
+            const double zz = std::max(std::fabs(e.zeta[2]), 1e-300);
+            const double nu = (std::fabs(A[0] * e.dx) + std::fabs(A[1] * e.dy)) / zz;
+            const double nv = (std::fabs(A[3] * e.dx) + std::fabs(A[4] * e.dy)) / zz;
+            const double s = std::fabs(e.u) + std::fabs(e.v);
+            kap_sum += w * std::max(kz, (nu + nv + s * kz) / (1.0 + s));
         } else {
             kap_sum += w;
         }

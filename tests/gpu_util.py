@@ -7,6 +7,7 @@ import numpy as np
 import oracle
 
 IMG_TOL = 2e-5        # max abs error of rgb and alpha against the FP64 oracle
+COND_TOL = 32 * 2.0 ** -24  # per unit of the oracle's conditioning: the bar is max(IMG_TOL, COND_TOL*cond)
 GRAD_REL = 1e-3       # per-tensor relative gradient tolerance
 MARGIN_FWD = 1e-5     # pixels this close (relative) to a forward decision are excluded
 MARGIN_GRAD = 1e-4    # pixels this close to any decision get zero upstream gradient
@@ -51,7 +52,16 @@ def oracle_run(scene, cam, bg=None, prefilter=False):
 
 
 def compare_images(gpu_img, ref, what="rgb", tol=IMG_TOL, relative_to=None):
-    """Max error over pixels whose forward decisions are not within the margin."""
+    """Max error, in units of the ``tol`` bar, over pixels whose forward
+    decisions are not within the margin.
+
+    The kernels evaluate every pixel/splat pair in FP32 (Sec. 3.2), so a
+    pixel's error scales with the conditioning of that evaluation: the oracle's
+    ``cond`` is the alpha*T-weighted sensitivity of (u, v) to relative rounding
+    of the centre-relative terms, about 1 for most pixels and up to a few
+    hundred where a sub-pixel-thin splat is seen from far along its long axis.
+    A pixel's bar is max(tol, COND_TOL * cond); its error is scaled by
+    tol / bar, so the returned value compares directly with ``tol``."""
     mask = ref["margin_fwd"] > MARGIN_FWD
     a = np.asarray(gpu_img, np.float64)
     b = ref[what]
@@ -60,6 +70,7 @@ def compare_images(gpu_img, ref, what="rgb", tol=IMG_TOL, relative_to=None):
         err = err / np.maximum(1.0, np.abs(relative_to))
     if err.ndim == 3:
         err = err.max(axis=2)
+    err = err * (tol / np.maximum(tol, COND_TOL * ref["cond"]))
     excluded = int((~mask).sum())
     return float(err[mask].max()) if mask.any() else 0.0, excluded
 

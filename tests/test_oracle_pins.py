@@ -254,6 +254,41 @@ def test_fronto_parallel_uv_and_colour_closed_form():
     np.testing.assert_allclose(r["depth"], zmap, atol=1e-9)
 
 
+def test_conditioning_closed_form_rotated_fronto_splat():
+    """The oracle's per-pixel conditioning (the test tolerance's scale for the
+    FP32 evaluation of Sec. 3.2): for one splat parallel to the image plane
+    and turned by theta about the optical axis, zeta_z is constant (its
+    sensitivity is 1) and u = (dx cos + dy sin) z / (f s_u), so the numerator
+    sensitivities are (|dx cos| + |dy sin|) z / (f s_u) and likewise for v.
+    cond = alpha * max(1, (n_u + n_v + |u| + |v|) / (1 + |u| + |v|)) on the uv
+    branch and alpha on the low-pass branch."""
+    th = math.radians(30.0)
+    sc, cam = _fronto_scene(s=(0.01, 0.6), o=0.8, z=5.0, N=4, sigma=1.0)
+    sc["quats"] = np.array([[math.cos(th / 2), 0, 0, math.sin(th / 2)]], np.float32)
+    r = oracle.render(sc, cam)
+    q = sc["quats"][0].astype(np.float64)
+    q /= np.linalg.norm(q)
+    th = 2 * math.atan2(q[3], q[0])
+    p = sc["means"][0].astype(np.float64)
+    f, z = 64.0, p[2]
+    c = (f * p[0] / z + 32, f * p[1] / z + 24)
+    s32 = sc["scales"][0].astype(np.float64)
+    xs, ys = np.meshgrid(np.arange(64) + 0.5, np.arange(48) + 0.5)
+    dx, dy = xs - c[0], ys - c[1]
+    co, si = math.cos(th), math.sin(th)
+    u = (dx * co + dy * si) * z / (f * s32[0])
+    v = (-dx * si + dy * co) * z / (f * s32[1])
+    nu = (np.abs(dx * co) + np.abs(dy * si)) * z / (f * s32[0])
+    nv = (np.abs(dx * si) + np.abs(dy * co)) * z / (f * s32[1])
+    rho_uv, rho_lp = u * u + v * v, 2 * (dx * dx + dy * dy)
+    alpha = np.minimum(0.99, np.float32(0.8) * np.exp(-np.minimum(rho_uv, rho_lp) / 2))
+    sa = np.abs(u) + np.abs(v)
+    kap = np.where(rho_uv <= rho_lp, np.maximum(1.0, (nu + nv + sa) / (1 + sa)), 1.0)
+    expect = np.where(alpha >= 1 / 255, alpha * kap, 0.0)
+    assert expect.max() > 5.0  # pixels along the long axis are ill-conditioned
+    np.testing.assert_allclose(r["cond"], expect, rtol=1e-9, atol=1e-12)
+
+
 def test_lowpass_branch_closed_form():
     """A splat far smaller than a pixel is drawn by the screen-space low-pass
     disk: alpha = o exp(-|x - c|^2) (rho = 2 |x - c|^2)."""
