@@ -153,8 +153,11 @@ def oracle_sample(wl, crop: int):
     d = wl["d_rgb"][0][y0:y0 + h, x0:x0 + w]
     t0 = time.perf_counter()
     ref = oracle.render(sc, cam, window=win, prefilter=True)
-    oracle.backward(sc, cam, d, window=win, prefilter=True)
+    # upstream gradient zeroed at pixels within 1e-4 of a decision threshold
+    d = d * (ref["margin_grad"] > 1e-4)[..., None]
+    ref["grads"] = oracle.backward(sc, cam, d, window=win, prefilter=True)
     dt = time.perf_counter() - t0
+    ref["d_rgb"] = d
     return dt, w * h, ref, win
 
 
@@ -310,7 +313,8 @@ def run_ours(args, world, rank, local):
 
     # --- CPU oracle baseline + max error vs FP64 (rank 0)
     if rank == 0 and not args.no_cpu_baseline:
-        result["cpu_baseline"], result["max_err_vs_fp64"] = cpu_baseline(args, wl, rgb, alpha, depth, cams)
+        result["cpu_baseline"], result["max_err_vs_fp64"] = cpu_baseline(args, wl, rgb, alpha, depth, cams,
+                                                                          rast, dev_scene)
 
     if rank == 0:
         print(json.dumps(result), flush=True)
@@ -441,7 +445,20 @@ def e2e(args, wl, rast, R, L, torch, cams, P):
             "note": "synchronizing forward (sizes the instance list on the host each step)"}
 
 
-def cpu_baseline(args, wl, rgb, alpha, depth, cams):
+def grad_ratios(g_gpu, g_ref):
+    """Worst |g - g*| / (1e-3 max(|g*|, 1e-2 max|g*|)) per tensor; <= 1 is within tolerance."""
+    out = {}
+    for k, ref in g_ref.items():
+        a = g_gpu[k].detach().double().cpu().numpy().reshape(ref.shape)
+        scale = np.abs(ref).max()
+        den = 1e-3 * np.maximum(np.abs(ref), 1e-2 * scale) if scale > 0 else 1.0
+        out[k] = float((np.abs(a - ref) / den).max())
+    return out
+
+
+def cpu_baseline(args, wl, rgb, alpha, depth, cams, rast, dev_scene):
+    import torch
+
     import oracle
     oracle.build()
     dt, px, ref, win = oracle_sample(wl, args.crop)
@@ -466,6 +483,13 @@ def cpu_baseline(args, wl, rgb, alpha, depth, cams):
             "excluded_px": int((~mask).sum()), "pixels": int(w * h),
             "storage": "errors are against the FP64 oracle on the stored FP16 values; cond is the "
                        "oracle's per-pixel conditioning of the FP32 plane-hit evaluation"}
+    # gradients of camera 0 alone (same masked upstream gradient) against the oracle's
+    d_full = np.zeros((H, W, 3), np.float32)
+    d_full[y0:y0 + h, x0:x0 + w] = ref["d_rgb"]
+    s0 = rast.forward([dev_scene], cams[:1])[3]
+    g = rast.backward(s0, torch.as_tensor(d_full.reshape(-1, 3), device="cuda"))[0]
+    errs["grad_worst_ratio"] = grad_ratios(g, ref["grads"])
+    errs["grad_tolerance"] = "per element |g-g*| <= 1e-3 max(|g*|, 1e-2 max|g*|); ratio <= 1 passes"
     return base, errs
 
 
