@@ -84,6 +84,10 @@ __device__ __forceinline__ float warp_reduce_scatter32(float v[32], int lane) {
 // Warp-reduced values: 0..13 record gradients, 14..25 the RGB gradient of the
 // grid's four corner texels (0,0), (0,N-1), (N-1,0), (N-1,N-1).
 constexpr int kCornerSlot = 14;
+// For N = 8, above this many distinct edge/interior cells in a (warp, splat)
+// pair the lanes add their texel weights to shared memory directly instead of
+// one reduce-scatter per cell (measured: faster at N = 8, slower at N <= 4).
+constexpr int kGroupCells8 = 4;
 
 template <int TS, int N, typename TexT>
 __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b, int batch, uint32_t tile) {
@@ -96,7 +100,8 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
     int32_t *s_k = reinterpret_cast<int32_t *>(s_tex + batch * NN);
     uint32_t *s_j = reinterpret_cast<uint32_t *>(s_k + batch);
     uint2 *s_box = reinterpret_cast<uint2 *>(s_j + batch);
-    float *s_g = reinterpret_cast<float *>(s_box + batch);  // [batch][16]
+    uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_box + batch);
+    float *s_g = reinterpret_cast<float *>(s_mask + batch);  // [batch][16]
     float *s_tg = s_g + batch * kRecGrad;                  // [batch][TEXF]
     __shared__ uint32_t s_maxlast;
 
@@ -114,7 +119,7 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
     const uint2 range = b.fw.ranges[tile];
     const float sigma = sc.sigma;
     const float kN = float(N - 1) / (2.0f * sigma);
-    const WarpBox wb = warp_box<TS>(tx, ty, threadIdx.x);
+    const uint32_t wbit = 1u << (threadIdx.x >> 5);  // this warp's 8 x 4 block in the splat masks
 
     float T = 1.0f, T_final = 1.0f, dC0 = 0, dC1 = 0, dC2 = 0, dD = 0, dA = 0;
     uint32_t last = 0, npairs = 0, ncontrib = 0;
@@ -149,12 +154,13 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
         const int bs = max(0, be - batch), nb = be - bs;
         for (int e = threadIdx.x; e < nb * kRecGrad; e += NT) s_g[e] = 0.0f;
         for (int e = threadIdx.x; e < nb * TEXF; e += NT) s_tg[e] = 0.0f;
-        stage_batch<N, NT, TexT>(b.fw, cam, sc, range.x + bs, nb, s_rec, s_tex, s_k, s_j, s_box);
+        stage_batch<N, NT, TexT, TS, 4>(b.fw, cam, sc, range.x + bs, nb, tx * TS, ty * TS, s_rec, s_tex, s_k, s_j,
+                                        s_box, s_mask);
         __syncthreads();
         // splats at or beyond the warp's last contributor are skipped warp-wide
         const int i_hi = min(nb, int(wlast) - bs);
         for (int i = i_hi - 1; i >= 0; --i) {
-            if (wb.misses(s_box[i])) continue;
+            if (!(s_mask[i] & wbit)) continue;
             float g[32];
 #pragma unroll
             for (int q = 0; q < 32; ++q) g[q] = 0.0f;
@@ -285,11 +291,38 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
                     if (lane < kCornerSlot) atomicAdd(s_g + i * kRecGrad + lane, tot);
                     else if (my_corner >= 0) atomicAdd(s_tg + i * TEXF + my_corner_off, tot);
                 }
-                // edge / interior texels: lanes sharing a cell touch the same four
-                // texels; each group is one reduce-scatter and one conflict-free atomic
+                // edge / interior texels: lanes sharing a cell are reduced together
+                // (one reduce-scatter and one conflict-free atomic per cell); at
+                // N = 8, when many distinct cells are hit, each lane adds its
+                // weights to shared memory directly instead.
                 if (N > 2) {
-                    unsigned pending = __ballot_sync(0xffffffffu, (rw00 != 0.0f) | (rw10 != 0.0f) | (rw01 != 0.0f) |
-                                                                     (rw11 != 0.0f));
+                    const bool has_rem = (rw00 != 0.0f) | (rw10 != 0.0f) | (rw01 != 0.0f) | (rw11 != 0.0f);
+                    unsigned pending = __ballot_sync(0xffffffffu, has_rem);
+                    int cells = 0;
+                    if (N >= 8 && pending) {
+                        const unsigned same = __match_any_sync(0xffffffffu, has_rem ? rbase : -1);
+                        cells = __popc(__ballot_sync(0xffffffffu, has_rem && (__ffs(same) - 1) == lane));
+                    }
+                    if (cells > kGroupCells8) {
+                        if (has_rem) {
+                            float *t = s_tg + i * TEXF + 3 * rbase;
+                            if (rw00 != 0.0f) {
+                                atomicAdd(t + 0, rw00 * rch0); atomicAdd(t + 1, rw00 * rch1); atomicAdd(t + 2, rw00 * rch2);
+                            }
+                            if (rw10 != 0.0f) {
+                                atomicAdd(t + 3 * N + 0, rw10 * rch0); atomicAdd(t + 3 * N + 1, rw10 * rch1);
+                                atomicAdd(t + 3 * N + 2, rw10 * rch2);
+                            }
+                            if (rw01 != 0.0f) {
+                                atomicAdd(t + 3, rw01 * rch0); atomicAdd(t + 4, rw01 * rch1); atomicAdd(t + 5, rw01 * rch2);
+                            }
+                            if (rw11 != 0.0f) {
+                                atomicAdd(t + 3 * N + 3, rw11 * rch0); atomicAdd(t + 3 * N + 4, rw11 * rch1);
+                                atomicAdd(t + 3 * N + 5, rw11 * rch2);
+                            }
+                        }
+                        pending = 0u;
+                    }
                     while (pending) {
                         const int leader = __ffs(pending) - 1;
                         const int key = __shfl_sync(0xffffffffu, rbase, leader);

@@ -117,7 +117,8 @@ __device__ __forceinline__ void bwd2_tile(const Frame &f, const RenderBwdBufs &b
     int32_t *s_k = reinterpret_cast<int32_t *>(s_tex + batch * NN);
     uint32_t *s_j = reinterpret_cast<uint32_t *>(s_k + batch);
     uint2 *s_box = reinterpret_cast<uint2 *>(s_j + batch);
-    float *s_g = reinterpret_cast<float *>(s_box + batch);  // [batch][16]
+    uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_box + batch);
+    float *s_g = reinterpret_cast<float *>(s_mask + batch);  // [batch][16]
     float *s_tg = s_g + batch * kRecGrad;                    // [batch][TEXF]
     __shared__ uint32_t s_maxlast;
 
@@ -136,11 +137,7 @@ __device__ __forceinline__ void bwd2_tile(const Frame &f, const RenderBwdBufs &b
     const uint2 range = b.fw.ranges[tile];
     const float sigma = sc.sigma;
     const float kN = float(N - 1) / (2.0f * sigma);
-    WarpBox wb;
-    wb.x0 = tx * TS + bx;
-    wb.y0 = ty * TS + by;
-    wb.x1 = wb.x0 + 7;
-    wb.y1 = wb.y0 + 7;
+    const uint32_t wbit = 1u << warp;  // this warp's 8 x 8 block in the splat masks
 
     float2 T = bc(1.0f), Tfin = bc(1.0f), dR = bc(0.0f), dG = bc(0.0f), dB = bc(0.0f), dDp = bc(0.0f), dA = bc(0.0f);
     uint32_t last0 = 0, last1 = 0, npairs = 0;
@@ -181,11 +178,12 @@ __device__ __forceinline__ void bwd2_tile(const Frame &f, const RenderBwdBufs &b
         const int bs = max(0, be - batch), nb = be - bs;
         for (int e = threadIdx.x; e < nb * kRecGrad; e += NT) s_g[e] = 0.0f;
         for (int e = threadIdx.x; e < nb * TEXF; e += NT) s_tg[e] = 0.0f;
-        stage_batch<N, NT, TexT>(b.fw, cam, sc, range.x + bs, nb, s_rec, s_tex, s_k, s_j, s_box);
+        stage_batch<N, NT, TexT, TS, 8>(b.fw, cam, sc, range.x + bs, nb, tx * TS, ty * TS, s_rec, s_tex, s_k, s_j,
+                                        s_box, s_mask);
         __syncthreads();
         const int i_hi = min(nb, int(wlast) - bs);
         for (int i = i_hi - 1; i >= 0; --i) {
-            if (wb.misses(s_box[i])) continue;
+            if (!(s_mask[i] & wbit)) continue;
             const uint32_t idx = uint32_t(bs + i);
             bool a0 = in0 && idx < last0, a1 = in1 && idx < last1;
             if (!__any_sync(0xffffffffu, a0 || a1)) continue;

@@ -27,6 +27,7 @@ __device__ __forceinline__ void fwd_tile(const Frame &f, const RenderBufs &b, in
     int32_t *s_k = reinterpret_cast<int32_t *>(s_tex + batch * NN);
     uint32_t *s_j = reinterpret_cast<uint32_t *>(s_k + batch);
     uint2 *s_box = reinterpret_cast<uint2 *>(s_j + batch);
+    uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_box + batch);
 
     const int ci = camera_of_tile(f, tile);
     const CamDev &cam = f.cams[ci];
@@ -40,7 +41,7 @@ __device__ __forceinline__ void fwd_tile(const Frame &f, const RenderBufs &b, in
     const float xf = float(px) + 0.5f, yf = float(py) + 0.5f;
     const uint2 range = b.ranges[tile];
     const int n_inst = int(range.y - range.x);
-    const WarpBox wb = warp_box<TS>(tx, ty, threadIdx.x);
+    const uint32_t wbit = 1u << (threadIdx.x >> 5);  // this warp's 8 x 4 block in the splat masks
     const float sigma = sc.sigma;
     const float kN = float(N - 1) / (2.0f * sigma);
 
@@ -50,12 +51,13 @@ __device__ __forceinline__ void fwd_tile(const Frame &f, const RenderBufs &b, in
     for (int bs = 0; bs < n_inst; bs += batch) {
         if (__syncthreads_count(done) == NT) break;
         const int nb = min(batch, n_inst - bs);
-        stage_batch<N, NT, TexT>(b, cam, sc, range.x + bs, nb, s_rec, s_tex, s_k, s_j, s_box);
+        stage_batch<N, NT, TexT, TS, 4>(b, cam, sc, range.x + bs, nb, tx * TS, ty * TS, s_rec, s_tex, s_k, s_j,
+                                        s_box, s_mask);
         __syncthreads();
         if (!done) {
             for (int i = 0; i < nb; ++i) {
                 if (__all_sync(__activemask(), done)) break;
-                if (done || wb.misses(s_box[i])) continue;
+                if (done || !(s_mask[i] & wbit)) continue;
                 ++npairs;
                 const float4 q0 = s_rec[4 * i + 0], q1 = s_rec[4 * i + 1], q2 = s_rec[4 * i + 2];
                 const float dx = (xf - q2.x) - q2.z, dy = (yf - q2.y) - q2.w;
