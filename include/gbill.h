@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define GBILL_ABI_VERSION 1
+#define GBILL_ABI_VERSION 2
 #define GBILL_MAX_CAMERAS 64
 #define GBILL_MAX_SCENES 16
 
@@ -104,7 +104,15 @@ typedef struct {
     int32_t tex_n;            /* N in {1,2,4,8}                                  */
     int32_t tex_dtype;        /* gb_dtype                                        */
     float sigma;              /* grid extent in uv units (paper default 0.5)     */
-    int32_t reserved;         /* must be 0                                       */
+    int32_t mip_level;        /* 0: render the N x N grid.  l in 1..log2(N):     */
+                              /* render every grid box-filtered to N/2^l x N/2^l */
+                              /* (texel = mean of its 2^l x 2^l block; Sec. 5.1, */
+                              /* Fig. 3 f, g); gradients still reach the N x N   */
+                              /* texels (1/4^l of the coarse texel's gradient).  */
+                              /* The filtered grids live in FP32 scratch of the  */
+                              /* saved state, sized by a synchronizing forward;  */
+                              /* a no-sync forward that needs more fails with    */
+                              /* GB_ERR_CAPACITY.                                 */
 } gb_scene;
 
 /* Gradient outputs of one scene, FP32 device arrays shaped like the inputs.
@@ -314,7 +322,8 @@ gb_status gb_adam_step(gb_context *ctx, const gb_adam_tensor *tensors, int32_t n
  * Limits per call: 131,072 records (splats x cameras), 524,288 (tile, splat)
  * instances, 1,048,576 pixels, 8,192 tiles; beyond them the call returns
  * GB_ERR_CAPACITY with a message and renders nothing.  GB_FLAG_TIMING and
- * GB_FLAG_PERSISTENT are rejected (GB_ERR_UNSUPPORTED).
+ * GB_FLAG_PERSISTENT, and scenes with a mip_level, are rejected
+ * (GB_ERR_UNSUPPORTED).
  * It calls no cudaMalloc, cudaFree or other allocating routine.  The first
  * call on a device looks up the array's device address (cudaGetSymbolAddress,
  * with that device current); make that first call before any stream capture.

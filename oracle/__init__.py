@@ -14,7 +14,8 @@ them (numpy's stable argsort).
 
 Sections cited: Sec. 3.1 Eq. 2-4 (compositing, 2DGS plane, uv Gaussian),
 Sec. 3.2 Eq. 5 (bilinear colour grid), Sec. 4.2 (SH added to the grid colour),
-Alg. 1 (rasterize fwd/bwd), Alg. 2 (bilinear / adj-bilinear).
+Alg. 1 (rasterize fwd/bwd), Alg. 2 (bilinear / adj-bilinear), Sec. 5.1 and
+Fig. 3 f, g (colour grid box-filtered to a coarser mip level at render time).
 """
 from __future__ import annotations
 
@@ -96,15 +97,41 @@ def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
 
 
+def mip_grid(textures, level: int):
+    """Colour grids box-filtered to mip level ``level`` (Sec. 5.1, Fig. 3 f, g):
+    texel (i, j) of the (N/2^l) x (N/2^l) grid is the mean of the 2^l x 2^l
+    block of texels (2^l i + a, 2^l j + b), a, b < 2^l.  Level 0 is the grid
+    itself."""
+    t = _f64(textures)
+    K, N = t.shape[0], t.shape[1]
+    f = 1 << int(level)
+    if N % f:
+        raise ValueError(f"mip level {level} needs N divisible by {f}")
+    return np.ascontiguousarray(t.reshape(K, N // f, f, N // f, f, 3).mean(axis=(2, 4)))
+
+
+def mip_grid_adjoint(d_coarse, level: int):
+    """Adjoint of mip_grid: every fine texel of a block receives 1/4^l of the
+    block's coarse gradient."""
+    f = 1 << int(level)
+    return np.repeat(np.repeat(_f64(d_coarse), f, axis=1), f, axis=2) / float(f * f)
+
+
 class _SceneRef:
-    """Holds FP64 copies (exact upcasts of the stored values) alive for a call."""
+    """Holds FP64 copies (exact upcasts of the stored values) alive for a call.
+    A scene with ``mip_level`` l > 0 is rendered with its grids box-filtered
+    to N / 2^l (mip_grid)."""
 
     def __init__(self, scene: dict):
         self.arrays = {k: _f64(scene[k]) for k in
                        ("means", "quats", "scales", "opacities", "sh", "textures")}
         self.K = int(self.arrays["means"].shape[0])
         self.D = int(scene["sh_degree"])
-        self.N = int(scene["tex_n"])
+        self.mip = int(scene.get("mip_level", 0))
+        self.N_src = int(scene["tex_n"])
+        if self.mip:
+            self.arrays["textures"] = mip_grid(self.arrays["textures"], self.mip)
+        self.N = self.N_src >> self.mip
         s = _Scene()
         s.num_splats = self.K
         for k, a in self.arrays.items():
@@ -146,9 +173,10 @@ def render(scene: dict, cam: dict, window=None, bg=None, prefilter: bool = False
     Returns rgb [h,w,3], depth, alpha, t_final, n_contrib, margin_fwd,
     margin_grad, cond (each [h,w]) and the number of (pixel, splat) pairs
     evaluated.  cond = sum over blended splats of alpha T kappa, where kappa
-    is the condition number of the plane-hit denominator evaluated about the
-    splat's projected centre (1 on the low-pass branch): the factor by which
-    relative perturbations of the homography entries reach u and v.
+    is the first-order sensitivity of the plane hit (u, v), evaluated about
+    the splat's projected centre, to relative perturbations of its terms,
+    over 1 + |u| + |v| (1 on the low-pass branch): the factor by which
+    rounding of the homography entries and pixel offsets reaches u and v.
     """
     S = _SceneRef(scene)
     cm = _camera(cam)
@@ -180,7 +208,7 @@ def backward(scene: dict, cam: dict, dL_drgb, dL_ddepth=None, dL_dalpha=None, wi
     S = _SceneRef(scene)
     cm = _camera(cam)
     win = _window(cam, window)
-    K, D, N = S.K, S.D, S.N
+    K, D, N = S.K, S.D, S.N_src
     if grads is None:
         grads = {
             "means": np.zeros((K, 3)), "quats": np.zeros((K, 4)), "scales": np.zeros((K, 2)),
@@ -191,6 +219,11 @@ def backward(scene: dict, cam: dict, dL_drgb, dL_ddepth=None, dL_dalpha=None, wi
     for k in ("means", "quats", "scales", "opacities", "sh", "textures"):
         assert grads[k].dtype == np.float64 and grads[k].flags.c_contiguous
         setattr(g, "d_" + k, _p(grads[k]))
+    d_coarse = None
+    if S.mip:
+        # the C oracle differentiates the box-filtered grid; mip_grid_adjoint maps back
+        d_coarse = np.zeros((K, S.N, S.N, 3))
+        g.d_textures = _p(d_coarse)
     drgb = _f64(dL_drgb).reshape(win.h, win.w, 3)
     ddep = _f64(dL_ddepth).reshape(win.h, win.w) if dL_ddepth is not None else None
     dalp = _f64(dL_dalpha).reshape(win.h, win.w) if dL_dalpha is not None else None
@@ -200,6 +233,8 @@ def backward(scene: dict, cam: dict, dL_drgb, dL_ddepth=None, dL_dalpha=None, wi
                                    _p(ddep) if ddep is not None else None,
                                    _p(dalp) if dalp is not None else None, C.byref(g))
     assert rc == 0
+    if d_coarse is not None:
+        grads["textures"] += mip_grid_adjoint(d_coarse, S.mip)
     return grads
 
 

@@ -48,6 +48,12 @@ struct gb_saved {
     Counters *cnt_host;
     void *scratch;
     size_t scratch_bytes;
+    // mip-level grids: box-filtered FP32 grids of the last forward and their
+    // gradient, packed per scene at mip_off[] (floats)
+    float *mip_tex, *mip_grad;
+    int64_t mip_cap;
+    int64_t mip_off[kMaxScenes];
+    int32_t mip_ns[kMaxScenes];
     // last forward
     Frame frame;
     bool has_forward;
@@ -224,7 +230,9 @@ gb_status build_frame(gb_context *ctx, const gb_scene *scenes, int32_t n_scenes,
             return fail(ctx, GB_ERR_INVALID_ARG, "scene %d: bad storage dtype", s);
         if (!(g.sigma > 0.0f) || !isfinite(g.sigma))
             return fail(ctx, GB_ERR_INVALID_ARG, "scene %d: sigma must be positive", s);
-        if (g.reserved != 0) return fail(ctx, GB_ERR_INVALID_ARG, "scene %d: reserved field must be 0", s);
+        if (g.mip_level < 0 || (g.tex_n >> g.mip_level) < 1 || g.mip_level > 3)
+            return fail(ctx, GB_ERR_INVALID_ARG, "scene %d: mip_level %d not in 0..log2(%d)", s, g.mip_level,
+                        g.tex_n);
         if (g.num_splats > 0 && (!g.means || !g.quats || !g.scales || !g.opacities || !g.sh || !g.textures))
             return fail(ctx, GB_ERR_INVALID_ARG, "scene %d: null parameter pointer", s);
         d.K = g.num_splats;
@@ -239,18 +247,22 @@ gb_status build_frame(gb_context *ctx, const gb_scene *scenes, int32_t n_scenes,
         d.N = g.tex_n;
         d.tex_dtype = g.tex_dtype;
         d.sigma = g.sigma;
+        d.mip = g.mip_level;
         max_k = std::max(max_k, g.num_splats);
     }
-    // render groups: one per distinct (tex_n, tex_dtype) among the cameras' scenes
+    // render groups: one per distinct (rendered grid size, tex_dtype) among the scenes
     int scene_group[kMaxScenes];
     for (int sidx = 0; sidx < n_scenes; ++sidx) {
+        // a scene at a mip level is rendered from its FP32 filtered grid
+        const int n_eff = scenes[sidx].tex_n >> scenes[sidx].mip_level;
+        const int dt = scenes[sidx].mip_level ? int(GB_F32) : scenes[sidx].tex_dtype;
         int g = -1;
         for (int k = 0; k < f.n_groups; ++k)
-            if (f.group_N[k] == scenes[sidx].tex_n && f.group_dtype[k] == scenes[sidx].tex_dtype) g = k;
+            if (f.group_N[k] == n_eff && f.group_dtype[k] == dt) g = k;
         if (g < 0) {
             g = f.n_groups++;
-            f.group_N[g] = scenes[sidx].tex_n;
-            f.group_dtype[g] = scenes[sidx].tex_dtype;
+            f.group_N[g] = n_eff;
+            f.group_dtype[g] = dt;
         }
         scene_group[sidx] = g;
     }
@@ -378,7 +390,7 @@ gb_status gb_saved_destroy(gb_saved *s) {
                     s->offsets, s->rect, s->pbox, s->inv, s->rec_grad, s->inst_tile, s->inst_val, s->inst_tile_tmp,
                     s->inst_val_tmp, s->tiles_sorted, s->vals_sorted, s->ranges, s->tl_keys, s->tl_vals,
                     s->tl_keys_tmp, s->tl_vals_tmp, s->tl_keys_out, s->tile_list, s->work, s->t_final, s->last,
-                    s->cnt, s->scratch};
+                    s->cnt, s->scratch, s->mip_tex, s->mip_grad};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (s->cnt_host) cudaFreeHost(s->cnt_host);
@@ -533,6 +545,33 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
         if ((r = reserve_instances(s, std::max<int64_t>(s->cap_inst, 1 << 16))) != GB_OK) return r;
         if ((r = reserve_scratch(s)) != GB_OK) return r;
     }
+    // mip-level scenes: filter their grids into FP32 scratch the render reads
+    int64_t mip_need = 0;
+    for (int i = 0; i < f.n_scenes; ++i) {
+        s->mip_off[i] = mip_need;
+        s->mip_ns[i] = f.scenes[i].N;
+        if (f.scenes[i].mip) {
+            const int64_t n = f.scenes[i].N >> f.scenes[i].mip;
+            mip_need += f.scenes[i].K * n * n * 3;
+        }
+    }
+    if (mip_need > s->mip_cap) {
+        if (nosync)
+            return fail(ctx, GB_ERR_CAPACITY,
+                        "mip-level grids need %lld floats of scratch: run a synchronizing forward first",
+                        (long long)mip_need);
+        GB_CUDA(ctx, alloc_t(&s->mip_tex, mip_need));
+        GB_CUDA(ctx, alloc_t(&s->mip_grad, mip_need));
+        s->mip_cap = mip_need;
+    }
+    for (int i = 0; i < f.n_scenes; ++i) {
+        SceneDev &d = f.scenes[i];
+        if (!d.mip) continue;
+        GB_CUDA(ctx, launch_mip_filter(d.tex, d.tex_dtype, d.K, d.N, d.mip, s->mip_tex + s->mip_off[i], st));
+        d.tex = s->mip_tex + s->mip_off[i];
+        d.tex_dtype = GB_F32;
+        d.N >>= d.mip;
+    }
     const int64_t R = f.n_records;
     int tile_bits = 1;
     while ((int64_t(1) << tile_bits) < int64_t(f.n_tiles)) ++tile_bits;
@@ -636,6 +675,7 @@ gb_status gb_render_backward(gb_context *ctx, gb_saved *s, const float *d_rgb, c
         d.g_opac = grads[i].d_opacities;
         d.g_sh = grads[i].d_sh;
         d.g_tex = grads[i].d_textures;
+        if (d.g_tex && d.mip) d.g_tex = s->mip_grad + s->mip_off[i];  // gradient of the filtered grid
         if (d.g_tex && d.K > 0)
             GB_CUDA(ctx, cudaMemsetAsync(d.g_tex, 0, size_t(d.K) * d.N * d.N * 3 * sizeof(float), st));
     }
@@ -665,12 +705,12 @@ gb_status gb_render_backward(gb_context *ctx, gb_saved *s, const float *d_rgb, c
     GB_CUDA(ctx, cudaMemsetAsync(&s->cnt->pairs_bwd, 0, sizeof(unsigned long long), st));
     GB_CUDA(ctx, cudaMemsetAsync(&s->cnt->contrib_bwd, 0, sizeof(unsigned long long), st));
     const bool persistent = (s->flags & GB_FLAG_PERSISTENT) != 0;
-    if (s->ppt == 2)
-        GB_CUDA(ctx, launch_render_bwd2(f, b, s->batch_bwd, s->use_list ? s->tile_list : nullptr,
-                                        persistent ? s->work + kMaxGroups : nullptr, persistent, st));
-    else
-        GB_CUDA(ctx, launch_render_bwd(f, b, s->batch_bwd, s->use_list ? s->tile_list : nullptr,
-                                       persistent ? s->work + kMaxGroups : nullptr, persistent, st));
+    GB_CUDA(ctx, launch_render_bwd(f, b, s->batch_bwd, s->ppt, s->use_list ? s->tile_list : nullptr,
+                                   persistent ? s->work + kMaxGroups : nullptr, persistent, st));
+    for (int i = 0; i < n_scenes; ++i)
+        if (f.scenes[i].mip && grads[i].d_textures)
+            GB_CUDA(ctx, launch_mip_grad(s->mip_grad + s->mip_off[i], f.scenes[i].K, s->mip_ns[i], f.scenes[i].mip,
+                                         grads[i].d_textures, st));
     if (timing) GB_CUDA(ctx, cudaEventRecord(s->ev[10], st));
     GB_CUDA(ctx, launch_preprocess_bwd(f, s->max_k, s->rec_grad, s->inv, st));
     if (timing) GB_CUDA(ctx, cudaEventRecord(s->ev[11], st));
@@ -741,6 +781,9 @@ gb_status gb_render_forward_noalloc(gb_context *ctx, const gb_scene *scenes, int
     int64_t max_k = 0;
     gb_status r = build_frame(ctx, scenes, n_scenes, cams, n_cams, tile, o.background, f, max_k);
     if (r != GB_OK) return r;
+    for (int i = 0; i < f.n_scenes; ++i)
+        if (f.scenes[i].mip)
+            return fail(ctx, GB_ERR_UNSUPPORTED, "the no-allocation forward renders no mip-level scene");
     if (f.n_records > kNaMaxRecords || f.n_pixels > kNaMaxPixels || int64_t(f.n_tiles) > kNaMaxTiles)
         return fail(ctx, GB_ERR_CAPACITY,
                     "no-allocation forward limits: %lld records (max %lld), %lld pixels (max %lld), %u tiles (max %lld)",

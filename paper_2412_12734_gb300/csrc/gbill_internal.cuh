@@ -46,9 +46,9 @@ struct SceneDev {
     const float *means, *quats, *scales, *opac;
     const void *sh;
     const void *tex;
-    int32_t D, sh_dtype, N, tex_dtype;
+    int32_t D, sh_dtype, N, tex_dtype;  // N, tex: the grid the render reads
     float sigma;
-    int32_t pad;
+    int32_t mip;                        // mip level (the render reads the filtered grid)
     float *g_means, *g_quats, *g_scales, *g_opac, *g_sh, *g_tex;
 };
 
@@ -194,10 +194,15 @@ struct RenderBwdBufs {
     const float *d_rgb, *d_depth, *d_alpha;
     float *rec_grad;          // [n_visible, 16], indexed by depth-sorted position
 };
-cudaError_t launch_render_bwd(const Frame &f, const RenderBwdBufs &b, int batch, const uint32_t *tile_list,
+// mip.cu: box filter of a scene's grids to N >> mip (FP32 out) and its adjoint
+cudaError_t launch_mip_filter(const void *src, int dtype, int64_t K, int ns, int mip, float *dst, cudaStream_t s);
+cudaError_t launch_mip_grad(const float *gc, int64_t K, int ns, int mip, float *gf, cudaStream_t s);
+
+// ppt = pixels per thread, 1 or 2 (render_bwd.cu, render_bwd2.cu)
+cudaError_t launch_render_bwd(const Frame &f, const RenderBwdBufs &b, int batch, int ppt, const uint32_t *tile_list,
                               uint32_t *work, bool persistent, cudaStream_t s);
-// two pixels per thread (render_bwd2.cu)
-cudaError_t launch_render_bwd2(const Frame &f, const RenderBwdBufs &b, int batch, const uint32_t *tile_list,
-                               uint32_t *work, bool persistent, cudaStream_t s);
+template <int P>
+cudaError_t launch_render_bwd_p(const Frame &f, const RenderBwdBufs &b, int batch, const uint32_t *tile_list,
+                                uint32_t *work, bool persistent, cudaStream_t s);
 
 }  // namespace gbill

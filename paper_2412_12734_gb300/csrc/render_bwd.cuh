@@ -1,0 +1,581 @@
+// Backward per-tile render (Alg. 1 bwd with Alg. 2 adj-bilinear), shared by
+// the one- and two-pixels-per-thread instantiations (render_bwd.cu,
+// render_bwd2.cu).
+//
+// One block per tile; thread t owns P pixels of its warp's 8 x 4P block
+// (P = 1: rows y; P = 2: rows y and y + 4 of the same column).  Batches of
+// the tile's splats are walked back to front from the last blended splat of
+// the warp.  Each pixel recomputes alpha and the colour of every splat it
+// blended and its transmittance T_i = T_{i+1} / (1 - alpha_i) from the saved
+// final T, then forms:
+//   colour adjoint  c^ = alpha T dL/dC                       (-> SH colour, grid)
+//   (C^, u^, v^)    = adj-bilinear(u, v, C_k, c^)            (Alg. 2)
+//   alpha^          = dL/dC . (c T - S / (1 - alpha)) + depth and alpha terms
+//   Gaussian:  rho^ -> (u^, v^) on the uv branch, -> centre on the low-pass one
+//   intersection:   (u^, v^) -> zeta^ -> record (adj(T'), centre) gradients
+// Scatter: a thread first sums its P pixels' values; the 14 record gradients
+// and the RGB gradients of the grid's four corner texels (where the weight of
+// clamped (u, v) lands) go through one 32-value warp reduce-scatter; the
+// weights of edge and interior texels are reduced per grid cell (one 16-value
+// reduce-scatter per distinct cell of the warp) or, at N = 8 when many cells
+// are hit, added to shared memory directly.  Per batch the per-splat sums
+// reach global memory with one atomic per value per tile.
+#pragma once
+
+#include <algorithm>
+
+#include "render_common.cuh"
+
+namespace gbill {
+namespace bwd {
+
+// Reduce-scatter of 16 values over the warp (16 shuffles): lane l ends with the
+// warp total of value index 8 b4 + 4 b3 + 2 b2 + b1 (b_i = bit i of l); lanes
+// l and l^1 hold the same total.
+__device__ __forceinline__ float warp_reduce_scatter16(float v[16], int lane) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const bool up = lane & 16;
+        const float send = up ? v[i] : v[i + 8], keep = up ? v[i + 8] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool up = lane & 8;
+        const float send = up ? v[i] : v[i + 4], keep = up ? v[i + 4] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool up = lane & 4;
+        const float send = up ? v[i] : v[i + 2], keep = up ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    const bool up = lane & 2;
+    const float send = up ? v[0] : v[1], keep = up ? v[1] : v[0];
+    const float t = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    return t + __shfl_xor_sync(0xffffffffu, t, 1);
+}
+
+// Reduce-scatter of 32 values over the warp (31 shuffles): lane l ends with
+// the warp total of value index l (bits of l select the kept half at each
+// exchange step, most significant first).
+__device__ __forceinline__ float warp_reduce_scatter32(float v[32], int lane) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const bool up = lane & 16;
+        const float send = up ? v[i] : v[i + 16], keep = up ? v[i + 16] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const bool up = lane & 8;
+        const float send = up ? v[i] : v[i + 8], keep = up ? v[i + 8] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool up = lane & 4;
+        const float send = up ? v[i] : v[i + 4], keep = up ? v[i + 4] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool up = lane & 2;
+        const float send = up ? v[i] : v[i + 2], keep = up ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    const bool up = lane & 1;
+    const float send = up ? v[0] : v[1], keep = up ? v[1] : v[0];
+    return keep + __shfl_xor_sync(0xffffffffu, send, 1);
+}
+
+// Warp-reduced values: 0..13 record gradients, 14..25 the RGB gradient of the
+// grid's four corner texels (0,0), (0,N-1), (N-1,0), (N-1,N-1).
+constexpr int kCornerSlot = 14;
+// For N = 8, above this many distinct edge/interior cells in a (warp, splat)
+// pair the lanes add their texel weights to shared memory directly instead of
+// one reduce-scatter per cell (measured: faster at N = 8, slower at N <= 4).
+constexpr int kGroupCells8 = 4;
+
+// State of one pixel in the reverse walk.
+struct Pix {
+    float xf, yf;                // pixel centre
+    float T;                     // transmittance in front of the current splat's successor
+    float dC0, dC1, dC2, dD;     // dL/drgb, dL/ddepth
+    float dTfin;                 // (dL/dalpha - dL/drgb . bg) T_final
+    float S0, S1, S2, SD;        // colour and depth blended behind the current splat
+    uint32_t last;               // 1 + index of the last blended splat (0: none)
+    bool inside;
+};
+
+// Texel weights of one pixel that are not routed through the corner slots,
+// with the colour adjoint they multiply and the cell they belong to.
+struct Rem {
+    float w00, w10, w01, w11, c0, c1, c2;
+    int base;
+    __device__ __forceinline__ bool any() const {
+        return (w00 != 0.0f) | (w10 != 0.0f) | (w01 != 0.0f) | (w11 != 0.0f);
+    }
+};
+
+// Adjoints of one (pixel, splat) pair: adds the record gradients and the
+// corner-texel gradients to g[], sets the remaining texel weights and steps
+// the pixel's reverse state.  Returns whether the pixel blended the splat.
+template <bool ACC>
+__device__ __forceinline__ void put(float &slot, float v) {
+    if (ACC) slot += v; else slot = v;
+}
+
+// ACC: add to g[] (second and later pixels of a thread); otherwise the slots
+// this pair owns are assigned (g[] holds zeros on entry).
+template <int N, bool ACC>
+__device__ __forceinline__ bool pair_adjoint(Pix &px, uint32_t idx, const float4 *rec, const float4 *tex,
+                                             float sigma, float kN, float g[32], Rem &rem, uint32_t &npairs,
+                                             uint32_t &ncontrib) {
+    rem.w00 = rem.w10 = rem.w01 = rem.w11 = 0.0f;
+    rem.c0 = rem.c1 = rem.c2 = 0.0f;
+    rem.base = 0;
+    if (!(px.inside && idx < px.last)) return false;
+    ++npairs;
+    const float4 q0 = rec[0], q1 = rec[1], q2 = rec[2], q3 = rec[3];
+    const float dx = (px.xf - q2.x) - q2.z, dy = (px.yf - q2.y) - q2.w;
+    const float zz = fmaf(q1.x, dx, fmaf(q1.y, dy, q1.z));
+    if (zz == 0.0f) return false;
+    const float rz = fast_rcp(zz);
+    const float u = fmaf(q0.x, dx, q0.y * dy) * rz;
+    const float v = fmaf(q0.z, dx, q0.w * dy) * rz;
+    const float ruv = fmaf(u, u, v * v);
+    const float rlp = kLowPass * fmaf(dx, dx, dy * dy);
+    const bool uvb = ruv <= rlp;
+    const float rho = uvb ? ruv : rlp;
+    const float G = gauss(rho);
+    const float ar = q3.x * G;
+    const bool clamped = ar > kAlphaMax;
+    const float alpha = clamped ? kAlphaMax : ar;
+    if (!(alpha >= kAlphaMin)) return false;
+    ++ncontrib;
+    const float iom = fast_rcp(1.0f - alpha);
+    const float Ti = px.T * iom;
+    const Cell<N> cell = grid_cell<N>(u, v, sigma, kN);
+    const Quad qd = grid_quad<N>(tex, cell);
+    float col[3];
+    grid_colour<N>(qd, cell, col);
+    col[0] += q3.y;
+    col[1] += q3.z;
+    col[2] += q3.w;
+    const float w = alpha * Ti;
+    const float ch0 = w * px.dC0, ch1 = w * px.dC1, ch2 = w * px.dC2;
+    put<ACC>(g[11], ch0);
+    put<ACC>(g[12], ch1);
+    put<ACC>(g[13], ch2);
+    // adj-bilinear: grid adjoint and uv adjoint
+    float uh = 0.0f, vh = 0.0f;
+    if (N == 1) {
+        // the single texel is corner 0
+        put<ACC>(g[kCornerSlot + 0], ch0);
+        put<ACC>(g[kCornerSlot + 1], ch1);
+        put<ACC>(g[kCornerSlot + 2], ch2);
+    } else {
+        const float fu = cell.fu, fv = cell.fv;
+        const float w00 = (1.0f - fu) * (1.0f - fv), w10 = fu * (1.0f - fv);
+        const float w01 = (1.0f - fu) * fv, w11 = fu * fv;
+        // d colour / d f_u and d f_v, dotted with the colour adjoint
+        const float fuh = ch0 * ((qd.c10.x - qd.c00.x) * (1.0f - fv) + (qd.c11.x - qd.c01.x) * fv) +
+                          ch1 * ((qd.c10.y - qd.c00.y) * (1.0f - fv) + (qd.c11.y - qd.c01.y) * fv) +
+                          ch2 * ((qd.c10.z - qd.c00.z) * (1.0f - fv) + (qd.c11.z - qd.c01.z) * fv);
+        const float fvh = ch0 * ((qd.c01.x - qd.c00.x) * (1.0f - fu) + (qd.c11.x - qd.c10.x) * fu) +
+                          ch1 * ((qd.c01.y - qd.c00.y) * (1.0f - fu) + (qd.c11.y - qd.c10.y) * fu) +
+                          ch2 * ((qd.c01.z - qd.c00.z) * (1.0f - fu) + (qd.c11.z - qd.c10.z) * fu);
+        // weights landing on a grid-corner texel go to the warp-reduced corner
+        // slots; the rest (edge and interior texels) to the per-cell pass
+        const int iu = cell.base / N, iv = cell.base - iu * N;
+        const float wc0 = (iu == 0 && iv == 0) ? w00 : 0.0f;
+        const float wc1 = (iu == 0 && iv == N - 2) ? w01 : 0.0f;
+        const float wc2 = (iu == N - 2 && iv == 0) ? w10 : 0.0f;
+        const float wc3 = (iu == N - 2 && iv == N - 2) ? w11 : 0.0f;
+        put<ACC>(g[kCornerSlot + 0], wc0 * ch0); put<ACC>(g[kCornerSlot + 1], wc0 * ch1); put<ACC>(g[kCornerSlot + 2], wc0 * ch2);
+        put<ACC>(g[kCornerSlot + 3], wc1 * ch0); put<ACC>(g[kCornerSlot + 4], wc1 * ch1); put<ACC>(g[kCornerSlot + 5], wc1 * ch2);
+        put<ACC>(g[kCornerSlot + 6], wc2 * ch0); put<ACC>(g[kCornerSlot + 7], wc2 * ch1); put<ACC>(g[kCornerSlot + 8], wc2 * ch2);
+        put<ACC>(g[kCornerSlot + 9], wc3 * ch0); put<ACC>(g[kCornerSlot + 10], wc3 * ch1); put<ACC>(g[kCornerSlot + 11], wc3 * ch2);
+        rem.w00 = w00 - wc0;
+        rem.w10 = w10 - wc2;
+        rem.w01 = w01 - wc1;
+        rem.w11 = w11 - wc3;
+        rem.base = cell.base;
+        rem.c0 = ch0;
+        rem.c1 = ch1;
+        rem.c2 = ch2;
+        if (u > -sigma && u < sigma) uh = kN * fuh;
+        if (v > -sigma && v < sigma) vh = kN * fvh;
+    }
+    // alpha adjoint
+    const float zi = uvb ? q1.z * q1.w * rz : q1.w;
+    float ah = px.dC0 * (col[0] * Ti - px.S0 * iom) + px.dC1 * (col[1] * Ti - px.S1 * iom) +
+               px.dC2 * (col[2] * Ti - px.S2 * iom);
+    ah += px.dD * (zi * Ti - px.SD * iom) + px.dTfin * iom;
+    px.S0 = fmaf(col[0], w, px.S0);
+    px.S1 = fmaf(col[1], w, px.S1);
+    px.S2 = fmaf(col[2], w, px.S2);
+    px.SD = fmaf(zi, w, px.SD);
+    px.T = Ti;
+    const float zih = px.dD * w;
+    float rhoh = 0.0f;
+    if (!clamped) {
+        put<ACC>(g[10], ah * G);
+        rhoh = -0.5f * alpha * ah;
+    }
+    float zzh = 0.0f, dxh = 0.0f, dyh = 0.0f;
+    if (uvb) {
+        uh = fmaf(2.0f * u, rhoh, uh);
+        vh = fmaf(2.0f * v, rhoh, vh);
+        // zi = m22 z / zeta_z
+        g[6] += zih * q1.w * rz;
+        g[7] += zih * q1.z * rz;
+        zzh = -zih * zi * rz;
+    } else {
+        dxh = 2.0f * kLowPass * dx * rhoh;
+        dyh = 2.0f * kLowPass * dy * rhoh;
+        g[7] += zih;
+    }
+    const float zxh = uh * rz, zyh = vh * rz;
+    zzh -= (uh * u + vh * v) * rz;
+    put<ACC>(g[0], zxh * dx);
+    put<ACC>(g[1], zxh * dy);
+    put<ACC>(g[2], zyh * dx);
+    put<ACC>(g[3], zyh * dy);
+    put<ACC>(g[4], zzh * dx);
+    put<ACC>(g[5], zzh * dy);
+    g[6] += zzh;
+    dxh += zxh * q0.x + zyh * q0.z + zzh * q1.x;
+    dyh += zxh * q0.y + zyh * q0.w + zzh * q1.y;
+    put<ACC>(g[8], -dxh);
+    put<ACC>(g[9], -dyh);
+    return true;
+}
+
+template <int TS, int N, typename TexT, int P>
+__device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b, int batch, uint32_t tile) {
+    constexpr int NT = TS * TS / P;
+    constexpr int NN = N * N;
+    constexpr int TEXF = NN * 3;
+    extern __shared__ float4 smem[];
+    float4 *s_rec = smem;
+    float4 *s_fp = s_rec + 4 * batch;  // [batch][3] footprints
+    float4 *s_tex = s_fp + 3 * batch;
+    int32_t *s_k = reinterpret_cast<int32_t *>(s_tex + batch * NN);
+    uint32_t *s_j = reinterpret_cast<uint32_t *>(s_k + batch);
+    uint2 *s_box = reinterpret_cast<uint2 *>(s_j + batch);
+    uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_box + batch);
+    float *s_g = reinterpret_cast<float *>(s_mask + batch);  // [batch][16]
+    float *s_tg = s_g + batch * kRecGrad;                    // [batch][TEXF]
+    __shared__ uint32_t s_maxlast;
+
+    const int ci = camera_of_tile(f, tile);
+    const CamDev &cam = f.cams[ci];
+    const SceneDev &sc = f.scenes[cam.scene];
+    const uint32_t lt = tile - cam.tile_off;
+    const int tx = int(lt % uint32_t(cam.tiles_x)), ty = int(lt / uint32_t(cam.tiles_x));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t wbit = 1u << warp;  // this warp's 8 x 4P block in the splat masks
+    const int px0 = tx * TS + (warp % (TS / 8)) * 8 + (lane & 7);
+    const int py0 = ty * TS + (warp / (TS / 8)) * (4 * P) + (lane >> 3);
+    const uint2 range = b.fw.ranges[tile];
+    const float sigma = sc.sigma;
+    const float kN = float(N - 1) / (2.0f * sigma);
+
+    Pix pix[P];
+    uint32_t mylast = 0, npairs = 0, ncontrib = 0;
+    if (threadIdx.x == 0) s_maxlast = 0;
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        Pix &q = pix[p];
+        const int py = py0 + 4 * p;
+        q.inside = px0 < cam.width && py < cam.height;
+        q.xf = float(px0) + 0.5f;
+        q.yf = float(py) + 0.5f;
+        q.T = 1.0f;
+        q.dC0 = q.dC1 = q.dC2 = q.dD = 0.0f;
+        q.S0 = q.S1 = q.S2 = q.SD = 0.0f;
+        q.last = 0;
+        float dA = 0.0f, T_final = 1.0f;
+        if (q.inside) {
+            const int64_t pi = cam.pix_off + int64_t(py) * cam.width + px0;
+            q.T = T_final = b.fw.t_final[pi];
+            q.last = b.fw.last[pi];
+            q.dC0 = b.d_rgb[3 * pi + 0];
+            q.dC1 = b.d_rgb[3 * pi + 1];
+            q.dC2 = b.d_rgb[3 * pi + 2];
+            if (b.d_depth) q.dD = b.d_depth[pi];
+            if (b.d_alpha) dA = b.d_alpha[pi];
+        }
+        const float bgdot = q.dC0 * f.bg[0] + q.dC1 * f.bg[1] + q.dC2 * f.bg[2];
+        q.dTfin = (dA - bgdot) * T_final;  // times 1/(1-alpha) per splat
+        mylast = max(mylast, q.last);
+    }
+    const uint32_t wlast = __reduce_max_sync(0xffffffffu, mylast);
+    if (lane == 0 && wlast) atomicMax(&s_maxlast, wlast);
+    __syncthreads();
+    const int max_last = int(s_maxlast);
+    float *g_tex = sc.g_tex;
+    const int my_q16 = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+    // flat index (i_u N + i_v) of the corner texel this lane's reduced value feeds
+    const int my_corner = lane >= kCornerSlot && lane < kCornerSlot + 12 ? (lane - kCornerSlot) / 3 : -1;
+    const int my_corner_off = my_corner < 0 ? 0
+                              : 3 * ((my_corner & 2 ? (N - 1) * N : 0) + (my_corner & 1 ? N - 1 : 0)) +
+                                    (lane - kCornerSlot) % 3;
+
+    for (int be = max_last; be > 0; be -= batch) {
+        const int bs = max(0, be - batch), nb = be - bs;
+        for (int e = threadIdx.x; e < nb * kRecGrad; e += NT) s_g[e] = 0.0f;
+        for (int e = threadIdx.x; e < nb * TEXF; e += NT) s_tg[e] = 0.0f;
+        stage_batch<N, NT, TexT, TS, 4 * P>(b.fw, cam, sc, range.x + bs, nb, tx * TS, ty * TS, s_rec, s_tex, s_k,
+                                            s_j, s_box, s_mask, s_fp);
+        __syncthreads();
+        // splats at or beyond the warp's last contributor are skipped warp-wide;
+        // below it at least one lane of the warp is active
+        const int i_hi = min(nb, int(wlast) - bs);
+        for (int i = i_hi - 1; i >= 0; --i) {
+            if (!(s_mask[i] & wbit)) continue;
+            float g[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) g[q] = 0.0f;
+            Rem rem[P];
+            bool act = pair_adjoint<N, false>(pix[0], uint32_t(bs + i), s_rec + 4 * i, s_tex + i * NN, sigma, kN,
+                                              g, rem[0], npairs, ncontrib);
+#pragma unroll
+            for (int p = 1; p < P; ++p)
+                act |= pair_adjoint<N, true>(pix[p], uint32_t(bs + i), s_rec + 4 * i, s_tex + i * NN, sigma, kN,
+                                             g, rem[p], npairs, ncontrib);
+            if (!__any_sync(0xffffffffu, act)) continue;
+            const float tot = warp_reduce_scatter32(g, lane);
+            if (tot != 0.0f) {
+                if (lane < kCornerSlot) atomicAdd(s_g + i * kRecGrad + lane, tot);
+                else if (my_corner >= 0) atomicAdd(s_tg + i * TEXF + my_corner_off, tot);
+            }
+            if (N > 2) {
+                // edge / interior texels: lanes sharing a cell touch the same four
+                // texels; each distinct cell is one reduce-scatter and one
+                // conflict-free atomic (a lane's P pixels join the same group
+                // when they share its cell)
+                bool has[P];
+                unsigned pend[P];
+                unsigned any_pend = 0u;
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    has[p] = rem[p].any();
+                    pend[p] = __ballot_sync(0xffffffffu, has[p]);
+                    any_pend |= pend[p];
+                }
+                int cells = 0;
+                if (N >= 8 && any_pend) {
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                        const unsigned same = __match_any_sync(0xffffffffu, has[p] ? rem[p].base : -1);
+                        cells += __popc(__ballot_sync(0xffffffffu, has[p] && (__ffs(same) - 1) == lane));
+                    }
+                }
+                if (cells > kGroupCells8) {
+                    float *st = s_tg + i * TEXF;
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                        if (!has[p]) continue;
+                        const Rem &r = rem[p];
+                        float *t = st + 3 * r.base;
+                        if (r.w00 != 0.0f) {
+                            atomicAdd(t + 0, r.w00 * r.c0); atomicAdd(t + 1, r.w00 * r.c1); atomicAdd(t + 2, r.w00 * r.c2);
+                        }
+                        if (r.w10 != 0.0f) {
+                            atomicAdd(t + 3 * N + 0, r.w10 * r.c0); atomicAdd(t + 3 * N + 1, r.w10 * r.c1);
+                            atomicAdd(t + 3 * N + 2, r.w10 * r.c2);
+                        }
+                        if (r.w01 != 0.0f) {
+                            atomicAdd(t + 3, r.w01 * r.c0); atomicAdd(t + 4, r.w01 * r.c1); atomicAdd(t + 5, r.w01 * r.c2);
+                        }
+                        if (r.w11 != 0.0f) {
+                            atomicAdd(t + 3 * N + 3, r.w11 * r.c0); atomicAdd(t + 3 * N + 4, r.w11 * r.c1);
+                            atomicAdd(t + 3 * N + 5, r.w11 * r.c2);
+                        }
+                    }
+                    any_pend = 0u;
+                }
+                while (any_pend) {
+                    // the first pending entry (pixel slot p0, lowest lane) names the cell
+                    int p0 = 0;
+#pragma unroll
+                    for (int p = P - 1; p >= 0; --p)
+                        if (pend[p]) p0 = p;
+                    int kb = rem[0].base;
+#pragma unroll
+                    for (int p = 1; p < P; ++p)
+                        if (p0 == p) kb = rem[p].base;
+                    unsigned lead_mask = pend[0];
+#pragma unroll
+                    for (int p = 1; p < P; ++p)
+                        if (p0 == p) lead_mask = pend[p];
+                    const int key = __shfl_sync(0xffffffffu, kb, __ffs(lead_mask) - 1);
+                    float h[16];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) h[q] = 0.0f;
+                    any_pend = 0u;
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                        const Rem &r = rem[p];
+                        const bool mine = ((pend[p] >> lane) & 1u) && r.base == key;
+                        pend[p] &= ~__ballot_sync(0xffffffffu, mine);
+                        any_pend |= pend[p];
+                        if (mine) {
+                            h[0] += r.w00 * r.c0; h[1] += r.w00 * r.c1; h[2] += r.w00 * r.c2;
+                            h[3] += r.w10 * r.c0; h[4] += r.w10 * r.c1; h[5] += r.w10 * r.c2;
+                            h[6] += r.w01 * r.c0; h[7] += r.w01 * r.c1; h[8] += r.w01 * r.c2;
+                            h[9] += r.w11 * r.c0; h[10] += r.w11 * r.c1; h[11] += r.w11 * r.c2;
+                        }
+                    }
+                    const float t = warp_reduce_scatter16(h, lane);
+                    if (!(lane & 1) && my_q16 < 12 && t != 0.0f) {
+                        const int k = my_q16 / 3, c = my_q16 - 3 * k;
+                        // k: 0 -> (iu, iv), 1 -> (iu+1, iv), 2 -> (iu, iv+1), 3 -> (iu+1, iv+1)
+                        const int off = 3 * (key + ((k & 1) ? N : 0) + ((k & 2) ? 1 : 0)) + c;
+                        atomicAdd(s_tg + i * TEXF + off, t);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < nb * kRecGrad; e += NT) {
+            const float v = s_g[e];
+            if (v != 0.0f) {
+                const int s = e / kRecGrad, q = e - s * kRecGrad;
+                atomicAdd(b.rec_grad + int64_t(s_j[s]) * kRecGrad + q, v);
+            }
+        }
+        if (g_tex)
+            for (int e = threadIdx.x; e < nb * TEXF; e += NT) {
+                const float v = s_tg[e];
+                if (v != 0.0f) {
+                    const int s = e / TEXF, o = e - s * TEXF;
+                    atomicAdd(g_tex + int64_t(s_k[s]) * TEXF + o, v);
+                }
+            }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
+        ncontrib += __shfl_xor_sync(0xffffffffu, ncontrib, o);
+    }
+    if (lane == 0 && npairs) atomicAdd(&b.fw.cnt->pairs_bwd, (unsigned long long)npairs);
+    if (lane == 0 && ncontrib) atomicAdd(&b.fw.cnt->contrib_bwd, (unsigned long long)ncontrib);
+}
+
+// Resident blocks per SM the register budget is set for: one pixel per thread
+// fits 64 registers at 1024 threads per SM; two pixels per thread get ~100.
+template <int TS, int P>
+constexpr int min_blocks() {
+    return P == 1 ? 1024 / (TS * TS) : 1280 / (TS * TS);
+}
+
+template <int TS, int N, typename TexT, int P>
+__global__ void __launch_bounds__(TS * TS / P, min_blocks<TS, P>())
+    render_bwd_kernel(Frame f, RenderBwdBufs b, int batch, TileSched ts) {
+    __shared__ uint32_t s_next;
+    for (int round = 0;; ++round) {
+        uint32_t idx;
+        if (ts.work) {
+            __syncthreads();
+            if (threadIdx.x == 0) s_next = atomicAdd(ts.work, 1u);
+            __syncthreads();
+            idx = s_next;
+        } else {
+            if (round) break;
+            idx = blockIdx.x;
+        }
+        if (idx >= ts.count) break;
+        const uint32_t tile = ts.list ? ts.list[ts.off + idx] : ts.off + idx;
+        bwd_tile<TS, N, TexT, P>(f, b, batch, tile);
+    }
+}
+
+template <int TS, int N, typename TexT, int P>
+cudaError_t launch_t(const Frame &f, const RenderBwdBufs &b, int batch, TileSched ts, bool persistent,
+                     cudaStream_t s) {
+    constexpr int NT = TS * TS / P;
+    const size_t smem = stage_bytes<N>(batch, true);
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(render_bwd_kernel<TS, N, TexT, P>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    unsigned grid = ts.count;
+    if (persistent) {
+        static int per_sm = 0, sms = 0;
+        static size_t smem_seen = 0;
+        if (!per_sm || smem_seen != smem) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_bwd_kernel<TS, N, TexT, P>, NT, smem);
+            smem_seen = smem;
+            if (per_sm < 1) per_sm = 1;
+        }
+        grid = std::min<unsigned>(grid, unsigned(per_sm * sms));
+    } else {
+        ts.work = nullptr;
+    }
+    if (grid == 0) return cudaSuccess;
+    render_bwd_kernel<TS, N, TexT, P><<<grid, NT, smem, s>>>(f, b, batch, ts);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <int TS, typename TexT, int P>
+cudaError_t launch_n(const Frame &f, const RenderBwdBufs &b, int N, int batch, TileSched ts, bool persistent,
+                     cudaStream_t s) {
+    switch (N) {
+        case 1: return launch_t<TS, 1, TexT, P>(f, b, batch, ts, persistent, s);
+        case 2: return launch_t<TS, 2, TexT, P>(f, b, batch, ts, persistent, s);
+        case 4: return launch_t<TS, 4, TexT, P>(f, b, batch, ts, persistent, s);
+        case 8: return launch_t<TS, 8, TexT, P>(f, b, batch, ts, persistent, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace bwd
+
+// Launches the backward render of every render group with P pixels per thread.
+template <int P>
+cudaError_t launch_render_bwd_p(const Frame &f, const RenderBwdBufs &b, int batch, const uint32_t *tile_list,
+                                uint32_t *work, bool persistent, cudaStream_t s) {
+    if (f.n_tiles == 0) return cudaSuccess;
+    for (int g = 0; g < f.n_groups; ++g) {
+        TileSched ts;
+        ts.list = tile_list;
+        ts.off = tile_list ? f.group_off[g] : 0;
+        ts.count = tile_list ? f.group_count[g] : f.n_tiles;
+        ts.work = work ? work + g : nullptr;
+        const int N = f.group_N[g];
+        cudaError_t e;
+        if (f.tile == 8) {
+            switch (f.group_dtype[g]) {
+                case GB_F16: e = bwd::launch_n<8, __half, P>(f, b, N, batch, ts, persistent, s); break;
+                case GB_BF16: e = bwd::launch_n<8, __nv_bfloat16, P>(f, b, N, batch, ts, persistent, s); break;
+                default: e = bwd::launch_n<8, float, P>(f, b, N, batch, ts, persistent, s); break;
+            }
+        } else if (f.tile == 16) {
+            switch (f.group_dtype[g]) {
+                case GB_F16: e = bwd::launch_n<16, __half, P>(f, b, N, batch, ts, persistent, s); break;
+                case GB_BF16: e = bwd::launch_n<16, __nv_bfloat16, P>(f, b, N, batch, ts, persistent, s); break;
+                default: e = bwd::launch_n<16, float, P>(f, b, N, batch, ts, persistent, s); break;
+            }
+        } else {
+            return cudaErrorInvalidValue;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace gbill

@@ -14,14 +14,14 @@ __device__ __forceinline__ void tile_pixel(int tid, int &lx, int &ly) {
     ly = (warp / (TS / 8)) * 4 + (lane >> 3);
 }
 
-// Bytes of dynamic shared memory for one staged batch: records, colour
-// grids, splat indices, pixel rectangles, warp-block masks and (backward)
+// Bytes of dynamic shared memory for one staged batch: records, footprints,
+// colour grids, splat indices, pixel rectangles, warp-block masks and (backward)
 // record/grid gradient accumulators.  Colour grids are staged as RGBA float4
 // texels (16 bytes, alpha unused) so a texel is one 128-bit shared load.
 template <int N>
 __host__ __device__ inline size_t stage_bytes(int batch, bool bwd) {
     const int texf = N * N * 3;
-    size_t b = size_t(batch) * (64 + 16 * N * N + 20);
+    size_t b = size_t(batch) * (64 + 48 + 16 * N * N + 20);
     if (bwd) b += size_t(batch) * (4 * kRecGrad + 4 * texf);
     return b;
 }
@@ -33,53 +33,65 @@ __device__ __forceinline__ float fast_rcp(float x) {
     return r;
 }
 
-// Whether the pixel centres of the block [bx0, bx0 + 7] x [by0, by0 + BH - 1]
-// can hold a pixel with alpha >= 1/255 for the splat of record (q0..q3) with
-// pixel rectangle `box`.  alpha = o exp(-rho/2) >= 1/255 exactly when
-// rho <= 2 ln(255 o), and rho = min(rho_uv, rho_lp), so the footprint is the
-// union of the low-pass disk 2 |d|^2 <= rho_c and the plane-hit region
-// (a.d)^2 + (b.d)^2 <= rho_c (c.d)^2, d = (dx, dy, 1) about the centre: a
-// quadratic q(d) <= 0 whose 2 x 2 part A is positive definite for a bounded
-// footprint.  The test intersects the block's centre rectangle (clipped to
-// `box`) with both: minimum of q over the rectangle (inside at the conic's
-// centre, else on one of the four edges, each a clamped 1-D minimum).  rho_c
-// carries a 1/64 relative margin, and a near-degenerate A (relative
-// cancellation below 2^-10 in a diagonal entry or the determinant) never
-// culls, so the test only drops blocks the per-pixel FP32 test would skip.
-template <int BH>
-__device__ __forceinline__ bool block_hits(const float4 &q0, const float4 &q1, const float4 &q2, float o,
-                                           uint2 box, int bx0, int by0) {
-    const int rx0 = max(int(box.x & 0xffffu), bx0), rx1 = min(int(box.y & 0xffffu), bx0 + 7);
-    const int ry0 = max(int(box.x >> 16), by0), ry1 = min(int(box.y >> 16), by0 + BH - 1);
-    if (rx0 > rx1 || ry0 > ry1) return false;
-    if (!(o * 255.0f > 1.0f)) return true;  // a culled record never reaches a tile; no claim here
-    const float X0 = (float(rx0) + 0.5f - q2.x) - q2.z, X1 = (float(rx1) + 0.5f - q2.x) - q2.z;
-    const float Y0 = (float(ry0) + 0.5f - q2.y) - q2.w, Y1 = (float(ry1) + 0.5f - q2.y) - q2.w;
+// Footprint of a splat for the warp-block test: alpha = o exp(-rho/2) >=
+// 1/255 exactly when rho <= rho_c = 2 ln(255 o), and rho = min(rho_uv,
+// rho_lp), so the footprint is the union of the low-pass disk 2 |d|^2 <= rho_c
+// and the plane-hit region (a.d)^2 + (b.d)^2 <= rho_c (c.d)^2, d = (dx, dy, 1)
+// about the projected centre: q(d) = d^T A d + 2 B.d + C <= 0 with A positive
+// definite for a bounded footprint.  rho_c carries a 1/64 relative margin; a
+// near-degenerate A (relative cancellation below 2^-10 in a diagonal entry
+// or the determinant) marks the splat as "never cull" through an infinite
+// disk radius.  Stored per staged splat as three float4:
+//   k0 = (A00, A01, A11, C), k1 = (B0, B1, 1/A00, 1/A11), k2 = (e_x, e_y, rho_c/2, 0)
+// with e the conic's centre (minimiser of q).
+__device__ __forceinline__ void footprint_setup(const float4 &q0, const float4 &q1, float o, float4 *k) {
+    k[0] = k[1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    k[2] = make_float4(0.0f, 0.0f, INFINITY, 0.0f);
+    if (!(o * 255.0f > 1.0f)) return;  // a culled record never reaches a tile; no claim here
     const float rc0 = 2.0f * __logf(255.0f * o);
     const float rc = fmaf(rc0, 1.0f / 64.0f, rc0) + 1.0f / 64.0f;
-    // low-pass disk: nearest point of the rectangle to the centre
-    const float nx = fminf(fmaxf(0.0f, X0), X1), ny = fminf(fmaxf(0.0f, Y0), Y1);
-    if (2.0f * fmaf(nx, nx, ny * ny) <= rc) return true;
     const float a0 = q0.x, a1 = q0.y, b0 = q0.z, b1 = q0.w, c0 = q1.x, c1 = q1.y, c2 = q1.z;
     const float p00 = fmaf(a0, a0, b0 * b0), n00 = rc * c0 * c0;
     const float p11 = fmaf(a1, a1, b1 * b1), n11 = rc * c1 * c1;
     const float A00 = p00 - n00, A11 = p11 - n11;
-    if (!(A00 > (p00 + n00) * (1.0f / 1024.0f)) || !(A11 > (p11 + n11) * (1.0f / 1024.0f))) return true;
+    if (!(A00 > (p00 + n00) * (1.0f / 1024.0f)) || !(A11 > (p11 + n11) * (1.0f / 1024.0f))) return;
     const float A01 = fmaf(a0, a1, b0 * b1) - rc * c0 * c1;
     const float det = A00 * A11 - A01 * A01;
-    if (!(det > A00 * A11 * (1.0f / 1024.0f))) return true;
+    if (!(det > A00 * A11 * (1.0f / 1024.0f))) return;
     const float B0 = -rc * c0 * c2, B1 = -rc * c1 * c2, Cq = -rc * c2 * c2;
-    const float idet = 1.0f / det;
-    const float ex = (A01 * B1 - A11 * B0) * idet, ey = (A01 * B0 - A00 * B1) * idet;
-    if (ex >= X0 && ex <= X1 && ey >= Y0 && ey <= Y1) return true;
+    const float idet = fast_rcp(det);
+    k[0] = make_float4(A00, A01, A11, Cq);
+    k[1] = make_float4(B0, B1, fast_rcp(A00), fast_rcp(A11));
+    k[2] = make_float4((A01 * B1 - A11 * B0) * idet, (A01 * B0 - A00 * B1) * idet, 0.5f * rc, 0.0f);
+}
+
+// Whether the pixel centres of the block [bx0, bx0 + 7] x [by0, by0 + BH - 1]
+// can hold a pixel with alpha >= 1/255 for a splat with centre record q2,
+// pixel rectangle `box` and footprint k (footprint_setup): the block's centre
+// rectangle, clipped to `box`, meets the low-pass disk or the plane-hit
+// region (minimum of q over the rectangle: at the conic's centre if inside,
+// else on one of the four edges, each a clamped 1-D minimum).  Only blocks
+// that the per-pixel FP32 test would skip are dropped.
+template <int BH>
+__device__ __forceinline__ bool block_hits(const float4 &q2, uint2 box, const float4 *k, int bx0, int by0) {
+    const int rx0 = max(int(box.x & 0xffffu), bx0), rx1 = min(int(box.y & 0xffffu), bx0 + 7);
+    const int ry0 = max(int(box.x >> 16), by0), ry1 = min(int(box.y >> 16), by0 + BH - 1);
+    if (rx0 > rx1 || ry0 > ry1) return false;
+    const float X0 = (float(rx0) + 0.5f - q2.x) - q2.z, X1 = (float(rx1) + 0.5f - q2.x) - q2.z;
+    const float Y0 = (float(ry0) + 0.5f - q2.y) - q2.w, Y1 = (float(ry1) + 0.5f - q2.y) - q2.w;
+    const float4 k0 = k[0], k1 = k[1], k2 = k[2];
+    // low-pass disk: nearest point of the rectangle to the centre
+    const float nx = fminf(fmaxf(0.0f, X0), X1), ny = fminf(fmaxf(0.0f, Y0), Y1);
+    if (fmaf(nx, nx, ny * ny) <= k2.z) return true;
+    if (k2.x >= X0 && k2.x <= X1 && k2.y >= Y0 && k2.y <= Y1) return true;
+    const float A00 = k0.x, A01 = k0.y, A11 = k0.z, Cq = k0.w, B0 = k1.x, B1 = k1.y;
     auto q = [&](float x, float y) {
         return fmaf(x, fmaf(A00, x, 2.0f * fmaf(A01, y, B0)), fmaf(y, fmaf(A11, y, 2.0f * B1), Cq));
     };
-    const float i00 = 1.0f / A00, i11 = 1.0f / A11;
-    const float yA = fminf(fmaxf(-(fmaf(A01, X0, B1)) * i11, Y0), Y1);
-    const float yB = fminf(fmaxf(-(fmaf(A01, X1, B1)) * i11, Y0), Y1);
-    const float xA = fminf(fmaxf(-(fmaf(A01, Y0, B0)) * i00, X0), X1);
-    const float xB = fminf(fmaxf(-(fmaf(A01, Y1, B0)) * i00, X0), X1);
+    const float yA = fminf(fmaxf(-fmaf(A01, X0, B1) * k1.w, Y0), Y1);
+    const float yB = fminf(fmaxf(-fmaf(A01, X1, B1) * k1.w, Y0), Y1);
+    const float xA = fminf(fmaxf(-fmaf(A01, Y0, B0) * k1.z, X0), X1);
+    const float xB = fminf(fmaxf(-fmaf(A01, Y1, B0) * k1.z, X0), X1);
     const float m = fminf(fminf(q(X0, yA), q(X1, yB)), fminf(q(xA, Y0), q(xB, Y1)));
     return m <= 0.0f;
 }
@@ -92,7 +104,7 @@ template <int N, int NT, typename TexT, int TS, int BH>
 __device__ __forceinline__ void stage_batch(const RenderBufs &b, const CamDev &cam, const SceneDev &sc,
                                             uint32_t first, int nb, int tx0, int ty0, float4 *s_rec,
                                             float4 *s_tex, int32_t *s_k, uint32_t *s_j, uint2 *s_box,
-                                            uint32_t *s_mask) {
+                                            uint32_t *s_mask, float4 *s_fp) {
     constexpr int NN = N * N;
     constexpr int NB = TS * TS / (8 * BH);  // warp blocks per tile: 1, 2, 4 or 8
     static_assert(32 % NB == 0 && NT % 32 == 0, "block masks are gathered within a warp");
@@ -108,14 +120,19 @@ __device__ __forceinline__ void stage_batch(const RenderBufs &b, const CamDev &c
         s_rec[4 * t + 3] = rp[3];
         s_k[t] = int32_t(int64_t(r) - cam.rec_off);
         s_j[t] = j;
+        float4 k[3];
+        footprint_setup(rp[0], rp[1], rp[3].x, k);
+        s_fp[3 * t + 0] = k[0];
+        s_fp[3 * t + 1] = k[1];
+        s_fp[3 * t + 2] = k[2];
     }
     __syncthreads();
     for (int base = 0; base < nb * NB; base += NT) {
         const int e = base + t, s = e / NB, w = e - s * NB;
         bool hit = false;
         if (e < nb * NB)
-            hit = block_hits<BH>(s_rec[4 * s + 0], s_rec[4 * s + 1], s_rec[4 * s + 2], s_rec[4 * s + 3].x,
-                                 s_box[s], tx0 + (w % (TS / 8)) * 8, ty0 + (w / (TS / 8)) * BH);
+            hit = block_hits<BH>(s_rec[4 * s + 2], s_box[s], s_fp + 3 * s, tx0 + (w % (TS / 8)) * 8,
+                                 ty0 + (w / (TS / 8)) * BH);
         const unsigned bal = __ballot_sync(0xffffffffu, hit);
         if (e < nb * NB && w == 0) s_mask[s] = (bal >> ((t & 31) & ~(NB - 1))) & ((1u << NB) - 1u);
     }

@@ -23,7 +23,8 @@ __device__ __forceinline__ void fwd_tile(const Frame &f, const RenderBufs &b, in
     constexpr int NN = N * N;
     extern __shared__ float4 smem[];
     float4 *s_rec = smem;
-    float4 *s_tex = s_rec + 4 * batch;
+    float4 *s_fp = s_rec + 4 * batch;  // [batch][3] footprints
+    float4 *s_tex = s_fp + 3 * batch;
     int32_t *s_k = reinterpret_cast<int32_t *>(s_tex + batch * NN);
     uint32_t *s_j = reinterpret_cast<uint32_t *>(s_k + batch);
     uint2 *s_box = reinterpret_cast<uint2 *>(s_j + batch);
@@ -52,7 +53,7 @@ __device__ __forceinline__ void fwd_tile(const Frame &f, const RenderBufs &b, in
         if (__syncthreads_count(done) == NT) break;
         const int nb = min(batch, n_inst - bs);
         stage_batch<N, NT, TexT, TS, 4>(b, cam, sc, range.x + bs, nb, tx * TS, ty * TS, s_rec, s_tex, s_k, s_j,
-                                        s_box, s_mask);
+                                        s_box, s_mask, s_fp);
         __syncthreads();
         if (!done) {
             for (int i = 0; i < nb; ++i) {

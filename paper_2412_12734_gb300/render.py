@@ -46,6 +46,7 @@ def scene_to_device(scene: dict, device="cuda") -> dict:
     out["sh_degree"] = int(scene["sh_degree"])
     out["tex_n"] = int(scene["tex_n"])
     out["sigma"] = float(scene.get("sigma", 0.5))
+    out["mip_level"] = int(scene.get("mip_level", 0))
     return out
 
 
@@ -79,7 +80,7 @@ def scene_struct(sc: dict) -> L.gb_scene:
     s.sh_degree, s.sh_dtype = D, DTYPES[sc["sh"].dtype]
     s.tex_n, s.tex_dtype = N, DTYPES[sc["textures"].dtype]
     s.sigma = float(sc.get("sigma", 0.5))
-    s.reserved = 0
+    s.mip_level = int(sc.get("mip_level", 0))
     return s
 
 
@@ -294,10 +295,10 @@ def default_rasterizer() -> Rasterizer:
 class _RenderFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, means, quats, scales, opacities, sh, textures, meta):
-        rast, cams, sh_degree, tex_n, sigma, background = meta
+        rast, cams, sh_degree, tex_n, sigma, background, mip_level = meta
         sc = {"means": means.contiguous(), "quats": quats.contiguous(), "scales": scales.contiguous(),
               "opacities": opacities.contiguous(), "sh": sh.contiguous(), "textures": textures.contiguous(),
-              "sh_degree": sh_degree, "tex_n": tex_n, "sigma": sigma}
+              "sh_degree": sh_degree, "tex_n": tex_n, "sigma": sigma, "mip_level": mip_level}
         rgb, depth, alpha, saved = rast.forward([sc], cams, background=background)
         ctx.saved_handle = saved
         ctx.rast = rast
@@ -318,14 +319,15 @@ class _RenderFn(torch.autograd.Function):
 
 
 def render(means, quats, scales, opacities, sh, textures, cams, sh_degree: int, tex_n: int,
-           sigma: float = 0.5, background=None, rasterizer: Rasterizer | None = None):
+           sigma: float = 0.5, background=None, rasterizer: Rasterizer | None = None, mip_level: int = 0):
     """Differentiable render of one scene into all ``cams``.
 
     Returns (rgb [P,3], depth [P], alpha [P]) with the cameras' pixels packed
-    one after another (row-major per camera).
+    one after another (row-major per camera).  mip_level l > 0 renders the
+    colour grids box-filtered to N / 2^l (Sec. 5.1, Fig. 3 f, g).
     """
     rast = rasterizer or default_rasterizer()
-    meta = (rast, list(cams), int(sh_degree), int(tex_n), float(sigma), background)
+    meta = (rast, list(cams), int(sh_degree), int(tex_n), float(sigma), background, int(mip_level))
     return _RenderFn.apply(means, quats, scales, opacities, sh, textures, meta)
 
 

@@ -73,3 +73,14 @@ def test_noalloc_forward_refuses_frames_beyond_its_limits():
     st, _, _, _ = _noalloc(rast, dev, [big], [0])
     assert st == 4  # GB_ERR_CAPACITY
     assert "limits" in L.load().gb_last_error(rast.ctx).decode()
+
+
+def test_noalloc_forward_refuses_mip_level_scenes():
+    from paper_2412_12734_gb300 import _lib as L
+    from paper_2412_12734_gb300 import render as R
+    rast = R.Rasterizer(0)
+    sc = scenes.tiny_scene(6, K=4, tex_n=4)
+    sc["mip_level"] = 1
+    st, _, _, _ = _noalloc(rast, [R.scene_to_device(sc)], [scenes.tiny_camera(16, 16)], [0])
+    assert st == 2  # GB_ERR_UNSUPPORTED
+    assert "mip" in L.load().gb_last_error(rast.ctx).decode()
