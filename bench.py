@@ -285,7 +285,7 @@ def run_ours(args, world, rank, local):
         pairs = saved.stats()
     phases = {k: sum(v) / len(v) for k, v in phase_acc.items()}
     dominant = max(phases, key=phases.get)
-    roofline = roofline_line(dominant, phases, pairs, clocks)
+    roofline = roofline_line(dominant, phases, pairs, clocks, measured_traffic(dominant, args))
 
     result = {
         "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
@@ -330,7 +330,40 @@ def launches_per_step(lib, step):
     return lib.gb_kernel_launches() - a
 
 
-def roofline_line(dominant, phases, st, clocks):
+# DRAM bytes (read + write) per launch of the render kernels on the full
+# 16-view batched_1m workload at 4x4 grids, tile 16, batch 64, one pixel per
+# thread, from one ncu capture (profiles/render_traffic_batched_1m.md), with
+# the digest of the kernel sources it was taken on.  A kernel whose sources
+# differ reports traffic null.
+TRAFFIC = {
+    "render_bwd": {"bytes": 3.53e9 + 1.03e9, "files": ("render_bwd.cuh", "render_common.cuh", "render_bwd.cu"),
+                   "sha256_16": "b895f4212e633226",
+                   "config": {"workload": "batched_1m", "tex_n": 4, "tile": 16, "batch": 64, "ppt": 1}},
+    "render_fwd": {"bytes": 1.77e9 + 0.555e9, "files": ("render_fwd.cu", "render_common.cuh"),
+                   "sha256_16": "2516b221e631f828",
+                   "config": {"workload": "batched_1m", "tex_n": 4, "tile": 16, "batch": 64, "ppt": 1}},
+}
+
+
+def measured_traffic(kernel, args):
+    """Bytes per launch from TRAFFIC when the kernel sources and the launch
+    configuration are the ones it was measured on, else None."""
+    import hashlib
+    t = TRAFFIC.get(kernel)
+    if t is None:
+        return None
+    h = hashlib.sha256()
+    for f in t["files"]:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2412_12734_gb300", "csrc", f),
+                  "rb") as fh:
+            h.update(fh.read())
+    cfg = {"workload": args.workload, "tex_n": args.tex_n, "tile": args.tile, "batch": args.batch, "ppt": args.ppt}
+    if h.hexdigest()[:16] != t["sha256_16"] or cfg != t["config"] or args.views:
+        return None
+    return t["bytes"]
+
+
+def roofline_line(dominant, phases, st, clocks, traffic=None):
     """ALU roofline of the dominant kernel: algorithmic FLOPs per launch over
     its measured launch time, against the FP32 FMA peak at the sampled clock.
 
@@ -352,7 +385,7 @@ def roofline_line(dominant, phases, st, clocks):
         flops = None
     achieved = flops / (ms / 1e3) / 1e12 if flops else None
     return {"kernel": dominant, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak if achieved else None, "traffic": None,
+            "frac": achieved / peak if achieved else None, "traffic": traffic,
             "peak_source": f"FP32 FMA lanes 152x128 x2 at median sampled SM clock {sm:.0f} MHz",
             "launch_ms": ms}
 

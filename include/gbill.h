@@ -335,6 +335,39 @@ gb_status gb_render_forward_noalloc(gb_context *ctx, const gb_scene *scenes, int
                                     const gb_camera *cams, int32_t n_cams, const gb_options *opt,
                                     float *rgb, float *depth, float *alpha, void *stream);
 
+/* --------------------------------------------------------- image fitting -- */
+
+/* Image fitting (Sec. 5.1): one camera looks down +z at splats that face it
+ * and may only turn about the view axis.  A splat's raw parameters are an
+ * angle theta [K], a position xy [K,2] in its plane at depth z [K],
+ * log-scales [K,2] and an opacity logit [K] (FP32 device arrays).  This
+ * writes the activated parameters gb_scene takes:
+ *   quats     = (cos(theta/2), 0, 0, sin(theta/2))   [K,4]
+ *   means     = (x, y, z)                              [K,3]
+ *   scales    = exp(log_scales)                        [K,2]
+ *   opacities = 1 / (1 + exp(-logit))                  [K]
+ * All pointers are device arrays of K >= 0 rows; no allocation, no sync. */
+gb_status gb_fit_params(gb_context *ctx, int64_t K, const float *theta, const float *xy, const float *z,
+                        const float *log_scales, const float *logit_opacities, float *quats, float *means,
+                        float *scales, float *opacities, void *stream);
+
+/* Adjoint of gb_fit_params: from the renderer's gradients of the activated
+ * parameters (d_quats [K,4], d_means [K,3], d_scales [K,2], d_opacities [K],
+ * e.g. the gb_grads of gb_render_backward) to the raw parameters'
+ * (d_theta [K], d_xy [K,2], d_log_scales [K,2], d_logit_opacities [K],
+ * overwritten).  The z gradient is not formed (the planes stay fixed). */
+gb_status gb_fit_params_backward(gb_context *ctx, int64_t K, const float *theta, const float *log_scales,
+                                 const float *logit_opacities, const float *d_quats, const float *d_means,
+                                 const float *d_scales, const float *d_opacities, float *d_theta, float *d_xy,
+                                 float *d_log_scales, float *d_logit_opacities, void *stream);
+
+/* Mean squared error over n values (e.g. n = 3 x pixels of an rgb image):
+ * *loss = mean (rgb - target)^2, a device FP64 scalar overwritten on
+ * `stream` (summed in FP64); d_rgb (device, nullable) = 2 (rgb - target) / n,
+ * the upstream gradient for gb_render_backward.  No allocation, no sync. */
+gb_status gb_mse_loss(gb_context *ctx, const float *rgb, const float *target, int64_t n, float *d_rgb,
+                      double *loss, void *stream);
+
 /* ---------------------------------------------------------------- tuning -- */
 
 /* Autotuner: times forward + backward of this frame for every candidate

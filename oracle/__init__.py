@@ -363,3 +363,64 @@ def adam_step(param, grad, m, v, step: int, lr: float, beta1: float, beta2: floa
     m_hat = m / (1.0 - beta1 ** step)
     v_hat = v / (1.0 - beta2 ** step)
     return p - lr * m_hat / (np.sqrt(v_hat) + eps), m, v
+
+
+# --------------------------------------------------------------------------
+# image fitting (Sec. 5.1): a camera looking down +z, splats turning about
+# the view axis only, MSE loss; FP64 numpy
+# --------------------------------------------------------------------------
+
+def fit_params(raw: dict) -> dict:
+    """Activated splat parameters of raw image-fitting parameters:
+    q = (cos(theta/2), 0, 0, sin(theta/2)) (a turn by theta about z),
+    p = (x, y, z), s = exp(log_s), o = 1 / (1 + exp(-logit))."""
+    th = _f64(raw["theta"])
+    K = th.shape[0]
+    q = np.zeros((K, 4))
+    q[:, 0] = np.cos(th / 2)
+    q[:, 3] = np.sin(th / 2)
+    means = np.concatenate([_f64(raw["xy"]), _f64(raw["z"])[:, None]], axis=1)
+    return {"quats": q, "means": means, "scales": np.exp(_f64(raw["log_scales"])),
+            "opacities": 1.0 / (1.0 + np.exp(-_f64(raw["logit_opacities"])))}
+
+
+def fit_params_backward(raw: dict, g: dict) -> dict:
+    """Chain rule through fit_params (the depth z is held fixed)."""
+    th = _f64(raw["theta"])
+    dq = _f64(g["quats"])
+    o = 1.0 / (1.0 + np.exp(-_f64(raw["logit_opacities"])))
+    return {"theta": 0.5 * (np.cos(th / 2) * dq[:, 3] - np.sin(th / 2) * dq[:, 0]),
+            "xy": _f64(g["means"])[:, :2].copy(),
+            "log_scales": _f64(g["scales"]) * np.exp(_f64(raw["log_scales"])),
+            "logit_opacities": _f64(g["opacities"]) * o * (1.0 - o)}
+
+
+def mse_loss(rgb, target):
+    """Mean squared error over all values and its gradient 2 (rgb - target) / n."""
+    r = _f64(rgb) - _f64(target)
+    return float(np.mean(r * r)), 2.0 * r / r.size
+
+
+def fit_scene(raw: dict, sh_degree: int = 0) -> dict:
+    """The renderer's scene for raw image-fitting parameters (FP64 activation
+    of the stored raw values)."""
+    sc = fit_params(raw)
+    sc.update({"sh": raw["sh"], "textures": raw["textures"], "sh_degree": int(sh_degree),
+               "tex_n": int(raw["tex_n"]), "sigma": float(raw.get("sigma", 0.5))})
+    return sc
+
+
+def fit_step(raw: dict, target, cam: dict, mask=None) -> dict:
+    """One image-fitting evaluation: render, MSE against ``target`` and the
+    gradients of the raw parameters (and of sh, textures).  ``mask``
+    (optional [H,W]) multiplies the loss gradient per pixel (test use: zero
+    at pixels whose decisions sit within the margin)."""
+    sc = fit_scene(raw)
+    ref = render(sc, cam)
+    loss, d = mse_loss(ref["rgb"], target)
+    if mask is not None:
+        d = d * mask[..., None]
+    g = backward(sc, cam, d)
+    out = fit_params_backward(raw, g)
+    out.update({"sh": g["sh"], "textures": g["textures"], "loss": loss, "render": ref, "d_rgb": d})
+    return out

@@ -116,6 +116,9 @@ def load() -> C.CDLL:
         "gb_adam_step": (C.c_int, [vp, C.POINTER(gb_adam_tensor), i32, C.POINTER(gb_adam_config), vp]),
         "gb_render_forward_noalloc": (C.c_int, [vp, C.POINTER(gb_scene), i32, C.POINTER(gb_camera), i32,
                                                 C.POINTER(gb_options), vp, vp, vp, vp]),
+        "gb_fit_params": (C.c_int, [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "gb_fit_params_backward": (C.c_int, [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "gb_mse_loss": (C.c_int, [vp, vp, vp, i64, vp, vp, vp]),
         "gb_autotune": (C.c_int, [vp, vp, C.POINTER(gb_scene), i32, C.POINTER(gb_camera), i32,
                                   C.POINTER(gb_options), i32, C.POINTER(gb_options), vp, vp, vp, vp, i32,
                                   C.POINTER(i32)]),

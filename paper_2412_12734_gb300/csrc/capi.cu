@@ -898,6 +898,43 @@ __global__ void fill_kernel(float *p, int64_t n, float v) {
         p[i] = v;
 }
 
+gb_status gb_fit_params(gb_context *ctx, int64_t K, const float *theta, const float *xy, const float *z,
+                        const float *log_scales, const float *logit_opacities, float *quats, float *means,
+                        float *scales, float *opacities, void *stream) {
+    if (!ctx) return GB_ERR_INVALID_ARG;
+    if (K < 0) return fail(ctx, GB_ERR_INVALID_ARG, "K must be >= 0");
+    if (K > 0 && (!theta || !xy || !z || !log_scales || !logit_opacities || !quats || !means || !scales ||
+                  !opacities))
+        return fail(ctx, GB_ERR_INVALID_ARG, "null array");
+    GB_CUDA(ctx, launch_fit_params(theta, xy, z, log_scales, logit_opacities, K, quats, means, scales, opacities,
+                                   static_cast<cudaStream_t>(stream)));
+    return GB_OK;
+}
+
+gb_status gb_fit_params_backward(gb_context *ctx, int64_t K, const float *theta, const float *log_scales,
+                                 const float *logit_opacities, const float *d_quats, const float *d_means,
+                                 const float *d_scales, const float *d_opacities, float *d_theta, float *d_xy,
+                                 float *d_log_scales, float *d_logit_opacities, void *stream) {
+    if (!ctx) return GB_ERR_INVALID_ARG;
+    if (K < 0) return fail(ctx, GB_ERR_INVALID_ARG, "K must be >= 0");
+    if (K > 0 && (!theta || !log_scales || !logit_opacities || !d_quats || !d_means || !d_scales || !d_opacities ||
+                  !d_theta || !d_xy || !d_log_scales || !d_logit_opacities))
+        return fail(ctx, GB_ERR_INVALID_ARG, "null array");
+    GB_CUDA(ctx, launch_fit_params_bwd(theta, log_scales, logit_opacities, K, d_quats, d_means, d_scales,
+                                       d_opacities, d_theta, d_xy, d_log_scales, d_logit_opacities,
+                                       static_cast<cudaStream_t>(stream)));
+    return GB_OK;
+}
+
+gb_status gb_mse_loss(gb_context *ctx, const float *rgb, const float *target, int64_t n, float *d_rgb,
+                      double *loss, void *stream) {
+    if (!ctx) return GB_ERR_INVALID_ARG;
+    if (n < 0) return fail(ctx, GB_ERR_INVALID_ARG, "n must be >= 0");
+    if (!loss || (n > 0 && (!rgb || !target))) return fail(ctx, GB_ERR_INVALID_ARG, "null array");
+    GB_CUDA(ctx, launch_mse(rgb, target, n, d_rgb, loss, static_cast<cudaStream_t>(stream)));
+    return GB_OK;
+}
+
 gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int32_t n_scenes,
                       const gb_camera *cams, int32_t n_cams, const gb_options *base, int32_t reps,
                       gb_options *best, float *ms, int32_t *tiles, int32_t *batches, int32_t *ppts,

@@ -194,6 +194,16 @@ struct RenderBwdBufs {
     const float *d_rgb, *d_depth, *d_alpha;
     float *rec_grad;          // [n_visible, 16], indexed by depth-sorted position
 };
+// fit2d.cu: image-fitting parameter map, its adjoint, MSE loss and gradient
+cudaError_t launch_fit_params(const float *theta, const float *xy, const float *z, const float *log_s,
+                              const float *logit, int64_t K, float *quats, float *means, float *scales, float *opac,
+                              cudaStream_t s);
+cudaError_t launch_fit_params_bwd(const float *theta, const float *log_s, const float *logit, int64_t K,
+                                  const float *d_quats, const float *d_means, const float *d_scales,
+                                  const float *d_opac, float *d_theta, float *d_xy, float *d_log_s, float *d_logit,
+                                  cudaStream_t s);
+cudaError_t launch_mse(const float *rgb, const float *target, int64_t n, float *d_rgb, double *loss, cudaStream_t s);
+
 // mip.cu: box filter of a scene's grids to N >> mip (FP32 out) and its adjoint
 cudaError_t launch_mip_filter(const void *src, int dtype, int64_t K, int ns, int mip, float *dst, cudaStream_t s);
 cudaError_t launch_mip_grad(const float *gc, int64_t K, int ns, int mip, float *gf, cudaStream_t s);

@@ -4,6 +4,8 @@
 // that the render kernels read like any other; the backward renders the
 // gradient of that grid and the adjoint of the filter spreads it over the
 // stored texels (1/4^l each).  Both passes are HBM-bound elementwise kernels.
+#include <algorithm>
+
 #include "gbill_internal.cuh"
 
 namespace gbill {

@@ -301,3 +301,97 @@ def tiny_scene(seed: int, K: int = 5, tex_n: int = 4, sh_degree: int = 3,
                   sh_std=0.2, sigma=sigma)
     out["opacities"] = rng.uniform(0.3, 0.95, K).astype(np.float32)
     return out
+
+
+# --------------------------------------------------------------------------
+# 2D image fitting (Sec. 5.1): synthetic targets, a camera facing the image
+# plane and raw (pre-activation) splat parameters in that plane
+# --------------------------------------------------------------------------
+
+# the three target resolutions of the paper's image-fitting ablations
+FIT_TARGETS = {"wide": (1920, 871), "landscape": (2016, 1512), "portrait": (1833, 2000)}
+
+
+def fit_target(name_or_size, seed: int = 0) -> np.ndarray:
+    """Seeded synthetic target image [H, W, 3] in [0, 1] (float32).
+
+    ``name_or_size`` is a key of FIT_TARGETS or a (width, height) pair.  The
+    image mixes a smooth colour field (random low-frequency cosines), 60
+    soft-edged ellipses of random colour, size and orientation and two
+    striped regions, so that it holds edges, gradients and texture at
+    several scales; it stands in for the paper's photographs, none of which
+    is reproduced."""
+    W, H = FIT_TARGETS[name_or_size] if isinstance(name_or_size, str) else name_or_size
+    rng = np.random.default_rng(seed + 7919)
+    y, x = np.mgrid[0:H, 0:W].astype(np.float32)
+    xn, yn = x / W, y / H
+    img = np.zeros((H, W, 3), np.float32)
+    for _ in range(8):
+        kx, ky = rng.uniform(0.5, 4.0, 2)
+        ph = rng.uniform(0, 2 * math.pi)
+        amp = rng.uniform(0.05, 0.15, 3).astype(np.float32)
+        img += amp * np.cos(2 * math.pi * (kx * xn + ky * yn) + ph)[..., None]
+    img += 0.45
+    for _ in range(60):
+        cx, cy = rng.uniform(0, 1, 2)
+        a, b = rng.uniform(0.01, 0.15, 2)
+        th = rng.uniform(0, math.pi)
+        c, s = math.cos(th), math.sin(th)
+        col = rng.uniform(0, 1, 3).astype(np.float32)
+        # window of the ellipse (1.5 x its larger semi-axis, in x-normalised units)
+        r = 1.5 * max(a, b)
+        x0, x1 = max(int((cx - r) * W), 0), min(int((cx + r) * W) + 1, W)
+        y0, y1 = max(int((cy - r * W / H) * H), 0), min(int((cy + r * W / H) * H) + 1, H)
+        if x0 >= x1 or y0 >= y1:
+            continue
+        xs, ys = xn[y0:y1, x0:x1], yn[y0:y1, x0:x1]
+        u = ((xs - cx) * c + (ys - cy) * s * H / W) / a
+        v = (-(xs - cx) * s + (ys - cy) * c * H / W) / b
+        m = (1.0 / (1.0 + np.exp(np.clip(12.0 * (u * u + v * v - 1.0), -30, 30))))[..., None]
+        img[y0:y1, x0:x1] = img[y0:y1, x0:x1] * (1 - 0.8 * m) + 0.8 * m * col
+    for _ in range(2):
+        x0, y0 = rng.uniform(0, 0.7, 2)
+        w, h = rng.uniform(0.1, 0.3, 2)
+        f = rng.uniform(20, 60)
+        th = rng.uniform(0, math.pi)
+        inside = (xn > x0) & (xn < x0 + w) & (yn > y0) & (yn < y0 + h)
+        stripes = 0.5 + 0.5 * np.sin(2 * math.pi * f * (xn * math.cos(th) + yn * math.sin(th)))
+        img = np.where(inside[..., None], 0.5 * img + 0.5 * stripes[..., None], img)
+    return np.ascontiguousarray(np.clip(img, 0.0, 1.0), np.float32)
+
+
+def fit_camera(width: int, height: int) -> dict:
+    """Camera at the origin looking down +z with camera axes = world axes and
+    focal length = width: the plane z = 1 spans x in [-1/2, 1/2]."""
+    return {"width": int(width), "height": int(height), "fx": np.float32(width), "fy": np.float32(width),
+            "cx": np.float32(width / 2), "cy": np.float32(height / 2), "R": np.eye(3, dtype=np.float32),
+            "t": np.zeros(3, np.float32), "near": np.float32(0.01)}
+
+
+def fit_init(K: int, width: int, height: int, seed: int = 0, tex_n: int = 4) -> dict:
+    """Raw parameters of K splats for fitting a width x height image (Sec. 5.1):
+    random position in the image plane z = 1 (plus a depth offset below 1e-3
+    that fixes a strict order), random rotation angle about the view axis,
+    random size (log-normal around the spacing of a K-splat grid over the
+    image), random opacity logit and a random colour, held by the colour grid
+    (constant per splat) with a zero SH term (degree 0).
+
+    Returns float32 arrays: theta [K], xy [K,2], z [K], log_scales [K,2],
+    logit_opacities [K], sh [K,1,3], textures [K,N,N,3]; plus tex_n and sigma.
+    """
+    rng = np.random.default_rng(seed + 104729)
+    half_w, half_h = 0.5, 0.5 * height / width
+    xy = np.stack([rng.uniform(-half_w, half_w, K), rng.uniform(-half_h, half_h, K)], 1)
+    spacing = math.sqrt(4.0 * half_w * half_h / K)
+    log_s = np.log(spacing * 0.5) + rng.normal(0.0, 0.3, (K, 2))
+    col = rng.uniform(0.0, 1.0, (K, 1, 1, 3))
+    return {
+        "theta": rng.uniform(0.0, math.pi, K).astype(np.float32),
+        "xy": xy.astype(np.float32),
+        "z": (1.0 + 1e-3 * rng.permutation(K) / max(K, 1)).astype(np.float32),
+        "log_scales": log_s.astype(np.float32),
+        "logit_opacities": rng.normal(0.0, 1.0, K).astype(np.float32),
+        "sh": np.zeros((K, 1, 3), np.float32),
+        "textures": np.ascontiguousarray(np.broadcast_to(col, (K, tex_n, tex_n, 3)), np.float32),
+        "tex_n": int(tex_n), "sigma": SIGMA_DEFAULT,
+    }
