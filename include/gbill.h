@@ -101,7 +101,7 @@ typedef struct {
     const void *textures;     /* [K,N,N,3] of tex_dtype                          */
     int32_t sh_degree;        /* D in 0..3                                       */
     int32_t sh_dtype;         /* gb_dtype                                        */
-    int32_t tex_n;            /* N in {1,2,4,8}                                  */
+    int32_t tex_n;            /* N in {1,2,4,8,16}                               */
     int32_t tex_dtype;        /* gb_dtype                                        */
     float sigma;              /* grid extent in uv units (paper default 0.5)     */
     int32_t mip_level;        /* 0: render the N x N grid.  l in 1..log2(N):     */
@@ -126,7 +126,9 @@ typedef struct {
 typedef struct {
     int32_t tile_size;   /* tile edge in pixels: 8 or 16 (0 = 16)                 */
     int32_t batch_depth; /* splats staged per shared-memory batch, 0 = automatic;
-                            otherwise a multiple of 32 up to the tile's pixels    */
+                            otherwise a multiple of 16 up to the tile's pixels
+                            whose staging fits 200 KB of shared memory (N = 16:
+                            16 splats)                                            */
     uint32_t flags;      /* GB_FLAG_*                                             */
     int32_t pixels_per_thread; /* backward: 1, or 2 (two pixels of a column per
                                   thread on the packed FP32x2 pipe); 0 = 1. With 2,
@@ -260,7 +262,7 @@ gb_status gb_saved_export_keys(gb_saved *saved, uint64_t *keys, int64_t *ids, in
  * sort, tile ranges, per-tile render.  Unless GB_FLAG_NO_SYNC is set the
  * call synchronizes once (to size the instance list) and may grow `saved`.
  * Returns GB_ERR_INVALID_ARG for bad sizes/pointers/options,
- * GB_ERR_UNSUPPORTED for tex_n not in {1,2,4,8} or sh_degree > 3. */
+ * GB_ERR_UNSUPPORTED for tex_n not in {1,2,4,8,16} or sh_degree > 3. */
 gb_status gb_render_forward(gb_context *ctx, gb_saved *saved, const gb_scene *scenes,
                             int32_t n_scenes, const gb_camera *cams, int32_t n_cams,
                             const gb_options *opt, float *rgb, float *depth, float *alpha,
@@ -371,7 +373,7 @@ gb_status gb_mse_loss(gb_context *ctx, const float *rgb, const float *target, in
 /* ---------------------------------------------------------------- tuning -- */
 
 /* Autotuner: times forward + backward of this frame for every candidate
- * (tile_size 8 and 16; batch_depth 32, 64, 128, 256 where it fits the tile and
+ * (tile_size 8 and 16; batch_depth 16, 32, 64, 128, 256 where it fits the tile and
  * the shared-memory budget; pixels_per_thread 1 and 2) and writes the fastest
  * options to *best (flags and
  * background are copied from *base, which may be NULL).  Each candidate runs

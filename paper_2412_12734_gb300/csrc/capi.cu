@@ -178,13 +178,14 @@ gb_status reserve_scratch(gb_saved *s) {
 size_t batch_smem(int N, int batch, bool bwd);
 
 // Batch depth giving ~64 KB of staged shared memory per 256-thread block
-// (three to four resident blocks per SM).
+// (three to four resident blocks per SM); a multiple of 16, at least 16 (the
+// 16 x 16 grids of N = 16 stage 4 KB per splat).
 int default_batch(int N, bool bwd) {
     const int per = int(batch_smem(N, 1, bwd));
     int b = (64 * 1024) / per;
     b = std::min(b, 256);
-    b &= ~31;
-    return std::max(b, 32);
+    b &= ~15;
+    return std::max(b, 16);
 }
 
 size_t batch_smem(int N, int batch, bool bwd) {
@@ -192,7 +193,8 @@ size_t batch_smem(int N, int batch, bool bwd) {
         case 1: return stage_bytes<1>(batch, bwd);
         case 2: return stage_bytes<2>(batch, bwd);
         case 4: return stage_bytes<4>(batch, bwd);
-        default: return stage_bytes<8>(batch, bwd);
+        case 8: return stage_bytes<8>(batch, bwd);
+        default: return stage_bytes<16>(batch, bwd);
     }
 }
 
@@ -224,13 +226,13 @@ gb_status build_frame(gb_context *ctx, const gb_scene *scenes, int32_t n_scenes,
             return fail(ctx, GB_ERR_INVALID_ARG, "scene %d: num_splats %lld out of range", s, (long long)g.num_splats);
         if (g.sh_degree < 0 || g.sh_degree > 3)
             return fail(ctx, GB_ERR_UNSUPPORTED, "scene %d: sh_degree %d not in 0..3", s, g.sh_degree);
-        if (!(g.tex_n == 1 || g.tex_n == 2 || g.tex_n == 4 || g.tex_n == 8))
-            return fail(ctx, GB_ERR_UNSUPPORTED, "scene %d: tex_n %d not in {1,2,4,8}", s, g.tex_n);
+        if (!(g.tex_n == 1 || g.tex_n == 2 || g.tex_n == 4 || g.tex_n == 8 || g.tex_n == 16))
+            return fail(ctx, GB_ERR_UNSUPPORTED, "scene %d: tex_n %d not in {1,2,4,8,16}", s, g.tex_n);
         if (!dtype_ok(g.sh_dtype) || !dtype_ok(g.tex_dtype))
             return fail(ctx, GB_ERR_INVALID_ARG, "scene %d: bad storage dtype", s);
         if (!(g.sigma > 0.0f) || !isfinite(g.sigma))
             return fail(ctx, GB_ERR_INVALID_ARG, "scene %d: sigma must be positive", s);
-        if (g.mip_level < 0 || (g.tex_n >> g.mip_level) < 1 || g.mip_level > 3)
+        if (g.mip_level < 0 || g.mip_level > 4 || (g.tex_n >> g.mip_level) < 1)
             return fail(ctx, GB_ERR_INVALID_ARG, "scene %d: mip_level %d not in 0..log2(%d)", s, g.mip_level,
                         g.tex_n);
         if (g.num_splats > 0 && (!g.means || !g.quats || !g.scales || !g.opacities || !g.sh || !g.textures))
@@ -529,7 +531,7 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
     const int nt = tile * tile;
     int bf = o.batch_depth ? o.batch_depth : std::min(default_batch(N, false), nt);
     int bb = o.batch_depth ? o.batch_depth : std::min(default_batch(N, true), nt / ppt);
-    if (bf < 32 || bf > nt || (bf & 31)) return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d invalid", bf);
+    if (bf < 16 || bf > nt || (bf & 15)) return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d invalid", bf);
     if (bb > nt / ppt) return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d exceeds the backward's %d threads", bb, nt / ppt);
     if (batch_smem(N, bf, false) > 200 * 1024 || batch_smem(N, bb, true) > 200 * 1024)
         return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d needs too much shared memory", bf);
@@ -793,7 +795,7 @@ gb_status gb_render_forward_noalloc(gb_context *ctx, const gb_scene *scenes, int
     for (int k = 0; k < f.n_groups; ++k) N = std::max(N, f.group_N[k]);
     const int nt = tile * tile;
     const int bf = o.batch_depth ? o.batch_depth : std::min(default_batch(N, false), nt);
-    if (bf < 32 || bf > nt || (bf & 31) || batch_smem(N, bf, false) > 200 * 1024)
+    if (bf < 16 || bf > nt || (bf & 15) || batch_smem(N, bf, false) > 200 * 1024)
         return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d invalid", bf);
     int dev = 0;
     GB_CUDA(ctx, cudaGetDevice(&dev));
@@ -986,10 +988,10 @@ gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int3
         float best_ms = INFINITY;
         int n = 0;
         const int tile_c[2] = {16, 8};
-        const int batch_c[4] = {32, 64, 128, 256};
+        const int batch_c[5] = {16, 32, 64, 128, 256};
         for (int pi = 1; pi <= 2 && st == GB_OK; ++pi)
         for (int ti = 0; ti < 2 && st == GB_OK; ++ti)
-            for (int bi = 0; bi < 4 && st == GB_OK; ++bi) {
+            for (int bi = 0; bi < 5 && st == GB_OK; ++bi) {
                 const int T = tile_c[ti], B = batch_c[bi];
                 if (B > T * T / pi) continue;
                 if (batch_smem(N, B, false) > 160 * 1024 || batch_smem(N, B, true) > 160 * 1024) continue;

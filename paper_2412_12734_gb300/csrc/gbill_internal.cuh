@@ -13,7 +13,7 @@ namespace gbill {
 
 constexpr int kMaxCams = GBILL_MAX_CAMERAS;
 constexpr int kMaxScenes = GBILL_MAX_SCENES;
-constexpr int kMaxGroups = 12;  // distinct (texture size, storage type) pairs of a frame
+constexpr int kMaxGroups = 16;  // distinct (texture size, storage type) pairs of a frame (5 x 3 possible)
 
 // Constants of the method (Sec. 3.1 Eq. 4 with the 3DGS-lineage clamp and
 // cutoffs; the screen-space low-pass of the 2DGS lineage).

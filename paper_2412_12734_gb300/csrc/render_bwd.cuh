@@ -93,7 +93,7 @@ __device__ __forceinline__ float warp_reduce_scatter32(float v[32], int lane) {
 // Warp-reduced values: 0..13 record gradients, 14..25 the RGB gradient of the
 // grid's four corner texels (0,0), (0,N-1), (N-1,0), (N-1,N-1).
 constexpr int kCornerSlot = 14;
-// For N = 8, above this many distinct edge/interior cells in a (warp, splat)
+// For N >= 8, above this many distinct edge/interior cells in a (warp, splat)
 // pair the lanes add their texel weights to shared memory directly instead of
 // one reduce-scatter per cell (measured: faster at N = 8, slower at N <= 4).
 constexpr int kGroupCells8 = 4;
@@ -539,6 +539,7 @@ cudaError_t launch_n(const Frame &f, const RenderBwdBufs &b, int N, int batch, T
         case 2: return launch_t<TS, 2, TexT, P>(f, b, batch, ts, persistent, s);
         case 4: return launch_t<TS, 4, TexT, P>(f, b, batch, ts, persistent, s);
         case 8: return launch_t<TS, 8, TexT, P>(f, b, batch, ts, persistent, s);
+        case 16: return launch_t<TS, 16, TexT, P>(f, b, batch, ts, persistent, s);
         default: return cudaErrorInvalidValue;
     }
 }

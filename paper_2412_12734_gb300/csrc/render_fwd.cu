@@ -174,6 +174,7 @@ cudaError_t launch_n(const Frame &f, const RenderBufs &b, int N, int batch, Tile
         case 2: return launch_t<TS, 2, TexT>(f, b, batch, ts, persistent, s);
         case 4: return launch_t<TS, 4, TexT>(f, b, batch, ts, persistent, s);
         case 8: return launch_t<TS, 8, TexT>(f, b, batch, ts, persistent, s);
+        case 16: return launch_t<TS, 16, TexT>(f, b, batch, ts, persistent, s);
         default: return cudaErrorInvalidValue;
     }
 }

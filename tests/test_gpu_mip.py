@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("N,lvl,dtype", [(4, 1, "f32"), (4, 2, "f32"), (8, 1, "f16"), (8, 2, "f32"),
-                                         (8, 3, "bf16"), (2, 1, "f32")])
+                                         (8, 3, "bf16"), (2, 1, "f32"), (16, 1, "f16"), (16, 4, "f32")])
 @pytest.mark.parametrize("ppt", [1, 2])
 def test_mip_image_and_gradients(N, lvl, dtype, ppt):
     sc = scenes.tiny_scene(40 + N + lvl, K=8, tex_n=N, sh_degree=2, tex_dtype=dtype)

@@ -48,6 +48,8 @@ CASES = {
     "tiny_n2_d3": lambda: ([scenes.tiny_scene(2, K=6, tex_n=2, sh_degree=3)], [scenes.tiny_camera(37, 29)]),
     "tiny_n4_d3": lambda: ([scenes.tiny_scene(3, K=8, tex_n=4, sh_degree=3)], [scenes.tiny_camera(48, 33)]),
     "tiny_n8_d2": lambda: ([scenes.tiny_scene(4, K=8, tex_n=8, sh_degree=2)], [scenes.tiny_camera(50, 50)]),
+    "tiny_n16_d1": lambda: ([scenes.tiny_scene(14, K=8, tex_n=16, sh_degree=1, tex_dtype="f16")],
+                            [scenes.tiny_camera(56, 44)]),
     "tiny_n4_sigma2": lambda: ([scenes.tiny_scene(5, K=8, tex_n=4, sh_degree=1, sigma=2.0)],
                                [scenes.tiny_camera(33, 47)]),
     "tiny_f16": lambda: ([scenes.tiny_scene(6, K=8, tex_n=4, sh_degree=3, sh_dtype="f16", tex_dtype="f16")],
@@ -310,7 +312,7 @@ def test_invalid_arguments_are_rejected():
         rast.forward([dev], [nan_cam])
     assert ei.value.status == 6
     with pytest.raises(L.GbillError) as ei:
-        rast.forward([dev], [cam], batch=48)
+        rast.forward([dev], [cam], batch=40)  # not a multiple of 16
     assert ei.value.status == 1
 
 

@@ -60,7 +60,7 @@ def _check(sc, cam, seed, bg=None, use_depth=True, use_alpha=True, n_sample=None
     return checked
 
 
-@pytest.mark.parametrize("N,D", [(1, 0), (2, 3), (4, 3), (8, 1)])
+@pytest.mark.parametrize("N,D", [(1, 0), (2, 3), (4, 3), (8, 1), (16, 0)])
 def test_fd_all_gradients(N, D):
     sc = scenes.tiny_scene(20 + N, K=5, tex_n=N, sh_degree=D)
     cam = scenes.tiny_camera(16, 16)

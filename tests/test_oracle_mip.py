@@ -55,7 +55,7 @@ def test_constant_grid_renders_the_same_at_every_level():
         np.testing.assert_array_equal(r["alpha"], base["alpha"])
 
 
-@pytest.mark.parametrize("N", [2, 4, 8])
+@pytest.mark.parametrize("N", [2, 4, 8, 16])
 def test_top_level_is_the_mean_colour(N):
     sc = scenes.tiny_scene(12, K=5, tex_n=N, sh_degree=2)
     cam = scenes.tiny_camera(20, 18)

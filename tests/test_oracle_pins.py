@@ -64,7 +64,7 @@ def test_sh_gradient_finite_difference():
 
 # ---------------------------------------------------------------- bilinear --
 
-@pytest.mark.parametrize("N", [2, 4, 8])
+@pytest.mark.parametrize("N", [2, 4, 8, 16])
 @pytest.mark.parametrize("sigma", [0.5, 2.0])
 def test_bilinear_reproduces_texels(N, sigma):
     """Corner-aligned grid: texel (i, j) sits at u = -sigma + 2 sigma i / (N-1)."""
@@ -77,7 +77,7 @@ def test_bilinear_reproduces_texels(N, sigma):
     np.testing.assert_allclose(out, grid.reshape(-1, 3), atol=1e-14)
 
 
-@pytest.mark.parametrize("N", [2, 3, 4, 8])
+@pytest.mark.parametrize("N", [2, 3, 4, 8, 16])
 def test_bilinear_affine_grid_is_exact_and_oriented(N):
     """Grid C[i_u][i_v] = a i_u + b i_v + c interpolates to a u' + b v' + c.
 
@@ -107,7 +107,7 @@ def test_bilinear_partition_of_unity_and_n1():
     assert np.all(out == col)
 
 
-@pytest.mark.parametrize("N", [2, 4, 8])
+@pytest.mark.parametrize("N", [2, 4, 8, 16])
 def test_adj_bilinear_matches_finite_differences(N):
     """Alg. 2 adj-bilinear: grid adjoint = interpolation weights, uv adjoint =
     derivative of the interpolant inside (-sigma, sigma), zero outside."""
@@ -198,7 +198,7 @@ def _fronto_scene(s=(0.5, 0.5), o=0.7, z=4.0, N=4, grid=None, colour=(0.1, 0.2, 
     return sc, cam
 
 
-@pytest.mark.parametrize("N", [1, 2, 4, 8])
+@pytest.mark.parametrize("N", [1, 2, 4, 8, 16])
 @pytest.mark.parametrize("o", [0.6, 0.995])
 def test_single_splat_at_pixel_centre(N, o):
     """u = v = 0 at the centre pixel: alpha = min(0.99, o) (Eq. 4, alpha clamp)
