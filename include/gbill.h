@@ -106,8 +106,8 @@ typedef struct {
     float sigma;              /* grid extent in uv units (paper default 0.5)     */
     int32_t mip_level;        /* 0: render the N x N grid.  l in 1..log2(N):     */
                               /* render every grid box-filtered to N/2^l x N/2^l */
-                              /* (texel = mean of its 2^l x 2^l block; Sec. 5.1, */
-                              /* Fig. 3 f, g); gradients still reach the N x N   */
+                              /* (texel = mean of its 2^l x 2^l block; Sec. 4.1, */
+                              /* Fig. 4 f, g); gradients still reach the N x N   */
                               /* texels (1/4^l of the coarse texel's gradient).  */
                               /* The filtered grids live in FP32 scratch of the  */
                               /* saved state, sized by a synchronizing forward;  */
@@ -339,7 +339,7 @@ gb_status gb_render_forward_noalloc(gb_context *ctx, const gb_scene *scenes, int
 
 /* --------------------------------------------------------- image fitting -- */
 
-/* Image fitting (Sec. 5.1): one camera looks down +z at splats that face it
+/* Image fitting (Sec. 4.1): one camera looks down +z at splats that face it
  * and may only turn about the view axis.  A splat's raw parameters are an
  * angle theta [K], a position xy [K,2] in its plane at depth z [K],
  * log-scales [K,2] and an opacity logit [K] (FP32 device arrays).  This

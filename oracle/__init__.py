@@ -14,8 +14,8 @@ them (numpy's stable argsort).
 
 Sections cited: Sec. 3.1 Eq. 2-4 (compositing, 2DGS plane, uv Gaussian),
 Sec. 3.2 Eq. 5 (bilinear colour grid), Sec. 4.2 (SH added to the grid colour),
-Alg. 1 (rasterize fwd/bwd), Alg. 2 (bilinear / adj-bilinear), Sec. 5.1 and
-Fig. 3 f, g (colour grid box-filtered to a coarser mip level at render time).
+Alg. 1 (rasterize fwd/bwd), Alg. 2 (bilinear / adj-bilinear), Sec. 4.1 and
+Fig. 4 f, g (colour grid box-filtered to a coarser mip level at render time).
 """
 from __future__ import annotations
 
@@ -98,7 +98,7 @@ def _f64(a) -> np.ndarray:
 
 
 def mip_grid(textures, level: int):
-    """Colour grids box-filtered to mip level ``level`` (Sec. 5.1, Fig. 3 f, g):
+    """Colour grids box-filtered to mip level ``level`` (Sec. 4.1, Fig. 4 f, g):
     texel (i, j) of the (N/2^l) x (N/2^l) grid is the mean of the 2^l x 2^l
     block of texels (2^l i + a, 2^l j + b), a, b < 2^l.  Level 0 is the grid
     itself."""
@@ -366,7 +366,7 @@ def adam_step(param, grad, m, v, step: int, lr: float, beta1: float, beta2: floa
 
 
 # --------------------------------------------------------------------------
-# image fitting (Sec. 5.1): a camera looking down +z, splats turning about
+# image fitting (Sec. 4.1): a camera looking down +z, splats turning about
 # the view axis only, MSE loss; FP64 numpy
 # --------------------------------------------------------------------------
 

@@ -1,4 +1,4 @@
-// Image fitting (Sec. 5.1): splats live in planes facing a camera that looks
+// Image fitting (Sec. 4.1): splats live in planes facing a camera that looks
 // down +z and may only turn about the view axis, so a splat's raw parameters
 // are an angle theta, a position (x, y) in its plane z, log-scales and an
 // opacity logit.  The map to the renderer's activated parameters and its

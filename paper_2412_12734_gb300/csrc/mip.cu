@@ -1,4 +1,4 @@
-// Mip-level colour grids (Sec. 5.1, Fig. 3 f, g): the renderer draws every
+// Mip-level colour grids (Sec. 4.1, Fig. 4 f, g): the renderer draws every
 // grid of a scene box-filtered to (N/2^l) x (N/2^l), each texel the mean of
 // its 2^l x 2^l block.  The filter runs once per forward into an FP32 grid
 // that the render kernels read like any other; the backward renders the

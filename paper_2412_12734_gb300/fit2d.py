@@ -1,4 +1,4 @@
-"""2D image fitting (Sec. 5.1) on the GPU library.
+"""2D image fitting (Sec. 4.1) on the GPU library.
 
 One camera looks down +z at an image plane; every splat faces the camera and
 may only turn about the view axis.  The trainable parameters are raw: angle
@@ -153,7 +153,7 @@ class ImageFit:
 
 
 def main(argv=None):
-    ap = argparse.ArgumentParser(description="Fit textured 2D Gaussian splats to a synthetic image (Sec. 5.1).")
+    ap = argparse.ArgumentParser(description="Fit textured 2D Gaussian splats to a synthetic image (Sec. 4.1).")
     ap.add_argument("--target", default="wide", help="wide | landscape | portrait, or WxH")
     ap.add_argument("--splats", type=int, default=1000)
     ap.add_argument("--tex-n", type=int, default=4)

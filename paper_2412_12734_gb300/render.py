@@ -324,7 +324,7 @@ def render(means, quats, scales, opacities, sh, textures, cams, sh_degree: int, 
 
     Returns (rgb [P,3], depth [P], alpha [P]) with the cameras' pixels packed
     one after another (row-major per camera).  mip_level l > 0 renders the
-    colour grids box-filtered to N / 2^l (Sec. 5.1, Fig. 3 f, g).
+    colour grids box-filtered to N / 2^l (Sec. 4.1, Fig. 4 f, g).
     """
     rast = rasterizer or default_rasterizer()
     meta = (rast, list(cams), int(sh_degree), int(tex_n), float(sigma), background, int(mip_level))

@@ -6,10 +6,10 @@ the very same arrays.  The workloads stand in for the paper's image-fitting,
 NeRF360 and face-capture scenes (Sec. 4), none of which ships with the paper:
 
 * ``cube``      - centres uniform in a cube, random frames (1k-splat case,
-                  the splat budget of the paper's Fig. 3 overfit).
+                  the splat budget of the paper's Fig. 4 overfit).
 * ``planes``    - 80 % of the splats on 6 random planes with normal-aligned
                   frames, 20 % uniform clutter in a 10^3 box (100k / 1M / 3M
-                  splat cases, the primitive budgets of Fig. 5 and Sec. 4.2).
+                  splat cases, the primitive budgets of Fig. 1, Fig. 6 and Sec. 4.2).
 
 Parameters are returned activated (linear scales, opacity in (0, 1)); the
 log-scale / logit draws are turned into those values here.  Texture and SH
@@ -304,7 +304,7 @@ def tiny_scene(seed: int, K: int = 5, tex_n: int = 4, sh_degree: int = 3,
 
 
 # --------------------------------------------------------------------------
-# 2D image fitting (Sec. 5.1): synthetic targets, a camera facing the image
+# 2D image fitting (Sec. 4.1): synthetic targets, a camera facing the image
 # plane and raw (pre-activation) splat parameters in that plane
 # --------------------------------------------------------------------------
 
@@ -369,7 +369,7 @@ def fit_camera(width: int, height: int) -> dict:
 
 
 def fit_init(K: int, width: int, height: int, seed: int = 0, tex_n: int = 4) -> dict:
-    """Raw parameters of K splats for fitting a width x height image (Sec. 5.1):
+    """Raw parameters of K splats for fitting a width x height image (Sec. 4.1):
     random position in the image plane z = 1 (plus a depth offset below 1e-3
     that fixes a strict order), random rotation angle about the view axis,
     random size (log-normal around the spacing of a K-splat grid over the

@@ -1,4 +1,4 @@
-"""Image fitting on the GPU (Sec. 5.1): the parameter map, its adjoint and the
+"""Image fitting on the GPU (Sec. 4.1): the parameter map, its adjoint and the
 MSE loss against the FP64 oracle; the raw-parameter gradients of a whole
 fitting iteration (activation, render, loss, backward, adjoint) against the
 oracle's; and a short fit that must lower the loss."""

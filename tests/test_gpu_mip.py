@@ -1,4 +1,4 @@
-"""Mip-level colour grids on the GPU (Sec. 5.1, Fig. 3 f, g): the grid is
+"""Mip-level colour grids on the GPU (Sec. 4.1, Fig. 4 f, g): the grid is
 box-filtered to N/2^l at staging and the texture gradient flows back to the
 stored N x N texels.  Parity with the FP64 oracle (which filters the grid in
 FP64 and renders it), at every level of N = 4 and N = 8, in FP32 and FP16

@@ -1,4 +1,4 @@
-"""Pins of the oracle's image-fitting pieces (Sec. 5.1): the parameter map
+"""Pins of the oracle's image-fitting pieces (Sec. 4.1): the parameter map
 (a turn about the view axis, exp scales, sigmoid opacity), the MSE loss and
 their composition with the renderer, against closed forms and central
 differences of the whole loss."""

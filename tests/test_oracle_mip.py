@@ -1,4 +1,4 @@
-"""Pins of the oracle's mip-level colour grids (Sec. 5.1, Fig. 3 f, g: the
+"""Pins of the oracle's mip-level colour grids (Sec. 4.1, Fig. 4 f, g: the
 grid box-filtered to 2x2 and to a single colour at render time).
 
 The box filter is checked against explicit loops; rendering is checked
