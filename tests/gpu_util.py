@@ -55,7 +55,7 @@ def compare_images(gpu_img, ref, what="rgb", tol=IMG_TOL, relative_to=None):
     """Max error, in units of the ``tol`` bar, over pixels whose forward
     decisions are not within the margin.
 
-    The kernels evaluate every pixel/splat pair in FP32 (Sec. 3.2), so a
+    The kernels evaluate every pixel/splat pair in FP32 (the design's precision; the paper fixes none), so a
     pixel's error scales with the conditioning of that evaluation: the oracle's
     ``cond`` is the alpha*T-weighted sensitivity of (u, v) to relative rounding
     of the centre-relative terms, about 1 for most pixels and up to a few
