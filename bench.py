@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--tex-n", type=int, default=4)
     ap.add_argument("--views", type=int, default=0, help="use only the first V cameras (0 = all; profiling)")
     ap.add_argument("--batch", type=int, default=0, help="splats per shared-memory batch (0 = auto)")
-    ap.add_argument("--tile", type=int, default=0, help="tile edge 8 or 16 (0 = autotune)")
+    ap.add_argument("--tile", type=int, default=0, help="tile edge 8, 16 or 32 (0 = autotune)")
     ap.add_argument("--ppt", type=int, default=1, help="backward pixels per thread, 1 or 2")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-plain", action="store_true")

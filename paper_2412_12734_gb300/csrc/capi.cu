@@ -177,12 +177,14 @@ gb_status reserve_scratch(gb_saved *s) {
 
 size_t batch_smem(int N, int batch, bool bwd);
 
-// Batch depth giving ~64 KB of staged shared memory per 256-thread block
-// (three to four resident blocks per SM); a multiple of 16, at least 16 (the
-// 16 x 16 grids of N = 16 stage 4 KB per splat).
+// Batch depth giving ~42 KB of staged shared memory per block, so that four
+// or more blocks stay resident per SM (measured on the 1M-splat, 16-view
+// workload: 64 is best at N = 4 and 16 at N = 8, where 64 would stage 127 KB
+// in the backward and leave one block per SM); a multiple of 16, at least 16.
 int default_batch(int N, bool bwd) {
-    const int per = int(batch_smem(N, 1, bwd));
-    int b = (64 * 1024) / per;
+    const int per = int(batch_smem(N, 1, true));
+    (void)bwd;  // one depth for both passes: the backward's staging decides
+    int b = (42 * 1024) / per;
     b = std::min(b, 256);
     b &= ~15;
     return std::max(b, 16);
@@ -520,7 +522,8 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
     const int ppt = o.pixels_per_thread ? o.pixels_per_thread : 1;
     if (ppt != 1 && ppt != 2) return fail(ctx, GB_ERR_INVALID_ARG, "pixels_per_thread must be 1 or 2");
     const int tile = o.tile_size ? o.tile_size : 16;
-    if (tile != 8 && tile != 16) return fail(ctx, GB_ERR_UNSUPPORTED, "tile_size %d not built (8 or 16)", tile);
+    if (tile != 8 && tile != 16 && tile != 32)
+        return fail(ctx, GB_ERR_UNSUPPORTED, "tile_size %d not built (8, 16 or 32)", tile);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Frame f;
     int64_t max_k = 0;
@@ -776,7 +779,8 @@ gb_status gb_render_forward_noalloc(gb_context *ctx, const gb_scene *scenes, int
     gb_options o{};
     if (opt) o = *opt;
     const int tile = o.tile_size ? o.tile_size : 16;
-    if (tile != 8 && tile != 16) return fail(ctx, GB_ERR_UNSUPPORTED, "tile_size %d not built (8 or 16)", tile);
+    if (tile != 8 && tile != 16 && tile != 32)
+        return fail(ctx, GB_ERR_UNSUPPORTED, "tile_size %d not built (8, 16 or 32)", tile);
     if (o.flags & (GB_FLAG_TIMING | GB_FLAG_PERSISTENT))
         return fail(ctx, GB_ERR_UNSUPPORTED, "the no-allocation forward takes no timing or persistent flag");
     Frame f;
@@ -987,10 +991,10 @@ gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int3
         o.flags &= ~(GB_FLAG_NO_SYNC | GB_FLAG_TIMING);
         float best_ms = INFINITY;
         int n = 0;
-        const int tile_c[2] = {16, 8};
+        const int tile_c[3] = {16, 8, 32};
         const int batch_c[5] = {16, 32, 64, 128, 256};
         for (int pi = 1; pi <= 2 && st == GB_OK; ++pi)
-        for (int ti = 0; ti < 2 && st == GB_OK; ++ti)
+        for (int ti = 0; ti < 3 && st == GB_OK; ++ti)
             for (int bi = 0; bi < 5 && st == GB_OK; ++bi) {
                 const int T = tile_c[ti], B = batch_c[bi];
                 if (B > T * T / pi) continue;

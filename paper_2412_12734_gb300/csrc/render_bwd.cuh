@@ -136,12 +136,13 @@ __device__ __forceinline__ bool pair_adjoint(Pix &px, uint32_t idx, const float4
     rem.w00 = rem.w10 = rem.w01 = rem.w11 = 0.0f;
     rem.c0 = rem.c1 = rem.c2 = 0.0f;
     rem.base = 0;
-    if (!(px.inside && idx < px.last)) return false;
-    ++npairs;
+    // every lane evaluates (lanes past their last splat too, result dropped) so
+    // that the only divergent region is the adjoint of the contributing lanes
+    const bool live = px.inside && idx < px.last;
+    npairs += live ? 1u : 0u;
     const float4 q0 = rec[0], q1 = rec[1], q2 = rec[2], q3 = rec[3];
     const float dx = (px.xf - q2.x) - q2.z, dy = (px.yf - q2.y) - q2.w;
     const float zz = fmaf(q1.x, dx, fmaf(q1.y, dy, q1.z));
-    if (zz == 0.0f) return false;
     const float rz = fast_rcp(zz);
     const float u = fmaf(q0.x, dx, q0.y * dy) * rz;
     const float v = fmaf(q0.z, dx, q0.w * dy) * rz;
@@ -153,7 +154,7 @@ __device__ __forceinline__ bool pair_adjoint(Pix &px, uint32_t idx, const float4
     const float ar = q3.x * G;
     const bool clamped = ar > kAlphaMax;
     const float alpha = clamped ? kAlphaMax : ar;
-    if (!(alpha >= kAlphaMin)) return false;
+    if (!(live && zz != 0.0f && alpha >= kAlphaMin)) return false;
     ++ncontrib;
     const float iom = fast_rcp(1.0f - alpha);
     const float Ti = px.T * iom;
@@ -544,6 +545,16 @@ cudaError_t launch_n(const Frame &f, const RenderBwdBufs &b, int N, int batch, T
     }
 }
 
+template <int TS, int P>
+cudaError_t launch_d(const Frame &f, const RenderBwdBufs &b, int g, int N, int batch, TileSched ts, bool persistent,
+                     cudaStream_t s) {
+    switch (f.group_dtype[g]) {
+        case GB_F16: return launch_n<TS, __half, P>(f, b, N, batch, ts, persistent, s);
+        case GB_BF16: return launch_n<TS, __nv_bfloat16, P>(f, b, N, batch, ts, persistent, s);
+        default: return launch_n<TS, float, P>(f, b, N, batch, ts, persistent, s);
+    }
+}
+
 }  // namespace bwd
 
 // Launches the backward render of every render group with P pixels per thread.
@@ -559,20 +570,11 @@ cudaError_t launch_render_bwd_p(const Frame &f, const RenderBwdBufs &b, int batc
         ts.work = work ? work + g : nullptr;
         const int N = f.group_N[g];
         cudaError_t e;
-        if (f.tile == 8) {
-            switch (f.group_dtype[g]) {
-                case GB_F16: e = bwd::launch_n<8, __half, P>(f, b, N, batch, ts, persistent, s); break;
-                case GB_BF16: e = bwd::launch_n<8, __nv_bfloat16, P>(f, b, N, batch, ts, persistent, s); break;
-                default: e = bwd::launch_n<8, float, P>(f, b, N, batch, ts, persistent, s); break;
-            }
-        } else if (f.tile == 16) {
-            switch (f.group_dtype[g]) {
-                case GB_F16: e = bwd::launch_n<16, __half, P>(f, b, N, batch, ts, persistent, s); break;
-                case GB_BF16: e = bwd::launch_n<16, __nv_bfloat16, P>(f, b, N, batch, ts, persistent, s); break;
-                default: e = bwd::launch_n<16, float, P>(f, b, N, batch, ts, persistent, s); break;
-            }
-        } else {
-            return cudaErrorInvalidValue;
+        switch (f.tile) {
+            case 8: e = bwd::launch_d<8, P>(f, b, g, N, batch, ts, persistent, s); break;
+            case 16: e = bwd::launch_d<16, P>(f, b, g, N, batch, ts, persistent, s); break;
+            case 32: e = bwd::launch_d<32, P>(f, b, g, N, batch, ts, persistent, s); break;
+            default: return cudaErrorInvalidValue;
         }
         if (e != cudaSuccess) return e;
     }

@@ -134,7 +134,8 @@ __device__ __forceinline__ void stage_batch(const RenderBufs &b, const CamDev &c
             hit = block_hits<BH>(s_rec[4 * s + 2], s_box[s], s_fp + 3 * s, tx0 + (w % (TS / 8)) * 8,
                                  ty0 + (w / (TS / 8)) * BH);
         const unsigned bal = __ballot_sync(0xffffffffu, hit);
-        if (e < nb * NB && w == 0) s_mask[s] = (bal >> ((t & 31) & ~(NB - 1))) & ((1u << NB) - 1u);
+        constexpr uint32_t kAll = NB == 32 ? 0xffffffffu : (1u << (NB & 31)) - 1u;
+        if (e < nb * NB && w == 0) s_mask[s] = (bal >> ((t & 31) & ~(NB - 1))) & kAll;
     }
     const TexT *tex = static_cast<const TexT *>(sc.tex);
     for (int e = t; e < nb * NN; e += NT) {

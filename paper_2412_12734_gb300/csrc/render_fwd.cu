@@ -55,30 +55,30 @@ __device__ __forceinline__ void fwd_tile(const Frame &f, const RenderBufs &b, in
         stage_batch<N, NT, TexT, TS, 4>(b, cam, sc, range.x + bs, nb, tx * TS, ty * TS, s_rec, s_tex, s_k, s_j,
                                         s_box, s_mask, s_fp);
         __syncthreads();
-        if (!done) {
-            for (int i = 0; i < nb; ++i) {
-                if (__all_sync(__activemask(), done)) break;
-                if (done || !(s_mask[i] & wbit)) continue;
-                ++npairs;
-                const float4 q0 = s_rec[4 * i + 0], q1 = s_rec[4 * i + 1], q2 = s_rec[4 * i + 2];
-                const float dx = (xf - q2.x) - q2.z, dy = (yf - q2.y) - q2.w;
-                const float zz = fmaf(q1.x, dx, fmaf(q1.y, dy, q1.z));
-                if (zz == 0.0f) continue;
-                const float rz = fast_rcp(zz);
-                const float u = fmaf(q0.x, dx, q0.y * dy) * rz;
-                const float v = fmaf(q0.z, dx, q0.w * dy) * rz;
-                const float ruv = fmaf(u, u, v * v);
-                const float rlp = kLowPass * fmaf(dx, dx, dy * dy);
-                const bool uvb = ruv <= rlp;
-                const float rho = uvb ? ruv : rlp;
-                const float4 q3 = s_rec[4 * i + 3];
-                const float alpha = fminf(kAlphaMax, q3.x * gauss(rho));
-                if (alpha < kAlphaMin) continue;
-                const float tT = T * (1.0f - alpha);
-                if (tT < kTMin) {
-                    done = true;
-                    continue;
-                }
+        // The warp's mask bit is uniform: a splat that misses the warp's block
+        // costs one branch.  Otherwise every lane evaluates it (finished lanes
+        // included, their result is dropped) so that the only divergent region
+        // is the blend of the lanes the splat actually covers.
+        for (int i = 0; i < nb; ++i) {
+            if ((i & 15) == 0 && __all_sync(0xffffffffu, done)) break;
+            if (!(s_mask[i] & wbit)) continue;
+            npairs += done ? 0u : 1u;
+            const float4 q0 = s_rec[4 * i + 0], q1 = s_rec[4 * i + 1], q2 = s_rec[4 * i + 2],
+                         q3 = s_rec[4 * i + 3];
+            const float dx = (xf - q2.x) - q2.z, dy = (yf - q2.y) - q2.w;
+            const float zz = fmaf(q1.x, dx, fmaf(q1.y, dy, q1.z));
+            const float rz = fast_rcp(zz);
+            const float u = fmaf(q0.x, dx, q0.y * dy) * rz;
+            const float v = fmaf(q0.z, dx, q0.w * dy) * rz;
+            const float ruv = fmaf(u, u, v * v);
+            const float rlp = kLowPass * fmaf(dx, dx, dy * dy);
+            const bool uvb = ruv <= rlp;
+            const float rho = uvb ? ruv : rlp;
+            const float alpha = fminf(kAlphaMax, q3.x * gauss(rho));
+            const float tT = T * (1.0f - alpha);
+            const bool hit = !done && zz != 0.0f && alpha >= kAlphaMin;
+            done = done || (hit && tT < kTMin);
+            if (hit && !(tT < kTMin)) {
                 const Cell<N> cell = grid_cell<N>(u, v, sigma, kN);
                 float col[3];
                 grid_colour<N>(grid_quad<N>(s_tex + i * NN, cell), cell, col);
@@ -179,6 +179,16 @@ cudaError_t launch_n(const Frame &f, const RenderBufs &b, int N, int batch, Tile
     }
 }
 
+template <int TS>
+cudaError_t launch_d(const Frame &f, const RenderBufs &b, int g, int N, int batch, TileSched ts, bool persistent,
+                     cudaStream_t s) {
+    switch (f.group_dtype[g]) {
+        case GB_F16: return launch_n<TS, __half>(f, b, N, batch, ts, persistent, s);
+        case GB_BF16: return launch_n<TS, __nv_bfloat16>(f, b, N, batch, ts, persistent, s);
+        default: return launch_n<TS, float>(f, b, N, batch, ts, persistent, s);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_render_fwd(const Frame &f, const RenderBufs &b, int batch, const uint32_t *tile_list,
@@ -192,20 +202,11 @@ cudaError_t launch_render_fwd(const Frame &f, const RenderBufs &b, int batch, co
         ts.work = work ? work + g : nullptr;
         const int N = f.group_N[g];
         cudaError_t e;
-        if (f.tile == 8) {
-            switch (f.group_dtype[g]) {
-                case GB_F16: e = launch_n<8, __half>(f, b, N, batch, ts, persistent, s); break;
-                case GB_BF16: e = launch_n<8, __nv_bfloat16>(f, b, N, batch, ts, persistent, s); break;
-                default: e = launch_n<8, float>(f, b, N, batch, ts, persistent, s); break;
-            }
-        } else if (f.tile == 16) {
-            switch (f.group_dtype[g]) {
-                case GB_F16: e = launch_n<16, __half>(f, b, N, batch, ts, persistent, s); break;
-                case GB_BF16: e = launch_n<16, __nv_bfloat16>(f, b, N, batch, ts, persistent, s); break;
-                default: e = launch_n<16, float>(f, b, N, batch, ts, persistent, s); break;
-            }
-        } else {
-            return cudaErrorInvalidValue;
+        switch (f.tile) {
+            case 8: e = launch_d<8>(f, b, g, N, batch, ts, persistent, s); break;
+            case 16: e = launch_d<16>(f, b, g, N, batch, ts, persistent, s); break;
+            case 32: e = launch_d<32>(f, b, g, N, batch, ts, persistent, s); break;
+            default: return cudaErrorInvalidValue;
         }
         if (e != cudaSuccess) return e;
     }

@@ -121,15 +121,17 @@ def test_gradient_parity_two_pixels_per_thread(case, tile):
     assert all(v <= 1.0 for v in errs.values()), errs
 
 
-@pytest.mark.parametrize("case", ["plain_1k", "tiny_n4_d3", "tiny_bf16", "dense_many_tiles"])
-def test_tile8_keys_image_gradients(case):
-    """8 x 8 tiles: same keys formula with tile = 8, same image and gradients."""
+@pytest.mark.parametrize("case", ["plain_1k", "tiny_n4_d3", "tiny_bf16", "dense_many_tiles", "tiny_n16_d1"])
+@pytest.mark.parametrize("tile", [8, 32])
+def test_tile8_tile32_keys_image_gradients(case, tile):
+    """8 x 8 and 32 x 32 tiles: the same keys formula with that tile edge, the
+    same image and gradients."""
     sc, cams = CASES[case]()
     rng = np.random.default_rng(17)
     ref = oracle_run(sc[0], cams[0])
     d_rgb = masked_upstream(ref, rng)
-    gpu = gpu_run(sc, cams, d_rgb=[d_rgb], keys=True, tile=8)
-    _check_keys(sc, cams, [0], gpu, tile=8)
+    gpu = gpu_run(sc, cams, d_rgb=[d_rgb], keys=True, tile=tile)
+    _check_keys(sc, cams, [0], gpu, tile=tile)
     e, _ = compare_images(gpu["rgb"][0], ref, "rgb")
     assert e <= IMG_TOL, e
     errs = grad_errors(gpu["grads"][0], oracle.backward(sc[0], cams[0], d_rgb))
@@ -142,7 +144,7 @@ def test_autotune_picks_a_valid_candidate(tmp_path):
     rast = R.Rasterizer(0)
     dev = [R.scene_to_device(s) for s in sc]
     res = rast.autotune(dev, cams, reps=2, cache=str(tmp_path / "tune.json"))
-    assert res["tile"] in (8, 16) and res["batch"] in (32, 64, 128, 256)
+    assert res["tile"] in (8, 16, 32) and res["batch"] in (16, 32, 64, 128, 256)
     assert len(res["candidates"]) >= 4
     best = min(res["candidates"], key=lambda c: c["ms"])
     assert (best["tile"], best["batch"]) == (res["tile"], res["batch"])
