@@ -367,12 +367,17 @@ __global__ void __launch_bounds__(256) preprocess_kernel(Frame f, uint32_t *dept
             float dx = p[0] - cam.campos[0], dy = p[1] - cam.campos[1], dz = p[2] - cam.campos[2];
             const float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
             dx *= dn; dy *= dn; dz *= dn;
+            // all 16 basis values (registers); coefficients beyond the scene's
+            // degree are skipped by a uniform predicate
             float Y[16];
-            sh_basis(sc.D, dx, dy, dz, Y);
+            sh_basis(3, dx, dy, dz, Y);
             const int M = (sc.D + 1) * (sc.D + 1);
             float rgb[3] = {0.0f, 0.0f, 0.0f};
-            for (int m = 0; m < M; ++m)
-                for (int ch = 0; ch < 3; ++ch) rgb[ch] += Y[m] * load_sh(sc, (k * M + m) * 3 + ch);
+#pragma unroll
+            for (int m = 0; m < 16; ++m)
+                if (m < M)
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) rgb[ch] += Y[m] * load_sh(sc, (k * M + m) * 3 + ch);
             Record R;
             R.q0 = make_float4(t11, -t01, -t10, t00);
             R.q1 = make_float4(m20, m21, m22, z);
@@ -387,9 +392,13 @@ __global__ void __launch_bounds__(256) preprocess_kernel(Frame f, uint32_t *dept
 }
 
 // -------------------------------------------------------- backward kernel --
-__global__ void __launch_bounds__(128) preprocess_bwd_kernel(Frame f, const float *rec_grad,
+// One thread per splat of scene `si`, summing its cameras.  The SH degree D
+// is a template parameter so that the per-coefficient accumulators and the
+// basis stay in registers.
+template <int D>
+__global__ void __launch_bounds__(128) preprocess_bwd_kernel(Frame f, int si, const float *rec_grad,
                                                              const int32_t *inv_perm) {
-    const SceneDev &sc = f.scenes[blockIdx.y];
+    const SceneDev &sc = f.scenes[si];
     const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (k >= sc.K) return;
     float p[3], q[4];
@@ -397,14 +406,15 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(Frame f, const floa
     for (int i = 0; i < 4; ++i) q[i] = sc.quats[4 * k + i];
     const float su = sc.scales[2 * k], sv = sc.scales[2 * k + 1];
     const Frame3 fr = tangent_frame(q);
-    const int M = (sc.D + 1) * (sc.D + 1);
+    constexpr int M = (D + 1) * (D + 1);
     float g_p[3] = {0, 0, 0}, g_tu[3] = {0, 0, 0}, g_tv[3] = {0, 0, 0};
     float g_su = 0.0f, g_sv = 0.0f, g_o = 0.0f;
-    float g_sh[16][3];
-    for (int m = 0; m < 16; ++m) g_sh[m][0] = g_sh[m][1] = g_sh[m][2] = 0.0f;
+    float g_sh[M][3];
+#pragma unroll
+    for (int m = 0; m < M; ++m) g_sh[m][0] = g_sh[m][1] = g_sh[m][2] = 0.0f;
     for (int ci = 0; ci < f.n_cams; ++ci) {
         const CamDev &cam = f.cams[ci];
-        if (cam.scene != int(blockIdx.y)) continue;
+        if (cam.scene != si) continue;
         const int32_t j = inv_perm[cam.rec_off + k];
         if (j < 0) continue;
         const float4 *gp = reinterpret_cast<const float4 *>(rec_grad + int64_t(j) * kRecGrad);
@@ -466,10 +476,12 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(Frame f, const floa
         const float dist = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         for (int i = 0; i < 3; ++i) d[i] /= dist;
         float Y[16], G[16][3];
-        sh_basis(sc.D, d[0], d[1], d[2], Y);
-        sh_basis_grad(sc.D, d[0], d[1], d[2], G);
+        sh_basis(D, d[0], d[1], d[2], Y);
+        sh_basis_grad(D, d[0], d[1], d[2], G);
         float gd[3] = {0, 0, 0};
+#pragma unroll
         for (int m = 0; m < M; ++m)
+#pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
                 g_sh[m][ch] += Y[m] * grgb[ch];
                 const float kc = load_sh(sc, (k * M + m) * 3 + ch) * grgb[ch];
@@ -495,7 +507,9 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(Frame f, const floa
     if (sc.g_scales) { sc.g_scales[2 * k] = g_su; sc.g_scales[2 * k + 1] = g_sv; }
     if (sc.g_opac) sc.g_opac[k] = g_o;
     if (sc.g_sh)
+#pragma unroll
         for (int m = 0; m < M; ++m)
+#pragma unroll
             for (int ch = 0; ch < 3; ++ch) sc.g_sh[(k * M + m) * 3 + ch] = g_sh[m][ch];
 }
 
@@ -513,10 +527,21 @@ cudaError_t launch_preprocess(const Frame &f, int64_t max_k, uint32_t *depth_key
 cudaError_t launch_preprocess_bwd(const Frame &f, int64_t max_k, const float *rec_grad,
                                   const int32_t *inv_perm, cudaStream_t s) {
     if (max_k <= 0) return cudaSuccess;
-    dim3 grid(unsigned(ceil_div(max_k, 128)), unsigned(f.n_scenes));
-    preprocess_bwd_kernel<<<grid, 128, 0, s>>>(f, rec_grad, inv_perm);
-    count_launches(1);
-    return cudaGetLastError();
+    for (int si = 0; si < f.n_scenes; ++si) {
+        const int64_t K = f.scenes[si].K;
+        if (K <= 0) continue;
+        const unsigned grid = unsigned(ceil_div(K, 128));
+        switch (f.scenes[si].D) {
+            case 0: preprocess_bwd_kernel<0><<<grid, 128, 0, s>>>(f, si, rec_grad, inv_perm); break;
+            case 1: preprocess_bwd_kernel<1><<<grid, 128, 0, s>>>(f, si, rec_grad, inv_perm); break;
+            case 2: preprocess_bwd_kernel<2><<<grid, 128, 0, s>>>(f, si, rec_grad, inv_perm); break;
+            default: preprocess_bwd_kernel<3><<<grid, 128, 0, s>>>(f, si, rec_grad, inv_perm); break;
+        }
+        count_launches(1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace gbill
