@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define GBILL_ABI_VERSION 2
+#define GBILL_ABI_VERSION 3
 #define GBILL_MAX_CAMERAS 64
 #define GBILL_MAX_SCENES 16
 
@@ -98,7 +98,8 @@ typedef struct {
     const float *scales;      /* [K,2]                                           */
     const float *opacities;   /* [K]                                             */
     const void *sh;           /* [K,(D+1)^2,3] of sh_dtype                       */
-    const void *textures;     /* [K,N,N,3] of tex_dtype                          */
+    const void *textures;     /* [K,N,N,3] of tex_dtype, or with tex_sh_degree   */
+                              /* Dt >= 1 [K,N,N,(Dt+1)^2,3]: per-texel SH        */
     int32_t sh_degree;        /* D in 0..3                                       */
     int32_t sh_dtype;         /* gb_dtype                                        */
     int32_t tex_n;            /* N in {1,2,4,8,16}                               */
@@ -113,6 +114,16 @@ typedef struct {
                               /* saved state, sized by a synchronizing forward;  */
                               /* a no-sync forward that needs more fails with    */
                               /* GB_ERR_CAPACITY.                                 */
+    int32_t tex_sh_degree;    /* 0: RGB texels.  Dt in 1..3: every texel holds   */
+                              /* (Dt+1)^2 SH coefficient triples and shows       */
+                              /* sum_lm k_lm Y_lm(d), d the splat's view         */
+                              /* direction (Sec. 4.2).  The grids of every       */
+                              /* (splat, camera) record are evaluated into FP32  */
+                              /* scratch of the saved state (records x N^2 x 3,  */
+                              /* sized by a synchronizing forward); gradients    */
+                              /* reach the coefficients and, through d, the      */
+                              /* means.  Not combined with mip_level.            */
+    int32_t reserved;         /* must be 0                                       */
 } gb_scene;
 
 /* Gradient outputs of one scene, FP32 device arrays shaped like the inputs.
@@ -324,8 +335,8 @@ gb_status gb_adam_step(gb_context *ctx, const gb_adam_tensor *tensors, int32_t n
  * Limits per call: 131,072 records (splats x cameras), 524,288 (tile, splat)
  * instances, 1,048,576 pixels, 8,192 tiles; beyond them the call returns
  * GB_ERR_CAPACITY with a message and renders nothing.  GB_FLAG_TIMING and
- * GB_FLAG_PERSISTENT, and scenes with a mip_level, are rejected
- * (GB_ERR_UNSUPPORTED).
+ * GB_FLAG_PERSISTENT, and scenes with a mip_level or per-texel SH, are
+ * rejected (GB_ERR_UNSUPPORTED).
  * It calls no cudaMalloc, cudaFree or other allocating routine.  The first
  * call on a device looks up the array's device address (cudaGetSymbolAddress,
  * with that device current); make that first call before any stream capture.

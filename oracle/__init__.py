@@ -167,6 +167,43 @@ def num_threads() -> int:
     return int(lib().orc_num_threads())
 
 
+def _campos(cam: dict) -> np.ndarray:
+    R = np.asarray(cam["R"], dtype=np.float32).astype(np.float64)
+    t = np.asarray(cam["t"], dtype=np.float32).astype(np.float64)
+    return -R.T @ t
+
+
+def tex_sh_grids(scene: dict, cam: dict):
+    """Per-texel spherical harmonics (Sec. 4.2: M coefficient triples per texel
+    instead of one RGB colour): the colour grid each splat shows to ``cam``,
+    texel colour = sum_lm k_texel,lm Y_lm(d) with d = (p - camera centre) /
+    |p - camera centre|, the splat's view direction.  ``scene["textures"]`` is
+    [K, N, N, (Dt+1)^2, 3] with Dt = scene["tex_sh_degree"] >= 1.
+
+    Returns (grids [K,N,N,3], Y [K,M], dY/dd [K,M,3], d [K,3], |p - c| [K],
+    coefficients [K,N,N,M,3])."""
+    Dt = int(scene["tex_sh_degree"])
+    M = (Dt + 1) ** 2
+    K, N = int(np.shape(scene["means"])[0]), int(scene["tex_n"])
+    p = _f64(scene["means"])
+    v = p - _campos(cam)[None, :]
+    dist = np.sqrt(np.sum(v * v, axis=1))
+    d = v / dist[:, None]
+    Y, dY = sh_basis(Dt, d)
+    k = _f64(scene["textures"]).reshape(K, N, N, M, 3)
+    return np.einsum("km,kijmc->kijc", Y, k), Y, dY, d, dist, k
+
+
+def _view_scene(scene: dict, cam: dict):
+    """The scene with plain RGB grids that ``cam`` sees (per-texel SH evaluated)."""
+    if int(scene.get("tex_sh_degree", 0)) <= 0:
+        return scene, None
+    if int(scene.get("mip_level", 0)):
+        raise ValueError("per-texel SH takes no mip level")
+    ev = tex_sh_grids(scene, cam)
+    return dict(scene, textures=ev[0], tex_sh_degree=0), ev
+
+
 def render(scene: dict, cam: dict, window=None, bg=None, prefilter: bool = False) -> dict:
     """Brute-force FP64 forward of one view (Alg. 1 fwd, Eq. 2, Eq. 5).
 
@@ -178,6 +215,7 @@ def render(scene: dict, cam: dict, window=None, bg=None, prefilter: bool = False
     over 1 + |u| + |v| (1 on the low-pass branch): the factor by which
     rounding of the homography entries and pixel offsets reaches u and v.
     """
+    scene, _ = _view_scene(scene, cam)
     S = _SceneRef(scene)
     cm = _camera(cam)
     win = _window(cam, window)
@@ -205,6 +243,8 @@ def backward(scene: dict, cam: dict, dL_drgb, dL_ddepth=None, dL_dalpha=None, wi
 
     Gradients are ACCUMULATED into ``grads`` when given (sum over views).
     """
+    if int(scene.get("tex_sh_degree", 0)) > 0:
+        return _backward_tex_sh(scene, cam, dL_drgb, dL_ddepth, dL_dalpha, window, bg, prefilter, grads)
     S = _SceneRef(scene)
     cm = _camera(cam)
     win = _window(cam, window)
@@ -235,6 +275,31 @@ def backward(scene: dict, cam: dict, dL_drgb, dL_ddepth=None, dL_dalpha=None, wi
     assert rc == 0
     if d_coarse is not None:
         grads["textures"] += mip_grid_adjoint(d_coarse, S.mip)
+    return grads
+
+
+def _backward_tex_sh(scene, cam, dL_drgb, dL_ddepth, dL_dalpha, window, bg, prefilter, grads):
+    """Backward with per-texel SH: the view's grid gradient C^ gives the
+    coefficient gradients Y_lm(d) C^ and, through d, a term of the centre
+    gradient: sum C^ . k dY/dd, projected by (I - d d^T) / |p - c|."""
+    view, (grid, Y, dY, d, dist, k) = _view_scene(scene, cam)
+    K, N = k.shape[0], k.shape[1]
+    M = Y.shape[1]
+    if grads is None:
+        D = int(scene["sh_degree"])
+        grads = {
+            "means": np.zeros((K, 3)), "quats": np.zeros((K, 4)), "scales": np.zeros((K, 2)),
+            "opacities": np.zeros(K), "sh": np.zeros((K, (D + 1) ** 2, 3)),
+            "textures": np.zeros((K, N, N, M, 3)),
+        }
+    g = backward(view, cam, dL_drgb, dL_ddepth, dL_dalpha, window=window, bg=bg, prefilter=prefilter)
+    for key in ("means", "quats", "scales", "opacities", "sh"):
+        grads[key] += g[key]
+    ch = g["textures"]  # [K, N, N, 3]
+    grads["textures"] += np.einsum("km,kijc->kijmc", Y, ch).reshape(grads["textures"].shape)
+    g_dir = np.einsum("kijc,kijmc,kmx->kx", ch, k, dY)
+    dd = np.sum(g_dir * d, axis=1)
+    grads["means"] += (g_dir - d * dd[:, None]) / dist[:, None]
     return grads
 
 

@@ -40,7 +40,8 @@ class gb_scene(C.Structure):
                 ("opacities", C.c_void_p), ("sh", C.c_void_p), ("textures", C.c_void_p),
                 ("sh_degree", C.c_int32), ("sh_dtype", C.c_int32),
                 ("tex_n", C.c_int32), ("tex_dtype", C.c_int32),
-                ("sigma", C.c_float), ("mip_level", C.c_int32)]
+                ("sigma", C.c_float), ("mip_level", C.c_int32), ("tex_sh_degree", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class gb_grads(C.Structure):

@@ -54,6 +54,13 @@ struct gb_saved {
     int64_t mip_cap;
     int64_t mip_off[kMaxScenes];
     int32_t mip_ns[kMaxScenes];
+    // per-texel SH: evaluated grids of every (splat, camera) record and their
+    // gradient, per scene at tsh_off[] (floats); the scenes' coefficients
+    float *tsh_tex, *tsh_grad;
+    int64_t tsh_cap;
+    int64_t tsh_off[kMaxScenes], tsh_rows[kMaxScenes];
+    const void *tsh_coef[kMaxScenes];
+    int32_t tsh_dtype[kMaxScenes];
     // last forward
     Frame frame;
     bool has_forward;
@@ -234,6 +241,11 @@ gb_status build_frame(gb_context *ctx, const gb_scene *scenes, int32_t n_scenes,
             return fail(ctx, GB_ERR_INVALID_ARG, "scene %d: bad storage dtype", s);
         if (!(g.sigma > 0.0f) || !isfinite(g.sigma))
             return fail(ctx, GB_ERR_INVALID_ARG, "scene %d: sigma must be positive", s);
+        if (g.tex_sh_degree < 0 || g.tex_sh_degree > 3)
+            return fail(ctx, GB_ERR_UNSUPPORTED, "scene %d: tex_sh_degree %d not in 0..3", s, g.tex_sh_degree);
+        if (g.tex_sh_degree && g.mip_level)
+            return fail(ctx, GB_ERR_UNSUPPORTED, "scene %d: per-texel SH takes no mip level", s);
+        if (g.reserved != 0) return fail(ctx, GB_ERR_INVALID_ARG, "scene %d: reserved field must be 0", s);
         if (g.mip_level < 0 || g.mip_level > 4 || (g.tex_n >> g.mip_level) < 1)
             return fail(ctx, GB_ERR_INVALID_ARG, "scene %d: mip_level %d not in 0..log2(%d)", s, g.mip_level,
                         g.tex_n);
@@ -252,6 +264,7 @@ gb_status build_frame(gb_context *ctx, const gb_scene *scenes, int32_t n_scenes,
         d.tex_dtype = g.tex_dtype;
         d.sigma = g.sigma;
         d.mip = g.mip_level;
+        d.tex_sh = g.tex_sh_degree;
         max_k = std::max(max_k, g.num_splats);
     }
     // render groups: one per distinct (rendered grid size, tex_dtype) among the scenes
@@ -259,7 +272,7 @@ gb_status build_frame(gb_context *ctx, const gb_scene *scenes, int32_t n_scenes,
     for (int sidx = 0; sidx < n_scenes; ++sidx) {
         // a scene at a mip level is rendered from its FP32 filtered grid
         const int n_eff = scenes[sidx].tex_n >> scenes[sidx].mip_level;
-        const int dt = scenes[sidx].mip_level ? int(GB_F32) : scenes[sidx].tex_dtype;
+        const int dt = (scenes[sidx].mip_level || scenes[sidx].tex_sh_degree) ? int(GB_F32) : scenes[sidx].tex_dtype;
         int g = -1;
         for (int k = 0; k < f.n_groups; ++k)
             if (f.group_N[k] == n_eff && f.group_dtype[k] == dt) g = k;
@@ -394,7 +407,7 @@ gb_status gb_saved_destroy(gb_saved *s) {
                     s->offsets, s->rect, s->pbox, s->inv, s->rec_grad, s->inst_tile, s->inst_val, s->inst_tile_tmp,
                     s->inst_val_tmp, s->tiles_sorted, s->vals_sorted, s->ranges, s->tl_keys, s->tl_vals,
                     s->tl_keys_tmp, s->tl_vals_tmp, s->tl_keys_out, s->tile_list, s->work, s->t_final, s->last,
-                    s->cnt, s->scratch, s->mip_tex, s->mip_grad};
+                    s->cnt, s->scratch, s->mip_tex, s->mip_grad, s->tsh_tex, s->tsh_grad};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (s->cnt_host) cudaFreeHost(s->cnt_host);
@@ -577,6 +590,41 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
         d.tex_dtype = GB_F32;
         d.N >>= d.mip;
     }
+    // per-texel SH scenes: one evaluated RGB grid per (splat, camera) record,
+    // camera blocks of K rows (CamDev::tex_row)
+    int64_t tsh_need = 0;
+    for (int i = 0; i < f.n_scenes; ++i) {
+        s->tsh_off[i] = tsh_need;
+        s->tsh_rows[i] = 0;
+        if (!f.scenes[i].tex_sh) continue;
+        for (int c = 0; c < f.n_cams; ++c)
+            if (f.cams[c].scene == i) {
+                f.cams[c].tex_row = s->tsh_rows[i];
+                s->tsh_rows[i] += f.scenes[i].K;
+            }
+        if (s->tsh_rows[i] >= (int64_t(1) << 31))
+            return fail(ctx, GB_ERR_INVALID_ARG, "scene %d: per-texel SH over %lld records exceeds 2^31", i,
+                        (long long)s->tsh_rows[i]);
+        tsh_need += s->tsh_rows[i] * f.scenes[i].N * f.scenes[i].N * 3;
+    }
+    if (tsh_need > s->tsh_cap) {
+        if (nosync)
+            return fail(ctx, GB_ERR_CAPACITY,
+                        "per-texel SH grids need %lld floats of scratch: run a synchronizing forward first",
+                        (long long)tsh_need);
+        GB_CUDA(ctx, alloc_t(&s->tsh_tex, tsh_need));
+        GB_CUDA(ctx, alloc_t(&s->tsh_grad, tsh_need));
+        s->tsh_cap = tsh_need;
+    }
+    for (int i = 0; i < f.n_scenes; ++i) {
+        SceneDev &d = f.scenes[i];
+        if (!d.tex_sh) continue;
+        s->tsh_coef[i] = d.tex;
+        s->tsh_dtype[i] = d.tex_dtype;
+        GB_CUDA(ctx, launch_texsh_eval(f, i, d.tex_sh, d.tex, d.tex_dtype, s->tsh_tex + s->tsh_off[i], st));
+        d.tex = s->tsh_tex + s->tsh_off[i];
+        d.tex_dtype = GB_F32;
+    }
     const int64_t R = f.n_records;
     int tile_bits = 1;
     while ((int64_t(1) << tile_bits) < int64_t(f.n_tiles)) ++tile_bits;
@@ -681,8 +729,11 @@ gb_status gb_render_backward(gb_context *ctx, gb_saved *s, const float *d_rgb, c
         d.g_sh = grads[i].d_sh;
         d.g_tex = grads[i].d_textures;
         if (d.g_tex && d.mip) d.g_tex = s->mip_grad + s->mip_off[i];  // gradient of the filtered grid
-        if (d.g_tex && d.K > 0)
-            GB_CUDA(ctx, cudaMemsetAsync(d.g_tex, 0, size_t(d.K) * d.N * d.N * 3 * sizeof(float), st));
+        // per-texel SH: gradient of every record's evaluated grid (post-pass below)
+        if (d.tex_sh) d.g_tex = s->tsh_grad + s->tsh_off[i];
+        const int64_t rows = d.tex_sh ? s->tsh_rows[i] : d.K;
+        if (d.g_tex && rows > 0)
+            GB_CUDA(ctx, cudaMemsetAsync(d.g_tex, 0, size_t(rows) * d.N * d.N * 3 * sizeof(float), st));
     }
     const int64_t R = s->n_records;
     zero_rec_grad<<<unsigned(std::min<int64_t>(ceil_div(std::max<int64_t>(R, 1) * 4, 256), 65535)), 256, 0, st>>>(
@@ -718,6 +769,13 @@ gb_status gb_render_backward(gb_context *ctx, gb_saved *s, const float *d_rgb, c
                                          grads[i].d_textures, st));
     if (timing) GB_CUDA(ctx, cudaEventRecord(s->ev[10], st));
     GB_CUDA(ctx, launch_preprocess_bwd(f, s->max_k, s->rec_grad, s->inv, st));
+    // per-texel SH: coefficient gradients and the centre gradient through the
+    // view direction (added to the means gradient written just above)
+    for (int i = 0; i < n_scenes; ++i)
+        if (f.scenes[i].tex_sh)
+            GB_CUDA(ctx, launch_texsh_grad(f, i, f.scenes[i].tex_sh, s->tsh_coef[i], s->tsh_dtype[i],
+                                           s->tsh_grad + s->tsh_off[i], grads[i].d_textures, grads[i].d_means,
+                                           st));
     if (timing) GB_CUDA(ctx, cudaEventRecord(s->ev[11], st));
     s->timed_bwd = timing;
     return GB_OK;
@@ -788,8 +846,9 @@ gb_status gb_render_forward_noalloc(gb_context *ctx, const gb_scene *scenes, int
     gb_status r = build_frame(ctx, scenes, n_scenes, cams, n_cams, tile, o.background, f, max_k);
     if (r != GB_OK) return r;
     for (int i = 0; i < f.n_scenes; ++i)
-        if (f.scenes[i].mip)
-            return fail(ctx, GB_ERR_UNSUPPORTED, "the no-allocation forward renders no mip-level scene");
+        if (f.scenes[i].mip || f.scenes[i].tex_sh)
+            return fail(ctx, GB_ERR_UNSUPPORTED,
+                        "the no-allocation forward renders no mip-level or per-texel SH scene");
     if (f.n_records > kNaMaxRecords || f.n_pixels > kNaMaxPixels || int64_t(f.n_tiles) > kNaMaxTiles)
         return fail(ctx, GB_ERR_CAPACITY,
                     "no-allocation forward limits: %lld records (max %lld), %lld pixels (max %lld), %u tiles (max %lld)",

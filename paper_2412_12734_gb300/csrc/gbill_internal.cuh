@@ -39,6 +39,8 @@ struct CamDev {
     uint32_t tile_off;  // first global tile id of this camera
     int64_t pix_off;    // first pixel of this camera in the packed outputs
     int64_t rec_off;    // first record (= tile_off-like offset over splats)
+    int64_t tex_row;    // grid row of splat k is tex_row + k: 0, or for per-texel SH
+                        // scenes the camera's block of evaluated grids
 };
 
 struct SceneDev {
@@ -49,6 +51,8 @@ struct SceneDev {
     int32_t D, sh_dtype, N, tex_dtype;  // N, tex: the grid the render reads
     float sigma;
     int32_t mip;                        // mip level (the render reads the filtered grid)
+    int32_t tex_sh;                     // per-texel SH degree (the render reads evaluated grids)
+    int32_t pad2;
     float *g_means, *g_quats, *g_scales, *g_opac, *g_sh, *g_tex;
 };
 
@@ -203,6 +207,12 @@ cudaError_t launch_fit_params_bwd(const float *theta, const float *log_s, const 
                                   const float *d_opac, float *d_theta, float *d_xy, float *d_log_s, float *d_logit,
                                   cudaStream_t s);
 cudaError_t launch_mse(const float *rgb, const float *target, int64_t n, float *d_rgb, double *loss, cudaStream_t s);
+
+// texsh.cu: per-texel SH grids per (splat, camera) and the backward post-pass
+cudaError_t launch_texsh_eval(const Frame &f, int si, int Dt, const void *coef, int dtype, float *out,
+                              cudaStream_t s);
+cudaError_t launch_texsh_grad(const Frame &f, int si, int Dt, const void *coef, int dtype, const float *grid_grad,
+                              float *g_coef, float *g_means, cudaStream_t s);
 
 // mip.cu: box filter of a scene's grids to N >> mip (FP32 out) and its adjoint
 cudaError_t launch_mip_filter(const void *src, int dtype, int64_t K, int ns, int mip, float *dst, cudaStream_t s);

@@ -118,7 +118,9 @@ __device__ __forceinline__ void stage_batch(const RenderBufs &b, const CamDev &c
         s_rec[4 * t + 1] = rp[1];
         s_rec[4 * t + 2] = rp[2];
         s_rec[4 * t + 3] = rp[3];
-        s_k[t] = int32_t(int64_t(r) - cam.rec_off);
+        // grid row of the splat: its index in the scene, offset by the
+        // camera's block for per-texel SH scenes (evaluated grid per record)
+        s_k[t] = int32_t(int64_t(r) - cam.rec_off + cam.tex_row);
         s_j[t] = j;
         float4 k[3];
         footprint_setup(rp[0], rp[1], rp[3].x, k);

@@ -47,6 +47,7 @@ def scene_to_device(scene: dict, device="cuda") -> dict:
     out["tex_n"] = int(scene["tex_n"])
     out["sigma"] = float(scene.get("sigma", 0.5))
     out["mip_level"] = int(scene.get("mip_level", 0))
+    out["tex_sh_degree"] = int(scene.get("tex_sh_degree", 0))
     return out
 
 
@@ -69,7 +70,8 @@ def scene_struct(sc: dict) -> L.gb_scene:
     _check_tensor(sc["scales"], "scales", (2,))
     _check_tensor(sc["opacities"], "opacities", ())
     _check_tensor(sc["sh"], "sh", ((D + 1) ** 2, 3), tuple(DTYPES))
-    _check_tensor(sc["textures"], "textures", (N, N, 3), tuple(DTYPES))
+    Dt = int(sc.get("tex_sh_degree", 0))
+    _check_tensor(sc["textures"], "textures", (N, N, 3) if Dt == 0 else (N, N, (Dt + 1) ** 2, 3), tuple(DTYPES))
     for k in PARAMS:
         if sc[k].shape[0] != K:
             raise ValueError(f"{k}: first dimension {sc[k].shape[0]} != {K}")
@@ -81,6 +83,8 @@ def scene_struct(sc: dict) -> L.gb_scene:
     s.tex_n, s.tex_dtype = N, DTYPES[sc["textures"].dtype]
     s.sigma = float(sc.get("sigma", 0.5))
     s.mip_level = int(sc.get("mip_level", 0))
+    s.tex_sh_degree = Dt
+    s.reserved = 0
     return s
 
 
@@ -196,7 +200,9 @@ class Rasterizer:
         if saved is None:
             saved = Saved(self)
         saved.n_scenes = n_s
-        saved.shapes = [(int(s["means"].shape[0]), int(s["sh_degree"]), int(s["tex_n"])) for s in scenes]
+        saved.shapes = [(int(s["means"].shape[0]), int(s["sh_degree"]), int(s["tex_n"]),
+                         (int(s.get("tex_sh_degree", 0)) + 1) ** 2 if int(s.get("tex_sh_degree", 0)) else 0)
+                        for s in scenes]
         s = stream if stream is not None else torch.cuda.current_stream(dev)
         st = lib.gb_render_forward(self.ctx, saved.handle, sarr, n_s, carr, n_c, C.byref(opt),
                                    rgb.data_ptr(), depth.data_ptr() if depth is not None else None,
@@ -211,12 +217,12 @@ class Rasterizer:
         dev = d_rgb.device
         if grads is None:
             grads = []
-            for K, D, N in saved.shapes:
+            for K, D, N, Mt in saved.shapes:
                 grads.append({
                     "means": torch.empty((K, 3), device=dev), "quats": torch.empty((K, 4), device=dev),
                     "scales": torch.empty((K, 2), device=dev), "opacities": torch.empty(K, device=dev),
                     "sh": torch.empty((K, (D + 1) ** 2, 3), device=dev),
-                    "textures": torch.empty((K, N, N, 3), device=dev),
+                    "textures": torch.empty((K, N, N, 3) if Mt == 0 else (K, N, N, Mt, 3), device=dev),
                 })
         garr = (L.gb_grads * len(grads))()
         for i, g in enumerate(grads):

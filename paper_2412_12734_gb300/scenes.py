@@ -395,3 +395,19 @@ def fit_init(K: int, width: int, height: int, seed: int = 0, tex_n: int = 4) -> 
         "textures": np.ascontiguousarray(np.broadcast_to(col, (K, tex_n, tex_n, 3)), np.float32),
         "tex_n": int(tex_n), "sigma": SIGMA_DEFAULT,
     }
+
+
+def with_texel_sh(scene: dict, degree: int, seed: int = 0, std: float = 0.1) -> dict:
+    """The scene with per-texel spherical harmonics of the given degree
+    (Sec. 4.2): textures [K, N, N, (degree+1)^2, 3] whose degree-0 term keeps
+    the texel's colour (k00 = colour 2 sqrt(pi)) and whose higher terms are
+    N(0, std), rounded to the scene's texture storage type."""
+    rng = np.random.default_rng(seed + 65537)
+    K, N = scene["textures"].shape[:2]
+    M = (degree + 1) ** 2
+    k = rng.normal(0.0, std, (K, N, N, M, 3))
+    k[:, :, :, 0, :] = scene["textures"].astype(np.float64) * (2.0 * math.sqrt(math.pi))
+    out = dict(scene)
+    out["textures"] = round_to(k, scene.get("tex_dtype", "f32"))
+    out["tex_sh_degree"] = int(degree)
+    return out
