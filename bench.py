@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--crop", type=int, default=0, help="oracle crop side in pixels (0 = all of camera 0)")
+    ap.add_argument("--mip", type=int, default=0, help="render the grids at this mip level (box filter)")
+    ap.add_argument("--tex-sh", type=int, default=0, help="per-texel SH degree of the grids (0 = RGB texels)")
     return ap.parse_args()
 
 
@@ -128,6 +130,10 @@ def allreduce_max(x: float, world: int) -> float:
 def make_workload(args):
     from paper_2412_12734_gb300 import scenes
     wl = scenes.workload(args.workload, seed=0, tex_n=args.tex_n)
+    if getattr(args, "mip", 0):
+        wl["scenes"] = [dict(sc, mip_level=args.mip) for sc in wl["scenes"]]
+    if getattr(args, "tex_sh", 0):
+        wl["scenes"] = [scenes.with_texel_sh(sc, args.tex_sh) for sc in wl["scenes"]]
     if args.views:
         for k in ("cams", "cam_scene", "d_rgb"):
             wl[k] = wl[k][:args.views]
@@ -184,7 +190,8 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "tex_n": args.tex_n, "crop": args.crop},
+        "config": {"workload": args.workload, "tex_n": args.tex_n, "crop": args.crop, "mip_level": args.mip,
+                   "tex_sh_degree": args.tex_sh},
         "cpu_baseline": {"value": value, "unit": "Mpixel/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -293,7 +300,8 @@ def run_ours(args, world, rank, local):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{args.workload}: 1,000,000 splats, {len(cams)} views 960x540/1280x720/1920x1080, "
                                f"{args.tex_n}x{args.tex_n} FP16 textures, SH3 FP16",
-                   "pixels_per_step": P, "tex_n": args.tex_n, "storage": "f16", "tile": args.tile,
+                   "pixels_per_step": P, "tex_n": args.tex_n, "mip_level": args.mip, "tex_sh_degree": args.tex_sh,
+                   "storage": "f16", "tile": args.tile,
                    "batch_depth": args.batch, "pixels_per_thread": args.ppt, "autotune": tune,
                    "graph": graph is not None, "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{world}"},
@@ -358,7 +366,7 @@ def measured_traffic(kernel, args):
                   "rb") as fh:
             h.update(fh.read())
     cfg = {"workload": args.workload, "tex_n": args.tex_n, "tile": args.tile, "batch": args.batch, "ppt": args.ppt}
-    if h.hexdigest()[:16] != t["sha256_16"] or cfg != t["config"] or args.views:
+    if h.hexdigest()[:16] != t["sha256_16"] or cfg != t["config"] or args.views or args.mip or args.tex_sh:
         return None
     return t["bytes"]
 

@@ -137,9 +137,8 @@ typedef struct {
 typedef struct {
     int32_t tile_size;   /* tile edge in pixels: 8, 16 or 32 (0 = 16)             */
     int32_t batch_depth; /* splats staged per shared-memory batch, 0 = automatic;
-                            otherwise a multiple of 16 up to the tile's pixels
-                            whose staging fits 200 KB of shared memory (N = 16:
-                            16 splats)                                            */
+                            otherwise a multiple of 8 up to the tile's pixels
+                            whose staging fits 200 KB of shared memory            */
     uint32_t flags;      /* GB_FLAG_*                                             */
     int32_t pixels_per_thread; /* backward: 1, or 2 (two pixels of a column per
                                   thread on the packed FP32x2 pipe); 0 = 1. With 2,
@@ -384,7 +383,7 @@ gb_status gb_mse_loss(gb_context *ctx, const float *rgb, const float *target, in
 /* ---------------------------------------------------------------- tuning -- */
 
 /* Autotuner: times forward + backward of this frame for every candidate
- * (tile_size 8, 16 and 32; batch_depth 16, 32, 64, 128, 256 where it fits the tile and
+ * (tile_size 8, 16 and 32; batch_depth 8, 16, 32, 64, 128, 256 where it fits the tile and
  * the shared-memory budget; pixels_per_thread 1 and 2) and writes the fastest
  * options to *best (flags and
  * background are copied from *base, which may be NULL).  Each candidate runs

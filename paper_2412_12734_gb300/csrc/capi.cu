@@ -187,14 +187,14 @@ size_t batch_smem(int N, int batch, bool bwd);
 // Batch depth giving ~42 KB of staged shared memory per block, so that four
 // or more blocks stay resident per SM (measured on the 1M-splat, 16-view
 // workload: 64 is best at N = 4 and 16 at N = 8, where 64 would stage 127 KB
-// in the backward and leave one block per SM); a multiple of 16, at least 16.
+// in the backward and leave one block per SM); a multiple of 8, at least 8.
 int default_batch(int N, bool bwd) {
     const int per = int(batch_smem(N, 1, true));
     (void)bwd;  // one depth for both passes: the backward's staging decides
     int b = (42 * 1024) / per;
     b = std::min(b, 256);
-    b &= ~15;
-    return std::max(b, 16);
+    b &= ~7;
+    return std::max(b, 8);
 }
 
 size_t batch_smem(int N, int batch, bool bwd) {
@@ -547,7 +547,7 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
     const int nt = tile * tile;
     int bf = o.batch_depth ? o.batch_depth : std::min(default_batch(N, false), nt);
     int bb = o.batch_depth ? o.batch_depth : std::min(default_batch(N, true), nt / ppt);
-    if (bf < 16 || bf > nt || (bf & 15)) return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d invalid", bf);
+    if (bf < 8 || bf > nt || (bf & 7)) return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d invalid", bf);
     if (bb > nt / ppt) return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d exceeds the backward's %d threads", bb, nt / ppt);
     if (batch_smem(N, bf, false) > 200 * 1024 || batch_smem(N, bb, true) > 200 * 1024)
         return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d needs too much shared memory", bf);
@@ -858,7 +858,7 @@ gb_status gb_render_forward_noalloc(gb_context *ctx, const gb_scene *scenes, int
     for (int k = 0; k < f.n_groups; ++k) N = std::max(N, f.group_N[k]);
     const int nt = tile * tile;
     const int bf = o.batch_depth ? o.batch_depth : std::min(default_batch(N, false), nt);
-    if (bf < 16 || bf > nt || (bf & 15) || batch_smem(N, bf, false) > 200 * 1024)
+    if (bf < 8 || bf > nt || (bf & 7) || batch_smem(N, bf, false) > 200 * 1024)
         return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d invalid", bf);
     int dev = 0;
     GB_CUDA(ctx, cudaGetDevice(&dev));
@@ -1016,9 +1016,15 @@ gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int3
     // scratch buffers owned by this call
     float *rgb = nullptr, *dep = nullptr, *alp = nullptr, *drgb = nullptr, *gbuf = nullptr;
     size_t gtot = 0;
+    // gradient outputs shaped like each scene's stored arrays: the stored grid
+    // (not the mip level rendered) and its per-texel SH coefficients
+    auto tex_floats = [](const gb_scene &sc) {
+        const int64_t Mt = sc.tex_sh_degree ? (sc.tex_sh_degree + 1) * (sc.tex_sh_degree + 1) : 1;
+        return int64_t(sc.tex_n) * sc.tex_n * 3 * Mt;
+    };
     for (int i = 0; i < n_scenes; ++i) {
         const int64_t K = scenes[i].num_splats, M = (scenes[i].sh_degree + 1) * (scenes[i].sh_degree + 1);
-        gtot += size_t(K) * (3 + 4 + 2 + 1 + 3 * M + 3 * N * N);
+        gtot += size_t(K) * (3 + 4 + 2 + 1 + 3 * M + tex_floats(scenes[i]));
     }
     cudaError_t e = cudaMalloc(&rgb, size_t(f.n_pixels) * 12 + 16);
     if (e == cudaSuccess) e = cudaMalloc(&dep, size_t(f.n_pixels) * 4 + 16);
@@ -1043,7 +1049,7 @@ gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int3
             g[i].d_scales = p; p += K * 2;
             g[i].d_opacities = p; p += K;
             g[i].d_sh = p; p += K * 3 * M;
-            g[i].d_textures = p; p += K * 3 * N * N;
+            g[i].d_textures = p; p += K * tex_floats(scenes[i]);
         }
         gb_options o{};
         if (base) o = *base;
@@ -1051,10 +1057,10 @@ gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int3
         float best_ms = INFINITY;
         int n = 0;
         const int tile_c[3] = {16, 8, 32};
-        const int batch_c[5] = {16, 32, 64, 128, 256};
+        const int batch_c[6] = {8, 16, 32, 64, 128, 256};
         for (int pi = 1; pi <= 2 && st == GB_OK; ++pi)
         for (int ti = 0; ti < 3 && st == GB_OK; ++ti)
-            for (int bi = 0; bi < 5 && st == GB_OK; ++bi) {
+            for (int bi = 0; bi < 6 && st == GB_OK; ++bi) {
                 const int T = tile_c[ti], B = batch_c[bi];
                 if (B > T * T / pi) continue;
                 if (batch_smem(N, B, false) > 160 * 1024 || batch_smem(N, B, true) > 160 * 1024) continue;

@@ -243,14 +243,17 @@ class Rasterizer:
 
     def autotune(self, scenes: list, cams: list, cam_scene=None, reps: int = 3, saved: Saved | None = None,
                  cache: str | None = None) -> dict:
-        """Picks (tile, batch_depth) with the library's autotuner; results are
-        cached in a JSON file keyed by texture size, storage types, SH degree,
-        splat count and pixel count (rounded to powers of two)."""
+        """Picks (tile, batch_depth, pixels per thread) with the library's
+        autotuner; results are cached in a JSON file keyed by every scene's
+        grid size, mip level, per-texel SH degree, storage types and SH
+        degree, the splat count and pixel count (rounded to powers of two)
+        and the number of cameras."""
         import json
         import os
         key = "|".join(str(x) for x in (
-            int(scenes[0]["tex_n"]), str(scenes[0]["textures"].dtype), str(scenes[0]["sh"].dtype),
-            int(scenes[0]["sh_degree"]), sum(int(s["means"].shape[0]) for s in scenes).bit_length(),
+            [(int(s["tex_n"]), int(s.get("mip_level", 0)), int(s.get("tex_sh_degree", 0)), str(s["textures"].dtype),
+              str(s["sh"].dtype), int(s["sh_degree"])) for s in scenes],
+            sum(int(s["means"].shape[0]) for s in scenes).bit_length(),
             self.pixel_count(cams).bit_length(), len(cams)))
         path = cache or os.path.join(os.path.expanduser("~"), ".cache", "gbill", "autotune.json")
         table = {}
@@ -267,14 +270,14 @@ class Rasterizer:
         sarr = (L.gb_scene * n_s)(*[scene_struct(s) for s in scenes])
         carr = (L.gb_camera * n_c)(*[camera_struct(c, cam_scene[i]) for i, c in enumerate(cams)])
         best = L.gb_options()
-        ms = (C.c_float * 32)()
-        tiles = (C.c_int32 * 32)()
-        batches = (C.c_int32 * 32)()
-        ppts = (C.c_int32 * 32)()
+        ms = (C.c_float * 48)()
+        tiles = (C.c_int32 * 48)()
+        batches = (C.c_int32 * 48)()
+        ppts = (C.c_int32 * 48)()
         n = C.c_int32()
         saved = saved or Saved(self)
         L.check(lib.gb_autotune(self.ctx, saved.handle, sarr, n_s, carr, n_c, None, reps, C.byref(best),
-                                C.addressof(ms), C.addressof(tiles), C.addressof(batches), C.addressof(ppts), 32,
+                                C.addressof(ms), C.addressof(tiles), C.addressof(batches), C.addressof(ppts), 48,
                                 C.byref(n)), self.ctx)
         res = {"tile": best.tile_size, "batch": best.batch_depth, "ppt": best.pixels_per_thread,
                "candidates": [{"tile": tiles[i], "batch": batches[i], "ppt": ppts[i], "ms": ms[i]}

@@ -61,3 +61,19 @@ def test_mip_level_out_of_range_is_rejected():
     with pytest.raises(L.GbillError) as ei:
         gpu_run([sc], [scenes.tiny_camera(16, 16)])
     assert ei.value.status == 1
+
+
+def test_autotune_on_mip_and_texel_sh_scenes(tmp_path):
+    """The autotuner allocates gradient outputs shaped like the stored grids
+    (N x N, and (Dt+1)^2 coefficient triples per texel) and returns a valid
+    candidate for frames that render filtered or evaluated grids."""
+    from paper_2412_12734_gb300 import render as R
+    rast = R.Rasterizer(0)
+    a = scenes.tiny_scene(61, K=12, tex_n=8, sh_degree=1)
+    a["mip_level"] = 1
+    b = scenes.with_texel_sh(scenes.tiny_scene(62, K=10, tex_n=4, sh_degree=1), 2)
+    cams = [scenes.tiny_camera(40, 32), scenes.tiny_camera(36, 36, eye=(0.3, 0.2, -4.0))]
+    res = rast.autotune([R.scene_to_device(a), R.scene_to_device(b)], cams, cam_scene=[0, 1], reps=1,
+                        cache=str(tmp_path / "tune.json"))
+    assert res["tile"] in (8, 16, 32) and res["batch"] in (8, 16, 32, 64, 128, 256)
+    assert len(res["candidates"]) > 0
