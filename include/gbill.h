@@ -38,6 +38,15 @@
  *   textures   [K,N,N,3] colour grid C_k[i_u][i_v][rgb] spanning
  *                     [-sigma, sigma]^2 of the uv plane, corner aligned, border
  *                     clamped                                        (Eq. 5, Alg. 2)
+ *                     or, with per-texel SH, [K,N,N,(Dt+1)^2,3] coefficients
+ *                     per texel (Sec. 4.2; gb_scene.tex_sh_degree); a scene
+ *                     may also be rendered at a mip level of its grid
+ *                     (Sec. 4.1, Fig. 4 f, g; gb_scene.mip_level)
+ *
+ * Beyond rendering: a fused multi-tensor Adam (gb_adam_step), the image-
+ * fitting parameter map, its adjoint and an MSE loss (Sec. 4.1;
+ * gb_fit_params, gb_fit_params_backward, gb_mse_loss), an autotuner, and a
+ * forward that allocates nothing (gb_render_forward_noalloc).
  */
 #ifndef GBILL_H
 #define GBILL_H

@@ -10,6 +10,10 @@ NeRF360 and face-capture scenes (Sec. 4), none of which ships with the paper:
 * ``planes``    - 80 % of the splats on 6 random planes with normal-aligned
                   frames, 20 % uniform clutter in a 10^3 box (100k / 1M / 3M
                   splat cases, the primitive budgets of Fig. 1, Fig. 6 and Sec. 4.2).
+* ``fit_*``     - the image-fitting setup of Sec. 4.1: seeded synthetic target
+                  images at the paper's three resolutions, a camera facing the
+                  image plane and raw splat parameters in that plane.
+* ``with_texel_sh`` - per-texel SH coefficients (Sec. 4.2) for a scene's grids.
 
 Parameters are returned activated (linear scales, opacity in (0, 1)); the
 log-scale / logit draws are turned into those values here.  Texture and SH
