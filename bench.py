@@ -118,13 +118,23 @@ def barrier(world):
 
 
 def allreduce_max(x: float, world: int) -> float:
+    """Max of x over the ranks (on the GPU under NCCL, on the host under gloo)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate(pixels_per_rank: int, ms: float, world: int):
+    """Whole-job throughput of replicas: every rank renders its own copy of the
+    workload (no data-path collective); the job takes the slowest rank's time.
+    Returns (ms_max, Mpixel/s over all ranks)."""
+    ms_max = allreduce_max(ms, world)
+    return ms_max, world * pixels_per_rank / (ms_max / 1e3) / 1e6
 
 
 def make_workload(args):
@@ -277,8 +287,7 @@ def run_ours(args, world, rank, local):
     if graph is not None:
         launches = args.steps * launches_per_step(lib, step)
     saved.check()
-    ms_max = allreduce_max(ms, world)
-    value = world * P / (ms_max / 1e3) / 1e6
+    ms_max, value = aggregate(P, ms, world)
 
     # --- per-phase times over a second pass of K steps (events on the launch stream)
     phase_acc = {}
