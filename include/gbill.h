@@ -164,7 +164,9 @@ typedef struct {
     int64_t pixels;      /* pixels over all cameras                                */
     int64_t capacity;    /* reserved instance capacity                             */
     int32_t overflow;    /* nonzero if a no-sync forward ran out of capacity       */
-    int32_t error_flags; /* device error bits (bit 0: bounded wait timed out)      */
+    int32_t error_flags; /* device error bits (bit 0: bounded wait timed out;
+                            bit 1: a splat with a non-finite mean, quaternion,
+                            scale, opacity or SH colour was culled)            */
     int64_t pairs_fwd;   /* (pixel, splat) pairs evaluated by the last forward     */
     int64_t pairs_bwd;   /* (pixel, splat) pairs evaluated by the last backward    */
     int64_t blended_fwd;      /* pairs blended by the last forward            */
@@ -231,7 +233,10 @@ gb_status gb_saved_stats(gb_saved *saved, gb_stats *out);
 
 /* Synchronizes and returns GB_ERR_CAPACITY if the last no-sync forward ran out
  * of instance capacity (its outputs are then invalid; reserve more and rerun),
- * GB_ERR_TIMEOUT if a bounded device wait gave up, else GB_OK. */
+ * GB_ERR_TIMEOUT if a bounded device wait gave up, GB_ERR_NONFINITE if the last
+ * forward culled splats with a non-finite mean, quaternion, scale, opacity or
+ * SH colour (the rest of the frame is rendered as if they were absent; texel
+ * values are not checked), else GB_OK. */
 gb_status gb_saved_check(gb_saved *saved);
 
 /* Durations in milliseconds (host array ms[GB_PHASE_COUNT]) of the phases of

@@ -473,6 +473,9 @@ gb_status gb_saved_check(gb_saved *s) {
         return fail(s->ctx, GB_ERR_CAPACITY, "instance capacity %lld exceeded (%lld needed)",
                     (long long)st.capacity, (long long)st.instances);
     if (st.error_flags & 1) return fail(s->ctx, GB_ERR_TIMEOUT, "a bounded device wait timed out");
+    if (st.error_flags & 2)
+        return fail(s->ctx, GB_ERR_NONFINITE,
+                    "non-finite splat parameters or SH colour: those splats were culled in the last forward");
     return GB_OK;
 }
 

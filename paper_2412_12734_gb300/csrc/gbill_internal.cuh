@@ -96,7 +96,7 @@ struct Counters {
     uint32_t n_visible;    // records surviving culling
     uint32_t n_instances;  // (tile, splat) pairs
     uint32_t overflow;     // capacity exceeded
-    uint32_t error_flags;  // bit 0: bounded wait timed out
+    uint32_t error_flags;  // bit 0: bounded wait timed out; bit 1: non-finite splat culled
     uint32_t work_next;    // persistent render work counter (forward)
     uint32_t work_next_bwd;
     uint32_t pad[2];

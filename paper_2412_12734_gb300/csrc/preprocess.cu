@@ -221,7 +221,7 @@ __device__ void homography_fp64(const float p[3], const float q[4], float su, fl
 }
 
 // --------------------------------------------------------- forward kernel --
-__global__ void __launch_bounds__(256) preprocess_kernel(Frame f, uint32_t *depth_key,
+__global__ void __launch_bounds__(256, 4) preprocess_kernel(Frame f, uint32_t *depth_key,
                                                          uint32_t *rec_id, uint2 *rect_out, uint2 *pbox,
                                                          Record *rec_out, Counters *cnt) {
     const int ci = blockIdx.y;
@@ -238,7 +238,34 @@ __global__ void __launch_bounds__(256) preprocess_kernel(Frame f, uint32_t *dept
         const float o = sc.opac[k];
         float zkey;
         int pr[4];
-        valid = key_rect(p, q, su, sv, o, cam, zkey, pr);
+        // a splat with a non-finite parameter is culled in every camera and
+        // raises error bit 1 (gb_saved_check: GB_ERR_NONFINITE)
+        bool finite = isfinite(su) && isfinite(sv) && isfinite(o);
+        for (int i = 0; i < 3; ++i) finite = finite && isfinite(p[i]);
+        for (int i = 0; i < 4; ++i) finite = finite && isfinite(q[i]);
+        if (!finite) atomicOr(&cnt->error_flags, 2u);
+        valid = finite && key_rect(p, q, su, sv, o, cam, zkey, pr);
+        // SH colour, d = (p - campos) / |p - campos|; all 16 basis values
+        // (registers), coefficients beyond the scene's degree skipped by a
+        // uniform predicate.  Non-finite coefficients cull the record too.
+        float rgb[3] = {0.0f, 0.0f, 0.0f};
+        if (valid) {
+            float dx = p[0] - cam.campos[0], dy = p[1] - cam.campos[1], dz = p[2] - cam.campos[2];
+            const float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
+            dx *= dn; dy *= dn; dz *= dn;
+            float Y[16];
+            sh_basis(3, dx, dy, dz, Y);
+            const int M = (sc.D + 1) * (sc.D + 1);
+#pragma unroll
+            for (int m = 0; m < 16; ++m)
+                if (m < M)
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) rgb[ch] += Y[m] * load_sh(sc, (k * M + m) * 3 + ch);
+            if (!(isfinite(rgb[0]) && isfinite(rgb[1]) && isfinite(rgb[2]))) {
+                atomicOr(&cnt->error_flags, 2u);
+                valid = false;
+            }
+        }
         rec_id[r] = uint32_t(r);
         if (!valid) {
             depth_key[r] = 0xFFFFFFFFu;
@@ -299,21 +326,6 @@ __global__ void __launch_bounds__(256) preprocess_kernel(Frame f, uint32_t *dept
                 t00 = t[0]; t01 = t[1]; t10 = t[2]; t11 = t[3];
                 m20 = m[0]; m21 = m[1]; m22 = m[2];
             }
-            // SH colour, d = (p - campos) / |p - campos|
-            float dx = p[0] - cam.campos[0], dy = p[1] - cam.campos[1], dz = p[2] - cam.campos[2];
-            const float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
-            dx *= dn; dy *= dn; dz *= dn;
-            // all 16 basis values (registers); coefficients beyond the scene's
-            // degree are skipped by a uniform predicate
-            float Y[16];
-            sh_basis(3, dx, dy, dz, Y);
-            const int M = (sc.D + 1) * (sc.D + 1);
-            float rgb[3] = {0.0f, 0.0f, 0.0f};
-#pragma unroll
-            for (int m = 0; m < 16; ++m)
-                if (m < M)
-#pragma unroll
-                    for (int ch = 0; ch < 3; ++ch) rgb[ch] += Y[m] * load_sh(sc, (k * M + m) * 3 + ch);
             Record R;
             R.q0 = make_float4(t11, -t01, -t10, t00);
             R.q1 = make_float4(m20, m21, m22, z);
@@ -348,11 +360,13 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(Frame f, int si, co
     float g_sh[M][3];
 #pragma unroll
     for (int m = 0; m < M; ++m) g_sh[m][0] = g_sh[m][1] = g_sh[m][2] = 0.0f;
+    bool seen = false;  // visible in some camera (else every gradient is zero, whatever the parameters)
     for (int ci = 0; ci < f.n_cams; ++ci) {
         const CamDev &cam = f.cams[ci];
         if (cam.scene != si) continue;
         const int32_t j = inv_perm[cam.rec_off + k];
         if (j < 0) continue;
+        seen = true;
         const float4 *gp = reinterpret_cast<const float4 *>(rec_grad + int64_t(j) * kRecGrad);
         const float4 g0 = gp[0], g1 = gp[1], g2 = gp[2], g3 = gp[3];
         // forward recompute (camera space)
@@ -436,6 +450,17 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(Frame f, int si, co
     gq[2] = 2.0f * (g_tu[1] * x - g_tu[2] * w + g_tv[0] * x + g_tv[2] * z) - 4.0f * g_tu[0] * y;
     gq[3] = 2.0f * (g_tu[1] * w + g_tu[2] * x - g_tv[0] * w + g_tv[2] * y) - 4.0f * (g_tu[0] + g_tv[1]) * z;
     const float qd = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * z;
+    if (!seen) {
+        // culled everywhere (possibly for non-finite parameters): exact zeros
+        if (sc.g_means) for (int i = 0; i < 3; ++i) sc.g_means[3 * k + i] = 0.0f;
+        if (sc.g_quats) for (int i = 0; i < 4; ++i) sc.g_quats[4 * k + i] = 0.0f;
+        if (sc.g_scales) { sc.g_scales[2 * k] = 0.0f; sc.g_scales[2 * k + 1] = 0.0f; }
+        if (sc.g_opac) sc.g_opac[k] = 0.0f;
+        if (sc.g_sh)
+            for (int m = 0; m < M; ++m)
+                for (int ch = 0; ch < 3; ++ch) sc.g_sh[(k * M + m) * 3 + ch] = 0.0f;
+        return;
+    }
     if (sc.g_means)
         for (int i = 0; i < 3; ++i) sc.g_means[3 * k + i] = g_p[i];
     if (sc.g_quats)

@@ -341,3 +341,37 @@ def test_no_sync_capacity_overflow_is_reported():
     rgb, _, _, _ = rast.forward(dev, cams, saved=big, flags=L.GB_FLAG_NO_SYNC)
     big.check()
     assert np.array_equal(rgb.cpu().numpy(), ref_rgb.cpu().numpy())
+
+
+def test_non_finite_splats_are_culled_and_reported():
+    """A splat with a NaN centre, one with an infinite scale and one with a
+    NaN SH coefficient are culled in every camera; the rest of the frame
+    equals the oracle's render without them, and gb_saved_check reports
+    GB_ERR_NONFINITE."""
+    from paper_2412_12734_gb300 import _lib as L
+    from paper_2412_12734_gb300 import render as R
+    sc = scenes.tiny_scene(95, K=9, tex_n=4, sh_degree=2)
+    bad = dict(sc)
+    bad["means"] = sc["means"].copy()
+    bad["scales"] = sc["scales"].copy()
+    bad["sh"] = sc["sh"].copy()
+    bad["quats"] = sc["quats"].copy()
+    bad["means"][2, 1] = np.nan
+    bad["scales"][5, 0] = np.inf
+    bad["sh"][7, 3, 1] = np.nan
+    bad["quats"][8, 0] = np.nan
+    keep = np.array([i for i in range(9) if i not in (2, 5, 7, 8)])
+    cam = scenes.tiny_camera(40, 32)
+    rast = R.Rasterizer(0)
+    rgb, _, _, saved = rast.forward([R.scene_to_device(bad)], [cam])
+    with pytest.raises(L.GbillError) as ei:
+        saved.check()
+    assert ei.value.status == 6
+    ref = oracle_run(scenes.subset(sc, keep), cam)
+    e, _ = compare_images(rgb.cpu().numpy().reshape(32, 40, 3), ref, "rgb")
+    assert e <= IMG_TOL, e
+    import torch
+    g = rast.backward(saved, torch.ones((32 * 40, 3), device="cuda"))[0]
+    for k, v in g.items():
+        assert torch.isfinite(v).all(), k
+        assert (v[[2, 5, 7, 8]] == 0).all(), k
