@@ -304,10 +304,11 @@ def default_rasterizer() -> Rasterizer:
 class _RenderFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, means, quats, scales, opacities, sh, textures, meta):
-        rast, cams, sh_degree, tex_n, sigma, background, mip_level = meta
+        rast, cams, sh_degree, tex_n, sigma, background, mip_level, tex_sh_degree = meta
         sc = {"means": means.contiguous(), "quats": quats.contiguous(), "scales": scales.contiguous(),
               "opacities": opacities.contiguous(), "sh": sh.contiguous(), "textures": textures.contiguous(),
-              "sh_degree": sh_degree, "tex_n": tex_n, "sigma": sigma, "mip_level": mip_level}
+              "sh_degree": sh_degree, "tex_n": tex_n, "sigma": sigma, "mip_level": mip_level,
+              "tex_sh_degree": tex_sh_degree}
         rgb, depth, alpha, saved = rast.forward([sc], cams, background=background)
         ctx.saved_handle = saved
         ctx.rast = rast
@@ -328,15 +329,19 @@ class _RenderFn(torch.autograd.Function):
 
 
 def render(means, quats, scales, opacities, sh, textures, cams, sh_degree: int, tex_n: int,
-           sigma: float = 0.5, background=None, rasterizer: Rasterizer | None = None, mip_level: int = 0):
+           sigma: float = 0.5, background=None, rasterizer: Rasterizer | None = None, mip_level: int = 0,
+           tex_sh_degree: int = 0):
     """Differentiable render of one scene into all ``cams``.
 
     Returns (rgb [P,3], depth [P], alpha [P]) with the cameras' pixels packed
     one after another (row-major per camera).  mip_level l > 0 renders the
-    colour grids box-filtered to N / 2^l (Sec. 4.1, Fig. 4 f, g).
+    colour grids box-filtered to N / 2^l (Sec. 4.1, Fig. 4 f, g);
+    tex_sh_degree Dt > 0 takes textures [K, N, N, (Dt+1)^2, 3] of per-texel SH
+    coefficients (Sec. 4.2).
     """
     rast = rasterizer or default_rasterizer()
-    meta = (rast, list(cams), int(sh_degree), int(tex_n), float(sigma), background, int(mip_level))
+    meta = (rast, list(cams), int(sh_degree), int(tex_n), float(sigma), background, int(mip_level),
+            int(tex_sh_degree))
     return _RenderFn.apply(means, quats, scales, opacities, sh, textures, meta)
 
 
