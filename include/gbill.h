@@ -176,7 +176,8 @@ typedef struct {
 /* Phases timed under GB_FLAG_TIMING, in the order gb_saved_phase_times
  * returns them. */
 typedef enum {
-    GB_PHASE_PREPROCESS = 0, /* homography, FP32 rectangle, depth key, SH colour  */
+    GB_PHASE_PREPROCESS = 0, /* grid pre-passes (mip filter, per-texel SH grids);
+                                homography, FP32 rectangle, depth key, SH colour */
     GB_PHASE_DEPTH_SORT,     /* radix sort of records by depth                    */
     GB_PHASE_COUNT_SCAN,     /* exclusive scan of per-record tile counts          */
     GB_PHASE_EMIT,           /* (tile, splat) duplication                         */
@@ -184,8 +185,9 @@ typedef enum {
     GB_PHASE_RANGES,         /* per-tile [begin, end)                             */
     GB_PHASE_RENDER_FWD,     /* per-tile front-to-back render                     */
     GB_PHASE_BWD_SETUP,      /* gradient buffers zeroed, inverse permutation      */
-    GB_PHASE_RENDER_BWD,     /* per-tile back-to-front adjoint                    */
-    GB_PHASE_PREPROCESS_BWD, /* chain to means, quats, scales, opacity, SH        */
+    GB_PHASE_RENDER_BWD,     /* per-tile back-to-front adjoint; mip-filter adjoint */
+    GB_PHASE_PREPROCESS_BWD, /* chain to means, quats, scales, opacity, SH;
+                                per-texel SH coefficient and centre gradients */
     GB_PHASE_COUNT
 } gb_phase;
 

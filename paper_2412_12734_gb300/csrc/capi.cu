@@ -566,6 +566,9 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
         if ((r = reserve_instances(s, std::max<int64_t>(s->cap_inst, 1 << 16))) != GB_OK) return r;
         if ((r = reserve_scratch(s)) != GB_OK) return r;
     }
+    const bool timing = (o.flags & GB_FLAG_TIMING) != 0;
+    // the preprocess phase starts with the grid pre-passes below
+    if (timing) GB_CUDA(ctx, cudaEventRecord(s->ev[0], st));
     // mip-level scenes: filter their grids into FP32 scratch the render reads
     int64_t mip_need = 0;
     for (int i = 0; i < f.n_scenes; ++i) {
@@ -642,12 +645,10 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
     s->flags = o.flags;
     s->stream = st;
     s->has_forward = false;
-    const bool timing = (o.flags & GB_FLAG_TIMING) != 0;
     s->timed_fwd = s->timed_bwd = false;
 #define GB_MARK(i) \
     if (timing) GB_CUDA(ctx, cudaEventRecord(s->ev[i], st))
 
-    GB_MARK(0);
     GB_CUDA(ctx, cudaMemsetAsync(s->cnt, 0, sizeof(Counters), st));
     GB_CUDA(ctx, cudaMemsetAsync(s->ranges, 0, size_t(f.n_tiles) * sizeof(uint2), st));
     GB_CUDA(ctx, launch_preprocess(f, max_k, s->depth_key, s->rec_id, s->rect, s->pbox, s->rec, s->cnt, st));
