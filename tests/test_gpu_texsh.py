@@ -67,3 +67,45 @@ def test_texel_sh_needs_reserved_scratch_in_no_sync_mode():
     with pytest.raises(L.GbillError) as ei:
         rast.forward([R.scene_to_device(sc)], [scenes.tiny_camera(16, 16)], saved=saved, flags=L.GB_FLAG_NO_SYNC)
     assert ei.value.status == 4
+
+
+@pytest.mark.parametrize("Dt,dtype", [(3, "f16"), (1, "f32"), (3, "bf16")])
+def test_texel_sh_unaligned_storage_matches_aligned(Dt, dtype):
+    """Coefficients and their gradient output that do not start on a 16-byte
+    boundary take the passes' scalar-load paths: the same images bit for bit
+    and the same gradients up to the order of the render's atomics."""
+    import torch
+
+    from paper_2412_12734_gb300 import render as R
+    sc = scenes.with_texel_sh(scenes.tiny_scene(95 + Dt, K=9, tex_n=4, sh_degree=1, tex_dtype=dtype), Dt, seed=3,
+                              std=0.3)
+    cams = [scenes.tiny_camera(36, 28), scenes.tiny_camera(30, 34, eye=(0.6, 0.4, -3.9))]
+    rast = R.Rasterizer(0)
+    d = torch.as_tensor(np.random.default_rng(4).standard_normal((36 * 28 + 30 * 34, 3)), dtype=torch.float32,
+                        device="cuda")
+
+    def run(offset):
+        dev = R.scene_to_device(sc)
+        tex = dev["textures"]
+        if offset:
+            # same values one element past a 16-byte boundary
+            buf = torch.empty(tex.numel() + 1, dtype=tex.dtype, device="cuda")
+            buf[1:] = tex.reshape(-1)
+            dev["textures"] = buf[1:].view(tex.shape)
+        rgb, _, _, saved = rast.forward([dev], cams, cam_scene=[0, 0])
+        K = tex.shape[0]
+        gbuf = torch.empty(tex.numel() + offset, device="cuda")
+        grads = [{"means": torch.empty((K, 3), device="cuda"), "quats": torch.empty((K, 4), device="cuda"),
+                  "scales": torch.empty((K, 2), device="cuda"), "opacities": torch.empty(K, device="cuda"),
+                  "sh": torch.empty_like(dev["sh"], dtype=torch.float32),
+                  "textures": gbuf[offset:].view(tex.shape)}]
+        rast.backward(saved, d, grads=grads)
+        torch.cuda.synchronize()
+        return rgb.cpu().numpy(), {k: v.cpu().numpy() for k, v in grads[0].items()}
+
+    rgb_a, g_a = run(0)
+    rgb_u, g_u = run(1)
+    assert np.array_equal(rgb_a, rgb_u)
+    for k in ("textures", "means"):
+        scale = np.abs(g_a[k]).max()
+        assert np.abs(g_a[k] - g_u[k]).max() <= 1e-5 * max(scale, 1e-12), k
