@@ -653,8 +653,12 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
     GB_CUDA(ctx, cudaMemsetAsync(s->ranges, 0, size_t(f.n_tiles) * sizeof(uint2), st));
     GB_CUDA(ctx, launch_preprocess(f, max_k, s->depth_key, s->rec_id, s->rect, s->pbox, s->rec, s->cnt, st));
     GB_MARK(1);
-    GB_CUDA(ctx, radix_sort_pairs(s->depth_key, s->rec_id, s->keys_tmp, s->vals_tmp, s->dkeys_sorted, s->perm, R,
-                                  nullptr, 0, 32, s->scratch, s->scratch_bytes, st));
+    // visible records to the front in record order, then sorted by depth
+    // (stable, so equal depths keep record order)
+    GB_CUDA(ctx, compact_visible(s->depth_key, R, s->offsets, s->dkeys_sorted, s->perm, s->scratch, s->scratch_bytes,
+                                 st));
+    GB_CUDA(ctx, radix_sort_pairs(s->dkeys_sorted, s->perm, s->keys_tmp, s->vals_tmp, s->dkeys_sorted, s->perm, R,
+                                  &s->cnt->n_visible, 0, 32, s->scratch, s->scratch_bytes, st));
     GB_MARK(2);
     GB_CUDA(ctx, tile_counts_scan(f, s->perm, s->rect, R, &s->cnt->n_visible, s->offsets, s->scratch,
                                   s->scratch_bytes, s->cnt, s->cap_inst, st));
@@ -819,7 +823,7 @@ constexpr int64_t kNaMaxInstances = int64_t(1) << 19;
 constexpr int64_t kNaMaxPixels = int64_t(1) << 20;
 constexpr int64_t kNaMaxTiles = int64_t(1) << 13;
 constexpr size_t na_round(size_t b) { return (b + 255) & ~size_t(255); }
-constexpr size_t kNaRadixBytes = size_t(kNaMaxInstances / 4096) * 256 * 4 + 64 * 1024;
+constexpr size_t kNaRadixBytes = size_t(kNaMaxInstances / 4096) * 512 * 4 + 64 * 1024;
 constexpr size_t kNaScratchBytes =
     na_round(sizeof(Counters)) + na_round(2 * kMaxGroups * 4) +
     na_round(kNaMaxRecords * sizeof(Record)) + 7 * na_round(kNaMaxRecords * 4) + 2 * na_round(kNaMaxRecords * 8) +

@@ -146,6 +146,10 @@ cudaError_t launch_preprocess_bwd(const Frame &f, int64_t max_k, const float *re
 
 // sort.cu
 size_t radix_scratch_bytes(int64_t n);
+// Visible records (depth key not 0xFFFFFFFF) of [0, n) to the front of
+// key_out / id_out in record order (id = record index); pos: n scan slots.
+cudaError_t compact_visible(const uint32_t *depth_key, int64_t n, uint32_t *pos, uint32_t *key_out,
+                            uint32_t *id_out, void *scratch, size_t scratch_bytes, cudaStream_t s);
 cudaError_t radix_sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *keys_tmp,
                              uint32_t *vals_tmp, uint32_t *keys_out, uint32_t *vals_out,
                              int64_t max_n, const uint32_t *n_dev, int begin_bit, int end_bit,

@@ -13,7 +13,7 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortRounds = 16;  // 32-key rounds per warp
 constexpr int kWarpTile = 32 * kSortRounds;
 constexpr int kSortTile = kWarpTile * kSortWarps;  // 4096 keys per block
-constexpr int kRadix = 256;
+constexpr int kMaxRadixBits = 9;                   // digits of 8 or 9 bits
 
 __device__ __forceinline__ uint32_t load_n(const uint32_t *n_dev, int64_t max_n) {
     return n_dev ? uint32_t(min(int64_t(*n_dev), max_n)) : uint32_t(max_n);
@@ -26,9 +26,11 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 }
 
 // Per-block digit histogram, written digit-major: hist[d * nblocks + block].
+template <int BITS>
 __global__ void __launch_bounds__(kSortThreads) radix_upsweep(const uint32_t *keys, int64_t max_n,
                                                               const uint32_t *n_dev, int shift,
                                                               uint32_t mask, uint32_t *hist) {
+    constexpr int kRadix = 1 << BITS;
     __shared__ uint32_t h[kRadix];
     const uint32_t n = load_n(n_dev, max_n);
     for (int i = threadIdx.x; i < kRadix; i += kSortThreads) h[i] = 0;
@@ -52,9 +54,11 @@ __global__ void __launch_bounds__(kSortThreads) radix_upsweep(const uint32_t *ke
 // Stable scatter: warp w owns keys [w*512, (w+1)*512) of the block tile and
 // ranks them in order with warp-match; per-digit warp counts are then
 // prefix-summed over warps so earlier warps come first.
+template <int BITS>
 __global__ void __launch_bounds__(kSortThreads) radix_downsweep(
     const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *keys_out, uint32_t *vals_out,
     int64_t max_n, const uint32_t *n_dev, int shift, uint32_t mask, const uint32_t *offs) {
+    constexpr int kRadix = 1 << BITS;
     __shared__ uint32_t wcount[kSortWarps][kRadix];
     __shared__ uint32_t goff[kRadix];
     const uint32_t n = load_n(n_dev, max_n);
@@ -264,10 +268,28 @@ __global__ void ranges_kernel(const uint32_t *tiles, int64_t max_n, const Counte
     if (i == n - 1 || tiles[i + 1] != t) ranges[t].y = uint32_t(i + 1);
 }
 
+// inv[perm[j]] = j for the visible records (the caller preset inv to -1).
 __global__ void inverse_perm_kernel(const uint32_t *perm, int64_t n_records, const Counters *cnt, int32_t *inv) {
     const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (j >= n_records) return;
-    inv[perm[j]] = j < int64_t(cnt->n_visible) ? int32_t(j) : -1;
+    if (j >= min(int64_t(cnt->n_visible), n_records)) return;
+    inv[perm[j]] = int32_t(j);
+}
+
+// Visible records (depth key not the culled marker) in record order.
+struct LoadVisible {
+    const uint32_t *key;
+    __device__ uint32_t operator()(int64_t i) const { return key[i] != 0xFFFFFFFFu ? 1u : 0u; }
+};
+
+__global__ void compact_kernel(const uint32_t *key, const uint32_t *pos, int64_t n, uint32_t *key_out,
+                               uint32_t *id_out) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t k = key[i];
+    if (k != 0xFFFFFFFFu) {
+        key_out[pos[i]] = k;
+        id_out[pos[i]] = uint32_t(i);
+    }
 }
 
 __global__ void export_keys_kernel(Frame f, const uint32_t *tiles, const uint32_t *vals, const uint32_t *perm,
@@ -304,7 +326,7 @@ cudaError_t launch_tile_list(const Frame &f, const uint2 *ranges, uint32_t *keys
 
 size_t radix_scratch_bytes(int64_t n) {
     const int64_t nb = ceil_div(n, kSortTile);
-    const int64_t h = nb * kRadix;
+    const int64_t h = nb * (int64_t(1) << kMaxRadixBits);
     return size_t(h) * sizeof(uint32_t) + size_t(ceil_div(h, kScanTile) + 1) * sizeof(uint32_t) + 256;
 }
 
@@ -316,33 +338,54 @@ cudaError_t radix_sort_pairs(const uint32_t *keys_in, const uint32_t *vals_in, u
                              size_t scratch_bytes, cudaStream_t s) {
     if (max_n <= 0) return cudaSuccess;
     const int64_t nb = ceil_div(max_n, kSortTile);
-    const int64_t h = nb * kRadix;
     if (scratch_bytes < radix_scratch_bytes(max_n)) return cudaErrorInvalidValue;
     uint32_t *hist = static_cast<uint32_t *>(scratch);
-    uint32_t *scan_tmp = hist + h;
-    const size_t scan_bytes = scratch_bytes - size_t(h) * sizeof(uint32_t);
-    const int passes = (end_bit - begin_bit + 7) / 8;
-    if (passes <= 0) {
+    uint32_t *scan_tmp = hist + nb * (int64_t(1) << kMaxRadixBits);
+    const size_t scan_bytes = scratch_bytes - size_t(nb << kMaxRadixBits) * sizeof(uint32_t);
+    const int bits = end_bit - begin_bit;
+    if (bits <= 0) {
+        if (keys_out == keys_in) return cudaSuccess;
         cudaMemcpyAsync(keys_out, keys_in, size_t(max_n) * 4, cudaMemcpyDeviceToDevice, s);
         cudaMemcpyAsync(vals_out, vals_in, size_t(max_n) * 4, cudaMemcpyDeviceToDevice, s);
         return cudaGetLastError();
     }
+    // fewest passes of at most 9 bits, the bits spread evenly (17 -> 9 + 8, 32 -> 4 x 8)
+    const int passes = (bits + kMaxRadixBits - 1) / kMaxRadixBits;
+    // the last pass writes keys_out; with the input there, pass 0 must not
+    if (keys_in == keys_out && (passes & 1)) return cudaErrorInvalidValue;
     const uint32_t *ki = keys_in, *vi = vals_in;
+    int shift = begin_bit;
     for (int p = 0; p < passes; ++p) {
-        const int shift = begin_bit + 8 * p;
-        const int bits = min(8, end_bit - shift);
-        const uint32_t mask = (1u << bits) - 1u;
+        const int w = bits / passes + (p < bits % passes ? 1 : 0);
+        const uint32_t mask = (1u << w) - 1u;
         uint32_t *ko = ((passes - p) & 1) ? keys_out : keys_tmp;
         uint32_t *vo = ((passes - p) & 1) ? vals_out : vals_tmp;
-        radix_upsweep<<<unsigned(nb), kSortThreads, 0, s>>>(ki, max_n, n_dev, shift, mask, hist);
+        const int64_t h = nb << (w > 8 ? 9 : 8);
+        if (w > 8) radix_upsweep<9><<<unsigned(nb), kSortThreads, 0, s>>>(ki, max_n, n_dev, shift, mask, hist);
+        else radix_upsweep<8><<<unsigned(nb), kSortThreads, 0, s>>>(ki, max_n, n_dev, shift, mask, hist);
         cudaError_t e = exclusive_scan(LoadArray{hist}, h, nullptr, hist, nullptr, scan_tmp, scan_bytes,
                                        nullptr, 0, s);
         if (e != cudaSuccess) return e;
-        radix_downsweep<<<unsigned(nb), kSortThreads, 0, s>>>(ki, vi, ko, vo, max_n, n_dev, shift, mask, hist);
+        if (w > 8)
+            radix_downsweep<9><<<unsigned(nb), kSortThreads, 0, s>>>(ki, vi, ko, vo, max_n, n_dev, shift, mask, hist);
+        else
+            radix_downsweep<8><<<unsigned(nb), kSortThreads, 0, s>>>(ki, vi, ko, vo, max_n, n_dev, shift, mask, hist);
         count_launches(2);
         ki = ko;
         vi = vo;
+        shift += w;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t compact_visible(const uint32_t *depth_key, int64_t n, uint32_t *pos, uint32_t *key_out,
+                            uint32_t *id_out, void *scratch, size_t scratch_bytes, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    cudaError_t e = exclusive_scan(LoadVisible{depth_key}, n, nullptr, pos, nullptr, scratch, scratch_bytes, nullptr,
+                                   0, s);
+    if (e != cudaSuccess) return e;
+    compact_kernel<<<unsigned(ceil_div(n, 256)), 256, 0, s>>>(depth_key, pos, n, key_out, id_out);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -375,6 +418,8 @@ cudaError_t launch_ranges(const uint32_t *tiles_sorted, int64_t max_n, const Cou
 cudaError_t launch_inverse_perm(const uint32_t *perm, int64_t n_records, const Counters *cnt, int32_t *inv,
                                 cudaStream_t s) {
     if (n_records <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(inv, 0xFF, size_t(n_records) * sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
     inverse_perm_kernel<<<unsigned(ceil_div(n_records, 256)), 256, 0, s>>>(perm, n_records, cnt, inv);
     count_launches(1);
     return cudaGetLastError();
