@@ -184,14 +184,15 @@ gb_status reserve_scratch(gb_saved *s) {
 
 size_t batch_smem(int N, int batch, bool bwd);
 
-// Batch depth giving ~42 KB of staged shared memory per block, so that four
-// or more blocks stay resident per SM (measured on the 1M-splat, 16-view
-// workload: 64 is best at N = 4 and 16 at N = 8, where 64 would stage 127 KB
-// in the backward and leave one block per SM); a multiple of 8, at least 8.
+// Batch depth giving at most 48 KB of staged shared memory per block, so that
+// four blocks (the register limit of the 256-thread backward) stay resident
+// per SM (measured on the 1M-splat, 16-view workload: 72 is best at N = 4,
+// 24 at N = 8, where 40 leaves three blocks per SM and runs 27 % slower); a
+// multiple of 8, at least 8.
 int default_batch(int N, bool bwd) {
     const int per = int(batch_smem(N, 1, true));
     (void)bwd;  // one depth for both passes: the backward's staging decides
-    int b = (42 * 1024) / per;
+    int b = (48 * 1024) / per;
     b = std::min(b, 256);
     b &= ~7;
     return std::max(b, 8);
@@ -1065,10 +1066,10 @@ gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int3
         float best_ms = INFINITY;
         int n = 0;
         const int tile_c[3] = {16, 8, 32};
-        const int batch_c[6] = {8, 16, 32, 64, 128, 256};
+        const int batch_c[8] = {8, 16, 24, 32, 48, 64, 72, 128};
         for (int pi = 1; pi <= 2 && st == GB_OK; ++pi)
         for (int ti = 0; ti < 3 && st == GB_OK; ++ti)
-            for (int bi = 0; bi < 6 && st == GB_OK; ++bi) {
+            for (int bi = 0; bi < 8 && st == GB_OK; ++bi) {
                 const int T = tile_c[ti], B = batch_c[bi];
                 if (B > T * T / pi) continue;
                 if (batch_smem(N, B, false) > 160 * 1024 || batch_smem(N, B, true) > 160 * 1024) continue;

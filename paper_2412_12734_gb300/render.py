@@ -270,18 +270,18 @@ class Rasterizer:
         sarr = (L.gb_scene * n_s)(*[scene_struct(s) for s in scenes])
         carr = (L.gb_camera * n_c)(*[camera_struct(c, cam_scene[i]) for i, c in enumerate(cams)])
         best = L.gb_options()
-        ms = (C.c_float * 48)()
-        tiles = (C.c_int32 * 48)()
-        batches = (C.c_int32 * 48)()
-        ppts = (C.c_int32 * 48)()
+        ms = (C.c_float * 64)()
+        tiles = (C.c_int32 * 64)()
+        batches = (C.c_int32 * 64)()
+        ppts = (C.c_int32 * 64)()
         n = C.c_int32()
         saved = saved or Saved(self)
         L.check(lib.gb_autotune(self.ctx, saved.handle, sarr, n_s, carr, n_c, None, reps, C.byref(best),
-                                C.addressof(ms), C.addressof(tiles), C.addressof(batches), C.addressof(ppts), 48,
+                                C.addressof(ms), C.addressof(tiles), C.addressof(batches), C.addressof(ppts), 64,
                                 C.byref(n)), self.ctx)
         res = {"tile": best.tile_size, "batch": best.batch_depth, "ppt": best.pixels_per_thread,
                "candidates": [{"tile": tiles[i], "batch": batches[i], "ppt": ppts[i], "ms": ms[i]}
-                              for i in range(n.value)]}
+                              for i in range(min(n.value, 64))]}
         table[key] = res
         try:
             os.makedirs(os.path.dirname(path), exist_ok=True)
