@@ -348,17 +348,17 @@ def launches_per_step(lib, step):
 
 
 # DRAM bytes (read + write) per launch of the render kernels on the full
-# 16-view batched_1m workload at 4x4 grids, tile 16, batch 64, one pixel per
+# 16-view batched_1m workload at 4x4 grids, tile 16, batch 72, one pixel per
 # thread, from one ncu capture (profiles/render_traffic_batched_1m.md), with
 # the digest of the kernel sources it was taken on.  A kernel whose sources
 # differ reports traffic null.
 TRAFFIC = {
-    "render_bwd": {"bytes": 3.53e9 + 1.03e9, "files": ("render_bwd.cuh", "render_common.cuh", "render_bwd.cu"),
+    "render_bwd": {"bytes": 3.522e9 + 1.026e9, "files": ("render_bwd.cuh", "render_common.cuh", "render_bwd.cu"),
                    "sha256_16": "4d73df68b22a9c6a",
-                   "config": {"workload": "batched_1m", "tex_n": 4, "tile": 16, "batch": 64, "ppt": 1}},
-    "render_fwd": {"bytes": 1.77e9 + 0.566e9, "files": ("render_fwd.cu", "render_common.cuh"),
+                   "config": {"workload": "batched_1m", "tex_n": 4, "tile": 16, "batch": 72, "ppt": 1}},
+    "render_fwd": {"bytes": 1.775e9 + 0.557e9, "files": ("render_fwd.cu", "render_common.cuh"),
                    "sha256_16": "597a37a4f6c9a700",
-                   "config": {"workload": "batched_1m", "tex_n": 4, "tile": 16, "batch": 64, "ppt": 1}},
+                   "config": {"workload": "batched_1m", "tex_n": 4, "tile": 16, "batch": 72, "ppt": 1}},
 }
 
 
