@@ -348,36 +348,42 @@ def launches_per_step(lib, step):
 
 
 # DRAM bytes (read + write) per launch of the render kernels on the full
-# 16-view batched_1m workload at 4x4 grids, tile 16, batch 72, one pixel per
-# thread, from one ncu capture (profiles/render_traffic_batched_1m.md), with
-# the digest of the kernel sources it was taken on.  A kernel whose sources
-# differ reports traffic null.
+# 16-view batched_1m workload at 4x4 grids, from ncu captures
+# (profiles/render_traffic_batched_1m.md), per launch configuration, with the
+# digest of the kernel sources they were taken on.  A kernel whose sources
+# differ, or a configuration not captured, reports traffic null.
 TRAFFIC = {
-    "render_bwd": {"bytes": 3.522e9 + 1.026e9, "files": ("render_bwd.cuh", "render_common.cuh", "render_bwd.cu"),
-                   "sha256_16": "4d73df68b22a9c6a",
-                   "config": {"workload": "batched_1m", "tex_n": 4, "tile": 16, "batch": 72, "ppt": 1}},
-    "render_fwd": {"bytes": 1.775e9 + 0.557e9, "files": ("render_fwd.cu", "render_common.cuh"),
-                   "sha256_16": "597a37a4f6c9a700",
-                   "config": {"workload": "batched_1m", "tex_n": 4, "tile": 16, "batch": 72, "ppt": 1}},
+    "render_bwd": {"files": ("render_bwd.cuh", "render_common.cuh", "render_bwd.cu", "render_bwd2.cu"),
+                   "sha256_16": "4da5e71c16ebd3c8", "keys": ("workload", "tex_n", "tile", "batch", "ppt"),
+                   "measured": [({"workload": "batched_1m", "tex_n": 4, "tile": 16, "batch": 64, "ppt": 2},
+                                 3.543e9 + 1.0125e9)]},
+    "render_fwd": {"files": ("render_fwd.cu", "render_common.cuh"),
+                   "sha256_16": "9730c88a9acff73e", "keys": ("workload", "tex_n", "tile", "batch"),
+                   "measured": [({"workload": "batched_1m", "tex_n": 4, "tile": 16, "batch": 64},
+                                 1.770e9 + 0.561e9)]},
 }
 
 
 def measured_traffic(kernel, args):
     """Bytes per launch from TRAFFIC when the kernel sources and the launch
-    configuration are the ones it was measured on, else None."""
+    configuration are ones it was measured on, else None."""
     import hashlib
     t = TRAFFIC.get(kernel)
-    if t is None:
+    if t is None or args.views or args.mip or args.tex_sh:
         return None
     h = hashlib.sha256()
     for f in t["files"]:
         with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2412_12734_gb300", "csrc", f),
                   "rb") as fh:
             h.update(fh.read())
-    cfg = {"workload": args.workload, "tex_n": args.tex_n, "tile": args.tile, "batch": args.batch, "ppt": args.ppt}
-    if h.hexdigest()[:16] != t["sha256_16"] or cfg != t["config"] or args.views or args.mip or args.tex_sh:
+    if h.hexdigest()[:16] != t["sha256_16"]:
         return None
-    return t["bytes"]
+    cfg = {"workload": args.workload, "tex_n": args.tex_n, "tile": args.tile, "batch": args.batch, "ppt": args.ppt}
+    cfg = {k: cfg[k] for k in t["keys"]}
+    for c, b in t["measured"]:
+        if c == cfg:
+            return b
+    return None
 
 
 def roofline_line(dominant, phases, st, clocks, traffic=None):

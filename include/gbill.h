@@ -399,7 +399,7 @@ gb_status gb_mse_loss(gb_context *ctx, const float *rgb, const float *target, in
 /* ---------------------------------------------------------------- tuning -- */
 
 /* Autotuner: times forward + backward of this frame for every candidate
- * (tile_size 8, 16 and 32; batch_depth 8, 16, 24, 32, 48, 64, 72, 128 where it fits the tile and
+ * (tile_size 8, 16 and 32; batch_depth 8, 16, 24, 32, 48, 64, 88, 128 where it fits the tile and
  * the shared-memory budget; pixels_per_thread 1 and 2) and writes the fastest
  * options to *best (flags and
  * background are copied from *base, which may be NULL).  Each candidate runs

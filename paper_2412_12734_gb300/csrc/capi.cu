@@ -182,30 +182,46 @@ gb_status reserve_scratch(gb_saved *s) {
     return GB_OK;
 }
 
-size_t batch_smem(int N, int batch, bool bwd);
+size_t frame_smem(const Frame &f, int batch, bool bwd);
 
 // Batch depth giving at most 48 KB of staged shared memory per block, so that
 // four blocks (the register limit of the 256-thread backward) stay resident
-// per SM (measured on the 1M-splat, 16-view workload: 72 is best at N = 4,
-// 24 at N = 8, where 40 leaves three blocks per SM and runs 27 % slower); a
-// multiple of 8, at least 8.
-int default_batch(int N, bool bwd) {
-    const int per = int(batch_smem(N, 1, true));
-    (void)bwd;  // one depth for both passes: the backward's staging decides
+// per SM; a multiple of 8, at least 8.  With FP16 grids staged at 8 bytes a
+// texel that is 88 at N = 4, 32 at N = 8 and 8 at N = 16 (measured on the
+// 1M-splat, 16-view workload: the best of the depths tried at N = 4 and 8;
+// with FP32-width staging N = 8 ran 27 % slower at 40, three blocks per SM,
+// than at 24, and N = 16 at 8 left three blocks per SM: 139 against 165
+// Mpixel/s).
+int default_batch(const Frame &f) {
+    // one depth for both passes: the backward's staging decides
+    const int per = int(frame_smem(f, 1, true));
     int b = (48 * 1024) / per;
     b = std::min(b, 256);
     b &= ~7;
     return std::max(b, 8);
 }
 
-size_t batch_smem(int N, int batch, bool bwd) {
+template <typename TexT>
+size_t batch_smem_t(int N, int batch, bool bwd) {
     switch (N) {
-        case 1: return stage_bytes<1>(batch, bwd);
-        case 2: return stage_bytes<2>(batch, bwd);
-        case 4: return stage_bytes<4>(batch, bwd);
-        case 8: return stage_bytes<8>(batch, bwd);
-        default: return stage_bytes<16>(batch, bwd);
+        case 1: return stage_bytes<1, TexT>(batch, bwd);
+        case 2: return stage_bytes<2, TexT>(batch, bwd);
+        case 4: return stage_bytes<4, TexT>(batch, bwd);
+        case 8: return stage_bytes<8, TexT>(batch, bwd);
+        default: return stage_bytes<16, TexT>(batch, bwd);
     }
+}
+
+// Staged bytes of one batch for a grid of size N stored as `dtype`.
+size_t batch_smem(int N, int dtype, int batch, bool bwd) {
+    return dtype == GB_F32 ? batch_smem_t<float>(N, batch, bwd) : batch_smem_t<__half>(N, batch, bwd);
+}
+
+// The largest over the frame's render groups (one batch depth serves all).
+size_t frame_smem(const Frame &f, int batch, bool bwd) {
+    size_t m = 0;
+    for (int g = 0; g < f.n_groups; ++g) m = std::max(m, batch_smem(f.group_N[g], f.group_dtype[g], batch, bwd));
+    return m;
 }
 
 __global__ void zero_rec_grad(float *g, const Counters *cnt, int64_t max_n) {
@@ -546,14 +562,12 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
     int64_t max_k = 0;
     gb_status r = build_frame(ctx, scenes, n_scenes, cams, n_cams, tile, o.background, f, max_k);
     if (r != GB_OK) return r;
-    int N = 1;
-    for (int k = 0; k < f.n_groups; ++k) N = std::max(N, f.group_N[k]);
     const int nt = tile * tile;
-    int bf = o.batch_depth ? o.batch_depth : std::min(default_batch(N, false), nt);
-    int bb = o.batch_depth ? o.batch_depth : std::min(default_batch(N, true), nt / ppt);
+    int bf = o.batch_depth ? o.batch_depth : std::min(default_batch(f), nt);
+    int bb = o.batch_depth ? o.batch_depth : std::min(default_batch(f), nt / ppt);
     if (bf < 8 || bf > nt || (bf & 7)) return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d invalid", bf);
     if (bb > nt / ppt) return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d exceeds the backward's %d threads", bb, nt / ppt);
-    if (batch_smem(N, bf, false) > 200 * 1024 || batch_smem(N, bb, true) > 200 * 1024)
+    if (frame_smem(f, bf, false) > 200 * 1024 || frame_smem(f, bb, true) > 200 * 1024)
         return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d needs too much shared memory", bf);
     const bool nosync = (o.flags & GB_FLAG_NO_SYNC) != 0;
     if (nosync) {
@@ -863,11 +877,9 @@ gb_status gb_render_forward_noalloc(gb_context *ctx, const gb_scene *scenes, int
                     "no-allocation forward limits: %lld records (max %lld), %lld pixels (max %lld), %u tiles (max %lld)",
                     (long long)f.n_records, (long long)kNaMaxRecords, (long long)f.n_pixels,
                     (long long)kNaMaxPixels, f.n_tiles, (long long)kNaMaxTiles);
-    int N = 1;
-    for (int k = 0; k < f.n_groups; ++k) N = std::max(N, f.group_N[k]);
     const int nt = tile * tile;
-    const int bf = o.batch_depth ? o.batch_depth : std::min(default_batch(N, false), nt);
-    if (bf < 8 || bf > nt || (bf & 7) || batch_smem(N, bf, false) > 200 * 1024)
+    const int bf = o.batch_depth ? o.batch_depth : std::min(default_batch(f), nt);
+    if (bf < 8 || bf > nt || (bf & 7) || frame_smem(f, bf, false) > 200 * 1024)
         return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d invalid", bf);
     int dev = 0;
     GB_CUDA(ctx, cudaGetDevice(&dev));
@@ -1020,8 +1032,6 @@ gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int3
     int64_t max_k = 0;
     gb_status r = build_frame(ctx, scenes, n_scenes, cams, n_cams, 16, nullptr, f, max_k);
     if (r != GB_OK) return r;
-    int N = 1;
-    for (int k = 0; k < f.n_groups; ++k) N = std::max(N, f.group_N[k]);
     // scratch buffers owned by this call
     float *rgb = nullptr, *dep = nullptr, *alp = nullptr, *drgb = nullptr, *gbuf = nullptr;
     size_t gtot = 0;
@@ -1066,13 +1076,13 @@ gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int3
         float best_ms = INFINITY;
         int n = 0;
         const int tile_c[3] = {16, 8, 32};
-        const int batch_c[8] = {8, 16, 24, 32, 48, 64, 72, 128};
+        const int batch_c[8] = {8, 16, 24, 32, 48, 64, 88, 128};
         for (int pi = 1; pi <= 2 && st == GB_OK; ++pi)
         for (int ti = 0; ti < 3 && st == GB_OK; ++ti)
             for (int bi = 0; bi < 8 && st == GB_OK; ++bi) {
                 const int T = tile_c[ti], B = batch_c[bi];
                 if (B > T * T / pi) continue;
-                if (batch_smem(N, B, false) > 160 * 1024 || batch_smem(N, B, true) > 160 * 1024) continue;
+                if (frame_smem(f, B, false) > 160 * 1024 || frame_smem(f, B, true) > 160 * 1024) continue;
                 o.tile_size = T;
                 o.batch_depth = B;
                 o.pixels_per_thread = pi;

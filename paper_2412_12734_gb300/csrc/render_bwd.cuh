@@ -129,8 +129,8 @@ __device__ __forceinline__ void put(float &slot, float v) {
 
 // ACC: add to g[] (second and later pixels of a thread); otherwise the slots
 // this pair owns are assigned (g[] holds zeros on entry).
-template <int N, bool ACC>
-__device__ __forceinline__ bool pair_adjoint(Pix &px, uint32_t idx, const float4 *rec, const float4 *tex,
+template <int N, typename TexT, bool ACC>
+__device__ __forceinline__ bool pair_adjoint(Pix &px, uint32_t idx, const float4 *rec, const staged_t<TexT> *tex,
                                              float sigma, float kN, float g[32], Rem &rem, uint32_t &npairs,
                                              uint32_t &ncontrib) {
     rem.w00 = rem.w10 = rem.w01 = rem.w11 = 0.0f;
@@ -159,7 +159,7 @@ __device__ __forceinline__ bool pair_adjoint(Pix &px, uint32_t idx, const float4
     const float iom = fast_rcp(1.0f - alpha);
     const float Ti = px.T * iom;
     const Cell<N> cell = grid_cell<N>(u, v, sigma, kN);
-    const Quad qd = grid_quad<N>(tex, cell);
+    const Quad qd = grid_quad<N, TexT>(tex, cell);
     float col[3];
     grid_colour<N>(qd, cell, col);
     col[0] += q3.y;
@@ -263,7 +263,7 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
     extern __shared__ float4 smem[];
     float4 *s_rec = smem;
     float4 *s_fp = s_rec + 4 * batch;  // [batch][3] footprints
-    float4 *s_tex = s_fp + 3 * batch;
+    staged_t<TexT> *s_tex = reinterpret_cast<staged_t<TexT> *>(s_fp + 3 * batch);
     int32_t *s_k = reinterpret_cast<int32_t *>(s_tex + batch * NN);
     uint32_t *s_j = reinterpret_cast<uint32_t *>(s_k + batch);
     uint2 *s_box = reinterpret_cast<uint2 *>(s_j + batch);
@@ -343,11 +343,11 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
 #pragma unroll
             for (int q = 0; q < 32; ++q) g[q] = 0.0f;
             Rem rem[P];
-            bool act = pair_adjoint<N, false>(pix[0], uint32_t(bs + i), s_rec + 4 * i, s_tex + i * NN, sigma, kN,
+            bool act = pair_adjoint<N, TexT, false>(pix[0], uint32_t(bs + i), s_rec + 4 * i, s_tex + i * NN, sigma, kN,
                                               g, rem[0], npairs, ncontrib);
 #pragma unroll
             for (int p = 1; p < P; ++p)
-                act |= pair_adjoint<N, true>(pix[p], uint32_t(bs + i), s_rec + 4 * i, s_tex + i * NN, sigma, kN,
+                act |= pair_adjoint<N, TexT, true>(pix[p], uint32_t(bs + i), s_rec + 4 * i, s_tex + i * NN, sigma, kN,
                                              g, rem[p], npairs, ncontrib);
             if (!__any_sync(0xffffffffu, act)) continue;
             const float tot = warp_reduce_scatter32(g, lane);
@@ -502,7 +502,7 @@ template <int TS, int N, typename TexT, int P>
 cudaError_t launch_t(const Frame &f, const RenderBwdBufs &b, int batch, TileSched ts, bool persistent,
                      cudaStream_t s) {
     constexpr int NT = TS * TS / P;
-    const size_t smem = stage_bytes<N>(batch, true);
+    const size_t smem = stage_bytes<N, TexT>(batch, true);
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(render_bwd_kernel<TS, N, TexT, P>,

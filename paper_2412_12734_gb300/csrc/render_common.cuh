@@ -14,14 +14,27 @@ __device__ __forceinline__ void tile_pixel(int tid, int &lx, int &ly) {
     ly = (warp / (TS / 8)) * 4 + (lane >> 3);
 }
 
+// A staged texel: FP32 grids as RGBA float4 (16 bytes, alpha unused: one
+// 128-bit shared load), FP16 and BF16 grids in their storage type as RGB + pad
+// (8 bytes: one 64-bit load, converted exactly to FP32 at use).
+template <typename TexT>
+struct StagedTexel {
+    using type = uint2;
+};
+template <>
+struct StagedTexel<float> {
+    using type = float4;
+};
+template <typename TexT>
+using staged_t = typename StagedTexel<TexT>::type;
+
 // Bytes of dynamic shared memory for one staged batch: records, footprints,
 // colour grids, splat indices, pixel rectangles, warp-block masks and (backward)
-// record/grid gradient accumulators.  Colour grids are staged as RGBA float4
-// texels (16 bytes, alpha unused) so a texel is one 128-bit shared load.
-template <int N>
+// record/grid gradient accumulators.
+template <int N, typename TexT>
 __host__ __device__ inline size_t stage_bytes(int batch, bool bwd) {
     const int texf = N * N * 3;
-    size_t b = size_t(batch) * (64 + 48 + 16 * N * N + 20);
+    size_t b = size_t(batch) * (64 + 48 + sizeof(staged_t<TexT>) * N * N + 20);
     if (bwd) b += size_t(batch) * (4 * kRecGrad + 4 * texf);
     return b;
 }
@@ -103,7 +116,7 @@ __device__ __forceinline__ bool block_hits(const float4 &q2, uint2 box, const fl
 template <int N, int NT, typename TexT, int TS, int BH>
 __device__ __forceinline__ void stage_batch(const RenderBufs &b, const CamDev &cam, const SceneDev &sc,
                                             uint32_t first, int nb, int tx0, int ty0, float4 *s_rec,
-                                            float4 *s_tex, int32_t *s_k, uint32_t *s_j, uint2 *s_box,
+                                            staged_t<TexT> *s_tex, int32_t *s_k, uint32_t *s_j, uint2 *s_box,
                                             uint32_t *s_mask, float4 *s_fp) {
     constexpr int NN = N * N;
     constexpr int NB = TS * TS / (8 * BH);  // warp blocks per tile: 1, 2, 4 or 8
@@ -143,7 +156,13 @@ __device__ __forceinline__ void stage_batch(const RenderBufs &b, const CamDev &c
     for (int e = t; e < nb * NN; e += NT) {
         const int s = e / NN, o = e - s * NN;
         const int64_t g = (int64_t(s_k[s]) * NN + o) * 3;
-        s_tex[e] = make_float4(load_as_float(tex, g), load_as_float(tex, g + 1), load_as_float(tex, g + 2), 0.0f);
+        if constexpr (sizeof(TexT) == 4) {
+            s_tex[e] = make_float4(load_as_float(tex, g), load_as_float(tex, g + 1), load_as_float(tex, g + 2), 0.0f);
+        } else {
+            // the stored 16-bit values, unconverted
+            const unsigned short *raw = reinterpret_cast<const unsigned short *>(tex);
+            s_tex[e] = make_uint2(uint32_t(raw[g]) | (uint32_t(raw[g + 1]) << 16), uint32_t(raw[g + 2]));
+        }
     }
 }
 
@@ -177,16 +196,27 @@ struct Quad {
     float4 c00, c10, c01, c11;
 };
 
-template <int N>
-__device__ __forceinline__ Quad grid_quad(const float4 *g, const Cell<N> &c) {
+// A staged texel as FP32 RGB (exact for FP16 / BF16 storage).
+__device__ __forceinline__ float4 texel_rgb(const float4 &t, float) { return t; }
+__device__ __forceinline__ float4 texel_rgb(const uint2 &t, __half) {
+    const float2 rg = __half22float2(*reinterpret_cast<const __half2 *>(&t.x));
+    return make_float4(rg.x, rg.y, __low2float(*reinterpret_cast<const __half2 *>(&t.y)), 0.0f);
+}
+__device__ __forceinline__ float4 texel_rgb(const uint2 &t, __nv_bfloat16) {
+    const float2 rg = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t.x));
+    return make_float4(rg.x, rg.y, __low2float(*reinterpret_cast<const __nv_bfloat162 *>(&t.y)), 0.0f);
+}
+
+template <int N, typename TexT>
+__device__ __forceinline__ Quad grid_quad(const staged_t<TexT> *g, const Cell<N> &c) {
     Quad q;
-    q.c00 = g[c.base];
+    q.c00 = texel_rgb(g[c.base], TexT());
     if (N == 1) {
         q.c10 = q.c01 = q.c11 = q.c00;
     } else {
-        q.c10 = g[c.base + N];
-        q.c01 = g[c.base + 1];
-        q.c11 = g[c.base + N + 1];
+        q.c10 = texel_rgb(g[c.base + N], TexT());
+        q.c01 = texel_rgb(g[c.base + 1], TexT());
+        q.c11 = texel_rgb(g[c.base + N + 1], TexT());
     }
     return q;
 }

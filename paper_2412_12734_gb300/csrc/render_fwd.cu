@@ -24,7 +24,7 @@ __device__ __forceinline__ void fwd_tile(const Frame &f, const RenderBufs &b, in
     extern __shared__ float4 smem[];
     float4 *s_rec = smem;
     float4 *s_fp = s_rec + 4 * batch;  // [batch][3] footprints
-    float4 *s_tex = s_fp + 3 * batch;
+    staged_t<TexT> *s_tex = reinterpret_cast<staged_t<TexT> *>(s_fp + 3 * batch);
     int32_t *s_k = reinterpret_cast<int32_t *>(s_tex + batch * NN);
     uint32_t *s_j = reinterpret_cast<uint32_t *>(s_k + batch);
     uint2 *s_box = reinterpret_cast<uint2 *>(s_j + batch);
@@ -81,7 +81,7 @@ __device__ __forceinline__ void fwd_tile(const Frame &f, const RenderBufs &b, in
             if (hit && !(tT < kTMin)) {
                 const Cell<N> cell = grid_cell<N>(u, v, sigma, kN);
                 float col[3];
-                grid_colour<N>(grid_quad<N>(s_tex + i * NN, cell), cell, col);
+                grid_colour<N>(grid_quad<N, TexT>(s_tex + i * NN, cell), cell, col);
                 const float w = alpha * T;
                 C0 = fmaf(col[0] + q3.y, w, C0);
                 C1 = fmaf(col[1] + q3.z, w, C1);
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(TS * TS, 1536 / (TS * TS)) render_fwd_kernel(F
 template <int TS, int N, typename TexT>
 cudaError_t launch_t(const Frame &f, const RenderBufs &b, int batch, TileSched ts, bool persistent,
                      cudaStream_t s) {
-    const size_t smem = stage_bytes<N>(batch, false);
+    const size_t smem = stage_bytes<N, TexT>(batch, false);
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(render_fwd_kernel<TS, N, TexT>,
