@@ -14,10 +14,11 @@
 //   Gaussian:  rho^ -> (u^, v^) on the uv branch, -> centre on the low-pass one
 //   intersection:   (u^, v^) -> zeta^ -> record (adj(T'), centre) gradients
 // Scatter: a thread first sums its P pixels' values; the 14 record gradients
-// and the RGB gradients of the grid's four corner texels (where the weight of
-// clamped (u, v) lands) go through one 32-value warp reduce-scatter; the
-// weights of edge and interior texels are reduced per grid cell (one 16-value
-// reduce-scatter per distinct cell of the warp) or, at N = 8 when many cells
+// and 12 texel values go through one 32-value warp reduce-scatter: at N = 2 the
+// four texels, at N = 4 the grid border line that holds most of the warp's
+// pixels (where the weight of a clamped u or v lands), at N >= 8 the four grid
+// corners; the other texel weights are reduced per grid cell (one 16-value
+// reduce-scatter per distinct cell of the warp) or, at N >= 8 when many cells
 // are hit, added to shared memory directly.  Per batch the per-splat sums
 // reach global memory with one atomic per value per tile.
 #pragma once
@@ -109,8 +110,10 @@ struct Pix {
     bool inside;
 };
 
-// Texel weights of one pixel that are not routed through the corner slots,
-// with the colour adjoint they multiply and the cell they belong to.
+// Texel weights of one pixel that the corner slots do not take (N = 4: the
+// four of its cell, routed through a border-line window of the reduce-scatter
+// or the per-cell pass; N >= 8: those off the grid corners), with the colour
+// adjoint they multiply and the cell they belong to.
 struct Rem {
     float w00, w10, w01, w11, c0, c1, c2;
     int base;
@@ -188,21 +191,37 @@ __device__ __forceinline__ bool pair_adjoint(Pix &px, uint32_t idx, const float4
         const float fvh = ch0 * ((qd.c01.x - qd.c00.x) * (1.0f - fu) + (qd.c11.x - qd.c10.x) * fu) +
                           ch1 * ((qd.c01.y - qd.c00.y) * (1.0f - fu) + (qd.c11.y - qd.c10.y) * fu) +
                           ch2 * ((qd.c01.z - qd.c00.z) * (1.0f - fu) + (qd.c11.z - qd.c10.z) * fu);
-        // weights landing on a grid-corner texel go to the warp-reduced corner
-        // slots; the rest (edge and interior texels) to the per-cell pass
-        const int iu = cell.base / N, iv = cell.base - iu * N;
-        const float wc0 = (iu == 0 && iv == 0) ? w00 : 0.0f;
-        const float wc1 = (iu == 0 && iv == N - 2) ? w01 : 0.0f;
-        const float wc2 = (iu == N - 2 && iv == 0) ? w10 : 0.0f;
-        const float wc3 = (iu == N - 2 && iv == N - 2) ? w11 : 0.0f;
-        put<ACC>(g[kCornerSlot + 0], wc0 * ch0); put<ACC>(g[kCornerSlot + 1], wc0 * ch1); put<ACC>(g[kCornerSlot + 2], wc0 * ch2);
-        put<ACC>(g[kCornerSlot + 3], wc1 * ch0); put<ACC>(g[kCornerSlot + 4], wc1 * ch1); put<ACC>(g[kCornerSlot + 5], wc1 * ch2);
-        put<ACC>(g[kCornerSlot + 6], wc2 * ch0); put<ACC>(g[kCornerSlot + 7], wc2 * ch1); put<ACC>(g[kCornerSlot + 8], wc2 * ch2);
-        put<ACC>(g[kCornerSlot + 9], wc3 * ch0); put<ACC>(g[kCornerSlot + 10], wc3 * ch1); put<ACC>(g[kCornerSlot + 11], wc3 * ch2);
-        rem.w00 = w00 - wc0;
-        rem.w10 = w10 - wc2;
-        rem.w01 = w01 - wc1;
-        rem.w11 = w11 - wc3;
+        if (N == 2) {
+            // every texel of a 2 x 2 grid is a corner: all four weights go to the
+            // warp-reduced corner slots
+            put<ACC>(g[kCornerSlot + 0], w00 * ch0); put<ACC>(g[kCornerSlot + 1], w00 * ch1); put<ACC>(g[kCornerSlot + 2], w00 * ch2);
+            put<ACC>(g[kCornerSlot + 3], w01 * ch0); put<ACC>(g[kCornerSlot + 4], w01 * ch1); put<ACC>(g[kCornerSlot + 5], w01 * ch2);
+            put<ACC>(g[kCornerSlot + 6], w10 * ch0); put<ACC>(g[kCornerSlot + 7], w10 * ch1); put<ACC>(g[kCornerSlot + 8], w10 * ch2);
+            put<ACC>(g[kCornerSlot + 9], w11 * ch0); put<ACC>(g[kCornerSlot + 10], w11 * ch1); put<ACC>(g[kCornerSlot + 11], w11 * ch2);
+        } else if (N == 4) {
+            // the warp routes these through a border-line window of the
+            // reduce-scatter (line_window) or the per-cell pass
+            rem.w00 = w00;
+            rem.w10 = w10;
+            rem.w01 = w01;
+            rem.w11 = w11;
+        } else {
+            // weights landing on a grid-corner texel go to the warp-reduced
+            // corner slots; the rest (edge and interior texels) to the per-cell pass
+            const int iu = cell.base / N, iv = cell.base - iu * N;
+            const float wc0 = (iu == 0 && iv == 0) ? w00 : 0.0f;
+            const float wc1 = (iu == 0 && iv == N - 2) ? w01 : 0.0f;
+            const float wc2 = (iu == N - 2 && iv == 0) ? w10 : 0.0f;
+            const float wc3 = (iu == N - 2 && iv == N - 2) ? w11 : 0.0f;
+            put<ACC>(g[kCornerSlot + 0], wc0 * ch0); put<ACC>(g[kCornerSlot + 1], wc0 * ch1); put<ACC>(g[kCornerSlot + 2], wc0 * ch2);
+            put<ACC>(g[kCornerSlot + 3], wc1 * ch0); put<ACC>(g[kCornerSlot + 4], wc1 * ch1); put<ACC>(g[kCornerSlot + 5], wc1 * ch2);
+            put<ACC>(g[kCornerSlot + 6], wc2 * ch0); put<ACC>(g[kCornerSlot + 7], wc2 * ch1); put<ACC>(g[kCornerSlot + 8], wc2 * ch2);
+            put<ACC>(g[kCornerSlot + 9], wc3 * ch0); put<ACC>(g[kCornerSlot + 10], wc3 * ch1); put<ACC>(g[kCornerSlot + 11], wc3 * ch2);
+            rem.w00 = w00 - wc0;
+            rem.w10 = w10 - wc2;
+            rem.w01 = w01 - wc1;
+            rem.w11 = w11 - wc3;
+        }
         rem.base = cell.base;
         rem.c0 = ch0;
         rem.c1 = ch1;
@@ -253,6 +272,75 @@ __device__ __forceinline__ bool pair_adjoint(Pix &px, uint32_t idx, const float4
     put<ACC>(g[8], -dxh);
     put<ACC>(g[9], -dyh);
     return true;
+}
+
+// Grids of N = 4: texel weights on one border line of the grid go through
+// slots 14..25 of the 32-value reduce-scatter.  The weights of a pixel whose
+// u (v) is clamped to the grid's border lie on the first or last column
+// i_u = 0, N-1 (row i_v = 0, N-1): two texels at cell indices (i, i+1) along
+// it.  The line holding most of the warp's pixels is taken, with a window of
+// four texels from the smallest cell index among them (the whole line at
+// N = 4); the weights of the pixels inside the window move to the slots
+// (window position q, channel c: slot 14 + 3q + c) and leave the per-cell
+// pass.  Returns the texel index of window position 0 and the step between
+// positions (0, 0: no line).  Measured on the 1M-splat, 16-view workload: the
+// backward 44.8 -> 41.3 ms at N = 4; at N = 8 and 16, where four texels cover
+// part of a line, slower than corner slots (55.8 against 54.2 ms, 85.5
+// against 79.6 ms), so larger grids keep those.
+template <int N, int P>
+__device__ __forceinline__ void line_window(Rem rem[P], float g[32], int &t0, int &step) {
+    constexpr int LOG2N = N == 4 ? 2 : N == 8 ? 3 : 4;
+    bool on[P][4];
+    int cnt[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const Rem &r = rem[p];
+        const bool has = r.any();
+        const int iu = r.base >> LOG2N, iv = r.base & (N - 1);
+        on[p][0] = has && iu == 0 && r.w10 == 0.0f && r.w11 == 0.0f;
+        on[p][1] = has && iu == N - 2 && r.w00 == 0.0f && r.w01 == 0.0f;
+        on[p][2] = has && iv == 0 && r.w01 == 0.0f && r.w11 == 0.0f;
+        on[p][3] = has && iv == N - 2 && r.w00 == 0.0f && r.w10 == 0.0f;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) cnt[l] += __popc(__ballot_sync(0xffffffffu, on[p][l]));
+    }
+    int L = 0;
+#pragma unroll
+    for (int l = 1; l < 4; ++l)
+        if (cnt[l] > cnt[L]) L = l;
+    t0 = step = 0;
+    if (cnt[L] == 0) return;
+    // positions along the line: i_v on a column, i_u on a row
+    int pos[P];
+    bool mem[P];
+    int mn = N;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        mem[p] = L == 0 ? on[p][0] : L == 1 ? on[p][1] : L == 2 ? on[p][2] : on[p][3];
+        pos[p] = L < 2 ? (rem[p].base & (N - 1)) : (rem[p].base >> LOG2N);
+        if (mem[p]) mn = min(mn, pos[p]);
+    }
+    const int s = min(int(__reduce_min_sync(0xffffffffu, unsigned(mn))), N - 4);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        Rem &r = rem[p];
+        if (!(mem[p] && pos[p] <= s + 2)) continue;
+        // the two weights along the line, at window positions rel and rel + 1
+        const float wa = L == 0 ? r.w00 : L == 1 ? r.w10 : L == 2 ? r.w00 : r.w01;
+        const float wb = L == 0 ? r.w01 : L == 1 ? r.w11 : L == 2 ? r.w10 : r.w11;
+        const int rel = pos[p] - s;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float w = q == rel ? wa : (q == rel + 1 ? wb : 0.0f);
+            g[kCornerSlot + 3 * q + 0] = fmaf(w, r.c0, g[kCornerSlot + 3 * q + 0]);
+            g[kCornerSlot + 3 * q + 1] = fmaf(w, r.c1, g[kCornerSlot + 3 * q + 1]);
+            g[kCornerSlot + 3 * q + 2] = fmaf(w, r.c2, g[kCornerSlot + 3 * q + 2]);
+        }
+        r.w00 = r.w10 = r.w01 = r.w11 = 0.0f;
+    }
+    // texel (i_u, i_v) of window position 0, and the index step along the line
+    t0 = L == 0 ? s : L == 1 ? (N - 1) * N + s : L == 2 ? s * N : s * N + N - 1;
+    step = L < 2 ? 1 : N;
 }
 
 template <int TS, int N, typename TexT, int P>
@@ -326,6 +414,8 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
     const int my_corner_off = my_corner < 0 ? 0
                               : 3 * ((my_corner & 2 ? (N - 1) * N : 0) + (my_corner & 1 ? N - 1 : 0)) +
                                     (lane - kCornerSlot) % 3;
+    // N = 4: window position and channel of this lane's reduced slot
+    const int my_q = (lane - kCornerSlot) / 3, my_c = (lane - kCornerSlot) - 3 * ((lane - kCornerSlot) / 3);
 
     for (int be = max_last; be > 0; be -= batch) {
         const int bs = max(0, be - batch), nb = be - bs;
@@ -350,10 +440,14 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
                 act |= pair_adjoint<N, TexT, true>(pix[p], uint32_t(bs + i), s_rec + 4 * i, s_tex + i * NN, sigma, kN,
                                              g, rem[p], npairs, ncontrib);
             if (!__any_sync(0xffffffffu, act)) continue;
+            int t0 = 0, step = 0;
+            if (N == 4) line_window<N, P>(rem, g, t0, step);
             const float tot = warp_reduce_scatter32(g, lane);
             if (tot != 0.0f) {
                 if (lane < kCornerSlot) atomicAdd(s_g + i * kRecGrad + lane, tot);
-                else if (my_corner >= 0) atomicAdd(s_tg + i * TEXF + my_corner_off, tot);
+                else if (N == 4 && lane < kCornerSlot + 12)
+                    atomicAdd(s_tg + i * TEXF + 3 * (t0 + my_q * step) + my_c, tot);
+                else if (N != 4 && my_corner >= 0) atomicAdd(s_tg + i * TEXF + my_corner_off, tot);
             }
             if (N > 2) {
                 // edge / interior texels: lanes sharing a cell touch the same four
