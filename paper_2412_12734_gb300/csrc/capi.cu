@@ -201,12 +201,13 @@ int default_batch(const Frame &f) {
     return std::max(b, 8);
 }
 
+// (the forward stages grids of N <= 4 as FP32 RGBA)
 template <typename TexT>
 size_t batch_smem_t(int N, int batch, bool bwd) {
     switch (N) {
-        case 1: return stage_bytes<1, TexT>(batch, bwd);
-        case 2: return stage_bytes<2, TexT>(batch, bwd);
-        case 4: return stage_bytes<4, TexT>(batch, bwd);
+        case 1: return bwd ? stage_bytes<1, TexT>(batch, true) : stage_bytes<1, TexT, true>(batch, false);
+        case 2: return bwd ? stage_bytes<2, TexT>(batch, true) : stage_bytes<2, TexT, true>(batch, false);
+        case 4: return bwd ? stage_bytes<4, TexT>(batch, true) : stage_bytes<4, TexT, true>(batch, false);
         case 8: return stage_bytes<8, TexT>(batch, bwd);
         default: return stage_bytes<16, TexT>(batch, bwd);
     }

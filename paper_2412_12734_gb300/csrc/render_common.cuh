@@ -1,6 +1,8 @@
 // Per-tile render helpers shared by the forward and backward kernels.
 #pragma once
 
+#include <type_traits>
+
 #include "gbill_internal.cuh"
 
 namespace gbill {
@@ -14,27 +16,22 @@ __device__ __forceinline__ void tile_pixel(int tid, int &lx, int &ly) {
     ly = (warp / (TS / 8)) * 4 + (lane >> 3);
 }
 
-// A staged texel: FP32 grids as RGBA float4 (16 bytes, alpha unused: one
-// 128-bit shared load), FP16 and BF16 grids in their storage type as RGB + pad
-// (8 bytes: one 64-bit load, converted exactly to FP32 at use).
-template <typename TexT>
-struct StagedTexel {
-    using type = uint2;
-};
-template <>
-struct StagedTexel<float> {
-    using type = float4;
-};
-template <typename TexT>
-using staged_t = typename StagedTexel<TexT>::type;
+// A staged texel: FP32 grids, and with WIDE any grid, as RGBA float4 (16
+// bytes, alpha unused: one 128-bit shared load); otherwise FP16 and BF16 grids
+// in their storage type as RGB + pad (8 bytes: one 64-bit load, converted
+// exactly to FP32 at use).  The forward stages grids of N <= 4 wide (its
+// shared memory has room, and the lookups skip the conversion); the backward,
+// whose staging also holds gradient accumulators, stages them narrow.
+template <typename TexT, bool WIDE = false>
+using staged_t = typename std::conditional<WIDE || sizeof(TexT) == 4, float4, uint2>::type;
 
 // Bytes of dynamic shared memory for one staged batch: records, footprints,
 // colour grids, splat indices, pixel rectangles, warp-block masks and (backward)
 // record/grid gradient accumulators.
-template <int N, typename TexT>
+template <int N, typename TexT, bool WIDE = false>
 __host__ __device__ inline size_t stage_bytes(int batch, bool bwd) {
     const int texf = N * N * 3;
-    size_t b = size_t(batch) * (64 + 48 + sizeof(staged_t<TexT>) * N * N + 20);
+    size_t b = size_t(batch) * (64 + 48 + sizeof(staged_t<TexT, WIDE>) * N * N + 20);
     if (bwd) b += size_t(batch) * (4 * kRecGrad + 4 * texf);
     return b;
 }
@@ -113,11 +110,11 @@ __device__ __forceinline__ bool block_hits(const float4 &q2, uint2 box, const fl
 // tile range into shared memory, and for every splat the mask of the tile's
 // 8 x BH warp blocks (row-major, TS/8 per row) that its footprint may touch
 // (block_hits).  Caller synchronizes before and after.
-template <int N, int NT, typename TexT, int TS, int BH>
+template <int N, int NT, typename TexT, int TS, int BH, bool WIDE = false>
 __device__ __forceinline__ void stage_batch(const RenderBufs &b, const CamDev &cam, const SceneDev &sc,
                                             uint32_t first, int nb, int tx0, int ty0, float4 *s_rec,
-                                            staged_t<TexT> *s_tex, int32_t *s_k, uint32_t *s_j, uint2 *s_box,
-                                            uint32_t *s_mask, float4 *s_fp) {
+                                            staged_t<TexT, WIDE> *s_tex, int32_t *s_k, uint32_t *s_j,
+                                            uint2 *s_box, uint32_t *s_mask, float4 *s_fp) {
     constexpr int NN = N * N;
     constexpr int NB = TS * TS / (8 * BH);  // warp blocks per tile: 1, 2, 4 or 8
     static_assert(32 % NB == 0 && NT % 32 == 0, "block masks are gathered within a warp");
@@ -156,7 +153,7 @@ __device__ __forceinline__ void stage_batch(const RenderBufs &b, const CamDev &c
     for (int e = t; e < nb * NN; e += NT) {
         const int s = e / NN, o = e - s * NN;
         const int64_t g = (int64_t(s_k[s]) * NN + o) * 3;
-        if constexpr (sizeof(TexT) == 4) {
+        if constexpr (sizeof(staged_t<TexT, WIDE>) == 16) {
             s_tex[e] = make_float4(load_as_float(tex, g), load_as_float(tex, g + 1), load_as_float(tex, g + 2), 0.0f);
         } else {
             // the stored 16-bit values, unconverted
@@ -197,7 +194,10 @@ struct Quad {
 };
 
 // A staged texel as FP32 RGB (exact for FP16 / BF16 storage).
-__device__ __forceinline__ float4 texel_rgb(const float4 &t, float) { return t; }
+template <typename T>
+__device__ __forceinline__ float4 texel_rgb(const float4 &t, T) {
+    return t;
+}
 __device__ __forceinline__ float4 texel_rgb(const uint2 &t, __half) {
     const float2 rg = __half22float2(*reinterpret_cast<const __half2 *>(&t.x));
     return make_float4(rg.x, rg.y, __low2float(*reinterpret_cast<const __half2 *>(&t.y)), 0.0f);
@@ -207,8 +207,8 @@ __device__ __forceinline__ float4 texel_rgb(const uint2 &t, __nv_bfloat16) {
     return make_float4(rg.x, rg.y, __low2float(*reinterpret_cast<const __nv_bfloat162 *>(&t.y)), 0.0f);
 }
 
-template <int N, typename TexT>
-__device__ __forceinline__ Quad grid_quad(const staged_t<TexT> *g, const Cell<N> &c) {
+template <int N, typename TexT, bool WIDE = false>
+__device__ __forceinline__ Quad grid_quad(const staged_t<TexT, WIDE> *g, const Cell<N> &c) {
     Quad q;
     q.c00 = texel_rgb(g[c.base], TexT());
     if (N == 1) {

@@ -24,7 +24,8 @@ __device__ __forceinline__ void fwd_tile(const Frame &f, const RenderBufs &b, in
     extern __shared__ float4 smem[];
     float4 *s_rec = smem;
     float4 *s_fp = s_rec + 4 * batch;  // [batch][3] footprints
-    staged_t<TexT> *s_tex = reinterpret_cast<staged_t<TexT> *>(s_fp + 3 * batch);
+    constexpr bool WIDE = N <= 4;  // grids staged as FP32 RGBA (room to spare in the forward)
+    staged_t<TexT, WIDE> *s_tex = reinterpret_cast<staged_t<TexT, WIDE> *>(s_fp + 3 * batch);
     int32_t *s_k = reinterpret_cast<int32_t *>(s_tex + batch * NN);
     uint32_t *s_j = reinterpret_cast<uint32_t *>(s_k + batch);
     uint2 *s_box = reinterpret_cast<uint2 *>(s_j + batch);
@@ -52,7 +53,7 @@ __device__ __forceinline__ void fwd_tile(const Frame &f, const RenderBufs &b, in
     for (int bs = 0; bs < n_inst; bs += batch) {
         if (__syncthreads_count(done) == NT) break;
         const int nb = min(batch, n_inst - bs);
-        stage_batch<N, NT, TexT, TS, 4>(b, cam, sc, range.x + bs, nb, tx * TS, ty * TS, s_rec, s_tex, s_k, s_j,
+        stage_batch<N, NT, TexT, TS, 4, WIDE>(b, cam, sc, range.x + bs, nb, tx * TS, ty * TS, s_rec, s_tex, s_k, s_j,
                                         s_box, s_mask, s_fp);
         __syncthreads();
         // The warp's mask bit is uniform: a splat that misses the warp's block
@@ -81,7 +82,7 @@ __device__ __forceinline__ void fwd_tile(const Frame &f, const RenderBufs &b, in
             if (hit && !(tT < kTMin)) {
                 const Cell<N> cell = grid_cell<N>(u, v, sigma, kN);
                 float col[3];
-                grid_colour<N>(grid_quad<N, TexT>(s_tex + i * NN, cell), cell, col);
+                grid_colour<N>(grid_quad<N, TexT, WIDE>(s_tex + i * NN, cell), cell, col);
                 const float w = alpha * T;
                 C0 = fmaf(col[0] + q3.y, w, C0);
                 C1 = fmaf(col[1] + q3.z, w, C1);
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(TS * TS, 1536 / (TS * TS)) render_fwd_kernel(F
 template <int TS, int N, typename TexT>
 cudaError_t launch_t(const Frame &f, const RenderBufs &b, int batch, TileSched ts, bool persistent,
                      cudaStream_t s) {
-    const size_t smem = stage_bytes<N, TexT>(batch, false);
+    const size_t smem = stage_bytes<N, TexT, (N <= 4)>(batch, false);
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(render_fwd_kernel<TS, N, TexT>,
