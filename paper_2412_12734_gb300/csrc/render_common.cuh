@@ -118,8 +118,7 @@ __device__ __forceinline__ void stage_batch(const RenderBufs &b, const CamDev &c
     constexpr int NN = N * N;
     constexpr int NB = TS * TS / (8 * BH);  // warp blocks per tile: 1, 2, 4 or 8
     static_assert(32 % NB == 0 && NT % 32 == 0, "block masks are gathered within a warp");
-    const int t = threadIdx.x;
-    if (t < nb) {
+    for (int t = threadIdx.x; t < nb; t += NT) {  // a batch deeper than the block: two or more per thread
         const uint32_t j = b.inst_val[first + t];
         const uint32_t r = b.perm[j];
         s_box[t] = b.pbox[r];
@@ -139,6 +138,7 @@ __device__ __forceinline__ void stage_batch(const RenderBufs &b, const CamDev &c
         s_fp[3 * t + 2] = k[2];
     }
     __syncthreads();
+    const int t = threadIdx.x;
     for (int base = 0; base < nb * NB; base += NT) {
         const int e = base + t, s = e / NB, w = e - s * NB;
         bool hit = false;
