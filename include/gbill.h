@@ -177,8 +177,10 @@ typedef struct {
  * returns them. */
 typedef enum {
     GB_PHASE_PREPROCESS = 0, /* grid pre-passes (mip filter, per-texel SH grids);
-                                homography, FP32 rectangle, depth key, SH colour */
-    GB_PHASE_DEPTH_SORT,     /* radix sort of records by depth                    */
+                                culling, FP32 rectangle, depth key, SH colour;
+                                compaction of the visible records and their
+                                homography records                           */
+    GB_PHASE_DEPTH_SORT,     /* radix sort of the visible records by depth        */
     GB_PHASE_COUNT_SCAN,     /* exclusive scan of per-record tile counts          */
     GB_PHASE_EMIT,           /* (tile, splat) duplication                         */
     GB_PHASE_TILE_SORT,      /* stable radix sort of instances by tile            */

@@ -668,11 +668,13 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
     GB_CUDA(ctx, cudaMemsetAsync(s->cnt, 0, sizeof(Counters), st));
     GB_CUDA(ctx, cudaMemsetAsync(s->ranges, 0, size_t(f.n_tiles) * sizeof(uint2), st));
     GB_CUDA(ctx, launch_preprocess(f, max_k, s->depth_key, s->rec_id, s->rect, s->pbox, s->rec, s->cnt, st));
-    GB_MARK(1);
-    // visible records to the front in record order, then sorted by depth
-    // (stable, so equal depths keep record order)
+    // visible records to the front in record order; their records' homography
+    // part, one thread per visible record; then sorted by depth (stable, so
+    // equal depths keep record order)
     GB_CUDA(ctx, compact_visible(s->depth_key, R, s->offsets, s->dkeys_sorted, s->perm, s->scratch, s->scratch_bytes,
                                  st));
+    GB_CUDA(ctx, launch_record(f, s->perm, &s->cnt->n_visible, nullptr, R, s->rec, st));
+    GB_MARK(1);
     GB_CUDA(ctx, radix_sort_pairs(s->dkeys_sorted, s->perm, s->keys_tmp, s->vals_tmp, s->dkeys_sorted, s->perm, R,
                                   &s->cnt->n_visible, 0, 32, s->scratch, s->scratch_bytes, st));
     GB_MARK(2);
@@ -940,6 +942,7 @@ gb_status gb_render_forward_noalloc(gb_context *ctx, const gb_scene *scenes, int
     GB_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(Counters), st));
     GB_CUDA(ctx, cudaMemsetAsync(ranges, 0, size_t(f.n_tiles) * sizeof(uint2), st));
     GB_CUDA(ctx, launch_preprocess(f, max_k, depth_key, rec_id, rect, pbox, rec, cnt, st));
+    GB_CUDA(ctx, launch_record(f, nullptr, nullptr, depth_key, R, rec, st));
     GB_CUDA(ctx, radix_sort_pairs(depth_key, rec_id, keys_tmp, vals_tmp, dkeys_sorted, perm, R, nullptr, 0, 32,
                                   scratch, kNaRadixBytes, st));
     GB_CUDA(ctx, tile_counts_scan(f, perm, rect, R, &cnt->n_visible, offsets, scratch, kNaRadixBytes, cnt,

@@ -136,11 +136,26 @@ __device__ __forceinline__ int camera_of_tile(const Frame &f, uint32_t tile) {
     return lo;
 }
 
+// Camera of record r (records are camera-major: camera c owns [rec_off, rec_off + K)).
+__device__ __forceinline__ int camera_of_record(const Frame &f, int64_t r) {
+    int lo = 0, hi = f.n_cams - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (f.cams[mid].rec_off <= r) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // ------------------------------------------------------- host-side launchers --
 
 // preprocess.cu
 cudaError_t launch_preprocess(const Frame &f, int64_t max_k, uint32_t *depth_key, uint32_t *rec_id,
                               uint2 *rect, uint2 *pbox, Record *rec, Counters *cnt, cudaStream_t s);
+// Homography part (q0..q2) of the render records: of ids[0 .. *n_dev) or,
+// with ids NULL, of every record whose depth key is not the culled marker.
+cudaError_t launch_record(const Frame &f, const uint32_t *ids, const uint32_t *n_dev, const uint32_t *depth_key,
+                          int64_t max_n, Record *rec, cudaStream_t s);
 cudaError_t launch_preprocess_bwd(const Frame &f, int64_t max_k, const float *rec_grad,
                                   const int32_t *inv_perm, cudaStream_t s);
 

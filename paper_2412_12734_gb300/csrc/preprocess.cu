@@ -276,67 +276,93 @@ __global__ void __launch_bounds__(256, 4) preprocess_kernel(Frame f, uint32_t *d
             rect_out[r] = make_uint2(uint32_t(pr[0] / T) | (uint32_t(pr[1] / T) << 16),
                                      uint32_t(pr[2] / T) | (uint32_t(pr[3] / T) << 16));
             pbox[r] = make_uint2(uint32_t(pr[0]) | (uint32_t(pr[1]) << 16), uint32_t(pr[2]) | (uint32_t(pr[3]) << 16));
-            // ---- render record ----
-            // The whole record chain in double-float (~48 bits): unit quaternion,
-            // tangent frame, camera-space axes A = s_u R t_u, B = s_v R t_v,
-            // normal n = A x B = s_u s_v R t_w, centre P, centre-relative block t
-            // and m = (fy n_x, fx n_y, fx fy n.P / z) / z.  Only n.P cancels (grazing
-            // view); below cos = 1/256 the block is redone in FP64.
-            DF qn2 = two_prod(q[0], q[0]);
-            for (int i = 1; i < 4; ++i) qn2 = df_add(qn2, two_prod(q[i], q[i]));
-            const DF qinv = df_div(DF{1.0f, 0.0f}, df_sqrt(qn2));
-            const DF w = df_mul_f(qinv, q[0]), x = df_mul_f(qinv, q[1]), y = df_mul_f(qinv, q[2]),
-                     zq = df_mul_f(qinv, q[3]);
-            const DF xx = df_mul(x, x), yy = df_mul(y, y), zz = df_mul(zq, zq), xy = df_mul(x, y), xzq = df_mul(x, zq),
-                     yzq = df_mul(y, zq), wx = df_mul(w, x), wy = df_mul(w, y), wz = df_mul(w, zq);
-            const DF tu[3] = {df_one_minus_twice(df_add(yy, zz)), df_twice(df_add(xy, wz)), df_twice(df_sub(xzq, wy))};
-            const DF tv[3] = {df_twice(df_sub(xy, wz)), df_one_minus_twice(df_add(xx, zz)), df_twice(df_add(yzq, wx))};
-            const DF tw[3] = {df_twice(df_add(xzq, wy)), df_twice(df_sub(yzq, wx)), df_one_minus_twice(df_add(xx, yy))};
-            const DF suv = two_prod(su, sv);
-            DF A[3], B[3], nv[3];
-            for (int i = 0; i < 3; ++i) {
-                const float *row = cam.R + 3 * i;
-                A[i] = df_mul_f(df_dot_fd(row, tu), su);
-                B[i] = df_mul_f(df_dot_fd(row, tv), sv);
-                nv[i] = df_mul(df_dot_fd(row, tw), suv);
-            }
-            const DF Px = df_affine(cam.R + 0, p, cam.t[0]);
-            const DF Py = df_affine(cam.R + 3, p, cam.t[1]);
-            const DF Pz = df_affine(cam.R + 6, p, cam.t[2]);
-            const DF xz = df_div(Px, Pz), yz = df_div(Py, Pz);
-            const DF cxd = df_add(df_mul_f(xz, cam.fx), DF{cam.cx, 0.0f});
-            const DF cyd = df_add(df_mul_f(yz, cam.fy), DF{cam.cy, 0.0f});
-            const float z = Pz.hi;
-            DF np = df_mul(nv[0], Px);
-            np = df_add(np, df_mul(nv[1], Py));
-            np = df_add(np, df_mul(nv[2], Pz));
-            const float nmag = fabsf(nv[0].hi * Px.hi) + fabsf(nv[1].hi * Py.hi) + fabsf(nv[2].hi * Pz.hi);
-            float t00, t01, t10, t11, m20, m21, m22;
-            if (fabsf(np.hi) * 256.0f > nmag) {
-                t00 = df_mul_f(df_sub(A[0], df_mul(A[2], xz)), cam.fx).hi;
-                t01 = df_mul_f(df_sub(B[0], df_mul(B[2], xz)), cam.fx).hi;
-                t10 = df_mul_f(df_sub(A[1], df_mul(A[2], yz)), cam.fy).hi;
-                t11 = df_mul_f(df_sub(B[1], df_mul(B[2], yz)), cam.fy).hi;
-                m20 = df_div(df_mul_f(nv[0], cam.fy), Pz).hi;
-                m21 = df_div(df_mul_f(nv[1], cam.fx), Pz).hi;
-                m22 = df_div(df_div(df_mul(np, two_prod(cam.fx, cam.fy)), Pz), Pz).hi;
-            } else {
-                float t[4], m[3];
-                homography_fp64(p, q, su, sv, cam, t, m);
-                t00 = t[0]; t01 = t[1]; t10 = t[2]; t11 = t[3];
-                m20 = m[0]; m21 = m[1]; m22 = m[2];
-            }
-            Record R;
-            R.q0 = make_float4(t11, -t01, -t10, t00);
-            R.q1 = make_float4(m20, m21, m22, z);
-            R.q2 = make_float4(cxd.hi, cyd.hi, cxd.lo, cyd.lo);
-            R.q3 = make_float4(o, rgb[0], rgb[1], rgb[2]);
-            rec_out[r] = R;
+            // the render record's opacity and SH colour; its homography part
+            // (q0..q2) is built by record_kernel for the visible records only
+            rec_out[r].q3 = make_float4(o, rgb[0], rgb[1], rgb[2]);
         }
     }
     // warp-aggregated visible count
     const unsigned m = __ballot_sync(0xffffffffu, valid);
     if ((threadIdx.x & 31) == 0 && m) atomicAdd(&cnt->n_visible, uint32_t(__popc(m)));
+}
+
+// ------------------------------------------------------- record kernel --
+// The homography part of the render record (q0..q2) of record r: the whole
+// record chain in double-float (~48 bits): unit quaternion, tangent frame,
+// camera-space axes A = s_u R t_u, B = s_v R t_v, normal n = A x B = s_u s_v
+// R t_w, centre P, centre-relative block t and m = (fy n_x, fx n_y, fx fy n.P
+// / z) / z.  Only n.P cancels (grazing view); below cos = 1/256 the block is
+// redone in FP64.
+__device__ __forceinline__ void record_homography(const Frame &f, int64_t r, Record *rec_out) {
+    const int ci = camera_of_record(f, r);
+    const CamDev &cam = f.cams[ci];
+    const SceneDev &sc = f.scenes[cam.scene];
+    const int64_t k = r - cam.rec_off;
+    float p[3], q[4];
+    for (int i = 0; i < 3; ++i) p[i] = sc.means[3 * k + i];
+    for (int i = 0; i < 4; ++i) q[i] = sc.quats[4 * k + i];
+    const float su = sc.scales[2 * k], sv = sc.scales[2 * k + 1];
+    DF qn2 = two_prod(q[0], q[0]);
+    for (int i = 1; i < 4; ++i) qn2 = df_add(qn2, two_prod(q[i], q[i]));
+    const DF qinv = df_div(DF{1.0f, 0.0f}, df_sqrt(qn2));
+    const DF w = df_mul_f(qinv, q[0]), x = df_mul_f(qinv, q[1]), y = df_mul_f(qinv, q[2]),
+             zq = df_mul_f(qinv, q[3]);
+    const DF xx = df_mul(x, x), yy = df_mul(y, y), zz = df_mul(zq, zq), xy = df_mul(x, y), xzq = df_mul(x, zq),
+             yzq = df_mul(y, zq), wx = df_mul(w, x), wy = df_mul(w, y), wz = df_mul(w, zq);
+    const DF tu[3] = {df_one_minus_twice(df_add(yy, zz)), df_twice(df_add(xy, wz)), df_twice(df_sub(xzq, wy))};
+    const DF tv[3] = {df_twice(df_sub(xy, wz)), df_one_minus_twice(df_add(xx, zz)), df_twice(df_add(yzq, wx))};
+    const DF tw[3] = {df_twice(df_add(xzq, wy)), df_twice(df_sub(yzq, wx)), df_one_minus_twice(df_add(xx, yy))};
+    const DF suv = two_prod(su, sv);
+    DF A[3], B[3], nv[3];
+    for (int i = 0; i < 3; ++i) {
+        const float *row = cam.R + 3 * i;
+        A[i] = df_mul_f(df_dot_fd(row, tu), su);
+        B[i] = df_mul_f(df_dot_fd(row, tv), sv);
+        nv[i] = df_mul(df_dot_fd(row, tw), suv);
+    }
+    const DF Px = df_affine(cam.R + 0, p, cam.t[0]);
+    const DF Py = df_affine(cam.R + 3, p, cam.t[1]);
+    const DF Pz = df_affine(cam.R + 6, p, cam.t[2]);
+    const DF xz = df_div(Px, Pz), yz = df_div(Py, Pz);
+    const DF cxd = df_add(df_mul_f(xz, cam.fx), DF{cam.cx, 0.0f});
+    const DF cyd = df_add(df_mul_f(yz, cam.fy), DF{cam.cy, 0.0f});
+    const float z = Pz.hi;
+    DF np = df_mul(nv[0], Px);
+    np = df_add(np, df_mul(nv[1], Py));
+    np = df_add(np, df_mul(nv[2], Pz));
+    const float nmag = fabsf(nv[0].hi * Px.hi) + fabsf(nv[1].hi * Py.hi) + fabsf(nv[2].hi * Pz.hi);
+    float t00, t01, t10, t11, m20, m21, m22;
+    if (fabsf(np.hi) * 256.0f > nmag) {
+        t00 = df_mul_f(df_sub(A[0], df_mul(A[2], xz)), cam.fx).hi;
+        t01 = df_mul_f(df_sub(B[0], df_mul(B[2], xz)), cam.fx).hi;
+        t10 = df_mul_f(df_sub(A[1], df_mul(A[2], yz)), cam.fy).hi;
+        t11 = df_mul_f(df_sub(B[1], df_mul(B[2], yz)), cam.fy).hi;
+        m20 = df_div(df_mul_f(nv[0], cam.fy), Pz).hi;
+        m21 = df_div(df_mul_f(nv[1], cam.fx), Pz).hi;
+        m22 = df_div(df_div(df_mul(np, two_prod(cam.fx, cam.fy)), Pz), Pz).hi;
+    } else {
+        float t[4], m[3];
+        homography_fp64(p, q, su, sv, cam, t, m);
+        t00 = t[0]; t01 = t[1]; t10 = t[2]; t11 = t[3];
+        m20 = m[0]; m21 = m[1]; m22 = m[2];
+    }
+    Record &R = rec_out[r];
+    R.q0 = make_float4(t11, -t01, -t10, t00);
+    R.q1 = make_float4(m20, m21, m22, z);
+    R.q2 = make_float4(cxd.hi, cyd.hi, cxd.lo, cyd.lo);
+}
+
+// One thread per visible record: ids[j] for j < *n_dev (the compacted visible
+// records), or, without ids, every record whose depth key is not the culled
+// marker.
+__global__ void __launch_bounds__(128) record_kernel(Frame f, const uint32_t *ids, const uint32_t *n_dev,
+                                                     const uint32_t *depth_key, int64_t max_n, Record *rec_out) {
+    const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t n = n_dev ? min(int64_t(*n_dev), max_n) : max_n;
+    if (j >= n) return;
+    const int64_t r = ids ? int64_t(ids[j]) : j;
+    if (!ids && depth_key[r] == 0xFFFFFFFFu) return;
+    record_homography(f, r, rec_out);
 }
 
 // -------------------------------------------------------- backward kernel --
@@ -481,6 +507,14 @@ cudaError_t launch_preprocess(const Frame &f, int64_t max_k, uint32_t *depth_key
     if (max_k <= 0) return cudaSuccess;
     dim3 grid(unsigned(ceil_div(max_k, 256)), unsigned(f.n_cams));
     preprocess_kernel<<<grid, 256, 0, s>>>(f, depth_key, rec_id, rect, pbox, rec, cnt);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_record(const Frame &f, const uint32_t *ids, const uint32_t *n_dev, const uint32_t *depth_key,
+                          int64_t max_n, Record *rec, cudaStream_t s) {
+    if (max_n <= 0) return cudaSuccess;
+    record_kernel<<<unsigned(ceil_div(max_n, 128)), 128, 0, s>>>(f, ids, n_dev, depth_key, max_n, rec);
     count_launches(1);
     return cudaGetLastError();
 }

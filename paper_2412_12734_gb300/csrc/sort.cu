@@ -229,15 +229,6 @@ cudaError_t exclusive_scan(Load ld, int64_t max_n, const uint32_t *n_dev, uint32
 }
 
 // ---------------------------------------------------------- duplication --
-__device__ __forceinline__ int camera_of_record(const Frame &f, int64_t r) {
-    int lo = 0, hi = f.n_cams - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (f.cams[mid].rec_off <= r) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
 __global__ void __launch_bounds__(256) emit_kernel(Frame f, const uint32_t *perm, const uint2 *rect,
                                                    const uint32_t *offsets, int64_t max_n,
                                                    const Counters *cnt, int64_t capacity,
