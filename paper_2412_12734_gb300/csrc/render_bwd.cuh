@@ -96,8 +96,11 @@ __device__ __forceinline__ float warp_reduce_scatter32(float v[32], int lane) {
 constexpr int kCornerSlot = 14;
 // For N >= 8, above this many distinct edge/interior cells in a (warp, splat)
 // pair the lanes add their texel weights to shared memory directly instead of
-// one reduce-scatter per cell (measured: faster at N = 8, slower at N <= 4).
-constexpr int kGroupCells8 = 4;
+// one reduce-scatter per cell (measured: faster at N = 8, slower at N <= 4;
+// on the 16-view workload the N = 8 / 16 backward took 53.1 / 76.8 ms with
+// 2, 54.1 / 77.0 with 1, 54.7 / 77.2 with 0, 53.4 / 77.6 with 4 and 57.9 /
+// 82.6 with 8).
+constexpr int kGroupCells8 = 2;
 
 // State of one pixel in the reverse walk.
 struct Pix {
