@@ -151,7 +151,9 @@ typedef struct {
     uint32_t flags;      /* GB_FLAG_*                                             */
     int32_t pixels_per_thread; /* backward: 1, or 2 (two pixels of a column per
                                   thread on the packed FP32x2 pipe); 0 = 1. With 2,
-                                  batch_depth is at most tile_size^2 / 2        */
+                                  batch_depth is at most tile_size^2 / 2.  (The
+                                  forward always runs two pixels per thread,
+                                  one for 16 x 16 grids.)                       */
     float background[3]; /* added as T_final * background (default black)        */
 } gb_options;
 
