@@ -33,7 +33,7 @@ struct gb_saved {
     gb_context *ctx;
     int64_t cap_rec, cap_inst, cap_pix, cap_tiles;
     Record *rec;
-    uint32_t *depth_key, *rec_id, *keys_tmp, *vals_tmp, *dkeys_sorted, *perm, *offsets;
+    uint32_t *depth_key, *keys_tmp, *vals_tmp, *dkeys_sorted, *perm, *offsets;
     uint2 *rect, *pbox;
     int32_t *inv;
     float *rec_grad;
@@ -113,7 +113,6 @@ gb_status reserve_records(gb_saved *s, int64_t n) {
     const int64_t c = n + n / 8 + 1024;
     GB_CUDA(ctx, alloc_t(&s->rec, c));
     GB_CUDA(ctx, alloc_t(&s->depth_key, c));
-    GB_CUDA(ctx, alloc_t(&s->rec_id, c));
     GB_CUDA(ctx, alloc_t(&s->keys_tmp, c));
     GB_CUDA(ctx, alloc_t(&s->vals_tmp, c));
     GB_CUDA(ctx, alloc_t(&s->dkeys_sorted, c));
@@ -421,7 +420,7 @@ gb_status gb_saved_create(gb_context *ctx, gb_saved **out) {
 gb_status gb_saved_destroy(gb_saved *s) {
     if (!s) return GB_OK;
     cudaDeviceSynchronize();
-    void *ptrs[] = {s->rec, s->depth_key, s->rec_id, s->keys_tmp, s->vals_tmp, s->dkeys_sorted, s->perm,
+    void *ptrs[] = {s->rec, s->depth_key, s->keys_tmp, s->vals_tmp, s->dkeys_sorted, s->perm,
                     s->offsets, s->rect, s->pbox, s->inv, s->rec_grad, s->inst_tile, s->inst_val, s->inst_tile_tmp,
                     s->inst_val_tmp, s->tiles_sorted, s->vals_sorted, s->ranges, s->tl_keys, s->tl_vals,
                     s->tl_keys_tmp, s->tl_vals_tmp, s->tl_keys_out, s->tile_list, s->work, s->t_final, s->last,
@@ -667,7 +666,7 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
 
     GB_CUDA(ctx, cudaMemsetAsync(s->cnt, 0, sizeof(Counters), st));
     GB_CUDA(ctx, cudaMemsetAsync(s->ranges, 0, size_t(f.n_tiles) * sizeof(uint2), st));
-    GB_CUDA(ctx, launch_preprocess(f, max_k, s->depth_key, s->rec_id, s->rect, s->pbox, s->rec, s->cnt, st));
+    GB_CUDA(ctx, launch_preprocess(f, max_k, s->depth_key, nullptr, s->rect, s->pbox, s->rec, s->cnt, st));
     // visible records to the front in record order; their records' homography
     // part, one thread per visible record; then sorted by depth (stable, so
     // equal depths keep record order)

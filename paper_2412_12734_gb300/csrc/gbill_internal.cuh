@@ -149,7 +149,8 @@ __device__ __forceinline__ int camera_of_record(const Frame &f, int64_t r) {
 
 // ------------------------------------------------------- host-side launchers --
 
-// preprocess.cu
+// preprocess.cu: culling, key, rectangle, SH colour per record (rec_id, if
+// not NULL, receives the identity for a sort of every record)
 cudaError_t launch_preprocess(const Frame &f, int64_t max_k, uint32_t *depth_key, uint32_t *rec_id,
                               uint2 *rect, uint2 *pbox, Record *rec, Counters *cnt, cudaStream_t s);
 // Homography part (q0..q2) of the render records: of ids[0 .. *n_dev) or,

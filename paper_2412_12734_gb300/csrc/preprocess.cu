@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(256, 4) preprocess_kernel(Frame f, uint32_t *d
                 valid = false;
             }
         }
-        rec_id[r] = uint32_t(r);
+        if (rec_id) rec_id[r] = uint32_t(r);  // identity values for a sort of every record
         if (!valid) {
             depth_key[r] = 0xFFFFFFFFu;
             rect_out[r] = make_uint2(0u, 0u);
