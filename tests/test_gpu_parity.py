@@ -281,12 +281,22 @@ def test_one_pixel_and_degenerate_quaternion():
         assert e <= IMG_TOL
 
 
-def test_batch_depth_does_not_change_results():
+@pytest.mark.parametrize("tile,batch", [(16, 32), (8, 64), (16, 128), (32, 8)])
+def test_batch_depth_does_not_change_results(tile, batch):
+    """Images are the same bit for bit at any batch depth, including batches
+    deeper than the forward block's threads (tile 8: 32 threads, two pixels
+    each) that stage two or more splats per thread; gradients agree up to the
+    order of atomics."""
     sc, cams = CASES["dense_many_tiles"]()
-    a = gpu_run(sc, cams, batch=32)
-    b = gpu_run(sc, cams, batch=0)
+    rng = np.random.default_rng(41)
+    d_rgb = rng.standard_normal((int(cams[0]["height"]), int(cams[0]["width"]), 3)).astype(np.float32)
+    a = gpu_run(sc, cams, d_rgb=[d_rgb], tile=tile, batch=batch)
+    b = gpu_run(sc, cams, d_rgb=[d_rgb], tile=tile, batch=0)
     np.testing.assert_array_equal(a["rgb"][0], b["rgb"][0])
     np.testing.assert_array_equal(a["depth"][0], b["depth"][0])
+    for k in a["grads"][0]:
+        x, y = a["grads"][0][k], b["grads"][0][k]
+        assert np.abs(x - y).max() <= 2e-5 * max(np.abs(y).max(), 1e-12), k
 
 
 def test_invalid_arguments_are_rejected():
