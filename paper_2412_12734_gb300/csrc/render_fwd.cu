@@ -5,9 +5,9 @@
 // (l % 8, l / 8 + 4) of it, so a splat's record and warp-block mask bit are
 // read once for two pixels (measured on the 1M-splat, 16-view workload:
 // 13.1 -> 9.9 ms against one pixel per thread with 8 x 4 warp blocks, although
-// the coarser blocks evaluate 19 % more pairs).  The tile's depth-sorted splats are staged in
-// batches (record, footprint, warp-block masks, colour grid) in shared memory;
-// every pixel walks them front to back:
+// the coarser blocks evaluate 19 % more pairs).  The tile's depth-sorted
+// splats are staged in batches (record, footprint, warp-block masks, colour
+// grid) in shared memory; every pixel walks them front to back:
 //   zeta = adj(T') (dx, dy, 1)                (ray/splat intersection)
 //   rho  = min(u^2 + v^2, 2 |x - c|^2)        (Eq. 4 plus screen low-pass)
 //   alpha = min(0.99, o exp(-rho/2)), skipped below 1/255
@@ -29,6 +29,9 @@ struct FPix {
     bool inside, done;
 };
 
+// One (pixel, splat) pair of the front-to-back walk: evaluated by every lane of
+// the warp (a finished pixel's result is dropped), blended only where alpha
+// passes the cutoff and the pixel's transmittance stays above the stop bound.
 template <int N, typename TexT, bool WIDE>
 __device__ __forceinline__ void fwd_pair(FPix &q, const float4 &q0, const float4 &q1, const float4 &q2,
                                          const float4 &q3, const staged_t<TexT, WIDE> *tex, uint32_t idx1,
