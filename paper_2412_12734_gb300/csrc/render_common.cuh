@@ -7,15 +7,6 @@
 
 namespace gbill {
 
-// Pixel of thread `tid` in a TS x TS tile: each warp covers an 8 x 4 block so
-// that its 32 pixels are compact (small splats touch few warps).
-template <int TS>
-__device__ __forceinline__ void tile_pixel(int tid, int &lx, int &ly) {
-    const int lane = tid & 31, warp = tid >> 5;
-    lx = (warp % (TS / 8)) * 8 + (lane & 7);
-    ly = (warp / (TS / 8)) * 4 + (lane >> 3);
-}
-
 // A staged texel: FP32 grids, and with WIDE any grid, as RGBA float4 (16
 // bytes, alpha unused: one 128-bit shared load); otherwise FP16 and BF16 grids
 // in their storage type as RGB + pad (8 bytes: one 64-bit load, converted
@@ -116,7 +107,7 @@ __device__ __forceinline__ void stage_batch(const RenderBufs &b, const CamDev &c
                                             staged_t<TexT, WIDE> *s_tex, int32_t *s_k, uint32_t *s_j,
                                             uint2 *s_box, uint32_t *s_mask, float4 *s_fp) {
     constexpr int NN = N * N;
-    constexpr int NB = TS * TS / (8 * BH);  // warp blocks per tile: 1, 2, 4 or 8
+    constexpr int NB = TS * TS / (8 * BH);  // warp blocks per tile: 1 to 32
     static_assert(32 % NB == 0 && NT % 32 == 0, "block masks are gathered within a warp");
     for (int t = threadIdx.x; t < nb; t += NT) {  // a batch deeper than the block: two or more per thread
         const uint32_t j = b.inst_val[first + t];
