@@ -354,13 +354,13 @@ def launches_per_step(lib, step):
 # differ, or a configuration not captured, reports traffic null.
 TRAFFIC = {
     "render_bwd": {"files": ("render_bwd.cuh", "render_common.cuh", "render_bwd.cu", "render_bwd2.cu"),
-                   "sha256_16": "cdd97318ba89cdc5", "keys": ("workload", "tex_n", "tile", "batch", "ppt"),
+                   "sha256_16": "b29a7483aba4a685", "keys": ("workload", "tex_n", "tile", "batch", "ppt"),
                    "measured": [({"workload": "batched_1m", "tex_n": 4, "tile": 16, "batch": 88, "ppt": 1},
-                                 3.4952e9 + 0.9556e9)]},
+                                 3.4896e9 + 0.9554e9)]},
     "render_fwd": {"files": ("render_fwd.cu", "render_common.cuh"),
-                   "sha256_16": "c7cfa234453086c0", "keys": ("workload", "tex_n", "tile", "batch"),
+                   "sha256_16": "67d2c4a4c04f3c0e", "keys": ("workload", "tex_n", "tile", "batch"),
                    "measured": [({"workload": "batched_1m", "tex_n": 4, "tile": 16, "batch": 88},
-                                 1.7196e9 + 0.5011e9)]},
+                                 1.7181e9 + 0.5008e9)]},
 }
 
 
