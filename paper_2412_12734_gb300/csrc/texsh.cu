@@ -114,21 +114,33 @@ __global__ void __launch_bounds__(256) texsh_coef_grad_kernel(Frame f, int si, c
             const int64_t k = e / NN;
             const int t = int(e - k * NN);
             const float p[3] = {sc.means[3 * k], sc.means[3 * k + 1], sc.means[3 * k + 2]};
-            for (int ci = 0; ci < f.n_cams; ++ci) {
-                const CamDev &cam = f.cams[ci];
-                if (cam.scene != si) continue;
-                const float *gg = grid_grad + ((cam.tex_row + k) * NN + t) * 3;
-                const float h0 = gg[0], h1 = gg[1], h2 = gg[2];
-                if (h0 == 0.0f && h1 == 0.0f && h2 == 0.0f) continue;
-                float d[3], dist;
-                view_dir(p, cam, d, dist);
-                float Y[16];
-                sh_basis(Dt, d[0], d[1], d[2], Y);
+            // cameras in groups of four: the group's grid-gradient loads are
+            // issued together (most are zero: the splat is culled in the camera)
+            for (int c0 = 0; c0 < f.n_cams; c0 += 4) {
+                float h[4][3];
 #pragma unroll
-                for (int m = 0; m < M; ++m) {
-                    acc[3 * m + 0] = fmaf(Y[m], h0, acc[3 * m + 0]);
-                    acc[3 * m + 1] = fmaf(Y[m], h1, acc[3 * m + 1]);
-                    acc[3 * m + 2] = fmaf(Y[m], h2, acc[3 * m + 2]);
+                for (int j = 0; j < 4; ++j) {
+                    h[j][0] = h[j][1] = h[j][2] = 0.0f;
+                    if (c0 + j < f.n_cams && f.cams[c0 + j].scene == si) {
+                        const float *gg = grid_grad + ((f.cams[c0 + j].tex_row + k) * NN + t) * 3;
+                        h[j][0] = gg[0];
+                        h[j][1] = gg[1];
+                        h[j][2] = gg[2];
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (h[j][0] == 0.0f && h[j][1] == 0.0f && h[j][2] == 0.0f) continue;
+                    float d[3], dist;
+                    view_dir(p, f.cams[c0 + j], d, dist);
+                    float Y[16];
+                    sh_basis(Dt, d[0], d[1], d[2], Y);
+#pragma unroll
+                    for (int m = 0; m < M; ++m) {
+                        acc[3 * m + 0] = fmaf(Y[m], h[j][0], acc[3 * m + 0]);
+                        acc[3 * m + 1] = fmaf(Y[m], h[j][1], acc[3 * m + 1]);
+                        acc[3 * m + 2] = fmaf(Y[m], h[j][2], acc[3 * m + 2]);
+                    }
                 }
             }
         }
