@@ -200,7 +200,9 @@ int default_batch(const Frame &f) {
     return std::max(b, 8);
 }
 
-// (the forward stages grids of N <= 4 as FP32 RGBA)
+// Staged bytes of one batch of the forward (bwd false) or the backward for a
+// grid of size N stored as TexT; the forward stages grids of N <= 4 as FP32
+// RGBA whatever their storage type.
 template <typename TexT>
 size_t batch_smem_t(int N, int batch, bool bwd) {
     switch (N) {
@@ -212,7 +214,7 @@ size_t batch_smem_t(int N, int batch, bool bwd) {
     }
 }
 
-// Staged bytes of one batch for a grid of size N stored as `dtype`.
+// The same for a grid stored as `dtype` (FP16 and BF16 stage alike).
 size_t batch_smem(int N, int dtype, int batch, bool bwd) {
     return dtype == GB_F32 ? batch_smem_t<float>(N, batch, bwd) : batch_smem_t<__half>(N, batch, bwd);
 }
