@@ -1,16 +1,18 @@
 // Preprocess (forward and backward) of the textured 2D-Gaussian rasterizer.
 //
-// Forward, one thread per (splat, camera) record:
-//   1. FP32 tile rectangle and depth key (culling and rectangles are FP32
-//      decisions; the operation sequence is fixed and contraction-free, so the
-//      (tile, depth) key list is reproducible bit for bit).
-//   2. The render record: the splat-to-screen homography of Eq. 3 composed
-//      with the pinhole camera, expressed relative to the projected centre
-//      (so its upper-right block vanishes), its adjugate (ray/splat
-//      intersection, u = zeta_x / zeta_z), the centre as a double-float pair,
-//      and the view-dependent SH colour added to the grid colour (Sec. 4.2).
-//      Near edge-on splats (|det| tiny against its terms) redo the homography
-//      and its inverse in FP64.
+// Forward:
+//   1. preprocess_kernel, one thread per (splat, camera) record: FP32 tile
+//      rectangle and depth key (culling and rectangles are FP32 decisions; the
+//      operation sequence is fixed and contraction-free, so the (tile, depth)
+//      key list is reproducible bit for bit), and the record's opacity and
+//      view-dependent SH colour, added to the grid colour (Sec. 4.2).
+//   2. record_kernel, one thread per visible record (after compaction): the
+//      rest of the render record, the splat-to-screen homography of Eq. 3
+//      composed with the pinhole camera, expressed relative to the projected
+//      centre (so its upper-right block vanishes), its adjugate (ray/splat
+//      intersection, u = zeta_x / zeta_z) and the centre as a double-float
+//      pair.  Near edge-on splats (|det| tiny against its terms) redo the
+//      homography and its inverse in FP64.
 // Backward, one thread per splat: sums over the scene's cameras the chain from
 // the record gradients back to means, quaternions, scales, opacity and SH.
 #include <math.h>
