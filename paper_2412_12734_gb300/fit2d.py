@@ -14,7 +14,11 @@ the library's kernels:
     gb_adam_step             Adam (Kingma & Ba) per parameter group
 
 The forward runs in no-sync mode on a saved state sized by one synchronizing
-forward, so an iteration never waits for the host.  ``python -m
+forward, so an iteration never waits for the host.  The steps up to the
+raw-parameter gradients are captured once in a CUDA graph and replayed (an
+iteration of a small fit is otherwise bound by the host's launch time); the
+Adam launches, whose bias corrections change every iteration, follow the
+replay with their argument arrays built once.  ``python -m
 paper_2412_12734_gb300.fit2d --target wide --splats 1000`` fits a seeded
 synthetic target (``scenes.fit_target``; the paper's photographs are not
 part of this project).
@@ -45,7 +49,7 @@ class ImageFit:
     """Fits K textured splats to a target image [H, W, 3] (float32 in [0, 1])."""
 
     def __init__(self, target: np.ndarray, K: int, tex_n: int = 4, seed: int = 0, lr: dict | None = None,
-                 rasterizer: R.Rasterizer | None = None, device: int = 0):
+                 rasterizer: R.Rasterizer | None = None, device: int = 0, graph: bool = True):
         self.rast = rasterizer or R.Rasterizer(device)
         H, W = target.shape[:2]
         self.cam = scenes.fit_camera(W, H)
@@ -74,6 +78,10 @@ class ImageFit:
         self.it = 0
         self.saved = R.Saved(self.rast)
         self.stream = torch.cuda.current_stream(dev)
+        self.use_graph = graph
+        self._graph = None
+        self._adam = [R.AdamStep(self.rast, [self.p[k]], [self.g[k]], [self.m[k]], [self.v[k]], lr=self.lr[k])
+                      for k in RAW]
         # one synchronizing forward sizes the saved state; later ones never sync
         self._activate()
         self.rast.forward([self._scene()], [self.cam], saved=self.saved, out=self.out, stream=self.stream)
@@ -85,27 +93,30 @@ class ImageFit:
                 "opacities": self.act["opacities"], "sh": self.p["sh"], "textures": self.p["textures"],
                 "sh_degree": 0, "tex_n": self.tex_n, "sigma": self.sigma}
 
-    def _activate(self):
+    def _activate(self, stream=None):
         a = self.act
+        s = stream if stream is not None else self.stream
         L.check(L.load().gb_fit_params(self.rast.ctx, self.K, self.p["theta"].data_ptr(), self.p["xy"].data_ptr(),
                                        self.z.data_ptr(), self.p["log_scales"].data_ptr(),
                                        self.p["logit_opacities"].data_ptr(), a["quats"].data_ptr(),
                                        a["means"].data_ptr(), a["scales"].data_ptr(), a["opacities"].data_ptr(),
-                                       C.c_void_p(self.stream.cuda_stream)), self.rast.ctx)
+                                       C.c_void_p(s.cuda_stream)), self.rast.ctx)
 
-    def forward_loss(self):
+    def forward_loss(self, stream=None):
         """Activation, render and MSE (loss and dL/drgb stay on the device)."""
-        lib, ctx, s = L.load(), self.rast.ctx, C.c_void_p(self.stream.cuda_stream)
-        self._activate()
-        self.rast.forward([self._scene()], [self.cam], saved=self.saved, out=self.out, stream=self.stream,
+        st = stream if stream is not None else self.stream
+        lib, ctx, s = L.load(), self.rast.ctx, C.c_void_p(st.cuda_stream)
+        self._activate(st)
+        self.rast.forward([self._scene()], [self.cam], saved=self.saved, out=self.out, stream=st,
                           flags=L.GB_FLAG_NO_SYNC)
         L.check(lib.gb_mse_loss(ctx, self.out[0].data_ptr(), self.target.data_ptr(), self.P * 3,
                                 self.d_rgb.data_ptr(), self.loss_dev.data_ptr(), s), ctx)
 
-    def backward(self):
+    def backward(self, stream=None):
         """Gradients of the raw parameters from the current dL/drgb (self.d_rgb)."""
-        lib, ctx, s = L.load(), self.rast.ctx, C.c_void_p(self.stream.cuda_stream)
-        self.rast.backward(self.saved, self.d_rgb, grads=[self.gact], stream=self.stream)
+        st = stream if stream is not None else self.stream
+        lib, ctx, s = L.load(), self.rast.ctx, C.c_void_p(st.cuda_stream)
+        self.rast.backward(self.saved, self.d_rgb, grads=[self.gact], stream=st)
         ga = self.gact
         L.check(lib.gb_fit_params_backward(ctx, self.K, self.p["theta"].data_ptr(), self.p["log_scales"].data_ptr(),
                                            self.p["logit_opacities"].data_ptr(), ga["quats"].data_ptr(),
@@ -117,14 +128,30 @@ class ImageFit:
     def update(self):
         """Adam step of every parameter group."""
         self.it += 1
-        for k in RAW:
-            R.adam_step(self.rast, [self.p[k]], [self.g[k]], [self.m[k]], [self.v[k]], self.it, lr=self.lr[k],
-                        stream=self.stream)
+        for adam in self._adam:
+            adam(self.it, self.stream)
+
+    def _capture(self):
+        """Records activation, render, loss, backward and the raw-parameter
+        adjoint as one CUDA graph; every buffer they touch is allocated
+        already and stays in place, so the graph replays any later iteration."""
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            s = torch.cuda.current_stream()
+            self.forward_loss(s)
+            self.backward(s)
+        self._graph = g
 
     def step(self):
         """One iteration; the loss of the image rendered in it stays on the device."""
-        self.forward_loss()
-        self.backward()
+        if self.use_graph:
+            if self._graph is None:
+                self._capture()
+            with torch.cuda.stream(self.stream):
+                self._graph.replay()
+        else:
+            self.forward_loss()
+            self.backward()
         self.update()
 
     def check(self):
@@ -138,6 +165,7 @@ class ImageFit:
         st = self.saved.stats()
         if st["instances"] > headroom * st["capacity"]:
             self.saved.reserve(st["records"], 2 * st["capacity"], self.P, st["tiles"])
+            self._graph = None  # the saved state's buffers moved: capture again
 
     def loss(self) -> float:
         """MSE of the image rendered in the last step (synchronizes)."""
@@ -160,10 +188,11 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--log-every", type=int, default=100)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-graph", action="store_true", help="launch every step from the host")
     args = ap.parse_args(argv)
     tgt = args.target if args.target in scenes.FIT_TARGETS else tuple(int(x) for x in args.target.split("x"))
     target = scenes.fit_target(tgt, seed=args.seed)
-    fit = ImageFit(target, args.splats, tex_n=args.tex_n, seed=args.seed)
+    fit = ImageFit(target, args.splats, tex_n=args.tex_n, seed=args.seed, graph=not args.no_graph)
     t0 = time.perf_counter()
     for i in range(1, args.steps + 1):
         fit.step()

@@ -345,12 +345,7 @@ def render(means, quats, scales, opacities, sh, textures, cams, sh_degree: int, 
     return _RenderFn.apply(means, quats, scales, opacities, sh, textures, meta)
 
 
-def adam_step(rast: Rasterizer, params: list, grads: list, ms: list, vs: list, step: int, lr: float = 1e-3,
-              betas=(0.9, 0.999), eps: float = 1e-15, shadows=None, stream=None):
-    """Fused Adam over up to 16 FP32 tensors in one launch (gb_adam_step).
-
-    shadows[i] (optional) receives the updated params[i] in its own dtype
-    (e.g. the BF16 textures the renderer reads)."""
+def _adam_tensors(params: list, grads: list, ms: list, vs: list, shadows=None):
     n = len(params)
     arr = (L.gb_adam_tensor * n)()
     for i in range(n):
@@ -364,6 +359,35 @@ def adam_step(rast: Rasterizer, params: list, grads: list, ms: list, vs: list, s
         arr[i].shadow_dtype = DTYPES[sh.dtype] if sh is not None else 0
         arr[i].reserved = 0
         arr[i].n = p.numel()
+    return arr, n
+
+
+def adam_step(rast: Rasterizer, params: list, grads: list, ms: list, vs: list, step: int, lr: float = 1e-3,
+              betas=(0.9, 0.999), eps: float = 1e-15, shadows=None, stream=None):
+    """Fused Adam over up to 16 FP32 tensors in one launch (gb_adam_step).
+
+    shadows[i] (optional) receives the updated params[i] in its own dtype
+    (e.g. the BF16 textures the renderer reads)."""
+    arr, n = _adam_tensors(params, grads, ms, vs, shadows)
     cfg = L.gb_adam_config(float(lr), float(betas[0]), float(betas[1]), float(eps), int(step), 0)
     s = stream if stream is not None else torch.cuda.current_stream()
     L.check(L.load().gb_adam_step(rast.ctx, arr, n, C.byref(cfg), C.c_void_p(s.cuda_stream)), rast.ctx)
+
+
+class AdamStep:
+    """gb_adam_step over a fixed set of tensors with its argument arrays built
+    once, for training loops whose host time matters; the tensors must stay
+    allocated (and in place) while the object is used."""
+
+    def __init__(self, rast: Rasterizer, params: list, grads: list, ms: list, vs: list, lr: float = 1e-3,
+                 betas=(0.9, 0.999), eps: float = 1e-15, shadows=None):
+        self.rast = rast
+        self.arr, self.n = _adam_tensors(params, grads, ms, vs, shadows)
+        self.cfg = L.gb_adam_config(float(lr), float(betas[0]), float(betas[1]), float(eps), 1, 0)
+        self.keep = (list(params), list(grads), list(ms), list(vs), shadows)
+
+    def __call__(self, step: int, stream=None):
+        self.cfg.step = int(step)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        L.check(L.load().gb_adam_step(self.rast.ctx, self.arr, self.n, C.byref(self.cfg),
+                                      C.c_void_p(s.cuda_stream)), self.rast.ctx)
