@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--tex-n", type=int, default=4)
     ap.add_argument("--views", type=int, default=0, help="use only the first V cameras (0 = all; profiling)")
     ap.add_argument("--batch", type=int, default=0, help="splats per shared-memory batch (0 = auto)")
+    ap.add_argument("--batch-fwd", type=int, default=0,
+                    help="the forward's batch depth (0 = --batch, or automatic when that is 0 too)")
     ap.add_argument("--tile", type=int, default=0, help="tile edge 8, 16 or 32 (0 = autotune)")
     ap.add_argument("--ppt", type=int, default=1, help="backward pixels per thread, 1 or 2")
     ap.add_argument("--no-graph", action="store_true")
@@ -237,17 +239,20 @@ def run_ours(args, world, rank, local):
         tune = rast.autotune([dev_scene], cams, reps=2,
                              cache=os.path.join(tempfile.gettempdir(), f"gbill_tune_{os.getpid()}.json"))
         args.tile, args.batch, args.ppt = tune["tile"], tune["batch"], tune["ppt"]
+        args.batch_fwd = tune.get("batch_fwd", 0)
 
     # --- size the saved state with one synchronizing forward, then reserve
     saved = R.Saved(rast)
-    rgb, depth, alpha, _ = rast.forward([dev_scene], cams, saved=saved, batch=args.batch, tile=args.tile, ppt=args.ppt)
+    rgb, depth, alpha, _ = rast.forward([dev_scene], cams, saved=saved, batch=args.batch, batch_fwd=args.batch_fwd,
+                                        tile=args.tile, ppt=args.ppt)
     st0 = saved.stats()
     saved.reserve(st0["records"], int(st0["instances"] * 1.1) + 4096, P, st0["tiles"])
     grads = rast.backward(saved, d_rgb)
     out = (rgb, depth, alpha)
 
     def step(flags=L.GB_FLAG_NO_SYNC):
-        rast.forward([dev_scene], cams, saved=saved, flags=flags, out=out, batch=args.batch, tile=args.tile, ppt=args.ppt)
+        rast.forward([dev_scene], cams, saved=saved, flags=flags, out=out, batch=args.batch, batch_fwd=args.batch_fwd,
+                     tile=args.tile, ppt=args.ppt)
         rast.backward(saved, d_rgb, grads=grads)
 
     for _ in range(args.warmup):
@@ -294,7 +299,7 @@ def run_ours(args, world, rank, local):
     pairs = None
     for _ in range(args.steps):
         rast.forward([dev_scene], cams, saved=saved, flags=L.GB_FLAG_NO_SYNC | L.GB_FLAG_TIMING, out=out,
-                     batch=args.batch, tile=args.tile, ppt=args.ppt)
+                     batch=args.batch, batch_fwd=args.batch_fwd, tile=args.tile, ppt=args.ppt)
         rast.backward(saved, d_rgb, grads=grads)
         for k, v in saved.phase_times().items():
             phase_acc.setdefault(k, []).append(v)
@@ -311,7 +316,8 @@ def run_ours(args, world, rank, local):
                                f"{args.tex_n}x{args.tex_n} FP16 textures, SH3 FP16",
                    "pixels_per_step": P, "tex_n": args.tex_n, "mip_level": args.mip, "tex_sh_degree": args.tex_sh,
                    "storage": "f16", "tile": args.tile,
-                   "batch_depth": args.batch, "pixels_per_thread": args.ppt, "autotune": tune,
+                   "batch_depth": args.batch, "batch_depth_fwd": args.batch_fwd or args.batch,
+                   "pixels_per_thread": args.ppt, "autotune": tune,
                    "graph": graph is not None, "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{world}"},
         "clocks": clocks, "gpu_launches": int(launches), "phases_ms": phases,
@@ -358,8 +364,8 @@ TRAFFIC = {
                    "measured": [({"workload": "batched_1m", "tex_n": 4, "tile": 16, "batch": 88, "ppt": 1},
                                  3.4896e9 + 0.9554e9)]},
     "render_fwd": {"files": ("render_fwd.cu", "render_common.cuh"),
-                   "sha256_16": "67d2c4a4c04f3c0e", "keys": ("workload", "tex_n", "tile", "batch"),
-                   "measured": [({"workload": "batched_1m", "tex_n": 4, "tile": 16, "batch": 88},
+                   "sha256_16": "67d2c4a4c04f3c0e", "keys": ("workload", "tex_n", "tile", "batch_fwd"),
+                   "measured": [({"workload": "batched_1m", "tex_n": 4, "tile": 16, "batch_fwd": 88},
                                  1.7181e9 + 0.5008e9)]},
 }
 
@@ -378,7 +384,8 @@ def measured_traffic(kernel, args):
             h.update(fh.read())
     if h.hexdigest()[:16] != t["sha256_16"]:
         return None
-    cfg = {"workload": args.workload, "tex_n": args.tex_n, "tile": args.tile, "batch": args.batch, "ppt": args.ppt}
+    cfg = {"workload": args.workload, "tex_n": args.tex_n, "tile": args.tile, "batch": args.batch, "ppt": args.ppt,
+           "batch_fwd": args.batch_fwd or args.batch}
     cfg = {k: cfg[k] for k in t["keys"]}
     for c, b in t["measured"]:
         if c == cfg:
@@ -483,8 +490,8 @@ def e2e(args, wl, rast, R, L, torch, cams, P):
     torch.cuda.synchronize()
     outs, grads = [], []
     for b in range(2):
-        o = rast.forward([dict(d_in[b], **meta)], cams, saved=saved, batch=args.batch, tile=args.tile,
-                         ppt=args.ppt)
+        o = rast.forward([dict(d_in[b], **meta)], cams, saved=saved, batch=args.batch, batch_fwd=args.batch_fwd,
+                         tile=args.tile, ppt=args.ppt)
         outs.append(o[:3])
         grads.append(rast.backward(saved, d_drgb[b]))
     st = saved.stats()
@@ -511,7 +518,7 @@ def e2e(args, wl, rast, R, L, torch, cams, P):
         comp.wait_event(uploaded[b])
         comp.wait_event(done_out[b])
         rast.forward([dict(d_in[b], **meta)], cams, saved=saved, out=outs[b], flags=L.GB_FLAG_NO_SYNC,
-                     batch=args.batch, tile=args.tile, ppt=args.ppt, stream=comp)
+                     batch=args.batch, batch_fwd=args.batch_fwd, tile=args.tile, ppt=args.ppt, stream=comp)
         rast.backward(saved, d_drgb[b], grads=grads[b], stream=comp)
         done_in[b].record(comp)
         computed[b].record(comp)

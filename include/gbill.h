@@ -145,9 +145,11 @@ typedef struct {
 /* Render options (host struct; NULL = defaults). */
 typedef struct {
     int32_t tile_size;   /* tile edge in pixels: 8, 16 or 32 (0 = 16)             */
-    int32_t batch_depth; /* splats staged per shared-memory batch, 0 = automatic;
-                            otherwise a multiple of 8 up to the tile's pixels
-                            whose staging fits 200 KB of shared memory            */
+    int32_t batch_depth; /* splats staged per shared-memory batch of the backward
+                            (and of the forward when batch_depth_fwd is 0),
+                            0 = automatic; otherwise a multiple of 8 up to the
+                            tile's pixels whose staging fits 200 KB of shared
+                            memory                                                */
     uint32_t flags;      /* GB_FLAG_*                                             */
     int32_t pixels_per_thread; /* backward: 1, or 2 (two pixels of a column per
                                   thread on the packed FP32x2 pipe); 0 = 1. With 2,
@@ -155,6 +157,9 @@ typedef struct {
                                   forward always runs two pixels per thread,
                                   one for 16 x 16 grids.)                       */
     float background[3]; /* added as T_final * background (default black)        */
+    int32_t batch_depth_fwd; /* the forward's batch depth under the same rules;
+                                0 = batch_depth, or the forward's own automatic
+                                depth when batch_depth is 0 too                */
 } gb_options;
 
 /* Counters of the last forward on a saved state (gb_saved_stats). */
@@ -404,8 +409,10 @@ gb_status gb_mse_loss(gb_context *ctx, const float *rgb, const float *target, in
 
 /* Autotuner: times forward + backward of this frame for every candidate
  * (tile_size 8, 16 and 32; batch_depth 8, 16, 24, 32, 48, 64, 88, 128 where it fits the tile and
- * the shared-memory budget; pixels_per_thread 1 and 2) and writes the fastest
- * options to *best (flags and
+ * the shared-memory budget; pixels_per_thread 1 and 2; the forward at the same
+ * depth), then, at the fastest of those, times the forward alone at every
+ * batch_depth_fwd candidate (listed with pixels_per_thread 0 and the forward's
+ * time), and writes the fastest options to *best (flags and
  * background are copied from *base, which may be NULL).  Each candidate runs
  * once untimed (which may grow `saved`) and then `reps` timed repetitions
  * (1..100) with dL/drgb = 1 for every pixel.  The call allocates its own

@@ -182,19 +182,29 @@ gb_status reserve_scratch(gb_saved *s) {
 }
 
 size_t frame_smem(const Frame &f, int batch, bool bwd);
+int default_batch(const Frame &f, bool bwd);
 
-// Batch depth giving at most 48 KB of staged shared memory per block, so that
-// four blocks (the register limit of the 256-thread backward) stay resident
-// per SM; a multiple of 8, at least 8.  With FP16 grids staged at 8 bytes a
-// texel that is 88 at N = 4, 32 at N = 8 and 8 at N = 16 (measured on the
-// 1M-splat, 16-view workload: the best of the depths tried at N = 4 and 8;
-// with FP32-width staging N = 8 ran 27 % slower at 40, three blocks per SM,
-// than at 24, and N = 16 at 8 left three blocks per SM: 139 against 165
-// Mpixel/s).
-int default_batch(const Frame &f) {
-    // one depth for both passes: the backward's staging decides
-    const int per = int(frame_smem(f, 1, true));
-    int b = (48 * 1024) / per;
+// The forward's batch depth: batch_depth_fwd, else batch_depth, else the
+// forward's automatic depth (at most the tile's pixels).
+int forward_batch(const gb_options &o, const Frame &f, int nt) {
+    if (o.batch_depth_fwd) return o.batch_depth_fwd;
+    if (o.batch_depth) return o.batch_depth;
+    return std::min(default_batch(f, false), nt);
+}
+
+// Automatic batch depth of one pass: the most splats whose staging fits the
+// pass's shared-memory budget per block, a multiple of 8, at least 8.  The
+// backward gets 48 KB, so that four blocks (the register limit of its 256
+// threads) stay resident per SM: with FP16 grids staged at 8 bytes a texel
+// that is 88 at N = 4, 32 at N = 8 and 8 at N = 16 (measured on the 1M-splat,
+// 16-view workload: the best of the depths tried at N = 4 and 8; with
+// FP32-width staging N = 8 ran 27 % slower at 40, three blocks per SM, than at
+// 24, and N = 16 at 8 left three blocks per SM: 139 against 165 Mpixel/s).
+// The forward gets 36 KB, so that six blocks (its register limit at 16 x 16
+// tiles) stay resident: 88 at N = 4, 56 at N = 8, 16 at N = 16.
+int default_batch(const Frame &f, bool bwd) {
+    const int per = int(frame_smem(f, 1, bwd));
+    int b = ((bwd ? 48 : 36) * 1024) / per;
     b = std::min(b, 256);
     b &= ~7;
     return std::max(b, 8);
@@ -565,12 +575,15 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
     gb_status r = build_frame(ctx, scenes, n_scenes, cams, n_cams, tile, o.background, f, max_k);
     if (r != GB_OK) return r;
     const int nt = tile * tile;
-    int bf = o.batch_depth ? o.batch_depth : std::min(default_batch(f), nt);
-    int bb = o.batch_depth ? o.batch_depth : std::min(default_batch(f), nt / ppt);
-    if (bf < 8 || bf > nt || (bf & 7)) return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d invalid", bf);
+    const int bf = forward_batch(o, f, nt);
+    const int bb = o.batch_depth ? o.batch_depth : std::min(default_batch(f, true), nt / ppt);
+    if (bf < 8 || bf > nt || (bf & 7)) return fail(ctx, GB_ERR_INVALID_ARG, "forward batch depth %d invalid", bf);
+    if (bb < 8 || (bb & 7)) return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d invalid", bb);
     if (bb > nt / ppt) return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d exceeds the backward's %d threads", bb, nt / ppt);
-    if (frame_smem(f, bf, false) > 200 * 1024 || frame_smem(f, bb, true) > 200 * 1024)
-        return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d needs too much shared memory", bf);
+    if (frame_smem(f, bf, false) > 200 * 1024)
+        return fail(ctx, GB_ERR_INVALID_ARG, "forward batch depth %d needs too much shared memory", bf);
+    if (frame_smem(f, bb, true) > 200 * 1024)
+        return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d needs too much shared memory", bb);
     const bool nosync = (o.flags & GB_FLAG_NO_SYNC) != 0;
     if (nosync) {
         if (f.n_records > s->cap_rec || f.n_pixels > s->cap_pix || int64_t(f.n_tiles) > s->cap_tiles ||
@@ -882,9 +895,9 @@ gb_status gb_render_forward_noalloc(gb_context *ctx, const gb_scene *scenes, int
                     (long long)f.n_records, (long long)kNaMaxRecords, (long long)f.n_pixels,
                     (long long)kNaMaxPixels, f.n_tiles, (long long)kNaMaxTiles);
     const int nt = tile * tile;
-    const int bf = o.batch_depth ? o.batch_depth : std::min(default_batch(f), nt);
+    const int bf = forward_batch(o, f, nt);
     if (bf < 8 || bf > nt || (bf & 7) || frame_smem(f, bf, false) > 200 * 1024)
-        return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d invalid", bf);
+        return fail(ctx, GB_ERR_INVALID_ARG, "forward batch depth %d invalid", bf);
     int dev = 0;
     GB_CUDA(ctx, cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return fail(ctx, GB_ERR_UNSUPPORTED, "device index %d beyond 63", dev);
@@ -1078,10 +1091,45 @@ gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int3
         gb_options o{};
         if (base) o = *base;
         o.flags &= ~(GB_FLAG_NO_SYNC | GB_FLAG_TIMING);
+        o.batch_depth_fwd = 0;
         float best_ms = INFINITY;
         int n = 0;
         const int tile_c[3] = {16, 8, 32};
         const int batch_c[8] = {8, 16, 24, 32, 48, 64, 88, 128};
+        // one untimed run of the candidate (sizes `saved`), then `reps` timed
+        // no-sync runs; *t = mean milliseconds
+        auto time_candidate = [&](gb_options &c, bool with_bwd, float *t) -> gb_status {
+            c.flags &= ~GB_FLAG_NO_SYNC;
+            gb_status r = gb_render_forward(ctx, s, scenes, n_scenes, cams, n_cams, &c, rgb, dep, alp, nullptr);
+            if (r == GB_OK && with_bwd) r = gb_render_backward(ctx, s, drgb, nullptr, nullptr, g, n_scenes, nullptr);
+            if (r != GB_OK) return r;
+            c.flags |= GB_FLAG_NO_SYNC;
+            cudaEventRecord(e0, nullptr);
+            for (int k = 0; k < reps && r == GB_OK; ++k) {
+                r = gb_render_forward(ctx, s, scenes, n_scenes, cams, n_cams, &c, rgb, dep, alp, nullptr);
+                if (r == GB_OK && with_bwd)
+                    r = gb_render_backward(ctx, s, drgb, nullptr, nullptr, g, n_scenes, nullptr);
+            }
+            cudaEventRecord(e1, nullptr);
+            c.flags &= ~GB_FLAG_NO_SYNC;
+            if (r != GB_OK) return r;
+            cudaError_t ce = cudaEventSynchronize(e1);
+            if (ce == cudaSuccess) ce = cudaEventElapsedTime(t, e0, e1);
+            if (ce != cudaSuccess) return fail(ctx, GB_ERR_CUDA, "autotune timing failed: %s", cudaGetErrorString(ce));
+            r = gb_saved_check(s);
+            *t /= float(reps);
+            return r;
+        };
+        auto list = [&](int T, int B, int pi, float t) {
+            if (n < cap) {
+                if (ms) ms[n] = t;
+                if (tiles) tiles[n] = T;
+                if (batches) batches[n] = B;
+                if (ppts) ppts[n] = pi;
+            }
+            ++n;
+        };
+        // forward + backward over tile, batch depth (both passes) and pixels per thread
         for (int pi = 1; pi <= 2 && st == GB_OK; ++pi)
         for (int ti = 0; ti < 3 && st == GB_OK; ++ti)
             for (int bi = 0; bi < 8 && st == GB_OK; ++bi) {
@@ -1091,42 +1139,37 @@ gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int3
                 o.tile_size = T;
                 o.batch_depth = B;
                 o.pixels_per_thread = pi;
-                o.flags &= ~GB_FLAG_NO_SYNC;
-                st = gb_render_forward(ctx, s, scenes, n_scenes, cams, n_cams, &o, rgb, dep, alp, nullptr);
-                if (st == GB_OK) st = gb_render_backward(ctx, s, drgb, nullptr, nullptr, g, n_scenes, nullptr);
-                if (st != GB_OK) break;
-                o.flags |= GB_FLAG_NO_SYNC;
-                cudaEventRecord(e0, nullptr);
-                for (int k = 0; k < reps && st == GB_OK; ++k) {
-                    st = gb_render_forward(ctx, s, scenes, n_scenes, cams, n_cams, &o, rgb, dep, alp, nullptr);
-                    if (st == GB_OK) st = gb_render_backward(ctx, s, drgb, nullptr, nullptr, g, n_scenes, nullptr);
-                }
-                cudaEventRecord(e1, nullptr);
-                if (st != GB_OK) break;
-                e = cudaEventSynchronize(e1);
                 float t = 0.0f;
-                if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
-                if (e != cudaSuccess) {
-                    st = fail(ctx, GB_ERR_CUDA, "autotune timing failed: %s", cudaGetErrorString(e));
-                    break;
-                }
-                const gb_status chk = gb_saved_check(s);
-                if (chk != GB_OK) { st = chk; break; }
-                t /= float(reps);
-                if (n < cap) {
-                    if (ms) ms[n] = t;
-                    if (tiles) tiles[n] = T;
-                    if (batches) batches[n] = B;
-                    if (ppts) ppts[n] = pi;
-                }
-                ++n;
+                if ((st = time_candidate(o, true, &t)) != GB_OK) break;
+                list(T, B, pi, t);
                 if (t < best_ms) {
                     best_ms = t;
                     *best = o;
-                    best->flags &= ~GB_FLAG_NO_SYNC;
-                    if (base) best->flags |= (base->flags & GB_FLAG_NO_SYNC);
                 }
             }
+        // the forward alone at every depth that fits the fastest tile (its time
+        // does not depend on the backward's options)
+        if (st == GB_OK && best_ms < INFINITY) {
+            gb_options c = *best;
+            const int T = c.tile_size;
+            float best_fwd = INFINITY;
+            for (int bi = 0; bi < 8 && st == GB_OK; ++bi) {
+                const int B = batch_c[bi];
+                if (B > T * T || frame_smem(f, B, false) > 160 * 1024) continue;
+                c.batch_depth_fwd = B;
+                float t = 0.0f;
+                if ((st = time_candidate(c, false, &t)) != GB_OK) break;
+                list(T, B, 0, t);
+                if (t < best_fwd) {
+                    best_fwd = t;
+                    best->batch_depth_fwd = B;
+                }
+            }
+        }
+        if (st == GB_OK && best_ms < INFINITY) {
+            best->flags &= ~GB_FLAG_NO_SYNC;
+            if (base) best->flags |= (base->flags & GB_FLAG_NO_SYNC);
+        }
         if (n_candidates) *n_candidates = n;
         if (st == GB_OK && n == 0) st = fail(ctx, GB_ERR_UNSUPPORTED, "no autotune candidate fits");
     }

@@ -156,13 +156,6 @@ __device__ __forceinline__ DF df_affine(const float *row, const float p[3], floa
     acc = df_add(acc, two_prod(row[2], p[2]));
     return df_add(acc, DF{t, 0.0f});
 }
-// a d - b c with one rounding error (Kahan's FMA scheme).
-__device__ __forceinline__ float det2(float a, float b, float c, float d) {
-    const float w = b * c;
-    const float e = __fmaf_rn(-b, c, w);
-    const float f = __fmaf_rn(a, d, -w);
-    return f + e;
-}
 
 __device__ __forceinline__ float load_sh(const SceneDev &s, int64_t i) {
     switch (s.sh_dtype) {

@@ -177,8 +177,11 @@ class Rasterizer:
 
     def forward(self, scenes: list, cams: list, cam_scene=None, saved: Saved | None = None,
                 tile: int = 16, batch: int = 0, flags: int = 0, background=None, stream=None,
-                out=None, ppt: int = 1):
-        """Renders every camera; returns (rgb [P,3], depth [P], alpha [P], saved)."""
+                out=None, ppt: int = 1, batch_fwd: int = 0):
+        """Renders every camera; returns (rgb [P,3], depth [P], alpha [P], saved).
+
+        batch is the backward's batch depth (and the forward's unless
+        batch_fwd is given); 0 picks each pass's automatic depth."""
         lib = L.load()
         n_s, n_c = len(scenes), len(cams)
         cam_scene = list(cam_scene) if cam_scene is not None else [0] * n_c
@@ -186,6 +189,7 @@ class Rasterizer:
         carr = (L.gb_camera * n_c)(*[camera_struct(c, cam_scene[i]) for i, c in enumerate(cams)])
         opt = L.gb_options()
         opt.tile_size, opt.batch_depth, opt.flags, opt.pixels_per_thread = tile, batch, flags, ppt
+        opt.batch_depth_fwd = batch_fwd
         if background is not None:
             for i in range(3):
                 opt.background[i] = float(background[i])
@@ -279,7 +283,9 @@ class Rasterizer:
         L.check(lib.gb_autotune(self.ctx, saved.handle, sarr, n_s, carr, n_c, None, reps, C.byref(best),
                                 C.addressof(ms), C.addressof(tiles), C.addressof(batches), C.addressof(ppts), 64,
                                 C.byref(n)), self.ctx)
+        # candidates with ppt 0 time the forward alone at batch depth "batch"
         res = {"tile": best.tile_size, "batch": best.batch_depth, "ppt": best.pixels_per_thread,
+               "batch_fwd": best.batch_depth_fwd,
                "candidates": [{"tile": tiles[i], "batch": batches[i], "ppt": ppts[i], "ms": ms[i]}
                               for i in range(min(n.value, 64))]}
         table[key] = res

@@ -41,8 +41,8 @@ def test_header_is_c_and_layouts_match():
 int main(void) {
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(gb_camera), sizeof(gb_scene), sizeof(gb_grads),
          sizeof(gb_options), sizeof(gb_stats), offsetof(gb_scene, sigma));
-  printf("%zu %zu %zu\n", offsetof(gb_camera, world_to_cam), offsetof(gb_camera, scene),
-         offsetof(gb_options, background));
+  printf("%zu %zu %zu %zu\n", offsetof(gb_camera, world_to_cam), offsetof(gb_camera, scene),
+         offsetof(gb_options, background), offsetof(gb_options, batch_depth_fwd));
   return 0;
 }
 '''
@@ -57,7 +57,8 @@ int main(void) {
     b = [int(x) for x in lines[1].split()]
     assert a == [C.sizeof(L.gb_camera), C.sizeof(L.gb_scene), C.sizeof(L.gb_grads),
                  C.sizeof(L.gb_options), C.sizeof(L.gb_stats), L.gb_scene.sigma.offset]
-    assert b == [L.gb_camera.world_to_cam.offset, L.gb_camera.scene.offset, L.gb_options.background.offset]
+    assert b == [L.gb_camera.world_to_cam.offset, L.gb_camera.scene.offset, L.gb_options.background.offset,
+                 L.gb_options.batch_depth_fwd.offset]
 
 
 def test_status_strings_and_null_arguments(lib):

@@ -146,11 +146,16 @@ def test_autotune_picks_a_valid_candidate(tmp_path):
     res = rast.autotune(dev, cams, reps=2, cache=str(tmp_path / "tune.json"))
     assert res["tile"] in (8, 16, 32) and res["batch"] in (8, 16, 24, 32, 48, 64, 88, 128)
     assert len(res["candidates"]) >= 4
-    best = min(res["candidates"], key=lambda c: c["ms"])
-    assert (best["tile"], best["batch"]) == (res["tile"], res["batch"])
+    both = [c for c in res["candidates"] if c["ppt"] > 0]
+    best = min(both, key=lambda c: c["ms"])
+    assert (best["tile"], best["batch"], best["ppt"]) == (res["tile"], res["batch"], res["ppt"])
+    # the second stage times the forward alone at the chosen tile (listed with ppt 0)
+    fwd = [c for c in res["candidates"] if c["ppt"] == 0]
+    assert fwd and all(c["tile"] == res["tile"] for c in fwd)
+    assert min(fwd, key=lambda c: c["ms"])["batch"] == res["batch_fwd"]
     again = rast.autotune(dev, cams, reps=2, cache=str(tmp_path / "tune.json"))
     assert again == res  # served from the cache
-    rgb, _, _, _ = rast.forward(dev, cams, tile=res["tile"], batch=res["batch"])
+    rgb, _, _, _ = rast.forward(dev, cams, tile=res["tile"], batch=res["batch"], batch_fwd=res["batch_fwd"])
     ref = oracle_run(sc[0], cams[0])
     e, _ = compare_images(rgb.cpu().numpy().reshape(ref["rgb"].shape), ref, "rgb")
     assert e <= IMG_TOL
@@ -328,16 +333,18 @@ def test_one_pixel_and_degenerate_quaternion():
         assert e <= IMG_TOL
 
 
-@pytest.mark.parametrize("tile,batch", [(16, 32), (8, 64), (16, 128), (32, 8)])
-def test_batch_depth_does_not_change_results(tile, batch):
+@pytest.mark.parametrize("tile,batch,batch_fwd", [(16, 32, 0), (8, 64, 0), (16, 128, 0), (32, 8, 0), (16, 8, 128),
+                                                 (16, 88, 16), (8, 16, 64)])
+def test_batch_depth_does_not_change_results(tile, batch, batch_fwd):
     """Images are the same bit for bit at any batch depth, including batches
     deeper than the forward block's threads (tile 8: 32 threads, two pixels
-    each) that stage two or more splats per thread; gradients agree up to the
-    order of atomics."""
+    each) that stage two or more splats per thread, and with the forward's
+    depth set apart from the backward's; gradients agree up to the order of
+    atomics."""
     sc, cams = CASES["dense_many_tiles"]()
     rng = np.random.default_rng(41)
     d_rgb = rng.standard_normal((int(cams[0]["height"]), int(cams[0]["width"]), 3)).astype(np.float32)
-    a = gpu_run(sc, cams, d_rgb=[d_rgb], tile=tile, batch=batch)
+    a = gpu_run(sc, cams, d_rgb=[d_rgb], tile=tile, batch=batch, batch_fwd=batch_fwd)
     b = gpu_run(sc, cams, d_rgb=[d_rgb], tile=tile, batch=0)
     np.testing.assert_array_equal(a["rgb"][0], b["rgb"][0])
     np.testing.assert_array_equal(a["depth"][0], b["depth"][0])
@@ -372,6 +379,12 @@ def test_invalid_arguments_are_rejected():
     assert ei.value.status == 6
     with pytest.raises(L.GbillError) as ei:
         rast.forward([dev], [cam], batch=36)  # not a multiple of 8
+    assert ei.value.status == 1
+    with pytest.raises(L.GbillError) as ei:
+        rast.forward([dev], [cam], batch_fwd=36)
+    assert ei.value.status == 1
+    with pytest.raises(L.GbillError) as ei:
+        rast.forward([dev], [cam], tile=8, batch=16, batch_fwd=128)  # deeper than the tile's 64 pixels
     assert ei.value.status == 1
 
 
