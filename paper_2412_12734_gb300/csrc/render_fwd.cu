@@ -160,8 +160,18 @@ __host__ __device__ constexpr int fwd_ppt() {
     return N >= 16 ? 1 : 2;
 }
 
+// Resident blocks per SM the register budget is sized for: 1536 threads (six
+// blocks of 16 x 16 tiles), but 1280 at N = 16, one pixel per thread, where
+// the 40-register cap of 1536 spilled 104 bytes (measured on the 16-view
+// workload, images identical: 25.68 ms at six blocks, 24.96 at five with 48
+// registers, 25.77 at four with 62).
+template <int TS, int N>
+__host__ __device__ constexpr int fwd_min_blocks() {
+    return (N >= 16 ? 1280 : 1536) / (TS * TS);
+}
+
 template <int TS, int N, typename TexT>
-__global__ void __launch_bounds__(TS * TS / fwd_ppt<N>(), 1536 / (TS * TS))
+__global__ void __launch_bounds__(TS * TS / fwd_ppt<N>(), fwd_min_blocks<TS, N>())
     render_fwd_kernel(Frame f, RenderBufs b, int batch, TileSched ts) {
     __shared__ uint32_t s_next;
     for (int round = 0;; ++round) {
