@@ -32,7 +32,7 @@ METRIC = "fwd+bwd Mpixel/s at 1M textured splats, batched vs plain FP32, max err
 FP32_PEAK_TFLOPS_AT_MAX = 152 * 128 * 2 * 2.070e9 / 1e12  # FMA = 2 FLOP, 2070 MHz
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--crop", type=int, default=0, help="oracle crop side in pixels (0 = all of camera 0)")
     ap.add_argument("--mip", type=int, default=0, help="render the grids at this mip level (box filter)")
     ap.add_argument("--tex-sh", type=int, default=0, help="per-texel SH degree of the grids (0 = RGB texels)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 # ------------------------------------------------------------------ helpers --
@@ -152,6 +152,19 @@ def make_workload(args):
     return wl
 
 
+STORAGE_NAMES = {"f32": "FP32", "f16": "FP16", "bf16": "BF16"}
+
+
+def workload_label(args, wl) -> str:
+    """config.workload of both arms: the workload's name, splats, views and storage."""
+    sc = wl["scenes"][0]
+    sizes = sorted({(int(c["width"]), int(c["height"])) for c in wl["cams"]}, key=lambda s: s[0] * s[1])
+    return (f"{args.workload}: {int(sc['means'].shape[0]):,} splats, {len(wl['cams'])} views "
+            f"{'/'.join(f'{w}x{h}' for w, h in sizes)}, {args.tex_n}x{args.tex_n} "
+            f"{STORAGE_NAMES[sc.get('tex_dtype', 'f32')]} textures, SH{int(sc['sh_degree'])} "
+            f"{STORAGE_NAMES[sc.get('sh_dtype', 'f32')]}")
+
+
 def crop_window(cam, side):
     W, H = int(cam["width"]), int(cam["height"])
     if side <= 0:
@@ -202,8 +215,8 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "tex_n": args.tex_n, "crop": args.crop, "mip_level": args.mip,
-                   "tex_sh_degree": args.tex_sh},
+        "config": {"workload": workload_label(args, wl), "tex_n": args.tex_n, "crop": args.crop,
+                   "mip_level": args.mip, "tex_sh_degree": args.tex_sh},
         "cpu_baseline": {"value": value, "unit": "Mpixel/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -312,8 +325,7 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: 1,000,000 splats, {len(cams)} views 960x540/1280x720/1920x1080, "
-                               f"{args.tex_n}x{args.tex_n} FP16 textures, SH3 FP16",
+        "config": {"workload": workload_label(args, wl),
                    "pixels_per_step": P, "tex_n": args.tex_n, "mip_level": args.mip, "tex_sh_degree": args.tex_sh,
                    "storage": "f16", "tile": args.tile,
                    "batch_depth": args.batch, "batch_depth_fwd": args.batch_fwd or args.batch,
