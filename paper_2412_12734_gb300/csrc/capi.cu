@@ -801,6 +801,9 @@ gb_status gb_render_backward(gb_context *ctx, gb_saved *s, const float *d_rgb, c
     GB_CUDA(ctx, cudaMemsetAsync(&s->cnt->pairs_bwd, 0, sizeof(unsigned long long), st));
     GB_CUDA(ctx, cudaMemsetAsync(&s->cnt->contrib_bwd, 0, sizeof(unsigned long long), st));
     const bool persistent = (s->flags & GB_FLAG_PERSISTENT) != 0;
+    // the backward's tile counters start from zero at every call (a forward
+    // may be followed by several backwards)
+    if (persistent) GB_CUDA(ctx, cudaMemsetAsync(s->work + kMaxGroups, 0, kMaxGroups * sizeof(uint32_t), st));
     GB_CUDA(ctx, launch_render_bwd(f, b, s->batch_bwd, s->ppt, s->use_list ? s->tile_list : nullptr,
                                    persistent ? s->work + kMaxGroups : nullptr, persistent, st));
     for (int i = 0; i < n_scenes; ++i)

@@ -397,3 +397,96 @@ class AdamStep:
         s = stream if stream is not None else torch.cuda.current_stream()
         L.check(L.load().gb_adam_step(self.rast.ctx, self.arr, self.n, C.byref(self.cfg),
                                       C.c_void_p(s.cuda_stream)), self.rast.ctx)
+
+
+class BatchedRenderer:
+    """Forward and backward of one fixed frame (scenes, cameras, options)
+    replayed from CUDA graphs.
+
+    The constructor renders once with a host sync to size the saved state,
+    reserves ``headroom`` times that instance count, allocates the outputs
+    (rgb, depth, alpha), the upstream-gradient buffer ``d_rgb`` [P, 3] and
+    the gradients (one dict per scene), and runs one no-sync forward and
+    backward.  ``forward()`` and ``backward()`` then replay a graph each
+    (captured on first use).  The scenes' tensors are read where they are:
+    parameters updated in place between steps (an optimiser step) are
+    rendered by the next replay, whatever their visible set and instance
+    count.  A replay never waits for the host and never allocates; ``check()``
+    reports an instance list that outgrew the reservation and
+    ``ensure_capacity()`` grows it and captures again.  With
+    ``flags=GB_FLAG_PERSISTENT`` every view and scene renders in one
+    persistent launch per pass.
+    """
+
+    def __init__(self, rast: Rasterizer, scenes: list, cams: list, cam_scene=None, tile: int = 16,
+                 batch: int = 0, batch_fwd: int = 0, ppt: int = 1, flags: int = 0, background=None,
+                 headroom: float = 1.25):
+        self.rast = rast
+        self.scenes, self.cams = list(scenes), list(cams)
+        self.cam_scene = list(cam_scene) if cam_scene is not None else [0] * len(self.cams)
+        self.opts = {"tile": tile, "batch": batch, "batch_fwd": batch_fwd, "ppt": ppt, "background": background}
+        self.flags = int(flags) & ~(L.GB_FLAG_NO_SYNC | L.GB_FLAG_TIMING)
+        self.P = rast.pixel_count(self.cams)
+        self.saved = Saved(rast)
+        rgb, depth, alpha, _ = rast.forward(self.scenes, self.cams, cam_scene=self.cam_scene, saved=self.saved,
+                                            flags=self.flags, **self.opts)
+        self.out = (rgb, depth, alpha)
+        st = self.saved.stats()
+        self.saved.reserve(st["records"], int(st["instances"] * headroom) + 4096, self.P, st["tiles"])
+        self.d_rgb = torch.zeros((self.P, 3), device=rgb.device)
+        self.grads = rast.backward(self.saved, self.d_rgb)
+        self._graphs = None
+        self._forward()
+        self._backward()
+        torch.cuda.synchronize(rgb.device)
+        self.saved.check()
+
+    def _forward(self):
+        self.rast.forward(self.scenes, self.cams, cam_scene=self.cam_scene, saved=self.saved, out=self.out,
+                          flags=self.flags | L.GB_FLAG_NO_SYNC, **self.opts)
+
+    def _backward(self):
+        self.rast.backward(self.saved, self.d_rgb, grads=self.grads)
+
+    def capture(self):
+        """Records the forward and the backward as one graph each."""
+        graphs = []
+        for run in (self._forward, self._backward):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                run()
+            graphs.append(g)
+        self._graphs = graphs
+
+    def forward(self):
+        """Renders every camera into self.out = (rgb [P,3], depth [P], alpha [P])."""
+        if self._graphs is None:
+            self.capture()
+        self._graphs[0].replay()
+        return self.out
+
+    def backward(self, d_rgb: torch.Tensor | None = None):
+        """Gradients of the last forward's splats from dL/drgb: ``d_rgb`` (a
+        [P, 3] float32 device tensor) is copied into self.d_rgb first; without
+        it self.d_rgb is used as it stands (write it in place).  Returns the
+        gradient dicts (overwritten by every call)."""
+        if d_rgb is not None:
+            self.d_rgb.copy_(d_rgb.reshape(self.P, 3))
+        if self._graphs is None:
+            self.capture()
+        self._graphs[1].replay()
+        return self.grads
+
+    def check(self):
+        """Raises if a replayed forward outgrew the reservation (synchronizes)."""
+        self.saved.check()
+
+    def ensure_capacity(self, headroom: float = 0.7):
+        """Checks the last forward and doubles the instance capacity once it is
+        more than ``headroom`` full; the graphs are captured again on next use
+        (the saved state's buffers moved).  Synchronizes."""
+        self.check()
+        st = self.saved.stats()
+        if st["instances"] > headroom * st["capacity"]:
+            self.saved.reserve(st["records"], 2 * st["capacity"], self.P, st["tiles"])
+            self._graphs = None

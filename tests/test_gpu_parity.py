@@ -211,6 +211,27 @@ def test_persistent_render_matches_one_block_per_tile(tile):
 
 
 
+@pytest.mark.parametrize("flags", [0, 2])
+def test_second_backward_after_one_forward_gives_the_same_gradients(flags):
+    """A forward may be followed by several backwards (other upstream
+    gradients, or the same again): each starts from zeroed accumulators and,
+    with persistent blocks (flag 2), from a fresh tile counter."""
+    import torch
+
+    from paper_2412_12734_gb300 import render as R
+    sc, cams = CASES["dense_many_tiles"]()
+    rast = R.Rasterizer(0)
+    dev = [R.scene_to_device(s) for s in sc]
+    d = torch.randn((cams[0]["width"] * cams[0]["height"], 3), device="cuda")
+    ref = rast.backward(rast.forward(dev, cams)[3], d)[0]
+    saved = rast.forward(dev, cams, flags=flags)[3]
+    g1 = {k: v.clone() for k, v in rast.backward(saved, d)[0].items()}
+    g2 = rast.backward(saved, d)[0]
+    for k in ref:
+        scale = ref[k].abs().max().item()
+        assert (g1[k] - ref[k]).abs().max().item() <= 1e-5 * scale, k
+        assert (g2[k] - ref[k]).abs().max().item() <= 1e-5 * scale, k
+
 def test_graph_replay_with_new_parameters_matches_eager():
     """A no-sync forward and backward captured in a CUDA graph, replayed after
     the splat parameters were overwritten in place (other centres and sizes:
@@ -256,6 +277,57 @@ def test_graph_replay_with_new_parameters_matches_eager():
     for k, v in gref.items():
         scale = v.abs().max().item()
         assert (grads[0][k] - v).abs().max().item() <= 1e-5 * max(scale, 1e-12), k
+
+@pytest.mark.parametrize("flags", [0, 2])
+def test_batched_renderer_replays_match_eager_calls(flags):
+    """BatchedRenderer over two scenes of uneven splat counts and three views of
+    uneven sizes (flag 2: one persistent launch per pass): graph replays equal
+    eager calls, also after the splat parameters changed in place, and a
+    repeated backward gives the same gradients."""
+    import torch
+
+    from paper_2412_12734_gb300 import render as R
+    big = CASES["dense_many_tiles"]()
+    a0, a1 = big[0][0], scenes.tiny_scene(22, K=5, tex_n=4, sh_degree=1)
+    cams = [big[1][0], scenes.tiny_camera(17, 33, eye=(0.5, 0.2, -4.0)), scenes.tiny_camera(40, 24)]
+    cam_scene = [0, 1, 1]
+    rng = np.random.default_rng(12)
+    b0 = dict(a0)
+    b0["means"] = a0["means"] + rng.normal(0.0, 0.15, a0["means"].shape)
+    b0["scales"] = a0["scales"] * rng.uniform(0.7, 1.4, a0["scales"].shape)
+    rast = R.Rasterizer(0)
+    dev = [R.scene_to_device(a0), R.scene_to_device(a1)]
+    br = R.BatchedRenderer(rast, dev, cams, cam_scene=cam_scene, flags=flags, headroom=3.0)
+    d = torch.randn((br.P, 3), device="cuda")
+
+    def eager(scene_list):
+        o = rast.forward(scene_list, cams, cam_scene=cam_scene, flags=flags)
+        return o[:3], rast.backward(o[3], d)
+
+    def compare(ref):
+        out = br.forward()
+        grads = br.backward(d)
+        torch.cuda.synchronize()
+        br.check()
+        for x, y in zip(out, ref[0]):
+            assert torch.equal(x, y)
+        for gs, gr in zip(grads, ref[1]):
+            for k, v in gr.items():
+                scale = v.abs().max().item()
+                assert (gs[k] - v).abs().max().item() <= 1e-5 * max(scale, 1e-12), k
+
+    compare(eager(dev))
+    db = R.scene_to_device(b0)
+    for k in ("means", "scales"):
+        dev[0][k].copy_(db[k])
+    ref_b = eager(dev)
+    compare(ref_b)
+    again = br.backward()
+    torch.cuda.synchronize()
+    for gs, gr in zip(again, ref_b[1]):
+        for k, v in gr.items():
+            scale = v.abs().max().item()
+            assert (gs[k] - v).abs().max().item() <= 1e-5 * max(scale, 1e-12), k
 
 def test_multi_view_multi_scene():
     """Two scenes, four cameras of different sizes in one launch: per-camera
