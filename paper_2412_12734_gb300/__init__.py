@@ -6,7 +6,9 @@ Modules:
   build    compiles csrc/*.cu into libgbill.so (nvcc, sm_103a)
   _lib     ctypes signatures of the C ABI (argument marshalling only)
   render   Rasterizer (forward, backward, autotune), Saved state, the
-           torch.autograd function ``render`` and the fused ``adam_step``
+           torch.autograd function ``render``, BatchedRenderer (a fixed
+           frame's forward and backward replayed from CUDA graphs) and the
+           fused Adam (``adam_step``, ``AdamStep``)
   fit2d    the image-fitting loop of Sec. 4.1 on the library's kernels
   scenes   seeded synthetic inputs (no method arithmetic)
 
