@@ -75,17 +75,22 @@ class _Grads(C.Structure):
                 ("d_means", "d_quats", "d_scales", "d_opacities", "d_sh", "d_textures")]
 
 
+def load(path: str) -> C.CDLL:
+    """Opens a compiled oracle (this directory's, or a test's variant of it)."""
+    L = C.CDLL(path)
+    for name in ("orc_render_forward", "orc_render_backward", "orc_keys32", "orc_project",
+                 "orc_eval_pairs", "orc_sh_basis", "orc_bilinear", "orc_adj_bilinear",
+                 "orc_num_threads", "orc_pixel_trace"):
+        getattr(L, name).restype = C.c_int
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            L = C.CDLL(_SO)
-            for name in ("orc_render_forward", "orc_render_backward", "orc_keys32", "orc_project",
-                         "orc_eval_pairs", "orc_sh_basis", "orc_bilinear", "orc_adj_bilinear",
-                         "orc_num_threads", "orc_pixel_trace"):
-                getattr(L, name).restype = C.c_int
-            _lib = L
+            _lib = load(_SO)
     return _lib
 
 

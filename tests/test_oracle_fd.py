@@ -74,13 +74,40 @@ def test_fd_with_background_and_ragged_view():
 
 
 def test_fd_clamped_opacity_and_lowpass():
-    """Opacity close to 1 (alpha clamp active near centres) and a tiny splat
-    drawn by the low-pass branch: both gradient branches are exercised."""
+    """Opacities close to 1 and a tiny splat drawn by the low-pass branch
+    (the near-opaque splats here are not blended clamped at any pixel outside
+    the decision margin: test_fd_through_clamped_alpha covers that branch)."""
     sc = scenes.tiny_scene(41, K=4, tex_n=2, sh_degree=0)
     sc["opacities"] = np.array([0.999, 0.9, 0.7, 0.98], np.float32)
     sc["scales"][1] = np.array([0.01, 0.02], np.float32)
     cam = scenes.tiny_camera(16, 16)
     assert _check(sc, cam, seed=4) > 0
+
+
+def test_fd_through_clamped_alpha():
+    """A large, mildly tilted splat with opacity 0.9995 in front of the camera
+    is clamped to alpha = 0.99 (Eq. 4) over a patch of pixels: there alpha
+    depends on neither the opacity nor the Gaussian, and only the colour and
+    depth reach the splat's parameters.  At least four pixels outside the
+    decision margin blend it clamped, so the finite differences see the
+    clamped branch."""
+    import math
+    sc = scenes.tiny_scene(43, K=3, tex_n=4, sh_degree=1)
+    sc["opacities"] = np.array([0.9995, 0.8, 0.6], np.float32)
+    sc["scales"][0] = np.array([1.4, 1.12], np.float32)
+    sc["means"][0] = np.array([0.05, -0.03, 0.2], np.float32)
+    h = math.radians(10.0)
+    sc["quats"][0] = np.array([math.cos(h), 0.8 * math.sin(h), 0.6 * math.sin(h), 0.0], np.float32)
+    cam = scenes.tiny_camera(16, 16, focal=45.0)
+    margin = oracle.render(sc, cam)["margin_grad"]
+    n = 0
+    for y in range(16):
+        for x in range(16):
+            if margin[y, x] > 1e-3:
+                tr = oracle.pixel_trace(sc, cam, x, y)
+                n += sum(1 for i, a in zip(tr["ids"], tr["alpha"]) if i == 0 and a == 0.99)
+    assert n >= 4
+    assert _check(sc, cam, seed=6) > 0
 
 
 def test_fd_texture_only_heavy_grid():

@@ -1,0 +1,122 @@
+"""Planted mistakes: every pin set must notice a plausible error in the oracle.
+
+Each mutant below is one small edit of ``oracle/gbill_oracle.cpp``:
+- a dropped term, a flipped sign, a wrong constant, swapped texels or a wrong index;
+- arithmetic only, so that no mutant can read or write out of bounds.
+
+The edited source is compiled into a temporary library. The oracle module is pointed at it,
+and the fast pins of ``test_oracle_pins.py`` and ``test_oracle_fd.py`` run in turn. The test
+passes when at least one pin fails for every mutant. Mistakes that the forward and the
+backward make consistently, such as a wrong SH sign or a wrong rotation entry, are left to
+the closed-form pins. Mistakes that split them, such as a missing adjoint term, are left to
+the finite differences.
+"""
+import concurrent.futures as cf
+import os
+import subprocess
+
+import pytest
+
+import oracle
+from tests import test_oracle_fd as fd
+from tests import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "gbill_oracle.cpp")
+
+# name: (original text, planted text)
+MUTANTS = {
+    # forward (Eq. 2-5, Alg. 1 fwd)
+    "low-pass factor 1 instead of 2": ("static const double kLowPass = 2.0;", "static const double kLowPass = 1.0;"),
+    "alpha clamp 0.999": ("static const double kAlphaMax = 0.99;", "static const double kAlphaMax = 0.999;"),
+    "alpha cutoff 1/128": ("static const double kAlphaMin = 1.0 / 255.0;",
+                           "static const double kAlphaMin = 1.0 / 128.0;"),
+    "transmittance cutoff 1e-3": ("static const double kTMin = 1e-4;", "static const double kTMin = 1e-3;"),
+    "Gaussian exp(-rho)": ("e.G = std::exp(-0.5 * e.rho);", "e.G = std::exp(-e.rho);"),
+    "texels transposed": ("const double *c10 = C + ((b.iu + 1) * N + b.iv) * 3;\n"
+                          "    const double *c01 = C + ((b.iu) * N + b.iv + 1) * 3;",
+                          "const double *c10 = C + ((b.iu) * N + b.iv + 1) * 3;\n"
+                          "    const double *c01 = C + ((b.iu + 1) * N + b.iv) * 3;"),
+    "blend weight with the next T": ("const double w = e.alpha * T;", "const double w = e.alpha * tT;"),
+    "depth without the tilt terms": ("cb.zi = e.uv_branch ? (pr.T[6] * e.u + pr.T[7] * e.v + pr.T[8]) : pr.T[8];",
+                                     "cb.zi = pr.T[8];"),
+    "background dropped": ("rgb[c] = C[c] + T * cx.bg[c];", "rgb[c] = C[c];"),
+    "SH basis sign (l = 1, m = -1)": ("put(-c1 * y, 0, -c1, 0);", "put(c1 * y, 0, c1, 0);"),
+    "rotation entry sign": ("R[1] = 2 * (x * y - w * z);", "R[1] = 2 * (x * y + w * z);"),
+    # backward (Alg. 1 bwd, Alg. 2 adj-bilinear) and the chain to the parameters
+    "adj-bilinear u difference reversed": ("fu_hat += chat[c] * ((C[i10 + c] - C[i00 + c])",
+                                           "fu_hat += chat[c] * ((C[i00 + c] - C[i10 + c])"),
+    "adj-bilinear missing the +-sigma mask": ("uv_hat[0] = (u > -sigma && u < sigma) ? k * fu_hat : 0.0;",
+                                              "uv_hat[0] = k * fu_hat;"),
+    "low-pass centre gradient sign": ("A.c_hat[0] += rho_hat * kLowPass * -2.0 * e.dx;",
+                                      "A.c_hat[0] += rho_hat * kLowPass * 2.0 * e.dx;"),
+    "background adjoint dropped": ("a_hat += (dA - bgdot) * t_final * inv1ma;", "a_hat += dA * t_final * inv1ma;"),
+    "gradient through a clamped alpha": ("if (!e.clamped) {", "if (true) {"),
+    "depth adjoint index": ("A.T_hat[7] += zi_hat * e.v;", "A.T_hat[7] += zi_hat * e.u;"),
+    "centre adjoint sign": ("That[8] -= (A.c_hat[0] * T[2] + A.c_hat[1] * T[5]) / (T[8] * T[8]);",
+                            "That[8] += (A.c_hat[0] * T[2] + A.c_hat[1] * T[5]) / (T[8] * T[8]);"),
+    "quaternion normalisation adjoint dropped": ("(qh[i] - pr.qn[i] * qd) / pr.qnorm", "qh[i] / pr.qnorm"),
+    "SH direction adjoint not projected": ("p_hat[i] += (dir_hat[i] - pr.dir[i] * dd) / pr.dist;",
+                                           "p_hat[i] += dir_hat[i] / pr.dist;"),
+    # FP32 tile rectangles (keys)
+    "rectangle radius too small": ("static const float kRhoMaxF = 11.0825270903f;",
+                                   "static const float kRhoMaxF = 9.0f;"),
+}
+
+# fast pins, cheapest first
+PINS = [
+    (pins.test_sh_basis_matches_scipy, {}),
+    (pins.test_bilinear_reproduces_texels, {"N": 4, "sigma": 0.5}),
+    (pins.test_bilinear_affine_grid_is_exact_and_oriented, {"N": 4}),
+    (pins.test_bilinear_partition_of_unity_and_n1, {}),
+    (pins.test_adj_bilinear_matches_finite_differences, {"N": 4}),
+    (pins.test_single_splat_at_pixel_centre, {"N": 4, "o": 0.6}),
+    (pins.test_single_splat_at_pixel_centre, {"N": 4, "o": 0.995}),
+    (pins.test_fronto_parallel_uv_and_colour_closed_form, {}),
+    (pins.test_lowpass_branch_closed_form, {}),
+    (pins.test_tilted_splat_ray_plane_intersection, {}),
+    (pins.test_two_splats_composite, {}),
+    (pins.test_transmittance_cutoff_stops_the_stack, {}),
+    (pins.test_constant_grid_equals_plain_2dgs, {}),
+    (pins.test_fig2_isoline_facts, {}),
+    (pins.test_invariants_plain_1k, {}),
+    (pins.test_fp32_rectangles_are_conservative, {}),
+    (pins.test_sh_gradient_finite_difference, {}),
+    (fd.test_fd_clamped_opacity_and_lowpass, {}),
+    (fd.test_fd_through_clamped_alpha, {}),
+    (fd.test_fd_with_background_and_ragged_view, {}),
+    (fd.test_fd_all_gradients, {"N": 4, "D": 3}),
+    (fd.test_fd_texture_only_heavy_grid, {}),
+]
+
+
+def _compile(src_text: str, out: str) -> str:
+    cpp = out[:-3] + ".cpp"
+    with open(cpp, "w") as f:
+        f.write(src_text)
+    subprocess.check_call(["g++", *oracle.GXX_FLAGS, "-o", out, cpp])
+    return out
+
+
+@pytest.fixture(scope="module")
+def mutant_libs(tmp_path_factory):
+    src = open(SRC).read()
+    d = tmp_path_factory.mktemp("mutants")
+    jobs = {}
+    for i, (name, (old, new)) in enumerate(MUTANTS.items()):
+        assert src.count(old) == 1, f"mutation site of {name!r} not found once in the oracle"
+        jobs[name] = (src.replace(old, new), str(d / f"m{i}.so"))
+    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        futs = {name: ex.submit(_compile, text, path) for name, (text, path) in jobs.items()}
+        return {name: f.result() for name, f in futs.items()}
+
+
+@pytest.mark.parametrize("name", list(MUTANTS))
+def test_planted_mistake_fails_a_pin(name, mutant_libs, monkeypatch):
+    monkeypatch.setattr(oracle, "_lib", oracle.load(mutant_libs[name]))
+    for pin, kw in PINS:
+        try:
+            pin(**kw)
+        except Exception as e:  # an assertion, or a check that raised on a malformed result
+            print(f"{name}: caught by {pin.__name__}{kw or ''} ({type(e).__name__})")
+            return
+    pytest.fail(f"no pin notices the planted mistake: {name}")

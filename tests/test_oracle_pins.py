@@ -356,6 +356,28 @@ def test_two_splats_composite():
     assert list(tr["ids"]) == [0, 1]
 
 
+def test_transmittance_cutoff_stops_the_stack():
+    """Alg. 1 fwd stops before a splat that would take T below 1e-4: eight
+    co-centred fronto-parallel splats of alpha a = 0.8 at depths 3, 3.5, ...
+    leave T = 0.2^j after j of them (3.2e-4 after five, 6.4e-5 after six),
+    so exactly the first five blend (Eq. 2 over them)."""
+    parts = []
+    for j in range(8):
+        g = np.full((2, 2, 3), (j + 1) / 8.0)
+        s, cam = _fronto_scene(o=0.8, z=3.0 + 0.5 * j, N=2, grid=g, colour=(0, 0, 0))
+        parts.append(s)
+    sc = {k: (np.concatenate([p[k] for p in parts]) if isinstance(parts[0][k], np.ndarray) else parts[0][k])
+          for k in parts[0]}
+    a = float(np.float32(0.8))
+    w = [a * (1 - a) ** j for j in range(5)]
+    x, y = 32, 24
+    r = oracle.render(sc, cam)
+    np.testing.assert_allclose(r["alpha"][y, x], 1 - (1 - a) ** 5, rtol=1e-12)
+    np.testing.assert_allclose(r["rgb"][y, x], sum(wj * (j + 1) / 8.0 for j, wj in enumerate(w)), rtol=1e-12)
+    np.testing.assert_allclose(r["depth"][y, x], sum(wj * (3.0 + 0.5 * j) for j, wj in enumerate(w)), rtol=1e-6)
+    assert list(oracle.pixel_trace(sc, cam, x, y)["ids"]) == [0, 1, 2, 3, 4]
+
+
 def test_constant_grid_equals_plain_2dgs():
     """N = 1 is plain 2DGS (Sec. 4.1); a constant N x N grid must give the same
     image up to rounding, and its texel gradients must sum to the N = 1 gradient
