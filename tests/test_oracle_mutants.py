@@ -42,6 +42,12 @@ MUTANTS = {
     "background dropped": ("rgb[c] = C[c] + T * cx.bg[c];", "rgb[c] = C[c];"),
     "SH basis sign (l = 1, m = -1)": ("put(-c1 * y, 0, -c1, 0);", "put(c1 * y, 0, c1, 0);"),
     "rotation entry sign": ("R[1] = 2 * (x * y - w * z);", "R[1] = 2 * (x * y + w * z);"),
+    "adjugate cofactor sign": ("A[i * 3 + j] = T[r1 * 3 + c1] * T[r2 * 3 + c2] - T[r1 * 3 + c2] * T[r2 * 3 + c1];",
+                               "A[i * 3 + j] = T[r1 * 3 + c1] * T[r2 * 3 + c2] + T[r1 * 3 + c2] * T[r2 * 3 + c1];"),
+    "low-pass branch comparison reversed": ("e.uv_branch = e.rho_uv <= e.rho_lp;", "e.uv_branch = e.rho_uv >= e.rho_lp;"),
+    "uv-to-texel scale N instead of N - 1": ("double up = (N - 1) * (u + sigma) / (2.0 * sigma);",
+                                             "double up = N * (u + sigma) / (2.0 * sigma);"),
+    "SH basis gradient component dropped": ("put(c1 * z, 0, 0, c1);", "put(c1 * z, 0, 0, 0);"),
     # backward (Alg. 1 bwd, Alg. 2 adj-bilinear) and the chain to the parameters
     "adj-bilinear u difference reversed": ("fu_hat += chat[c] * ((C[i10 + c] - C[i00 + c])",
                                            "fu_hat += chat[c] * ((C[i00 + c] - C[i10 + c])"),
@@ -49,6 +55,22 @@ MUTANTS = {
                                               "uv_hat[0] = k * fu_hat;"),
     "low-pass centre gradient sign": ("A.c_hat[0] += rho_hat * kLowPass * -2.0 * e.dx;",
                                       "A.c_hat[0] += rho_hat * kLowPass * 2.0 * e.dx;"),
+    "back-to-front sum weighted by T": ("for (int ch = 0; ch < 3; ++ch) S[ch] += c.col[ch] * w;",
+                                        "for (int ch = 0; ch < 3; ++ch) S[ch] += c.col[ch] * T;"),
+    "1 / (1 + alpha) in the alpha adjoint": ("const double inv1ma = 1.0 / (1.0 - a);",
+                                             "const double inv1ma = 1.0 / (1.0 + a);"),
+    "ray-intersection adjoint sign": ("-(u_hat * e.u + v_hat * e.v) * iz", "(u_hat * e.u + v_hat * e.v) * iz"),
+    "low-pass centre gradient y from dx": ("A.c_hat[1] += rho_hat * kLowPass * -2.0 * e.dy;",
+                                           "A.c_hat[1] += rho_hat * kLowPass * -2.0 * e.dx;"),
+    "depth uv adjoint from the wrong column": ("u_hat += zi_hat * pr.T[6];", "u_hat += zi_hat * pr.T[7];"),
+    "principal point cy dropped from the chain": (
+        "colhat[j][2] = cam.cx * That[0 * 3 + j] + cam.cy * That[1 * 3 + j] + That[2 * 3 + j];",
+        "colhat[j][2] = cam.cx * That[0 * 3 + j] + That[2 * 3 + j];"),
+    "scale adjoint against the other tangent": ("sv_hat += world_hat[1][i] * pr.tv[i];",
+                                                "sv_hat += world_hat[1][i] * pr.tu[i];"),
+    "tangent adjoint with the other scale": ("tu_hat[i] = s[0] * world_hat[0][i];", "tu_hat[i] = s[1] * world_hat[0][i];"),
+    "SH coefficient gradient without the basis": ("g->d_sh[(k * M + m) * 3 + c] += Y[m] * A.rgb_hat[c];",
+                                                  "g->d_sh[(k * M + m) * 3 + c] += A.rgb_hat[c];"),
     "background adjoint dropped": ("a_hat += (dA - bgdot) * t_final * inv1ma;", "a_hat += dA * t_final * inv1ma;"),
     "gradient through a clamped alpha": ("if (!e.clamped) {", "if (true) {"),
     "depth adjoint index": ("A.T_hat[7] += zi_hat * e.v;", "A.T_hat[7] += zi_hat * e.u;"),
