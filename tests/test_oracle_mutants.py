@@ -14,12 +14,17 @@ the finite differences.
 import concurrent.futures as cf
 import os
 import subprocess
+import types
 
 import pytest
 
 import oracle
+from tests import test_adam as adam
 from tests import test_oracle_fd as fd
+from tests import test_oracle_fit2d as fit
+from tests import test_oracle_mip as mip
 from tests import test_oracle_pins as pins
+from tests import test_oracle_texsh as texsh
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "gbill_oracle.cpp")
 
@@ -142,3 +147,70 @@ def test_planted_mistake_fails_a_pin(name, mutant_libs, monkeypatch):
             print(f"{name}: caught by {pin.__name__}{kw or ''} ({type(e).__name__})")
             return
     pytest.fail(f"no pin notices the planted mistake: {name}")
+
+
+# --- the oracle's numpy steps (mip filter, per-texel SH, tile keys, Adam,
+# the image-fitting map and loss): planted in a copy of the module source,
+# whose functions replace the module's for the test
+
+PY_SRC = os.path.join(os.path.dirname(oracle.__file__), "__init__.py")
+
+PY_MUTANTS = {
+    "mip block summed, not averaged": (".mean(axis=(2, 4)))", ".sum(axis=(2, 4)))"),
+    "mip adjoint divided by 2^l": ("/ float(f * f)", "/ float(f)"),
+    "texel SH grid transposed": ('"km,kijmc->kijc"', '"km,kjimc->kijc"'),
+    "texel SH view direction reversed": ("v = p - _campos(cam)[None, :]", "v = _campos(cam)[None, :] - p"),
+    "tile id with x and y swapped": ("t = (tile_offset + ty[:, None] * tiles_x + tx[None, :])",
+                                     "t = (tile_offset + ty[:, None] + tx[None, :] * tiles_x)"),
+    "tile offset dropped": ("t = (tile_offset + ty[:, None] * tiles_x + tx[None, :])",
+                            "t = (ty[:, None] * tiles_x + tx[None, :])"),
+    "Adam without bias correction": ("m_hat = m / (1.0 - beta1 ** step)", "m_hat = m"),
+    "Adam second moment of g, not g^2": ("(1.0 - beta2) * g * g", "(1.0 - beta2) * g"),
+    "fit quaternion with the full angle": ("q[:, 3] = np.sin(th / 2)", "q[:, 3] = np.sin(th)"),
+    "fit angle adjoint sign": ("0.5 * (np.cos(th / 2) * dq[:, 3] - np.sin(th / 2) * dq[:, 0])",
+                               "0.5 * (np.cos(th / 2) * dq[:, 3] + np.sin(th / 2) * dq[:, 0])"),
+    "fit logit adjoint without 1 - o": ("_f64(g[\"opacities\"]) * o * (1.0 - o)", "_f64(g[\"opacities\"]) * o"),
+    "MSE gradient without the factor 2": ("2.0 * r / r.size", "r / r.size"),
+}
+
+PY_PINS = [
+    (mip.test_mip_grid_matches_loops, {}),
+    (mip.test_mip_adjoint_is_the_transpose, {}),
+    (mip.test_top_level_is_the_mean_colour, {"N": 4}),
+    (mip.test_constant_grid_renders_the_same_at_every_level, {}),
+    (mip.test_texture_gradient_at_a_mip_level_by_central_differences, {"lvl": 1}),
+    (texsh.test_degree_zero_coefficient_is_the_colour, {}),
+    (texsh.test_identical_texel_sh_equals_splat_sh, {"Dt": 2}),
+    (texsh.test_texel_sh_gradients_by_central_differences, {"name": "means"}),
+    (texsh.test_texel_sh_gradients_by_central_differences, {"name": "textures"}),
+    (pins.test_tile_keys_by_brute_force, {"tile": 16}),
+    (pins.test_fp32_keys_against_fp64_projection, {}),
+    (adam.test_oracle_adam_constant_gradient_closed_form, {}),
+    (adam.test_oracle_adam_zero_gradient_keeps_parameters, {}),
+    (fit.test_fit_params_closed_forms, {}),
+    (fit.test_mse_closed_form_and_gradient, {}),
+    (fit.test_fit_gradients_by_central_differences, {"name": "theta"}),
+    (fit.test_fit_gradients_by_central_differences, {"name": "logit_opacities"}),
+]
+
+
+@pytest.mark.filterwarnings("ignore::RuntimeWarning")  # a mutant may take sqrt of a negative moment
+@pytest.mark.parametrize("name", list(PY_MUTANTS))
+def test_planted_numpy_mistake_fails_a_pin(name, monkeypatch):
+    old, new = PY_MUTANTS[name]
+    src = open(PY_SRC).read()
+    assert src.count(old) == 1, f"mutation site of {name!r} not found once in the oracle module"
+    mod = types.ModuleType("oracle_mutant")
+    mod.__file__ = oracle.__file__
+    exec(compile(src.replace(old, new), PY_SRC, "exec"), mod.__dict__)
+    for attr, val in vars(mod).items():
+        if callable(val) and getattr(val, "__module__", None) == "oracle_mutant":
+            monkeypatch.setattr(oracle, attr, val)
+    for pin, kw in PY_PINS:
+        try:
+            pin(**kw)
+        except Exception as e:  # an assertion, or a check that raised on a malformed result
+            print(f"{name}: caught by {pin.__name__}{kw or ''} ({type(e).__name__})")
+            return
+    pytest.fail(f"no pin notices the planted mistake: {name}")
+

@@ -482,3 +482,27 @@ def test_fp32_keys_against_fp64_projection():
     ny = (prect[:, 3] // 16 - prect[:, 1] // 16 + 1)
     assert np.array_equal(counts[valid], (nx * ny)[valid])
     assert tiles.max() < 64
+
+
+@pytest.mark.parametrize("tile", [8, 16])
+def test_tile_keys_by_brute_force(tile):
+    """Each splat's keys name exactly the tiles its FP32 pixel rectangle
+    touches (every tile of a non-square view tested against the rectangle),
+    offset by the view's first tile id, with the FP32 depth's bits below."""
+    sc = scenes.planes_scene(4, K=300, tex_n=4, log_scale=(-2.5, 0.7))
+    cam = scenes.look_at([0, 0, -9], [0, 0, 0], 100, 52)
+    off = 1000
+    valid, z32, prect = oracle.keys32(sc, cam)
+    keys, ids = oracle.tile_keys(sc, cam, tile, tile_offset=off)
+    tx_n, ty_n = -(-100 // tile), -(-52 // tile)
+    got = {}
+    for key, k in zip(keys.tolist(), ids.tolist()):
+        got.setdefault(k, set()).add((key >> 32) - off)
+        assert key & 0xFFFFFFFF == int(z32[k:k + 1].view(np.uint32)[0])
+    assert set(got) == set(np.nonzero(valid)[0].tolist())
+    for k, tiles in got.items():
+        x0, y0, x1, y1 = prect[k]
+        expect = {ty * tx_n + tx for ty in range(ty_n) for tx in range(tx_n)
+                  if tx * tile <= x1 and x0 < (tx + 1) * tile and ty * tile <= y1 and y0 < (ty + 1) * tile}
+        assert tiles == expect, k
+
