@@ -87,6 +87,11 @@ MUTANTS = {
     # FP32 tile rectangles (keys)
     "rectangle radius too small": ("static const float kRhoMaxF = 11.0825270903f;",
                                    "static const float kRhoMaxF = 9.0f;"),
+    "rectangle low bound rounded down": ("const float fx0 = std::fmax(std::ceil(lox - 0.5f), 0.0f);",
+                                         "const float fx0 = std::fmax(std::floor(lox - 0.5f), 0.0f);"),
+    "low-pass disk left out of the rectangle": (
+        "const float lox = std::fmin(elx, cx - kLowPassRadiusF), hix = std::fmax(ehx, cx + kLowPassRadiusF);",
+        "const float lox = elx, hix = ehx;"),
 }
 
 # fast pins, cheapest first
@@ -107,6 +112,8 @@ PINS = [
     (pins.test_fig2_isoline_facts, {}),
     (pins.test_invariants_plain_1k, {}),
     (pins.test_fp32_rectangles_are_conservative, {}),
+    (pins.test_fp32_rectangle_of_a_fronto_splat_is_tight, {"s": (0.5, 0.3), "z": 4.0, "f": 64.0}),
+    (pins.test_fp32_rectangle_of_a_fronto_splat_is_tight, {"s": (0.01, 0.02), "z": 5.0, "f": 64.0}),
     (pins.test_sh_gradient_finite_difference, {}),
     (fd.test_fd_clamped_opacity_and_lowpass, {}),
     (fd.test_fd_through_clamped_alpha, {}),

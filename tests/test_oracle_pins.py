@@ -463,6 +463,28 @@ def test_fp32_rectangles_are_conservative():
             assert np.all(r["alpha"][outside] < 1 / 255 * (1 - 1e-5))
 
 
+@pytest.mark.parametrize("s,z,f", [((0.5, 0.3), 4.0, 64.0), ((0.2, 0.45), 6.0, 40.0), ((0.01, 0.02), 5.0, 64.0)])
+def test_fp32_rectangle_of_a_fronto_splat_is_tight(s, z, f):
+    """R15 in closed form: for a splat parallel to the image plane the box of
+    the rho_max ellipse has half-widths sqrt(rho_max) f s / z about the
+    projected centre; united with the low-pass disk of radius sqrt(ln 255)
+    its pixels are [ceil(c - h - 1/2), floor(c + h - 1/2)], clamped to the
+    view (the last case is a sub-pixel splat: the disk decides)."""
+    sc, cam = _fronto_scene(s=s, z=z, f=f)
+    valid, _, prect = oracle.keys32(sc, cam)
+    assert valid[0]
+    rho, r_lp = 2 * math.log(255), math.sqrt(math.log(255))
+    s32 = np.asarray(s, np.float32).astype(np.float64)
+    cx, cy = 32.5, 24.5
+    hx = max(math.sqrt(rho) * f * s32[0] / z, r_lp)
+    hy = max(math.sqrt(rho) * f * s32[1] / z, r_lp)
+    for b in (cx - hx - 0.5, cx + hx - 0.5, cy - hy - 0.5, cy + hy - 0.5):
+        assert abs(b - round(b)) > 1e-3  # no bound within FP32 rounding of an integer
+    expect = [max(math.ceil(cx - hx - 0.5), 0), max(math.ceil(cy - hy - 0.5), 0),
+              min(math.floor(cx + hx - 0.5), 63), min(math.floor(cy + hy - 0.5), 47)]
+    assert [int(v) for v in prect[0]] == expect
+
+
 def test_fp32_keys_against_fp64_projection():
     """FP32 depth = FP64 camera depth to FP32 rounding; culled splats have no
     pixel with alpha >= 1/255; keys sort by tile, then depth, then splat id."""
