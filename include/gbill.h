@@ -297,7 +297,10 @@ gb_status gb_saved_export_keys(gb_saved *saved, uint64_t *keys, int64_t *ids, in
  * sort, tile ranges, per-tile render.  Unless GB_FLAG_NO_SYNC is set the
  * call synchronizes once (to size the instance list) and may grow `saved`.
  * Returns GB_ERR_INVALID_ARG for bad sizes/pointers/options,
- * GB_ERR_UNSUPPORTED for tex_n not in {1,2,4,8,16} or sh_degree > 3. */
+ * GB_ERR_UNSUPPORTED for tex_n not in {1,2,4,8,16} or sh_degree > 3,
+ * GB_ERR_CAPACITY when the frame has 0xF0000000 or more (tile, splat)
+ * instances (a synchronizing forward; a no-sync forward flags it for
+ * gb_saved_check like any instance count above its reservation). */
 gb_status gb_render_forward(gb_context *ctx, gb_saved *saved, const gb_scene *scenes,
                             int32_t n_scenes, const gb_camera *cams, int32_t n_cams,
                             const gb_options *opt, float *rgb, float *depth, float *alpha,

@@ -176,20 +176,23 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce(Load ld, int64_t max
 // Single block: exclusive scan of the block sums in place; total to *total.
 __global__ void __launch_bounds__(kScanThreads) scan_block_sums(uint32_t *sums, int64_t nb, uint32_t *total,
                                                                 Counters *cnt, int64_t capacity) {
-    uint32_t carry = 0;
+    // the carry across blocks is 64-bit: a frame whose instance count passes
+    // 2^32 saturates the reported count and is flagged, not wrapped
+    uint64_t carry = 0;
     for (int64_t base = 0; base < nb; base += kScanThreads) {
         const int64_t i = base + threadIdx.x;
         const uint32_t v = i < nb ? sums[i] : 0u;
         uint32_t tot;
         const uint32_t ex = block_exclusive_scan(v, &tot);
-        if (i < nb) sums[i] = carry + ex;
+        if (i < nb) sums[i] = uint32_t(carry + ex);
         carry += tot;
     }
     if (threadIdx.x == 0) {
-        if (total) *total = carry;
+        const uint32_t sat = carry > 0xFFFFFFFFull ? 0xFFFFFFFFu : uint32_t(carry);
+        if (total) *total = sat;
         if (cnt) {
-            cnt->n_instances = carry;
-            if (int64_t(carry) > capacity) cnt->overflow = 1u;
+            cnt->n_instances = sat;
+            if (carry > uint64_t(capacity)) cnt->overflow = 1u;
         }
     }
 }
