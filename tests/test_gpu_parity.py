@@ -485,6 +485,32 @@ def test_no_sync_capacity_overflow_is_reported():
     assert np.array_equal(rgb.cpu().numpy(), ref_rgb.cpu().numpy())
 
 
+def test_frame_beyond_the_32bit_instance_range_is_refused():
+    """600,000 fronto-parallel splats that each cover all 8,160 tiles of a
+    1920x1080 view make 4.9e9 (tile, splat) instances, past the 32-bit
+    instance index: the synchronizing forward reports GB_ERR_CAPACITY from
+    the device count (which must not wrap) before it allocates the list, and
+    the context renders the next frame normally."""
+    from paper_2412_12734_gb300 import _lib as L
+    from paper_2412_12734_gb300 import render as R
+    K = 600_000
+    big = {
+        "means": np.zeros((K, 3), np.float32), "quats": np.tile(np.array([1, 0, 0, 0], np.float32), (K, 1)),
+        "scales": np.ones((K, 2), np.float32), "opacities": np.full(K, 0.5, np.float32),
+        "sh": np.full((K, 1, 3), 0.5, np.float32), "textures": np.full((K, 1, 1, 3), 0.25, np.float32),
+        "sh_degree": 0, "tex_n": 1, "sigma": 0.5,
+    }
+    cam = scenes.look_at([0.0, 0.0, -2.0], [0, 0, 0], 1920, 1080)
+    rast = R.Rasterizer(0)
+    with pytest.raises(L.GbillError) as ei:
+        rast.forward([R.scene_to_device(big)], [cam])
+    assert ei.value.status == 4
+    sc, cams = CASES["tiny_n4_d3"]()
+    rgb = rast.forward([R.scene_to_device(sc[0])], cams)[0]
+    e, _ = compare_images(rgb.cpu().numpy().reshape(cams[0]["height"], cams[0]["width"], 3),
+                          oracle_run(sc[0], cams[0]), "rgb")
+    assert e <= IMG_TOL
+
 def test_non_finite_splats_are_culled_and_reported():
     """A splat with a NaN centre, one with an infinite scale and one with a
     NaN SH coefficient are culled in every camera; the rest of the frame
