@@ -1123,7 +1123,7 @@ gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int3
             *t /= float(reps);
             return r;
         };
-        auto list = [&](int T, int B, int pi, float t) {
+        auto report = [&](int T, int B, int pi, float t) {  // appends a candidate to the caller's arrays
             if (n < cap) {
                 if (ms) ms[n] = t;
                 if (tiles) tiles[n] = T;
@@ -1144,7 +1144,7 @@ gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int3
                 o.pixels_per_thread = pi;
                 float t = 0.0f;
                 if ((st = time_candidate(o, true, &t)) != GB_OK) break;
-                list(T, B, pi, t);
+                report(T, B, pi, t);
                 if (t < best_ms) {
                     best_ms = t;
                     *best = o;
@@ -1162,7 +1162,7 @@ gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int3
                 c.batch_depth_fwd = B;
                 float t = 0.0f;
                 if ((st = time_candidate(c, false, &t)) != GB_OK) break;
-                list(T, B, 0, t);
+                report(T, B, 0, t);
                 if (t < best_fwd) {
                     best_fwd = t;
                     best->batch_depth_fwd = B;
