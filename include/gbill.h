@@ -68,7 +68,10 @@ typedef enum {
     GB_ERR_UNSUPPORTED = 2, /* valid request the build does not implement          */
     GB_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has the reason)  */
     GB_ERR_CAPACITY = 4,    /* a reserved buffer was too small (no-sync mode)       */
-    GB_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up                   */
+    GB_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up (reserved: no
+                               kernel of this library waits on another block;
+                               persistent blocks take tiles from an atomic
+                               counter)                                        */
     GB_ERR_NONFINITE = 6    /* non-finite values were found where none may be       */
 } gb_status;
 
