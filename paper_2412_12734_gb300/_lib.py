@@ -87,6 +87,15 @@ def declared_symbols() -> list[str]:
     return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]*?\b(gb_\w+)\s*\(", text, re.M)))
 
 
+_bound: tuple = ()
+
+
+def signatures() -> tuple:
+    """Names of the C entry points bound (with argument and result types) by load()."""
+    load()
+    return _bound
+
+
 def load() -> C.CDLL:
     """Loads the CUDA library; raises if it has not been built."""
     global _lib
@@ -128,6 +137,8 @@ def load() -> C.CDLL:
         fn = getattr(L, name)
         fn.restype = res
         fn.argtypes = args
+    global _bound
+    _bound = tuple(sig)
     _lib = L
     return L
 

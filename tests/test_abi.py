@@ -71,6 +71,21 @@ def test_status_strings_and_null_arguments(lib):
     assert lib.gb_render_forward(None, None, None, 0, None, 0, None, None, None, None, None) == 1
 
 
+def test_every_entry_point_rejects_null_handles(lib):
+    """Every call that takes a context or a saved state returns
+    GB_ERR_INVALID_ARG for a null one, before any CUDA call: all arguments
+    null or zero."""
+    import ctypes as C
+    skip = {"gb_context_create", "gb_context_destroy", "gb_saved_destroy", "gb_last_error", "gb_status_string",
+            "gb_kernel_launches"}
+    names = [n for n in L.signatures() if n not in skip]
+    assert len(names) >= 15
+    for n in names:
+        f = getattr(lib, n)
+        args = [0 if t in (C.c_int, C.c_int32, C.c_int64, C.c_long, C.c_uint32) else None for t in f.argtypes]
+        assert f(*args) == 1, n
+
+
 def test_context_on_missing_device_reports_cuda_error(lib):
     """Device index far beyond any machine's count: GB_ERR_CUDA, no crash."""
     h = C.c_void_p()
