@@ -37,6 +37,8 @@ MUTANTS = {
                            "static const double kAlphaMin = 1.0 / 128.0;"),
     "transmittance cutoff 1e-3": ("static const double kTMin = 1e-4;", "static const double kTMin = 1e-3;"),
     "Gaussian exp(-rho)": ("e.G = std::exp(-0.5 * e.rho);", "e.G = std::exp(-e.rho);"),
+    "splats blended in input order": ("return a.first < b.first;", "return false;"),
+    "splats blended back to front": ("return a.first < b.first;", "return a.first > b.first;"),
     "texels transposed": ("const double *c10 = C + ((b.iu + 1) * N + b.iv) * 3;\n"
                           "    const double *c01 = C + ((b.iu) * N + b.iv + 1) * 3;",
                           "const double *c10 = C + ((b.iu) * N + b.iv + 1) * 3;\n"
