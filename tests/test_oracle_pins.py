@@ -199,7 +199,7 @@ def _fronto_scene(s=(0.5, 0.5), o=0.7, z=4.0, N=4, grid=None, colour=(0.1, 0.2, 
 
 
 @pytest.mark.parametrize("N", [1, 2, 4, 8, 16])
-@pytest.mark.parametrize("o", [0.6, 0.995])
+@pytest.mark.parametrize("o", [0.01, 0.6, 0.995])
 def test_single_splat_at_pixel_centre(N, o):
     """u = v = 0 at the centre pixel: alpha = min(0.99, o) (Eq. 4, alpha clamp)
     and colour = bilinear(C, 0, 0) + SH colour (Eq. 5, Sec. 4.2).  For even N
@@ -223,6 +223,19 @@ def test_single_splat_at_pixel_centre(N, o):
     np.testing.assert_allclose(r["alpha"][y, x], alpha, rtol=1e-12)
     np.testing.assert_allclose(r["rgb"][y, x], alpha * (centre + col), rtol=1e-12)
     np.testing.assert_allclose(r["depth"][y, x], alpha * 4.0, rtol=1e-6)
+
+
+def test_faint_splat_below_the_alpha_cutoff_is_culled():
+    """o = 0.003 < 1/255: alpha <= o < 1/255 everywhere, so the splat is culled
+    (R14) and draws nothing, even at its centre; o = 0.004 >= 1/255 draws
+    alpha = o there."""
+    sc, cam = _fronto_scene(o=0.003)
+    assert not oracle.keys32(sc, cam)[0][0]
+    r = oracle.render(sc, cam)
+    assert np.all(r["alpha"] == 0.0) and np.all(r["rgb"] == 0.0)
+    sc, cam = _fronto_scene(o=0.004)
+    assert oracle.keys32(sc, cam)[0][0]
+    np.testing.assert_allclose(oracle.render(sc, cam)["alpha"][24, 32], float(np.float32(0.004)), rtol=1e-12)
 
 
 def test_fronto_parallel_uv_and_colour_closed_form():
