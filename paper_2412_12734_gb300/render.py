@@ -414,8 +414,9 @@ class BatchedRenderer:
     count.  A replay never waits for the host and never allocates; ``check()``
     reports an instance list that outgrew the reservation and
     ``ensure_capacity()`` grows it and captures again.  With
-    ``flags=GB_FLAG_PERSISTENT`` every view and scene renders in one
-    persistent launch per pass.
+    ``flags=GB_FLAG_PERSISTENT`` the views and scenes of each render group
+    (grid size and storage type) share one persistent launch per pass, whose
+    blocks take tiles from a device counter, longest tiles first.
     """
 
     def __init__(self, rast: Rasterizer, scenes: list, cams: list, cam_scene=None, tile: int = 16,
