@@ -391,6 +391,28 @@ def test_transmittance_cutoff_stops_the_stack():
     assert list(oracle.pixel_trace(sc, cam, x, y)["ids"]) == [0, 1, 2, 3, 4]
 
 
+@pytest.mark.parametrize("seed", [2, 7, 12])
+def test_input_order_does_not_matter(seed):
+    """Alg. 1 blends in depth order: permuting the splat arrays leaves the
+    image unchanged and permutes the gradients with them (distinct depths,
+    so no tie is broken by the splat id)."""
+    sc = scenes.tiny_scene(seed, K=8, tex_n=4, sh_degree=2)
+    cam = scenes.tiny_camera(32, 24)
+    perm = np.random.default_rng(seed).permutation(8)
+    sp = dict(sc)
+    for k in ("means", "quats", "scales", "opacities", "sh", "textures"):
+        sp[k] = np.ascontiguousarray(np.asarray(sc[k])[perm])
+    _, z, _ = oracle.keys32(sc, cam)
+    assert len(set(z.view(np.uint32).tolist())) == 8
+    a, b = oracle.render(sc, cam), oracle.render(sp, cam)
+    for k in ("rgb", "depth", "alpha"):
+        np.testing.assert_allclose(b[k], a[k], rtol=0, atol=1e-14)
+    d = np.random.default_rng(seed + 1).standard_normal((24, 32, 3))
+    ga, gb = oracle.backward(sc, cam, d), oracle.backward(sp, cam, d)
+    for k in ("means", "quats", "scales", "opacities", "sh", "textures"):
+        np.testing.assert_allclose(gb[k], ga[k][perm], rtol=1e-12, atol=1e-14)
+
+
 def test_constant_grid_equals_plain_2dgs():
     """N = 1 is plain 2DGS (Sec. 4.1); a constant N x N grid must give the same
     image up to rounding, and its texel gradients must sum to the N = 1 gradient
