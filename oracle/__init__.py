@@ -67,7 +67,7 @@ class _Window(C.Structure):
 
 class _FwdOut(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in
-                ("rgb", "depth", "alpha", "t_final", "n_contrib", "margin_fwd", "margin_grad", "cond", "n_pairs")]
+                ("rgb", "depth", "alpha", "t_final", "n_contrib", "margin_fwd", "margin_grad", "n_pairs")]
 
 
 class _Grads(C.Structure):
@@ -213,12 +213,8 @@ def render(scene: dict, cam: dict, window=None, bg=None, prefilter: bool = False
     """Brute-force FP64 forward of one view (Alg. 1 fwd, Eq. 2, Eq. 5).
 
     Returns rgb [h,w,3], depth, alpha, t_final, n_contrib, margin_fwd,
-    margin_grad, cond (each [h,w]) and the number of (pixel, splat) pairs
-    evaluated.  cond = sum over blended splats of alpha T kappa, where kappa
-    is the first-order sensitivity of the plane hit (u, v), evaluated about
-    the splat's projected centre, to relative perturbations of its terms,
-    over 1 + |u| + |v| (1 on the low-pass branch): the factor by which
-    rounding of the homography entries and pixel offsets reaches u and v.
+    margin_grad (each [h,w]) and the number of (pixel, splat) pairs
+    evaluated.
     """
     scene, _ = _view_scene(scene, cam)
     S = _SceneRef(scene)
@@ -228,7 +224,7 @@ def render(scene: dict, cam: dict, window=None, bg=None, prefilter: bool = False
     out = {
         "rgb": np.zeros((h, w, 3)), "depth": np.zeros((h, w)), "alpha": np.zeros((h, w)),
         "t_final": np.zeros((h, w)), "n_contrib": np.zeros((h, w), np.int32),
-        "margin_fwd": np.zeros((h, w)), "margin_grad": np.zeros((h, w)), "cond": np.zeros((h, w)),
+        "margin_fwd": np.zeros((h, w)), "margin_grad": np.zeros((h, w)),
         "n_pairs": np.zeros(1, np.int64),
     }
     fo = _FwdOut()

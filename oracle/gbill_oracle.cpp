@@ -94,10 +94,6 @@ typedef struct {
     double *margin_fwd;   /* [h*w] min relative distance of a forward-        */
                           /*       discontinuous decision to its threshold  */
     double *margin_grad;  /* [h*w] same over every decision with a kink      */
-    double *cond;         /* [h*w] sum over blended splats of alpha T kappa,  */
-                          /*       kappa = first-order sensitivity of the    */
-                          /*       plane hit (u, v) about the projected      */
-                          /*       centre to relative rounding of its terms  */
     int64_t *n_pairs;     /* [1]   pairs evaluated                           */
 } orc_fwd_out;
 
@@ -324,7 +320,6 @@ struct Proj {
     double dist;      /* |p - cam|                                      */
     double tu[3], tv[3], Rm[9]; /* tangent frame                        */
     double qn[4], qnorm;
-    double m[3];      /* third row of adj(T') / z, T' = T about the centre  */
 };
 
 static void quat_to_rot(const double qn[4], double R[9]) {
@@ -367,16 +362,6 @@ static void project(const orc_scene &sc, const orc_camera &cam, int64_t k, Proj 
     adjugate3(pr.T, pr.adj);
     pr.c[0] = pr.T[2] / pr.T[8];
     pr.c[1] = pr.T[5] / pr.T[8];
-    {
-        /* T' = T with the screen origin moved to the centre: rows 0, 1 minus c times row 2 */
-        const double *T = pr.T;
-        const double z = T[8];
-        const double t00 = T[0] - pr.c[0] * T[6], t01 = T[1] - pr.c[0] * T[7];
-        const double t10 = T[3] - pr.c[1] * T[6], t11 = T[4] - pr.c[1] * T[7];
-        pr.m[0] = (t10 * T[7] - t11 * T[6]) / z;
-        pr.m[1] = (t01 * T[6] - t00 * T[7]) / z;
-        pr.m[2] = (t00 * t11 - t01 * t10) / z;
-    }
     /* camera position -R^T t and view direction */
     double campos[3];
     for (int i = 0; i < 3; ++i)
@@ -526,11 +511,11 @@ struct Ctx {
 /* Runs the front-to-back loop of one pixel; fills the contributor list. */
 static void pixel_forward(const Ctx &cx, int px, int py, std::vector<Contrib> *contribs,
                           double rgb[3], double *depth, double *t_final, int *n_contrib,
-                          double *mfwd, double *mgrad, int64_t *npairs, double *cond = nullptr) {
+                          double *mfwd, double *mgrad, int64_t *npairs) {
     const orc_scene &sc = *cx.sc;
     const double X = px + 0.5, Y = py + 0.5;
     const int N = sc.tex_n;
-    double T = 1.0, C[3] = {0, 0, 0}, Dp = 0.0, kap_sum = 0.0;
+    double T = 1.0, C[3] = {0, 0, 0}, Dp = 0.0;
     double mf = INFINITY, mg = INFINITY;
     int n = 0;
     if (contribs) contribs->clear();
@@ -582,24 +567,6 @@ static void pixel_forward(const Ctx &cx, int px, int py, std::vector<Contrib> *c
         for (int c = 0; c < 3; ++c) cb.col[c] += pr.rgb_sh[c];
         cb.zi = e.uv_branch ? (pr.T[6] * e.u + pr.T[7] * e.v + pr.T[8]) : pr.T[8];
         const double w = e.alpha * T;
-        if (e.uv_branch) {
-            /* first-order sensitivity of (u, v) to relative perturbations of
-               the centre-relative offsets and coefficients, over (1+|u|+|v|):
-               the denominator's cancellation times |u|+|v|, plus the
-               numerators' cancellation (a sub-pixel-thin splat seen from far
-               along its long axis) */
-            const double a0 = std::fabs(pr.m[0] * e.dx), a1 = std::fabs(pr.m[1] * e.dy), a2 = std::fabs(pr.m[2]);
-            const double den = std::fabs(pr.m[0] * e.dx + pr.m[1] * e.dy + pr.m[2]);
-            const double kz = (a0 + a1 + a2) / std::max(den, 1e-300);
-            const double *A = pr.adj;
-            const double zz = std::max(std::fabs(e.zeta[2]), 1e-300);
-            const double nu = (std::fabs(A[0] * e.dx) + std::fabs(A[1] * e.dy)) / zz;
-            const double nv = (std::fabs(A[3] * e.dx) + std::fabs(A[4] * e.dy)) / zz;
-            const double s = std::fabs(e.u) + std::fabs(e.v);
-            kap_sum += w * std::max(kz, (nu + nv + s * kz) / (1.0 + s));
-        } else {
-            kap_sum += w;
-        }
         for (int c = 0; c < 3; ++c) C[c] += cb.col[c] * w;
         Dp += cb.zi * w;
         T = tT;
@@ -612,7 +579,6 @@ static void pixel_forward(const Ctx &cx, int px, int py, std::vector<Contrib> *c
     *n_contrib = n;
     *mfwd = mf;
     *mgrad = mg;
-    if (cond) *cond = kap_sum;
 }
 
 static int num_threads() {
@@ -671,10 +637,10 @@ int orc_render_forward(const orc_scene *sc, const orc_camera *cam, const orc_win
             if (r >= win->h) break;
             for (int c = 0; c < win->w; ++c) {
                 const int64_t o = int64_t(r) * win->w + c;
-                double rgb[3], depth, tf, mf, mg, kp;
+                double rgb[3], depth, tf, mf, mg;
                 int nc;
                 pixel_forward(cx, win->x0 + c, win->y0 + r, nullptr, rgb, &depth, &tf, &nc, &mf, &mg,
-                              &pairs[tid], &kp);
+                              &pairs[tid]);
                 for (int ch = 0; ch < 3; ++ch) out->rgb[o * 3 + ch] = rgb[ch];
                 out->depth[o] = depth;
                 out->alpha[o] = 1.0 - tf;
@@ -682,7 +648,6 @@ int orc_render_forward(const orc_scene *sc, const orc_camera *cam, const orc_win
                 out->n_contrib[o] = nc;
                 out->margin_fwd[o] = mf;
                 out->margin_grad[o] = mg;
-                if (out->cond) out->cond[o] = kp;
             }
         }
     };

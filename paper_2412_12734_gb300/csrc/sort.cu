@@ -133,62 +133,73 @@ struct LoadTileCount {
     }
 };
 
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total) {
-    __shared__ uint32_t wsum[kScanThreads / 32];
+// Exclusive scan over the block's threads, in the type T (uint32_t for the
+// radix histograms, uint64_t for tile counts, whose totals may pass 2^32).
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T *total) {
+    __shared__ T wsum[kScanThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t x = v;
+    T x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        const T y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
     if (lane == 31) wsum[warp] = x;
     __syncthreads();
     if (warp == 0) {
-        uint32_t s = lane < kScanThreads / 32 ? wsum[lane] : 0;
+        T s = lane < kScanThreads / 32 ? wsum[lane] : T(0);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            const T y = __shfl_up_sync(0xffffffffu, s, o);
             if (lane >= o) s += y;
         }
         if (lane < kScanThreads / 32) wsum[lane] = s;
     }
     __syncthreads();
-    const uint32_t before = warp ? wsum[warp - 1] : 0u;
+    const T before = warp ? wsum[warp - 1] : T(0);
     *total = wsum[kScanThreads / 32 - 1];
     __syncthreads();
     return before + x - v;
 }
 
+__device__ __forceinline__ uint32_t saturate32(uint64_t x) {
+    return x > 0xFFFFFFFFull ? 0xFFFFFFFFu : uint32_t(x);
+}
+
+// Every partial sum is formed in 64 bits: one block holds 4,096 counts of up
+// to 2^32 - 1 each, so its total, the running offsets and the frame total can
+// all pass 2^32.  Block sums and offsets are stored saturated at 2^32 - 1;
+// such a frame sets the overflow flag (its total exceeds any capacity), and
+// every emit past the capacity is skipped.
 template <class Load>
 __global__ void __launch_bounds__(kScanThreads) scan_reduce(Load ld, int64_t max_n, const uint32_t *n_dev,
                                                             uint32_t *block_sums) {
     const uint32_t n = load_n(n_dev, max_n);
     const int64_t base = int64_t(blockIdx.x) * kScanTile + int64_t(threadIdx.x) * kScanItems;
-    uint32_t s = 0;
+    uint64_t s = 0;
     for (int i = 0; i < kScanItems; ++i)
         if (base + i < n) s += ld(base + i);
-    uint32_t tot;
-    block_exclusive_scan(s, &tot);
-    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+    uint64_t tot;
+    block_exclusive_scan<uint64_t>(s, &tot);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = saturate32(tot);
 }
 
-// Single block: exclusive scan of the block sums in place; total to *total.
+// Single block: exclusive scan of the block sums in place (64-bit running
+// sums, stored saturated); the total to *total and the counters.
 __global__ void __launch_bounds__(kScanThreads) scan_block_sums(uint32_t *sums, int64_t nb, uint32_t *total,
                                                                 Counters *cnt, int64_t capacity) {
-    // the carry across blocks is 64-bit: a frame whose instance count passes
-    // 2^32 saturates the reported count and is flagged, not wrapped
     uint64_t carry = 0;
     for (int64_t base = 0; base < nb; base += kScanThreads) {
         const int64_t i = base + threadIdx.x;
-        const uint32_t v = i < nb ? sums[i] : 0u;
-        uint32_t tot;
-        const uint32_t ex = block_exclusive_scan(v, &tot);
-        if (i < nb) sums[i] = uint32_t(carry + ex);
+        const uint64_t v = i < nb ? uint64_t(sums[i]) : 0ull;
+        uint64_t tot;
+        const uint64_t ex = block_exclusive_scan<uint64_t>(v, &tot);
+        if (i < nb) sums[i] = saturate32(carry + ex);
         carry += tot;
     }
     if (threadIdx.x == 0) {
-        const uint32_t sat = carry > 0xFFFFFFFFull ? 0xFFFFFFFFu : uint32_t(carry);
+        const uint32_t sat = saturate32(carry);
         if (total) *total = sat;
         if (cnt) {
             cnt->n_instances = sat;
@@ -203,15 +214,15 @@ __global__ void __launch_bounds__(kScanThreads) scan_downsweep(Load ld, int64_t 
     const uint32_t n = load_n(n_dev, max_n);
     const int64_t base = int64_t(blockIdx.x) * kScanTile + int64_t(threadIdx.x) * kScanItems;
     uint32_t v[kScanItems];
-    uint32_t s = 0;
+    uint64_t s = 0;
     for (int i = 0; i < kScanItems; ++i) {
         v[i] = base + i < n ? ld(base + i) : 0u;
         s += v[i];
     }
-    uint32_t tot;
-    uint32_t run = block_sums[blockIdx.x] + block_exclusive_scan(s, &tot);
+    uint64_t tot;
+    uint64_t run = uint64_t(block_sums[blockIdx.x]) + block_exclusive_scan<uint64_t>(s, &tot);
     for (int i = 0; i < kScanItems; ++i) {
-        if (base + i < n) out[base + i] = run;
+        if (base + i < n) out[base + i] = saturate32(run);
         run += v[i];
     }
 }
