@@ -58,7 +58,7 @@
 extern "C" {
 #endif
 
-#define GBILL_ABI_VERSION 3
+#define GBILL_ABI_VERSION 4
 #define GBILL_MAX_CAMERAS 64
 #define GBILL_MAX_SCENES 16
 
@@ -270,10 +270,17 @@ uint64_t gb_kernel_launches(void);
  * screen homography with the projected centre c moved to the origin and
  * (m20, m21, m22) = third row of adj(T') / z; a pixel at offset (dx, dy) from
  * c hits the splat at u = (t11 dx - t01 dy) / (m20 dx + m21 dy + m22), v =
- * (t00 dy - t10 dx) / (same).  visible[r] = 1 if the record survived culling
- * (other rows are undefined).  `cap` = records the host arrays hold.
- * Synchronizes. */
-gb_status gb_saved_export_records(gb_saved *saved, float *rec, uint8_t *visible, int64_t cap,
+ * (t00 dy - t10 dx) / (same).  c = c_hi + c_lo with c_hi on the 1/512-pixel
+ * grid.  Every field is the FP32 rounding of its double-float value.  A record
+ * whose plane-hit evaluation is ill-conditioned (a thin splat seen along its
+ * long axis, or a grazing one) stores z negated and is evaluated in extended
+ * precision from its low parts: rec_lo[r][12] (host, nullable) receives them,
+ * lo(t11), -lo(t01), -lo(t10), lo(t00), lo(m20), lo(m21), 0, 0, then the
+ * centre terms -(t11 c_lo.x - t01 c_lo.y), -(t00 c_lo.y - t10 c_lo.x),
+ * lo(m22) - (m20 c_lo.x + m21 c_lo.y), 0 (zeros for other records).
+ * visible[r] = 1 if the record survived culling (other rows are undefined).
+ * `cap` = records the host arrays hold.  Synchronizes. */
+gb_status gb_saved_export_records(gb_saved *saved, float *rec, float *rec_lo, uint8_t *visible, int64_t cap,
                                   int64_t *count);
 
 /* Copies the sorted instance list of the last forward to HOST arrays: keys[i]

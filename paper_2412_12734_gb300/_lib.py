@@ -119,7 +119,7 @@ def load() -> C.CDLL:
         "gb_saved_phase_times": (C.c_int, [vp, C.POINTER(C.c_float), i32]),
         "gb_kernel_launches": (C.c_uint64, []),
         "gb_saved_export_keys": (C.c_int, [vp, vp, vp, vp, i64, C.POINTER(i64)]),
-        "gb_saved_export_records": (C.c_int, [vp, vp, vp, i64, C.POINTER(i64)]),
+        "gb_saved_export_records": (C.c_int, [vp, vp, vp, vp, i64, C.POINTER(i64)]),
         "gb_render_forward": (C.c_int, [vp, vp, C.POINTER(gb_scene), i32, C.POINTER(gb_camera), i32,
                                         C.POINTER(gb_options), vp, vp, vp, vp]),
         "gb_render_backward": (C.c_int, [vp, vp, vp, vp, vp, C.POINTER(gb_grads), i32, vp]),

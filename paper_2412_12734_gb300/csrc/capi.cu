@@ -33,6 +33,7 @@ struct gb_saved {
     gb_context *ctx;
     int64_t cap_rec, cap_inst, cap_pix, cap_tiles;
     Record *rec;
+    RecordLo *rec_lo;
     uint32_t *depth_key, *keys_tmp, *vals_tmp, *dkeys_sorted, *perm, *offsets;
     uint2 *rect, *pbox;
     int32_t *inv;
@@ -112,6 +113,7 @@ gb_status reserve_records(gb_saved *s, int64_t n) {
     GB_CUDA(ctx, cudaDeviceSynchronize());
     const int64_t c = n + n / 8 + 1024;
     GB_CUDA(ctx, alloc_t(&s->rec, c));
+    GB_CUDA(ctx, alloc_t(&s->rec_lo, c));
     GB_CUDA(ctx, alloc_t(&s->depth_key, c));
     GB_CUDA(ctx, alloc_t(&s->keys_tmp, c));
     GB_CUDA(ctx, alloc_t(&s->vals_tmp, c));
@@ -432,7 +434,7 @@ gb_status gb_saved_create(gb_context *ctx, gb_saved **out) {
 gb_status gb_saved_destroy(gb_saved *s) {
     if (!s) return GB_OK;
     cudaDeviceSynchronize();
-    void *ptrs[] = {s->rec, s->depth_key, s->keys_tmp, s->vals_tmp, s->dkeys_sorted, s->perm,
+    void *ptrs[] = {s->rec, s->rec_lo, s->depth_key, s->keys_tmp, s->vals_tmp, s->dkeys_sorted, s->perm,
                     s->offsets, s->rect, s->pbox, s->inv, s->rec_grad, s->inst_tile, s->inst_val, s->inst_tile_tmp,
                     s->inst_val_tmp, s->tiles_sorted, s->vals_sorted, s->ranges, s->tl_keys, s->tl_vals,
                     s->tl_keys_tmp, s->tl_vals_tmp, s->tl_keys_out, s->tile_list, s->work, s->t_final, s->last,
@@ -538,7 +540,8 @@ gb_status gb_saved_export_keys(gb_saved *s, uint64_t *keys, int64_t *ids, int32_
     return GB_OK;
 }
 
-gb_status gb_saved_export_records(gb_saved *s, float *rec, uint8_t *visible, int64_t cap, int64_t *count) {
+gb_status gb_saved_export_records(gb_saved *s, float *rec, float *rec_lo, uint8_t *visible, int64_t cap,
+                                  int64_t *count) {
     if (!s || !count || cap < 0) return fail(s ? s->ctx : nullptr, GB_ERR_INVALID_ARG, "bad arguments");
     if (!s->has_forward) return fail(s->ctx, GB_ERR_INVALID_ARG, "no forward recorded on this saved state");
     *count = s->n_records;
@@ -547,10 +550,15 @@ gb_status gb_saved_export_records(gb_saved *s, float *rec, uint8_t *visible, int
     if (!rec || !visible) return fail(s->ctx, GB_ERR_INVALID_ARG, "null output array");
     GB_CUDA(s->ctx, cudaStreamSynchronize(s->stream));
     GB_CUDA(s->ctx, cudaMemcpy(rec, s->rec, size_t(n) * sizeof(Record), cudaMemcpyDeviceToHost));
+    if (rec_lo) GB_CUDA(s->ctx, cudaMemcpy(rec_lo, s->rec_lo, size_t(n) * sizeof(RecordLo), cudaMemcpyDeviceToHost));
     uint32_t *keys = static_cast<uint32_t *>(malloc(size_t(n) * 4));
     if (!keys) return fail(s->ctx, GB_ERR_INVALID_ARG, "host allocation failed");
     cudaError_t e = cudaMemcpy(keys, s->depth_key, size_t(n) * 4, cudaMemcpyDeviceToHost);
-    for (int64_t i = 0; i < n && e == cudaSuccess; ++i) visible[i] = keys[i] != 0xFFFFFFFFu;
+    for (int64_t i = 0; i < n && e == cudaSuccess; ++i) {
+        visible[i] = keys[i] != 0xFFFFFFFFu;
+        // low parts exist for visible flagged records only (depth stored negated)
+        if (rec_lo && !(visible[i] && rec[16 * i + 7] < 0.0f)) memset(rec_lo + 12 * i, 0, 12 * sizeof(float));
+    }
     free(keys);
     GB_CUDA(s->ctx, e);
     return GB_OK;
@@ -687,7 +695,7 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
     // equal depths keep record order)
     GB_CUDA(ctx, compact_visible(s->depth_key, R, s->offsets, s->dkeys_sorted, s->perm, s->scratch, s->scratch_bytes,
                                  st));
-    GB_CUDA(ctx, launch_record(f, s->perm, &s->cnt->n_visible, nullptr, R, s->rec, st));
+    GB_CUDA(ctx, launch_record(f, s->perm, &s->cnt->n_visible, nullptr, R, s->rec, s->rec_lo, st));
     GB_MARK(1);
     GB_CUDA(ctx, radix_sort_pairs(s->dkeys_sorted, s->perm, s->keys_tmp, s->vals_tmp, s->dkeys_sorted, s->perm, R,
                                   &s->cnt->n_visible, 0, 32, s->scratch, s->scratch_bytes, st));
@@ -729,6 +737,7 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
     }
     RenderBufs b;
     b.rec = s->rec;
+    b.rec_lo = s->rec_lo;
     b.perm = s->perm;
     b.inst_val = s->vals_sorted;
     b.ranges = s->ranges;
@@ -776,7 +785,7 @@ gb_status gb_render_backward(gb_context *ctx, gb_saved *s, const float *d_rgb, c
             GB_CUDA(ctx, cudaMemsetAsync(d.g_tex, 0, size_t(rows) * d.N * d.N * 3 * sizeof(float), st));
     }
     const int64_t R = s->n_records;
-    zero_rec_grad<<<unsigned(std::min<int64_t>(ceil_div(std::max<int64_t>(R, 1) * 4, 256), 65535)), 256, 0, st>>>(
+    zero_rec_grad<<<unsigned(std::min<int64_t>(ceil_div(std::max<int64_t>(R, 1) * (kRecGrad / 4), 256), 65535)), 256, 0, st>>>(
         s->rec_grad, s->cnt, R);
     GB_CUDA(ctx, cudaGetLastError());
     count_launches(1);
@@ -784,6 +793,7 @@ gb_status gb_render_backward(gb_context *ctx, gb_saved *s, const float *d_rgb, c
     if (timing) GB_CUDA(ctx, cudaEventRecord(s->ev[9], st));
     RenderBwdBufs b;
     b.fw.rec = s->rec;
+    b.fw.rec_lo = s->rec_lo;
     b.fw.perm = s->perm;
     b.fw.inst_val = s->vals_sorted;
     b.fw.ranges = s->ranges;
@@ -861,7 +871,7 @@ constexpr size_t na_round(size_t b) { return (b + 255) & ~size_t(255); }
 constexpr size_t kNaRadixBytes = size_t(kNaMaxInstances / 4096) * 512 * 4 + 64 * 1024;
 constexpr size_t kNaScratchBytes =
     na_round(sizeof(Counters)) + na_round(2 * kMaxGroups * 4) +
-    na_round(kNaMaxRecords * sizeof(Record)) + 7 * na_round(kNaMaxRecords * 4) + 2 * na_round(kNaMaxRecords * 8) +
+    na_round(kNaMaxRecords * sizeof(Record)) + na_round(kNaMaxRecords * sizeof(RecordLo)) + 7 * na_round(kNaMaxRecords * 4) + 2 * na_round(kNaMaxRecords * 8) +
     6 * na_round(kNaMaxInstances * 4) + 2 * na_round(kNaMaxPixels * 4) + na_round(kNaMaxTiles * 8) +
     6 * na_round(kNaMaxTiles * 4) + na_round(kNaRadixBytes);
 
@@ -923,6 +933,7 @@ gb_status gb_render_forward_noalloc(gb_context *ctx, const gb_scene *scenes, int
     Counters *cnt = static_cast<Counters *>(carve(sizeof(Counters)));
     carve(2 * kMaxGroups * 4);  // work counters (persistent mode is not offered here)
     Record *rec = static_cast<Record *>(carve(kNaMaxRecords * sizeof(Record)));
+    RecordLo *rec_lo = static_cast<RecordLo *>(carve(kNaMaxRecords * sizeof(RecordLo)));
     uint32_t *depth_key = static_cast<uint32_t *>(carve(kNaMaxRecords * 4));
     uint32_t *rec_id = static_cast<uint32_t *>(carve(kNaMaxRecords * 4));
     uint32_t *keys_tmp = static_cast<uint32_t *>(carve(kNaMaxRecords * 4));
@@ -959,7 +970,7 @@ gb_status gb_render_forward_noalloc(gb_context *ctx, const gb_scene *scenes, int
     GB_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(Counters), st));
     GB_CUDA(ctx, cudaMemsetAsync(ranges, 0, size_t(f.n_tiles) * sizeof(uint2), st));
     GB_CUDA(ctx, launch_preprocess(f, max_k, depth_key, rec_id, rect, pbox, rec, cnt, st));
-    GB_CUDA(ctx, launch_record(f, nullptr, nullptr, depth_key, R, rec, st));
+    GB_CUDA(ctx, launch_record(f, nullptr, nullptr, depth_key, R, rec, rec_lo, st));
     GB_CUDA(ctx, radix_sort_pairs(depth_key, rec_id, keys_tmp, vals_tmp, dkeys_sorted, perm, R, nullptr, 0, 32,
                                   scratch, kNaRadixBytes, st));
     GB_CUDA(ctx, tile_counts_scan(f, perm, rect, R, &cnt->n_visible, offsets, scratch, kNaRadixBytes, cnt,
@@ -986,6 +997,7 @@ gb_status gb_render_forward_noalloc(gb_context *ctx, const gb_scene *scenes, int
     }
     RenderBufs b;
     b.rec = rec;
+    b.rec_lo = rec_lo;
     b.perm = perm;
     b.inst_val = vals_sorted;
     b.ranges = ranges;

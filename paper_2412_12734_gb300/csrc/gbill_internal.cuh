@@ -83,13 +83,63 @@ struct Frame {
 //   q1 = ( m20,  m21,  m22,  z  )           zeta_z  = m20 dx + m21 dy + m22
 //   q2 = ( c_hi.x, c_hi.y, c_lo.x, c_lo.y ) c = c_hi + c_lo (double-float centre)
 //   q3 = ( o, r_sh, g_sh, b_sh )            opacity and SH colour
+//
+// The centre is split so that c_hi lies on a 1/512-pixel grid: x + 0.5 - c_hi
+// is then exact for |x - c_hi| < 2^15, and c_lo = c - c_hi (|c_lo| <= 2^-10).
+// A record whose plane-hit evaluation is ill-conditioned (a thin splat seen
+// along its long axis, or one seen at a grazing angle: see kPreciseKappa)
+// stores its depth negated (q1.w = -z) and takes the extended-precision
+// evaluation of render_common.cuh with its RecordLo.
 struct __align__(16) Record {
     float4 q0, q1, q2, q3;
 };
 
-// Gradient of one record (16 floats): d q0 (4), d m20, d m21, d m22, d z,
-// d c (2), d o, d rgb (3), 2 unused.
+// Low parts of a flagged record (48 bytes, indexed like Record): the FP32
+// residues of the homography entries, hi + lo = the double-float value, and
+// the products of the hi entries with the centre's low part, so that for a
+// pixel offset dh = x + 0.5 - c_hi (exact) the plane hit is
+//   zeta_x = q0.x dh_x + q0.y dh_y + (l0.x dh_x + l0.y dh_y) + l2.x
+//   zeta_y = q0.z dh_x + q0.w dh_y + (l0.z dh_x + l0.w dh_y) + l2.y
+//   zeta_z = q1.x dh_x + q1.y dh_y + q1.z + (l1.x dh_x + l1.y dh_y) + l2.z
+// up to the dropped lo x lo products.
+//   l0 = lo of (t11, -t01, -t10, t00)
+//   l1 = (lo m20, lo m21, 0, 0)
+//   l2 = (-(q0.x c_lo.x + q0.y c_lo.y), -(q0.z c_lo.x + q0.w c_lo.y),
+//         lo m22 - (q1.x c_lo.x + q1.y c_lo.y), 0)
+struct __align__(16) RecordLo {
+    float4 l0, l1, l2;
+};
+
+// A record is flagged for the extended-precision evaluation when its
+// conditioning bound exceeds this: kappa bounds, over the part of the
+// footprint where the plane hit decides alpha (u^2 + v^2 <= 2 ln 255), the
+// ratio of the magnitudes of the terms summed into zeta (times |u|, |v| for
+// zeta_z) to |zeta_z|, so an FP32 evaluation about the centre has an error of
+// about kappa 2^-24 in u and v.  Below 32 that is < 2e-6.
+constexpr float kPreciseKappa = 32.0f;
+
+// Gradient of one record, accumulated by the backward render in the splat's
+// own (u, v) frame.  With N = [A | B | P] the camera-space splat frame (A =
+// s_u R t_u, B = s_v R t_v, P the centre; Eq. 3 up to the intrinsics K), a
+// pixel's plane hit (u, v) solves K N (u, v, 1) ~ (x, y, 1), and for any
+// change of the parameters
+//   du = -e0 + u e2,  dv = -e1 + v e2,  dw = w e2,   e = N^-1 dN (u, v, 1)
+// (w the hit depth).  So the plane-hit part of the gradient is
+//   dL/dN = -N^-T H,   H = sum over pairs (u^, v^, W) (x) (u, v, 1),
+// W = -(u^ u + v^ v) - w^ w, w^ the depth adjoint of a plane-hit pair: nine
+// sums of O(1) multiples of the adjoints (|u|, |v| <= 3.33 where alpha >=
+// 1/255), without the cancellation that gradients of the homography entries
+// about the centre carry for a thin splat seen along its long axis (there the
+// entries' gradients are sums of terms |d| times larger that cancel in the
+// parameter chain).  The scale gradients are then -H00 / s_u and -H11 / s_v.
+// Slots (16 floats, 4 float4):
+//   0..8   H row-major (u^ u, u^ v, u^, v^ u, v^ v, v^, W u, W v, W)
+//   9, 10  d c from the screen-space low-pass branch
+//   11     sum of the depth adjoints of low-pass pairs (depth = centre z)
+//   12     d o;  13..15  d rgb (SH colour)
 constexpr int kRecGrad = 16;
+constexpr int kGH = 0, kGCentreLP = 9, kGDepthLP = 11, kGOpacity = 12, kGRgb = 13;
+constexpr int kRecVals = 16;  // slots the backward render fills
 
 // Device-side counters of one forward.
 struct Counters {
@@ -156,7 +206,7 @@ cudaError_t launch_preprocess(const Frame &f, int64_t max_k, uint32_t *depth_key
 // Homography part (q0..q2) of the render records: of ids[0 .. *n_dev) or,
 // with ids NULL, of every record whose depth key is not the culled marker.
 cudaError_t launch_record(const Frame &f, const uint32_t *ids, const uint32_t *n_dev, const uint32_t *depth_key,
-                          int64_t max_n, Record *rec, cudaStream_t s);
+                          int64_t max_n, Record *rec, RecordLo *rec_lo, cudaStream_t s);
 cudaError_t launch_preprocess_bwd(const Frame &f, int64_t max_k, const float *rec_grad,
                                   const int32_t *inv_perm, cudaStream_t s);
 
@@ -192,6 +242,7 @@ cudaError_t launch_adam(const gb_adam_tensor *ts, int n, const gb_adam_config &c
 // render_fwd.cu / render_bwd.cu
 struct RenderBufs {
     const Record *rec;        // indexed by record id
+    const RecordLo *rec_lo;   // indexed by record id; read for flagged records only
     const uint32_t *perm;     // depth-sorted position -> record id
     const uint32_t *inst_val; // sorted instances -> depth-sorted position
     const uint2 *ranges;      // [n_tiles] (begin, end)

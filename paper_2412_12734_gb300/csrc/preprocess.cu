@@ -188,31 +188,62 @@ __device__ __forceinline__ Frame3 tangent_frame(const float q[4]) {
 
 // Homography block in FP64 for splats seen at a grazing angle, where the
 // determinant J = fx fy (n . P) / z of the block cancels: t = (t00, t01, t10,
-// t11), m = (m20, m21, m22) = (fy n_x, fx n_y, fx fy n.P / z) / z.
+// t11), m = (m20, m21, m22) = (fy n_x, fx n_y, fx fy n.P / z) / z, each as an
+// FP32 pair hi + lo.
 __device__ void homography_fp64(const float p[3], const float q[4], float su, float sv,
-                                const CamDev &c, float t[4], float m[3]) {
+                                const CamDev &c, DF t[4], DF m[3]) {
     const double qn = sqrt((double)q[0] * q[0] + (double)q[1] * q[1] + (double)q[2] * q[2] +
                            (double)q[3] * q[3]);
     const double w = q[0] / qn, x = q[1] / qn, y = q[2] / qn, z = q[3] / qn;
     const double tu[3] = {1 - 2 * (y * y + z * z), 2 * (x * y + w * z), 2 * (x * z - w * y)};
     const double tv[3] = {2 * (x * y - w * z), 1 - 2 * (x * x + z * z), 2 * (y * z + w * x)};
-    const double tw[3] = {2 * (x * z + w * y), 2 * (y * z - w * x), 1 - 2 * (x * x + y * y)};
     double A[3], B[3], P[3], n[3];
     for (int i = 0; i < 3; ++i) {
         const float *r = c.R + 3 * i;
         A[i] = su * ((double)r[0] * tu[0] + (double)r[1] * tu[1] + (double)r[2] * tu[2]);
         B[i] = sv * ((double)r[0] * tv[0] + (double)r[1] * tv[1] + (double)r[2] * tv[2]);
-        n[i] = (double)su * sv * ((double)r[0] * tw[0] + (double)r[1] * tw[1] + (double)r[2] * tw[2]);
         P[i] = (double)r[0] * p[0] + (double)r[1] * p[1] + (double)r[2] * p[2] + (double)c.t[i];
     }
+    // the homography's normal A x B (not s_u s_v R t_w: the camera's FP32 R is
+    // orthonormal only to ~1e-8, which a grazing view's n . P would magnify)
+    n[0] = A[1] * B[2] - A[2] * B[1];
+    n[1] = A[2] * B[0] - A[0] * B[2];
+    n[2] = A[0] * B[1] - A[1] * B[0];
     const double iz = 1.0 / P[2], xz = P[0] * iz, yz = P[1] * iz;
-    t[0] = (float)(c.fx * (A[0] - A[2] * xz));
-    t[1] = (float)(c.fx * (B[0] - B[2] * xz));
-    t[2] = (float)(c.fy * (A[1] - A[2] * yz));
-    t[3] = (float)(c.fy * (B[1] - B[2] * yz));
-    m[0] = (float)(c.fy * n[0] * iz);
-    m[1] = (float)(c.fx * n[1] * iz);
-    m[2] = (float)((double)c.fx * c.fy * (n[0] * P[0] + n[1] * P[1] + n[2] * P[2]) * iz * iz);
+    const double tv_[4] = {c.fx * (A[0] - A[2] * xz), c.fx * (B[0] - B[2] * xz), c.fy * (A[1] - A[2] * yz),
+                           c.fy * (B[1] - B[2] * yz)};
+    const double mv[3] = {c.fy * n[0] * iz, c.fx * n[1] * iz,
+                          (double)c.fx * c.fy * (n[0] * P[0] + n[1] * P[1] + n[2] * P[2]) * iz * iz};
+    for (int i = 0; i < 4; ++i) {
+        t[i].hi = (float)tv_[i];
+        t[i].lo = (float)(tv_[i] - (double)t[i].hi);
+    }
+    for (int i = 0; i < 3; ++i) {
+        m[i].hi = (float)mv[i];
+        m[i].lo = (float)(mv[i] - (double)m[i].hi);
+    }
+}
+
+// Conditioning bound of the FP32 plane-hit evaluation about the centre (the
+// flag threshold kPreciseKappa).  Over the disk u^2 + v^2 <= r^2 (r^2 = 2 ln
+// 255, beyond which alpha < 1/255) the pixel offset is d = T2 (u, v) / w, w =
+// t20 u + t21 v + z the hit depth, and zeta_z = J / w (J = t00 t11 - t01 t10
+// = m22 z).  The terms summed into zeta_x = t11 d_x - t01 d_y are at most
+// (|t11| |row 0| + |t01| |row 1|) r / w, so relative to |zeta_z| the factor w
+// cancels; the terms of zeta_z times |u| <= r add r ((|m20| |row 0| + |m21|
+// |row 1|) r / |J| + w_max / z).  The bound is the screen-space anisotropy of
+// the splat (large for a thin splat seen along its long axis) plus the
+// grazing-angle cancellation of zeta_z.
+__device__ __forceinline__ float plane_hit_kappa(float t00, float t01, float t10, float t11, float t20, float t21,
+                                                 float m20, float m21, float m22, float z) {
+    const float r = kLowPassRadius * 1.41421356f;  // sqrt(2 ln 255)
+    const float n0 = sqrtf(t00 * t00 + t01 * t01), n1 = sqrtf(t10 * t10 + t11 * t11);
+    const float aJ = fabsf(m22) * z;
+    const float ku = fmaxf(fabsf(t11) * n0 + fabsf(t01) * n1, fabsf(t10) * n0 + fabsf(t00) * n1);
+    const float kz = (fabsf(m20) * n0 + fabsf(m21) * n1) * r;
+    const float wmax = z + r * sqrtf(t20 * t20 + t21 * t21);
+    const float k = r * (ku + kz) / aJ + r * wmax / z;
+    return k == k ? k : INFINITY;  // J = 0: unbounded
 }
 
 // --------------------------------------------------------- forward kernel --
@@ -284,11 +315,11 @@ __global__ void __launch_bounds__(256, 4) preprocess_kernel(Frame f, uint32_t *d
 // ------------------------------------------------------- record kernel --
 // The homography part of the render record (q0..q2) of record r: the whole
 // record chain in double-float (~48 bits): unit quaternion, tangent frame,
-// camera-space axes A = s_u R t_u, B = s_v R t_v, normal n = A x B = s_u s_v
-// R t_w, centre P, centre-relative block t and m = (fy n_x, fx n_y, fx fy n.P
+// camera-space axes A = s_u R t_u, B = s_v R t_v, normal n = A x B, centre P, centre-relative block t and m = (fy n_x, fx n_y, fx fy n.P
 // / z) / z.  Only n.P cancels (grazing view); below cos = 1/256 the block is
-// redone in FP64.
-__device__ __forceinline__ void record_homography(const Frame &f, int64_t r, Record *rec_out) {
+// redone in FP64.  A record whose conditioning bound passes kPreciseKappa is
+// flagged (depth stored negated) and gets its low parts in rec_lo.
+__device__ __forceinline__ void record_homography(const Frame &f, int64_t r, Record *rec_out, RecordLo *lo_out) {
     const int ci = camera_of_record(f, r);
     const CamDev &cam = f.cams[ci];
     const SceneDev &sc = f.scenes[cam.scene];
@@ -306,15 +337,16 @@ __device__ __forceinline__ void record_homography(const Frame &f, int64_t r, Rec
              yzq = df_mul(y, zq), wx = df_mul(w, x), wy = df_mul(w, y), wz = df_mul(w, zq);
     const DF tu[3] = {df_one_minus_twice(df_add(yy, zz)), df_twice(df_add(xy, wz)), df_twice(df_sub(xzq, wy))};
     const DF tv[3] = {df_twice(df_sub(xy, wz)), df_one_minus_twice(df_add(xx, zz)), df_twice(df_add(yzq, wx))};
-    const DF tw[3] = {df_twice(df_add(xzq, wy)), df_twice(df_sub(yzq, wx)), df_one_minus_twice(df_add(xx, yy))};
-    const DF suv = two_prod(su, sv);
-    DF A[3], B[3], nv[3];
+    DF A[3], B[3];
     for (int i = 0; i < 3; ++i) {
         const float *row = cam.R + 3 * i;
         A[i] = df_mul_f(df_dot_fd(row, tu), su);
         B[i] = df_mul_f(df_dot_fd(row, tv), sv);
-        nv[i] = df_mul(df_dot_fd(row, tw), suv);
     }
+    // normal of the homography, A x B (the camera's FP32 R is orthonormal only
+    // to ~1e-8, so s_u s_v R t_w would differ by that, magnified in a grazing n . P)
+    const DF nv[3] = {df_sub(df_mul(A[1], B[2]), df_mul(A[2], B[1])), df_sub(df_mul(A[2], B[0]), df_mul(A[0], B[2])),
+                      df_sub(df_mul(A[0], B[1]), df_mul(A[1], B[0]))};
     const DF Px = df_affine(cam.R + 0, p, cam.t[0]);
     const DF Py = df_affine(cam.R + 3, p, cam.t[1]);
     const DF Pz = df_affine(cam.R + 6, p, cam.t[2]);
@@ -326,44 +358,66 @@ __device__ __forceinline__ void record_homography(const Frame &f, int64_t r, Rec
     np = df_add(np, df_mul(nv[1], Py));
     np = df_add(np, df_mul(nv[2], Pz));
     const float nmag = fabsf(nv[0].hi * Px.hi) + fabsf(nv[1].hi * Py.hi) + fabsf(nv[2].hi * Pz.hi);
-    float t00, t01, t10, t11, m20, m21, m22;
+    DF t[4], m[3];  // t00, t01, t10, t11; m20, m21, m22
     if (fabsf(np.hi) * 256.0f > nmag) {
-        t00 = df_mul_f(df_sub(A[0], df_mul(A[2], xz)), cam.fx).hi;
-        t01 = df_mul_f(df_sub(B[0], df_mul(B[2], xz)), cam.fx).hi;
-        t10 = df_mul_f(df_sub(A[1], df_mul(A[2], yz)), cam.fy).hi;
-        t11 = df_mul_f(df_sub(B[1], df_mul(B[2], yz)), cam.fy).hi;
-        m20 = df_div(df_mul_f(nv[0], cam.fy), Pz).hi;
-        m21 = df_div(df_mul_f(nv[1], cam.fx), Pz).hi;
-        m22 = df_div(df_div(df_mul(np, two_prod(cam.fx, cam.fy)), Pz), Pz).hi;
+        t[0] = df_mul_f(df_sub(A[0], df_mul(A[2], xz)), cam.fx);
+        t[1] = df_mul_f(df_sub(B[0], df_mul(B[2], xz)), cam.fx);
+        t[2] = df_mul_f(df_sub(A[1], df_mul(A[2], yz)), cam.fy);
+        t[3] = df_mul_f(df_sub(B[1], df_mul(B[2], yz)), cam.fy);
+        m[0] = df_div(df_mul_f(nv[0], cam.fy), Pz);
+        m[1] = df_div(df_mul_f(nv[1], cam.fx), Pz);
+        m[2] = df_div(df_div(df_mul(np, two_prod(cam.fx, cam.fy)), Pz), Pz);
     } else {
-        float t[4], m[3];
         homography_fp64(p, q, su, sv, cam, t, m);
-        t00 = t[0]; t01 = t[1]; t10 = t[2]; t11 = t[3];
-        m20 = m[0]; m21 = m[1]; m22 = m[2];
     }
+    // centre: c_hi on the 1/512-pixel grid (exact offsets x + 0.5 - c_hi), c_lo the rest
+    const float chx = rintf(cxd.hi * 512.0f) * (1.0f / 512.0f), chy = rintf(cyd.hi * 512.0f) * (1.0f / 512.0f);
+    const float clx = __fadd_rn(__fsub_rn(cxd.hi, chx), cxd.lo), cly = __fadd_rn(__fsub_rn(cyd.hi, chy), cyd.lo);
+    const float kap = plane_hit_kappa(t[0].hi, t[1].hi, t[2].hi, t[3].hi, A[2].hi, B[2].hi, m[0].hi, m[1].hi, m[2].hi,
+                                      z);
+    const bool precise = !(kap <= kPreciseKappa);
     Record &R = rec_out[r];
-    R.q0 = make_float4(t11, -t01, -t10, t00);
-    R.q1 = make_float4(m20, m21, m22, z);
-    R.q2 = make_float4(cxd.hi, cyd.hi, cxd.lo, cyd.lo);
+    R.q0 = make_float4(t[3].hi, -t[1].hi, -t[2].hi, t[0].hi);
+    R.q1 = make_float4(m[0].hi, m[1].hi, m[2].hi, precise ? -z : z);
+    R.q2 = make_float4(chx, chy, clx, cly);
+    if (precise) {
+        RecordLo &L = lo_out[r];
+        L.l0 = make_float4(t[3].lo, -t[1].lo, -t[2].lo, t[0].lo);
+        L.l1 = make_float4(m[0].lo, m[1].lo, 0.0f, 0.0f);
+        L.l2 = make_float4(-fmaf(t[3].hi, clx, -t[1].hi * cly), -fmaf(-t[2].hi, clx, t[0].hi * cly),
+                           m[2].lo - fmaf(m[0].hi, clx, m[1].hi * cly), 0.0f);
+    }
 }
 
 // One thread per visible record: ids[j] for j < *n_dev (the compacted visible
 // records), or, without ids, every record whose depth key is not the culled
 // marker.
 __global__ void __launch_bounds__(128) record_kernel(Frame f, const uint32_t *ids, const uint32_t *n_dev,
-                                                     const uint32_t *depth_key, int64_t max_n, Record *rec_out) {
+                                                     const uint32_t *depth_key, int64_t max_n, Record *rec_out,
+                                                     RecordLo *lo_out) {
     const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t n = n_dev ? min(int64_t(*n_dev), max_n) : max_n;
     if (j >= n) return;
     const int64_t r = ids ? int64_t(ids[j]) : j;
     if (!ids && depth_key[r] == 0xFFFFFFFFu) return;
-    record_homography(f, r, rec_out);
+    record_homography(f, r, rec_out, lo_out);
 }
 
 // -------------------------------------------------------- backward kernel --
-// One thread per splat of scene `si`, summing its cameras.  The SH degree D
-// is a template parameter so that the per-coefficient accumulators and the
-// basis stay in registers.
+__device__ __forceinline__ void cross3(const float a[3], const float b[3], float c[3]) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// One thread per splat of scene `si`, summing its cameras: the record
+// gradient (kRecGrad layout) of each camera through dL/dN = -N^-T H, N = [A B
+// P] (N^-1 has rows (B x P, P x A, A x B) / det N), to the centre (plus the
+// low-pass projection and depth terms), the scales (-H00 / s_u, -H11 / s_v)
+// and a torque A x dL/dA + B x dL/dB of the splat frame, which becomes the
+// quaternion gradient 2 (0, tau) q / |q| once summed.  The SH degree D is a
+// template parameter so that the per-coefficient accumulators and the basis
+// stay in registers.
 template <int D>
 __global__ void __launch_bounds__(128) preprocess_bwd_kernel(Frame f, int si, const float *rec_grad,
                                                              const int32_t *inv_perm) {
@@ -376,7 +430,7 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(Frame f, int si, co
     const float su = sc.scales[2 * k], sv = sc.scales[2 * k + 1];
     const Frame3 fr = tangent_frame(q);
     constexpr int M = (D + 1) * (D + 1);
-    float g_p[3] = {0, 0, 0}, g_tu[3] = {0, 0, 0}, g_tv[3] = {0, 0, 0};
+    float g_p[3] = {0, 0, 0}, g_tau[3] = {0, 0, 0};
     float g_su = 0.0f, g_sv = 0.0f, g_o = 0.0f;
     float g_sh[M][3];
 #pragma unroll
@@ -388,67 +442,61 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(Frame f, int si, co
         const int32_t j = inv_perm[cam.rec_off + k];
         if (j < 0) continue;
         seen = true;
+        float g[kRecGrad];
         const float4 *gp = reinterpret_cast<const float4 *>(rec_grad + int64_t(j) * kRecGrad);
-        const float4 g0 = gp[0], g1 = gp[1], g2 = gp[2], g3 = gp[3];
-        // forward recompute (camera space)
-        float a[3], b[3], A[3], B[3], P[3];
-        for (int i = 0; i < 3; ++i) { a[i] = su * fr.tu[i]; b[i] = sv * fr.tv[i]; }
+#pragma unroll
+        for (int i = 0; i < kRecGrad / 4; ++i) {
+            const float4 v = gp[i];
+            g[4 * i] = v.x; g[4 * i + 1] = v.y; g[4 * i + 2] = v.z; g[4 * i + 3] = v.w;
+        }
+        // camera-space frame N = [A B P]
+        float A[3], B[3], P[3];
         for (int i = 0; i < 3; ++i) {
             const float *row = cam.R + 3 * i;
-            A[i] = row[0] * a[0] + row[1] * a[1] + row[2] * a[2];
-            B[i] = row[0] * b[0] + row[1] * b[1] + row[2] * b[2];
+            A[i] = su * (row[0] * fr.tu[0] + row[1] * fr.tu[1] + row[2] * fr.tu[2]);
+            B[i] = sv * (row[0] * fr.tv[0] + row[1] * fr.tv[1] + row[2] * fr.tv[2]);
             P[i] = row[0] * p[0] + row[1] * p[1] + row[2] * p[2] + cam.t[i];
         }
-        const float z = P[2], iz = 1.0f / z;
-        const float xz = P[0] * iz, yz = P[1] * iz;
-        const float t00 = cam.fx * (A[0] - A[2] * xz), t01 = cam.fx * (B[0] - B[2] * xz);
-        const float t10 = cam.fy * (A[1] - A[2] * yz), t11 = cam.fy * (B[1] - B[2] * yz);
-        const float t20 = A[2], t21 = B[2];
-        const float m20 = (t10 * t21 - t11 * t20) * iz;
-        const float m21 = (t01 * t20 - t00 * t21) * iz;
-        const float m22 = (t00 * t11 - t01 * t10) * iz;
-        // record gradients
-        float h00 = g0.w, h01 = -g0.y, h10 = -g0.z, h11 = g0.x;  // d t00, d t01, d t10, d t11
-        float h20 = 0.0f, h21 = 0.0f;
-        const float gm20 = g1.x, gm21 = g1.y, gm22 = g1.z;
-        float gz = g1.w;
-        // m20 = (t10 t21 - t11 t20) / z
-        h10 += gm20 * t21 * iz; h21 += gm20 * t10 * iz; h11 -= gm20 * t20 * iz; h20 -= gm20 * t11 * iz;
-        gz -= gm20 * m20 * iz;
-        // m21 = (t01 t20 - t00 t21) / z
-        h01 += gm21 * t20 * iz; h20 += gm21 * t01 * iz; h00 -= gm21 * t21 * iz; h21 -= gm21 * t00 * iz;
-        gz -= gm21 * m21 * iz;
-        // m22 = (t00 t11 - t01 t10) / z
-        h00 += gm22 * t11 * iz; h11 += gm22 * t00 * iz; h01 -= gm22 * t10 * iz; h10 -= gm22 * t01 * iz;
-        gz -= gm22 * m22 * iz;
-        // centre c = (fx xz + cx, fy yz + cy)
-        float gxz = g2.x * cam.fx, gyz = g2.y * cam.fy;
-        // t00 = fx (A0 - A2 xz) ...
-        float gA[3] = {cam.fx * h00, cam.fy * h10, 0.0f}, gB[3] = {cam.fx * h01, cam.fy * h11, 0.0f};
-        gA[2] = -cam.fx * h00 * xz - cam.fy * h10 * yz + h20;
-        gB[2] = -cam.fx * h01 * xz - cam.fy * h11 * yz + h21;
-        gxz -= cam.fx * (h00 * A[2] + h01 * B[2]);
-        gyz -= cam.fy * (h10 * A[2] + h11 * B[2]);
-        float gP[3] = {gxz * iz, gyz * iz, gz - (gxz * xz + gyz * yz) * iz};
+        float n0[3], n1[3], n2[3];
+        cross3(B, P, n0);
+        cross3(P, A, n1);
+        cross3(A, B, n2);
+        const float det = A[0] * n0[0] + A[1] * n0[1] + A[2] * n0[2];
+        // det = 0: the plane holds the camera centre, every pair was skipped (H = 0)
+        const float idet = det != 0.0f ? 1.0f / det : 0.0f;
+        // dL/dA, dL/dB, dL/dP: columns of -N^-T H
+        float gN[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                gN[c][i] = -(g[kGH + c] * n0[i] + g[kGH + 3 + c] * n1[i] + g[kGH + 6 + c] * n2[i]) * idet;
+        // low-pass branch: centre c = (fx P0 / P2 + cx, fy P1 / P2 + cy); depth P2
+        const float iz = 1.0f / P[2];
+        const float gcx = g[kGCentreLP] * cam.fx * iz, gcy = g[kGCentreLP + 1] * cam.fy * iz;
+        gN[2][0] += gcx;
+        gN[2][1] += gcy;
+        gN[2][2] += g[kGDepthLP] - (gcx * P[0] + gcy * P[1]) * iz;
+        g_su -= g[kGH + 0] / su;
+        g_sv -= g[kGH + 4] / sv;
+        float ta[3], tb[3];
+        cross3(A, gN[0], ta);
+        cross3(B, gN[1], tb);
         // back to world space (R^T)
         for (int i = 0; i < 3; ++i) {
-            const float ga = cam.R[i] * gA[0] + cam.R[3 + i] * gA[1] + cam.R[6 + i] * gA[2];
-            const float gb = cam.R[i] * gB[0] + cam.R[3 + i] * gB[1] + cam.R[6 + i] * gB[2];
-            g_p[i] += cam.R[i] * gP[0] + cam.R[3 + i] * gP[1] + cam.R[6 + i] * gP[2];
-            g_su += ga * fr.tu[i];
-            g_sv += gb * fr.tv[i];
-            g_tu[i] += su * ga;
-            g_tv[i] += sv * gb;
+            const float r0 = cam.R[i], r1 = cam.R[3 + i], r2 = cam.R[6 + i];
+            g_p[i] += r0 * gN[2][0] + r1 * gN[2][1] + r2 * gN[2][2];
+            g_tau[i] += r0 * (ta[0] + tb[0]) + r1 * (ta[1] + tb[1]) + r2 * (ta[2] + tb[2]);
         }
-        g_o += g2.z;
+        g_o += g[kGOpacity];
         // SH colour
-        const float grgb[3] = {g2.w, g3.x, g3.y};
+        const float grgb[3] = {g[kGRgb], g[kGRgb + 1], g[kGRgb + 2]};
         float d[3] = {p[0] - cam.campos[0], p[1] - cam.campos[1], p[2] - cam.campos[2]};
         const float dist = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         for (int i = 0; i < 3; ++i) d[i] /= dist;
-        float Y[16], G[16][3];
+        float Y[16], Gs[16][3];
         sh_basis(D, d[0], d[1], d[2], Y);
-        sh_basis_grad(D, d[0], d[1], d[2], G);
+        sh_basis_grad(D, d[0], d[1], d[2], Gs);
         float gd[3] = {0, 0, 0};
 #pragma unroll
         for (int m = 0; m < M; ++m)
@@ -456,21 +504,13 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(Frame f, int si, co
             for (int ch = 0; ch < 3; ++ch) {
                 g_sh[m][ch] += Y[m] * grgb[ch];
                 const float kc = load_sh(sc, (k * M + m) * 3 + ch) * grgb[ch];
-                gd[0] += kc * G[m][0];
-                gd[1] += kc * G[m][1];
-                gd[2] += kc * G[m][2];
+                gd[0] += kc * Gs[m][0];
+                gd[1] += kc * Gs[m][1];
+                gd[2] += kc * Gs[m][2];
             }
         const float dd = gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2];
         for (int i = 0; i < 3; ++i) g_p[i] += (gd[i] - d[i] * dd) / dist;
     }
-    // tangents -> normalised quaternion -> raw quaternion
-    const float w = fr.qn[0], x = fr.qn[1], y = fr.qn[2], z = fr.qn[3];
-    float gq[4];
-    gq[0] = 2.0f * (g_tu[1] * z - g_tu[2] * y - g_tv[0] * z + g_tv[2] * x);
-    gq[1] = 2.0f * (g_tu[1] * y + g_tu[2] * z + g_tv[0] * y + g_tv[2] * w) - 4.0f * g_tv[1] * x;
-    gq[2] = 2.0f * (g_tu[1] * x - g_tu[2] * w + g_tv[0] * x + g_tv[2] * z) - 4.0f * g_tu[0] * y;
-    gq[3] = 2.0f * (g_tu[1] * w + g_tu[2] * x - g_tv[0] * w + g_tv[2] * y) - 4.0f * (g_tu[0] + g_tv[1]) * z;
-    const float qd = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * z;
     if (!seen) {
         // culled everywhere (possibly for non-finite parameters): exact zeros
         if (sc.g_means) for (int i = 0; i < 3; ++i) sc.g_means[3 * k + i] = 0.0f;
@@ -484,8 +524,16 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(Frame f, int si, co
     }
     if (sc.g_means)
         for (int i = 0; i < 3; ++i) sc.g_means[3 * k + i] = g_p[i];
-    if (sc.g_quats)
-        for (int i = 0; i < 4; ++i) sc.g_quats[4 * k + i] = (gq[i] - fr.qn[i] * qd) / fr.qnorm;
+    if (sc.g_quats) {
+        // a world rotation delta turns q into (1, delta / 2) q: the gradient of the unit
+        // quaternion is 2 (0, tau) q (tangent to the sphere), divided by |q| for the raw one
+        const float w = fr.qn[0], x = fr.qn[1], y = fr.qn[2], z = fr.qn[3];
+        const float s2 = 2.0f / fr.qnorm;
+        sc.g_quats[4 * k + 0] = -s2 * (g_tau[0] * x + g_tau[1] * y + g_tau[2] * z);
+        sc.g_quats[4 * k + 1] = s2 * (w * g_tau[0] + g_tau[1] * z - g_tau[2] * y);
+        sc.g_quats[4 * k + 2] = s2 * (w * g_tau[1] + g_tau[2] * x - g_tau[0] * z);
+        sc.g_quats[4 * k + 3] = s2 * (w * g_tau[2] + g_tau[0] * y - g_tau[1] * x);
+    }
     if (sc.g_scales) { sc.g_scales[2 * k] = g_su; sc.g_scales[2 * k + 1] = g_sv; }
     if (sc.g_opac) sc.g_opac[k] = g_o;
     if (sc.g_sh)
@@ -507,9 +555,9 @@ cudaError_t launch_preprocess(const Frame &f, int64_t max_k, uint32_t *depth_key
 }
 
 cudaError_t launch_record(const Frame &f, const uint32_t *ids, const uint32_t *n_dev, const uint32_t *depth_key,
-                          int64_t max_n, Record *rec, cudaStream_t s) {
+                          int64_t max_n, Record *rec, RecordLo *rec_lo, cudaStream_t s) {
     if (max_n <= 0) return cudaSuccess;
-    record_kernel<<<unsigned(ceil_div(max_n, 128)), 128, 0, s>>>(f, ids, n_dev, depth_key, max_n, rec);
+    record_kernel<<<unsigned(ceil_div(max_n, 128)), 128, 0, s>>>(f, ids, n_dev, depth_key, max_n, rec, rec_lo);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -91,9 +91,11 @@ __device__ __forceinline__ float warp_reduce_scatter32(float v[32], int lane) {
     return keep + __shfl_xor_sync(0xffffffffu, send, 1);
 }
 
-// Warp-reduced values: 0..13 record gradients, 14..25 the RGB gradient of the
-// grid's four corner texels (0,0), (0,N-1), (N-1,0), (N-1,N-1).
-constexpr int kCornerSlot = 14;
+// Warp-reduced values: 0..15 record gradients (kRecGrad layout), 16..27 the
+// RGB gradient of the grid's four corner texels (0,0), (0,N-1), (N-1,0),
+// (N-1,N-1).
+constexpr int kCornerSlot = kRecVals;
+static_assert(kCornerSlot + 12 <= 32, "record and corner-texel values share one 32-value reduce-scatter");
 // For N >= 8, above this many distinct edge/interior cells in a (warp, splat)
 // pair the lanes add their texel weights to shared memory directly instead of
 // one reduce-scatter per cell (measured: faster at N = 8, slower at N <= 4;
@@ -135,10 +137,12 @@ __device__ __forceinline__ void put(float &slot, float v) {
 
 // ACC: add to g[] (second and later pixels of a thread); otherwise the slots
 // this pair owns are assigned (g[] holds zeros on entry).
+// lo: the splat's RecordLo when its record is flagged for the extended-
+// precision plane hit (the same splat for the whole warp), else null.
 template <int N, typename TexT, bool ACC>
-__device__ __forceinline__ bool pair_adjoint(Pix &px, uint32_t idx, const float4 *rec, const staged_t<TexT> *tex,
-                                             float sigma, float kN, float g[32], Rem &rem, uint32_t &npairs,
-                                             uint32_t &ncontrib) {
+__device__ __forceinline__ bool pair_adjoint(Pix &px, uint32_t idx, const float4 *rec, const RecordLo *lo,
+                                             const staged_t<TexT> *tex, float sigma, float kN, float g[32], Rem &rem,
+                                             uint32_t &npairs, uint32_t &ncontrib) {
     rem.w00 = rem.w10 = rem.w01 = rem.w11 = 0.0f;
     rem.c0 = rem.c1 = rem.c2 = 0.0f;
     rem.base = 0;
@@ -147,11 +151,11 @@ __device__ __forceinline__ bool pair_adjoint(Pix &px, uint32_t idx, const float4
     const bool live = px.inside && idx < px.last;
     npairs += live ? 1u : 0u;
     const float4 q0 = rec[0], q1 = rec[1], q2 = rec[2], q3 = rec[3];
-    const float dx = (px.xf - q2.x) - q2.z, dy = (px.yf - q2.y) - q2.w;
-    const float zz = fmaf(q1.x, dx, fmaf(q1.y, dy, q1.z));
+    const Hit h = lo ? plane_hit_ext(px.xf, px.yf, q0, q1, q2, *lo) : plane_hit(px.xf, px.yf, q0, q1, q2);
+    const float dx = h.dx, dy = h.dy, zz = h.zz;
     const float rz = fast_rcp(zz);
-    const float u = fmaf(q0.x, dx, q0.y * dy) * rz;
-    const float v = fmaf(q0.z, dx, q0.w * dy) * rz;
+    const float u = h.zx * rz;
+    const float v = h.zy * rz;
     const float ruv = fmaf(u, u, v * v);
     const float rlp = kLowPass * fmaf(dx, dx, dy * dy);
     const bool uvb = ruv <= rlp;
@@ -173,9 +177,9 @@ __device__ __forceinline__ bool pair_adjoint(Pix &px, uint32_t idx, const float4
     col[2] += q3.w;
     const float w = alpha * Ti;
     const float ch0 = w * px.dC0, ch1 = w * px.dC1, ch2 = w * px.dC2;
-    put<ACC>(g[11], ch0);
-    put<ACC>(g[12], ch1);
-    put<ACC>(g[13], ch2);
+    put<ACC>(g[kGRgb + 0], ch0);
+    put<ACC>(g[kGRgb + 1], ch1);
+    put<ACC>(g[kGRgb + 2], ch2);
     // adj-bilinear: grid adjoint and uv adjoint
     float uh = 0.0f, vh = 0.0f;
     if (N == 1) {
@@ -233,7 +237,8 @@ __device__ __forceinline__ bool pair_adjoint(Pix &px, uint32_t idx, const float4
         if (v > -sigma && v < sigma) vh = kN * fvh;
     }
     // alpha adjoint
-    const float zi = uvb ? q1.z * q1.w * rz : q1.w;
+    const float z = fabsf(q1.w);  // negated on flagged records
+    const float zi = uvb ? q1.z * z * rz : z;
     float ah = px.dC0 * (col[0] * Ti - px.S0 * iom) + px.dC1 * (col[1] * Ti - px.S1 * iom) +
                px.dC2 * (col[2] * Ti - px.S2 * iom);
     ah += px.dD * (zi * Ti - px.SD * iom) + px.dTfin * iom;
@@ -245,40 +250,38 @@ __device__ __forceinline__ bool pair_adjoint(Pix &px, uint32_t idx, const float4
     const float zih = px.dD * w;
     float rhoh = 0.0f;
     if (!clamped) {
-        put<ACC>(g[10], ah * G);
+        put<ACC>(g[kGOpacity], ah * G);
         rhoh = -0.5f * alpha * ah;
     }
-    float zzh = 0.0f, dxh = 0.0f, dyh = 0.0f;
+    // W = zeta_z zeta_z^: the depth's and (u, v)'s dependence on zeta_z
+    float W;
     if (uvb) {
         uh = fmaf(2.0f * u, rhoh, uh);
         vh = fmaf(2.0f * v, rhoh, vh);
-        // zi = m22 z / zeta_z
-        g[6] += zih * q1.w * rz;
-        g[7] += zih * q1.z * rz;
-        zzh = -zih * zi * rz;
+        // the hit depth zi moves with the plane coordinates: its adjoint enters W
+        W = -zih * zi;
     } else {
-        dxh = 2.0f * kLowPass * dx * rhoh;
-        dyh = 2.0f * kLowPass * dy * rhoh;
-        g[7] += zih;
+        const float c = -2.0f * kLowPass * rhoh;
+        g[kGCentreLP + 0] += c * dx;
+        g[kGCentreLP + 1] += c * dy;
+        g[kGDepthLP] += zih;
+        W = 0.0f;
     }
-    const float zxh = uh * rz, zyh = vh * rz;
-    zzh -= (uh * u + vh * v) * rz;
-    put<ACC>(g[0], zxh * dx);
-    put<ACC>(g[1], zxh * dy);
-    put<ACC>(g[2], zyh * dx);
-    put<ACC>(g[3], zyh * dy);
-    put<ACC>(g[4], zzh * dx);
-    put<ACC>(g[5], zzh * dy);
-    g[6] += zzh;
-    dxh += zxh * q0.x + zyh * q0.z + zzh * q1.x;
-    dyh += zxh * q0.y + zyh * q0.w + zzh * q1.y;
-    put<ACC>(g[8], -dxh);
-    put<ACC>(g[9], -dyh);
+    W = W - fmaf(uh, u, vh * v);
+    put<ACC>(g[kGH + 0], uh * u);
+    put<ACC>(g[kGH + 1], uh * v);
+    put<ACC>(g[kGH + 2], uh);
+    put<ACC>(g[kGH + 3], vh * u);
+    put<ACC>(g[kGH + 4], vh * v);
+    put<ACC>(g[kGH + 5], vh);
+    put<ACC>(g[kGH + 6], W * u);
+    put<ACC>(g[kGH + 7], W * v);
+    put<ACC>(g[kGH + 8], W);
     return true;
 }
 
 // Grids of N = 4: texel weights on one border line of the grid go through
-// slots 14..25 of the 32-value reduce-scatter.  The weights of a pixel whose
+// slots kCornerSlot .. kCornerSlot + 11 of the 32-value reduce-scatter.  The weights of a pixel whose
 // u (v) is clamped to the grid's border lie on the first or last column
 // i_u = 0, N-1 (row i_v = 0, N-1): two texels at cell indices (i, i+1) along
 // it.  The line holding most of the warp's pixels is taken, with a window of
@@ -436,12 +439,13 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
 #pragma unroll
             for (int q = 0; q < 32; ++q) g[q] = 0.0f;
             Rem rem[P];
-            bool act = pair_adjoint<N, TexT, false>(pix[0], uint32_t(bs + i), s_rec + 4 * i, s_tex + i * NN, sigma, kN,
-                                              g, rem[0], npairs, ncontrib);
+            const RecordLo *lo = s_rec[4 * i + 1].w < 0.0f ? b.fw.rec_lo + staged_record(cam, s_k[i]) : nullptr;
+            bool act = pair_adjoint<N, TexT, false>(pix[0], uint32_t(bs + i), s_rec + 4 * i, lo, s_tex + i * NN, sigma,
+                                                    kN, g, rem[0], npairs, ncontrib);
 #pragma unroll
             for (int p = 1; p < P; ++p)
-                act |= pair_adjoint<N, TexT, true>(pix[p], uint32_t(bs + i), s_rec + 4 * i, s_tex + i * NN, sigma, kN,
-                                             g, rem[p], npairs, ncontrib);
+                act |= pair_adjoint<N, TexT, true>(pix[p], uint32_t(bs + i), s_rec + 4 * i, lo, s_tex + i * NN, sigma,
+                                                   kN, g, rem[p], npairs, ncontrib);
             if (!__any_sync(0xffffffffu, act)) continue;
             int t0 = 0, step = 0;
             if (N == 4) line_window<N, P>(rem, g, t0, step);

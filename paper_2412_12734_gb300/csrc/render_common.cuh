@@ -232,4 +232,63 @@ __device__ __forceinline__ void grid_colour(const Quad &q, const Cell<N> &c, flo
 // exp(-rho / 2) through the SFU exponential.
 __device__ __forceinline__ float gauss(float rho) { return __expf(-0.5f * rho); }
 
+// Plane hit of the pixel centre (xf, yf) for a record (Record): the offset
+// d = (dx, dy) from the projected centre and zeta = adj(T') (d, 1) up to the
+// record's scale, so that u = zx / zz, v = zy / zz.
+struct Hit {
+    float dx, dy, zx, zy, zz;
+};
+
+// FP32 evaluation about the centre (every record not flagged precise).
+__device__ __forceinline__ Hit plane_hit(float xf, float yf, const float4 &q0, const float4 &q1, const float4 &q2) {
+    Hit h;
+    h.dx = (xf - q2.x) - q2.z;
+    h.dy = (yf - q2.y) - q2.w;
+    h.zz = fmaf(q1.x, h.dx, fmaf(q1.y, h.dy, q1.z));
+    h.zx = fmaf(q0.x, h.dx, q0.y * h.dy);
+    h.zy = fmaf(q0.z, h.dx, q0.w * h.dy);
+    return h;
+}
+
+// a0 x + a1 y + (l0 x + l1 y + k) with one rounding of the leading sum: the
+// product a1 y splits exactly into p + e (FMA), a0 x + p is rounded once (FMA),
+// and the low-order terms are added in FP32.
+__device__ __forceinline__ float dot2_ext(float a0, float a1, float l0, float l1, float k, float x, float y) {
+    const float p = __fmul_rn(a1, y);
+    const float e = __fmaf_rn(a1, y, -p);
+    const float s = __fmaf_rn(a0, x, p);
+    return __fadd_rn(s, __fmaf_rn(l1, y, __fmaf_rn(l0, x, __fadd_rn(e, k))));
+}
+
+// Extended-precision evaluation for a flagged record (depth stored negated):
+// the offsets from c_hi are exact (c_hi lies on the 1/512-pixel grid), the
+// homography entries are the double-float pairs of Record + RecordLo, and
+// each zeta component is the sum of its terms with only its own rounding
+// left (error-free products and, for zeta_z, an error-free two-sum of the
+// m21 dy + m22 part), so u and v carry a few ulps whatever the cancellation
+// between the terms.  dx, dy (rounded) serve the low-pass term and the
+// adjoints.
+__device__ __forceinline__ Hit plane_hit_ext(float xf, float yf, const float4 &q0, const float4 &q1, const float4 &q2,
+                                             const RecordLo &L) {
+    Hit h;
+    const float dxh = __fsub_rn(xf, q2.x), dyh = __fsub_rn(yf, q2.y);
+    h.dx = __fsub_rn(dxh, q2.z);
+    h.dy = __fsub_rn(dyh, q2.w);
+    h.zx = dot2_ext(q0.x, q0.y, L.l0.x, L.l0.y, L.l2.x, dxh, dyh);
+    h.zy = dot2_ext(q0.z, q0.w, L.l0.z, L.l0.w, L.l2.y, dxh, dyh);
+    const float p = __fmul_rn(q1.y, dyh);
+    const float e1 = __fmaf_rn(q1.y, dyh, -p);
+    const float t = __fadd_rn(p, q1.z);
+    const float bb = __fsub_rn(t, p);
+    const float e2 = __fadd_rn(__fsub_rn(p, __fsub_rn(t, bb)), __fsub_rn(q1.z, bb));
+    const float sz = __fmaf_rn(q1.x, dxh, t);
+    h.zz = __fadd_rn(sz, __fmaf_rn(L.l1.y, dyh, __fmaf_rn(L.l1.x, dxh, __fadd_rn(__fadd_rn(e1, e2), L.l2.z))));
+    return h;
+}
+
+// Record id of staged splat s (its grid row s_k minus the camera's block offset).
+__device__ __forceinline__ int64_t staged_record(const CamDev &cam, int32_t s_k) {
+    return int64_t(s_k) - cam.tex_row + cam.rec_off;
+}
+
 }  // namespace gbill

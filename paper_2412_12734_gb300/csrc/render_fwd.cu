@@ -33,17 +33,16 @@ struct FPix {
 // the warp (a finished pixel's result is dropped), blended only where alpha
 // passes the cutoff and the pixel's transmittance stays above the stop bound.
 template <int N, typename TexT, bool WIDE>
-__device__ __forceinline__ void fwd_pair(FPix &q, const float4 &q0, const float4 &q1, const float4 &q2,
-                                         const float4 &q3, const staged_t<TexT, WIDE> *tex, uint32_t idx1,
-                                         float sigma, float kN, uint32_t &npairs, uint32_t &nblend) {
+__device__ __forceinline__ void fwd_pair(FPix &q, const Hit &h, const float4 &q1, const float4 &q3,
+                                         const staged_t<TexT, WIDE> *tex, uint32_t idx1, float sigma, float kN,
+                                         uint32_t &npairs, uint32_t &nblend) {
     npairs += q.done ? 0u : 1u;
-    const float dx = (q.xf - q2.x) - q2.z, dy = (q.yf - q2.y) - q2.w;
-    const float zz = fmaf(q1.x, dx, fmaf(q1.y, dy, q1.z));
+    const float zz = h.zz;
     const float rz = fast_rcp(zz);
-    const float u = fmaf(q0.x, dx, q0.y * dy) * rz;
-    const float v = fmaf(q0.z, dx, q0.w * dy) * rz;
+    const float u = h.zx * rz;
+    const float v = h.zy * rz;
     const float ruv = fmaf(u, u, v * v);
-    const float rlp = kLowPass * fmaf(dx, dx, dy * dy);
+    const float rlp = kLowPass * fmaf(h.dx, h.dx, h.dy * h.dy);
     const bool uvb = ruv <= rlp;
     const float rho = uvb ? ruv : rlp;
     const float alpha = fminf(kAlphaMax, q3.x * gauss(rho));
@@ -58,7 +57,8 @@ __device__ __forceinline__ void fwd_pair(FPix &q, const float4 &q0, const float4
         q.C0 = fmaf(col[0] + q3.y, w, q.C0);
         q.C1 = fmaf(col[1] + q3.z, w, q.C1);
         q.C2 = fmaf(col[2] + q3.w, w, q.C2);
-        const float zi = uvb ? q1.z * q1.w * rz : q1.w;
+        const float z = fabsf(q1.w);  // negated on flagged records
+        const float zi = uvb ? q1.z * z * rz : z;
         q.Dp = fmaf(zi, w, q.Dp);
         q.T = tT;
         q.last = idx1;
@@ -124,10 +124,19 @@ __device__ __forceinline__ void fwd_tile(const Frame &f, const RenderBufs &b, in
             if (!(s_mask[i] & wbit)) continue;
             const float4 q0 = s_rec[4 * i + 0], q1 = s_rec[4 * i + 1], q2 = s_rec[4 * i + 2],
                          q3 = s_rec[4 * i + 3];
+            if (q1.w < 0.0f) {
+                // flagged record (the same for the whole warp): extended-precision plane hit
+                const RecordLo L = b.rec_lo[staged_record(cam, s_k[i])];
 #pragma unroll
-            for (int p = 0; p < P; ++p)
-                fwd_pair<N, TexT, WIDE>(pix[p], q0, q1, q2, q3, s_tex + i * NN, uint32_t(bs + i + 1), sigma, kN,
-                                        npairs, nblend);
+                for (int p = 0; p < P; ++p)
+                    fwd_pair<N, TexT, WIDE>(pix[p], plane_hit_ext(pix[p].xf, pix[p].yf, q0, q1, q2, L), q1, q3,
+                                            s_tex + i * NN, uint32_t(bs + i + 1), sigma, kN, npairs, nblend);
+            } else {
+#pragma unroll
+                for (int p = 0; p < P; ++p)
+                    fwd_pair<N, TexT, WIDE>(pix[p], plane_hit(pix[p].xf, pix[p].yf, q0, q1, q2), q1, q3,
+                                            s_tex + i * NN, uint32_t(bs + i + 1), sigma, kN, npairs, nblend);
+            }
         }
     }
 #pragma unroll

@@ -116,16 +116,18 @@ class Saved:
         L.check(L.load().gb_saved_phase_times(self.handle, arr, len(L.PHASES)), self.rast.ctx)
         return dict(zip(L.PHASES, (float(x) for x in arr)))
 
-    def export_records(self):
-        """(records [R,16] float32, visible [R] bool) of the last forward."""
+    def export_records(self, lo: bool = False):
+        """(records [R,16] float32, visible [R] bool) of the last forward, and
+        with ``lo`` the low parts [R,12] of the flagged records as a third item."""
         n = C.c_int64()
-        L.check(L.load().gb_saved_export_records(self.handle, None, None, 0, C.byref(n)), self.rast.ctx)
+        L.check(L.load().gb_saved_export_records(self.handle, None, None, None, 0, C.byref(n)), self.rast.ctx)
         rec = np.zeros((n.value, 16), np.float32)
+        rlo = np.zeros((n.value, 12), np.float32)
         vis = np.zeros(n.value, np.uint8)
         if n.value:
-            L.check(L.load().gb_saved_export_records(self.handle, rec.ctypes.data, vis.ctypes.data, n.value,
-                                                     C.byref(n)), self.rast.ctx)
-        return rec, vis.astype(bool)
+            L.check(L.load().gb_saved_export_records(self.handle, rec.ctypes.data, rlo.ctypes.data, vis.ctypes.data,
+                                                     n.value, C.byref(n)), self.rast.ctx)
+        return (rec, vis.astype(bool), rlo) if lo else (rec, vis.astype(bool))
 
     def export_keys(self):
         """Sorted (key, splat id, camera) instance list of the last forward."""
