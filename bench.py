@@ -29,7 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "fwd+bwd Mpixel/s at 1M textured splats, batched vs plain FP32, max err vs FP64"
-FP32_PEAK_TFLOPS_AT_MAX = 152 * 128 * 2 * 2.070e9 / 1e12  # FMA = 2 FLOP, 2070 MHz
+FP32_PEAK_TFLOPS_AT_MAX = 152 * 128 * 2 * 2.070e9 / 1e12  # 152 SMs, FMA = 2 FLOP, 2070 MHz (no clock sample)
 
 
 def parse(argv=None):
@@ -53,6 +53,8 @@ def parse(argv=None):
     ap.add_argument("--crop", type=int, default=0, help="oracle crop side in pixels (0 = all of camera 0)")
     ap.add_argument("--mip", type=int, default=0, help="render the grids at this mip level (box filter)")
     ap.add_argument("--tex-sh", type=int, default=0, help="per-texel SH degree of the grids (0 = RGB texels)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the other configurations (8x8 grids, persistent launch, training step, multi-scene)")
     return ap.parse_args(argv)
 
 
@@ -238,88 +240,29 @@ def run_ours(args, world, rank, local):
         B.build()
     barrier(world)
     lib = L.load()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
     wl = make_workload(args)
     cams = wl["cams"]
     P = sum(int(c["width"]) * int(c["height"]) for c in cams)
     dev_scene = R.scene_to_device(wl["scenes"][0])
     d_rgb = torch.as_tensor(np.concatenate([d.reshape(-1, 3) for d in wl["d_rgb"]]), device="cuda")
     rast = R.Rasterizer(local)
-    stream = torch.cuda.current_stream()
 
     # --- tile size and batch depth: explicit, or from the library's autotuner
     tune = None
     if args.tile == 0:
-        tune = rast.autotune([dev_scene], cams, reps=2,
-                             cache=os.path.join(tempfile.gettempdir(), f"gbill_tune_{os.getpid()}.json"))
+        tune = tune_frame(rast, [dev_scene], cams)
         args.tile, args.batch, args.ppt = tune["tile"], tune["batch"], tune["ppt"]
         args.batch_fwd = tune.get("batch_fwd", 0)
+    opts = {"tile": args.tile, "batch": args.batch, "batch_fwd": args.batch_fwd, "ppt": args.ppt}
 
-    # --- size the saved state with one synchronizing forward, then reserve
-    saved = R.Saved(rast)
-    rgb, depth, alpha, _ = rast.forward([dev_scene], cams, saved=saved, batch=args.batch, batch_fwd=args.batch_fwd,
-                                        tile=args.tile, ppt=args.ppt)
-    st0 = saved.stats()
-    saved.reserve(st0["records"], int(st0["instances"] * 1.1) + 4096, P, st0["tiles"])
-    grads = rast.backward(saved, d_rgb)
-    out = (rgb, depth, alpha)
-
-    def step(flags=L.GB_FLAG_NO_SYNC):
-        rast.forward([dev_scene], cams, saved=saved, flags=flags, out=out, batch=args.batch, batch_fwd=args.batch_fwd,
-                     tile=args.tile, ppt=args.ppt)
-        rast.backward(saved, d_rgb, grads=grads)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    saved.check()
-
-    graph = None
-    if not args.no_graph:
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph):
-            step()
-        graph.replay()
-        torch.cuda.synchronize()
-        saved.check()
-
-    # --- timed region
-    sampler = ClockSampler(local)
-    launches0 = lib.gb_kernel_launches()
-    sampler.start()
-    time.sleep(0.3)
-    barrier(world)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        if graph is not None:
-            graph.replay()
-        else:
-            step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
-    clocks = sampler.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    launches = lib.gb_kernel_launches() - launches0
-    if graph is not None:
-        launches = args.steps * launches_per_step(lib, step)
-    saved.check()
-    ms_max, value = aggregate(P, ms, world)
-
-    # --- per-phase times over a second pass of K steps (events on the launch stream)
-    phase_acc = {}
-    pairs = None
-    for _ in range(args.steps):
-        rast.forward([dev_scene], cams, saved=saved, flags=L.GB_FLAG_NO_SYNC | L.GB_FLAG_TIMING, out=out,
-                     batch=args.batch, batch_fwd=args.batch_fwd, tile=args.tile, ppt=args.ppt)
-        rast.backward(saved, d_rgb, grads=grads)
-        for k, v in saved.phase_times().items():
-            phase_acc.setdefault(k, []).append(v)
-        pairs = saved.stats()
-    phases = {k: sum(v) / len(v) for k, v in phase_acc.items()}
+    run = BatchedStep(rast, torch, R, L, [dev_scene], cams, None, d_rgb, opts)
+    head = run.time(args, world, lib, sample_clocks=local, graph=not args.no_graph)
+    ms_max, value = aggregate(P, head["ms"], world)
+    phases, pairs = run.phase_times(args)
     dominant = max(phases, key=phases.get)
-    roofline = roofline_line(dominant, phases, pairs, clocks, measured_traffic(dominant, args))
+    roofline = roofline_line(dominant, phases, pairs, head["clocks"], measured_traffic(dominant, args), sms=sms)
+    rgb, depth, alpha = run.out
 
     result = {
         "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
@@ -330,13 +273,22 @@ def run_ours(args, world, rank, local):
                    "storage": "f16", "tile": args.tile,
                    "batch_depth": args.batch, "batch_depth_fwd": args.batch_fwd or args.batch,
                    "pixels_per_thread": args.ppt, "autotune": tune,
-                   "graph": graph is not None, "l2": "inputs larger than L2 (no flush)",
+                   "graph": not args.no_graph, "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{world}"},
-        "clocks": clocks, "gpu_launches": int(launches), "phases_ms": phases,
+        "clocks": head["clocks"], "gpu_launches": int(head["launches"]), "phases_ms": phases,
         "stats": {k: pairs[k] for k in ("visible", "instances", "pairs_fwd", "pairs_bwd", "blended_fwd",
                                         "contributing_bwd", "records")},
         "roofline": roofline,
     }
+
+    # --- the same frame with persistent render blocks (one launch per pass, tiles from a counter)
+    if not args.no_extra:
+        prun = BatchedStep(rast, torch, R, L, [dev_scene], cams, None, d_rgb, opts, flags=L.GB_FLAG_PERSISTENT)
+        pt = prun.time(args, world, lib, graph=not args.no_graph)
+        result["persistent"] = {"value": aggregate(P, pt["ms"], world)[1], "unit": "Mpixel/s", "ms_per_step": pt["ms"],
+                                "note": "GB_FLAG_PERSISTENT: render blocks pull tiles from a device counter, longest "
+                                        "tiles first; same frame and options as the headline"}
+        del prun
 
     # --- plain FP32 path: the same views one by one
     if not args.no_plain:
@@ -350,11 +302,213 @@ def run_ours(args, world, rank, local):
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"], result["max_err_vs_fp64"] = cpu_baseline(args, wl, rgb, alpha, depth, cams,
                                                                           rast, dev_scene)
+    del run, dev_scene, d_rgb
+
+    # --- the rest of the benchmark configurations, timed the same way
+    if not args.no_extra and args.workload == "batched_1m" and not (args.mip or args.tex_sh or args.views):
+        if args.tex_n == 4:
+            result["per_tex_n"] = {"8": other_tex_n(args, world, rast, torch, R, L, lib, 8, sms)}
+        result["train_3m"] = train_step(args, world, rast, torch, R, L, lib)
+        result["multi_scene"] = multi_scene(args, world, rast, torch, R, L, lib)
 
     if rank == 0:
         print(json.dumps(result), flush=True)
     barrier(world)
     return 0
+
+
+def tune_frame(rast, scenes, cams, cam_scene=None):
+    return rast.autotune(scenes, cams, cam_scene=cam_scene, reps=2,
+                         cache=os.path.join(tempfile.gettempdir(), f"gbill_tune_{os.getpid()}.json"))
+
+
+class BatchedStep:
+    """One forward + backward of a frame on a saved state reserved from a
+    synchronizing forward, then run without host synchronization; ``post``
+    (optional) runs after each backward outside the captured graph (an
+    optimiser step whose step count changes)."""
+
+    def __init__(self, rast, torch, R, L, scenes, cams, cam_scene, d_rgb, opts, flags=0, post=None):
+        self.rast, self.torch, self.R, self.L = rast, torch, R, L
+        self.scenes, self.cams, self.cam_scene = scenes, cams, cam_scene
+        self.d_rgb, self.opts, self.flags, self.post = d_rgb, opts, flags, post
+        self.P = sum(int(c["width"]) * int(c["height"]) for c in cams)
+        self.saved = R.Saved(rast)
+        rgb, depth, alpha, _ = rast.forward(scenes, cams, cam_scene=cam_scene, saved=self.saved, flags=flags, **opts)
+        st0 = self.saved.stats()
+        self.saved.reserve(st0["records"], int(st0["instances"] * 1.1) + 4096, self.P, st0["tiles"])
+        self.grads = rast.backward(self.saved, d_rgb)
+        self.out = (rgb, depth, alpha)
+        self.graph = None
+        self.n_post = 0
+
+    def step(self, extra_flags=0):
+        L = self.L
+        self.rast.forward(self.scenes, self.cams, cam_scene=self.cam_scene, saved=self.saved,
+                          flags=self.flags | L.GB_FLAG_NO_SYNC | extra_flags, out=self.out, **self.opts)
+        self.rast.backward(self.saved, self.d_rgb, grads=self.grads)
+
+    def replay(self):
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self.step()
+        if self.post is not None:
+            self.n_post += 1
+            self.post(self.n_post)
+
+    def time(self, args, world, lib, sample_clocks=None, graph=True):
+        """Mean ms per step over args.steps after args.warmup, CUDA events on the
+        launch stream, barrier and synchronize on both sides; clocks sampled
+        during the timed region when sample_clocks is a device index."""
+        torch = self.torch
+        for _ in range(args.warmup):
+            self.replay()
+        torch.cuda.synchronize()
+        self.saved.check()
+        if graph and self.graph is None:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                self.step()
+            self.graph = g
+            self.replay()
+            torch.cuda.synchronize()
+            self.saved.check()
+        per_step = launches_per_step(lib, self.step)
+        sampler = ClockSampler(sample_clocks) if sample_clocks is not None else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        barrier(world)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            self.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        clocks = sampler.stop() if sampler else None
+        self.saved.check()
+        return {"ms": e0.elapsed_time(e1) / args.steps, "clocks": clocks,
+                "launches": args.steps * (per_step + (1 if self.post is not None else 0))}
+
+    def phase_times(self, args):
+        """Per-phase ms (library events, GB_FLAG_TIMING) over args.steps eager steps, and the counters."""
+        acc = {}
+        st = None
+        for _ in range(args.steps):
+            self.step(self.L.GB_FLAG_TIMING)
+            for k, v in self.saved.phase_times().items():
+                acc.setdefault(k, []).append(v)
+            st = self.saved.stats()
+        return {k: sum(v) / len(v) for k, v in acc.items()}, st
+
+
+def other_tex_n(args, world, rast, torch, R, L, lib, tex_n, sms):
+    """The headline frame with N x N grids of another size, tuned and timed the same way."""
+    from paper_2412_12734_gb300 import scenes
+    wl = scenes.workload(args.workload, seed=0, tex_n=tex_n)
+    cams = wl["cams"]
+    P = sum(int(c["width"]) * int(c["height"]) for c in cams)
+    dev = R.scene_to_device(wl["scenes"][0])
+    d = torch.as_tensor(np.concatenate([x.reshape(-1, 3) for x in wl["d_rgb"]]), device="cuda")
+    tune = tune_frame(rast, [dev], cams)
+    opts = {"tile": tune["tile"], "batch": tune["batch"], "batch_fwd": tune.get("batch_fwd", 0), "ppt": tune["ppt"]}
+    run = BatchedStep(rast, torch, R, L, [dev], cams, None, d, opts)
+    t = run.time(args, world, lib, sample_clocks=torch.cuda.current_device(), graph=not args.no_graph)
+    phases, st = run.phase_times(args)
+    dominant = max(phases, key=phases.get)
+    return {"value": aggregate(P, t["ms"], world)[1], "unit": "Mpixel/s", "ms_per_step": t["ms"],
+            "workload": workload_label(argparse.Namespace(**dict(vars(args), tex_n=tex_n)), wl),
+            "options": {k: v for k, v in opts.items()}, "clocks": t["clocks"], "phases_ms": phases,
+            "gpu_launches": int(t["launches"]),
+            "roofline": roofline_line(dominant, phases, st, t["clocks"], sms=sms)}
+
+
+def train_step(args, world, rast, torch, R, L, lib):
+    """The training-step shape: 3,000,000 splats with BF16 SH (degree 3) and
+    8 x 8 BF16 grids, 8 views at 1600 x 1067; a step is the forward, the
+    backward and one fused Adam launch over every parameter tensor (FP32
+    masters and moments; the kernel writes the BF16 copies the renderer
+    reads)."""
+    from paper_2412_12734_gb300 import scenes
+    wl = scenes.workload("train_3m")
+    sc, cams = wl["scenes"][0], wl["cams"]
+    P = sum(int(c["width"]) * int(c["height"]) for c in cams)
+    dev = R.scene_to_device(sc)
+    names = ("means", "quats", "scales", "opacities", "sh", "textures")
+    master = {k: dev[k].float().clone() for k in names}
+    # the renderer reads the FP32 masters of the geometry and the BF16 copies of SH and grids
+    for k in ("means", "quats", "scales", "opacities"):
+        dev[k] = master[k]
+    d = torch.as_tensor(np.concatenate([x.reshape(-1, 3) for x in wl["d_rgb"]]), device="cuda") * 1e-3
+    tune = tune_frame(rast, [dev], cams)
+    opts = {"tile": tune["tile"], "batch": tune["batch"], "batch_fwd": tune.get("batch_fwd", 0), "ppt": tune["ppt"]}
+    run = BatchedStep(rast, torch, R, L, [dev], cams, None, d, opts)
+    m = {k: torch.zeros_like(master[k]) for k in names}
+    v = {k: torch.zeros_like(master[k]) for k in names}
+    adam = R.AdamStep(rast, [master[k] for k in names], [run.grads[0][k] for k in names], [m[k] for k in names],
+                      [v[k] for k in names], lr=1e-4, betas=(0.9, 0.999), eps=1e-15,
+                      shadows=[None, None, None, None, dev["sh"], dev["textures"]])
+    run.post = adam
+    t = run.time(args, world, lib, graph=not args.no_graph)
+    n_params = sum(master[k].numel() for k in names)
+    return {"value": aggregate(P, t["ms"], world)[1], "unit": "Mpixel/s", "ms_per_step": t["ms"],
+            "params_per_step": int(n_params), "gpu_launches": int(t["launches"]),
+            "workload": f"train_3m: 3,000,000 splats, 8 views 1600x1067, 8x8 BF16 grids, SH3 BF16, fused Adam",
+            "options": opts,
+            "note": "forward + backward from one CUDA graph, then one fused Adam launch (step count advances); "
+                    "parameters change every step, so the visible set and instance list are rebuilt each step"}
+
+
+def multi_scene(args, world, rast, torch, R, L, lib):
+    """Twelve scenes (10k-2M splats, 2/4/8 grids, FP16) with 1-4 views each
+    rendered forward + backward in one persistent launch sequence per pass,
+    against the same scenes one at a time on the plain FP32 path."""
+    from paper_2412_12734_gb300 import scenes
+    wl = scenes.workload("multi_scene")
+    sl, cams, cs = wl["scenes"], wl["cams"], wl["cam_scene"]
+    P = sum(int(c["width"]) * int(c["height"]) for c in cams)
+    dev = [R.scene_to_device(s) for s in sl]
+    d = torch.as_tensor(np.concatenate([x.reshape(-1, 3) for x in wl["d_rgb"]]), device="cuda")
+    tune = tune_frame(rast, dev, cams, cam_scene=cs)
+    opts = {"tile": tune["tile"], "batch": tune["batch"], "batch_fwd": tune.get("batch_fwd", 0), "ppt": tune["ppt"]}
+    run = BatchedStep(rast, torch, R, L, dev, cams, cs, d, opts, flags=L.GB_FLAG_PERSISTENT)
+    t = run.time(args, world, lib, graph=not args.no_graph)
+    batched = {"value": aggregate(P, t["ms"], world)[1], "ms_per_step": t["ms"], "options": opts,
+               "gpu_launches": int(t["launches"])}
+    del run
+    # one by one, FP32 storage, each scene's views in one call
+    off = np.cumsum([0] + [int(c["width"]) * int(c["height"]) for c in cams])
+    runs = []
+    for s_i, s in enumerate(sl):
+        mine = [i for i in range(len(cams)) if cs[i] == s_i]
+        s32 = dict(s, sh_dtype="f32", tex_dtype="f32")
+        d32 = R.scene_to_device(s32)
+        ds = torch.cat([d[off[i]:off[i + 1]] for i in mine]).contiguous()
+        runs.append(BatchedStep(rast, torch, R, L, [d32], [cams[i] for i in mine], None, ds, {"tile": 16}))
+    for r in runs:
+        for _ in range(args.warmup):
+            r.step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        for r in runs:
+            r.step()
+    e1.record()
+    torch.cuda.synchronize()
+    for r in runs:
+        r.saved.check()
+    ms1 = e0.elapsed_time(e1) / args.steps
+    return {"unit": "Mpixel/s", "pixels_per_step": int(P), "views": len(cams),
+            "splats": int(sum(int(s["means"].shape[0]) for s in sl)),
+            "batched_persistent": batched,
+            "one_by_one_fp32": {"value": aggregate(P, ms1, world)[1], "ms_per_step": ms1,
+                                "note": "each scene alone (its views in one call), FP32 storage, tile 16, "
+                                        "automatic batch depths, eager launches"}}
 
 
 def launches_per_step(lib, step):
@@ -407,9 +561,11 @@ def measured_traffic(kernel, args):
     return None
 
 
-def roofline_line(dominant, phases, st, clocks, traffic=None):
+def roofline_line(dominant, phases, st, clocks, traffic=None, sms=152):
     """ALU roofline of the dominant kernel: algorithmic FLOPs per launch over
-    its measured launch time, against the FP32 FMA peak at the sampled clock.
+    its measured launch time, against the nominal FP32 FMA rate of the
+    device (its SM count, as queried, x 128 FP32 lanes x 2 FLOP per FMA) at
+    the median sampled SM clock.
 
     FLOPs per (pixel, splat) pair (FMA = 2), counted from the kernels' math:
     forward: 30 per evaluated pair (offset, intersection, rho, Gaussian, alpha
@@ -419,8 +575,8 @@ def roofline_line(dominant, phases, st, clocks, traffic=None):
     Pair counts come from device counters of the same launches.
     """
     ms = phases[dominant]
-    sm = clocks.get("sm_mhz") or 2070.0
-    peak = 152 * 128 * 2 * sm * 1e6 / 1e12
+    sm = (clocks or {}).get("sm_mhz") or 2070.0
+    peak = sms * 128 * 2 * sm * 1e6 / 1e12
     if dominant == "render_bwd":
         flops = 30 * st["pairs_bwd"] + 200 * st["contributing_bwd"]
     elif dominant == "render_fwd":
@@ -430,7 +586,8 @@ def roofline_line(dominant, phases, st, clocks, traffic=None):
     achieved = flops / (ms / 1e3) / 1e12 if flops else None
     return {"kernel": dominant, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak if achieved else None, "traffic": traffic,
-            "peak_source": f"FP32 FMA lanes 152x128 x2 at median sampled SM clock {sm:.0f} MHz",
+            "peak_source": f"nominal FP32 FMA rate: {sms} SMs (queried) x 128 lanes x 2 FLOP at the median "
+                           f"sampled SM clock {sm:.0f} MHz",
             "launch_ms": ms}
 
 

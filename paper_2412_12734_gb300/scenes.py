@@ -48,9 +48,13 @@ def round_to(x: np.ndarray, dtype: str) -> np.ndarray:
     if dtype == "f16":
         return x.astype(np.float16).astype(np.float32)
     if dtype == "bf16":
-        u = x.view(np.uint32).astype(np.uint64)
-        u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
-        return u.astype(np.uint32).view(np.float32)
+        # round to nearest even on the upper 16 bits; finite inputs stay below 2^32
+        u = x.view(np.uint32).copy()
+        lsb = (u >> 16) & 1
+        u += np.uint32(0x7FFF)
+        u += lsb
+        u &= np.uint32(0xFFFF0000)
+        return u.view(np.float32)
     raise ValueError(f"unknown storage dtype {dtype!r}")
 
 
