@@ -45,7 +45,10 @@ def parse(argv=None):
     ap.add_argument("--batch-fwd", type=int, default=0,
                     help="the forward's batch depth (0 = --batch, or automatic when that is 0 too)")
     ap.add_argument("--tile", type=int, default=0, help="tile edge 8, 16 or 32 (0 = autotune)")
-    ap.add_argument("--ppt", type=int, default=1, help="backward pixels per thread, 1 or 2")
+    ap.add_argument("--ppt", type=int, default=0,
+                    help="pixel-parallel backward with 1 or 2 pixels per thread (0 = automatic)")
+    ap.add_argument("--bwd-kernel", type=int, default=0,
+                    help="backward loop: 0 automatic, 1 pixel-parallel, 2 splat-parallel")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -254,7 +257,9 @@ def run_ours(args, world, rank, local):
         tune = tune_frame(rast, [dev_scene], cams)
         args.tile, args.batch, args.ppt = tune["tile"], tune["batch"], tune["ppt"]
         args.batch_fwd = tune.get("batch_fwd", 0)
-    opts = {"tile": args.tile, "batch": args.batch, "batch_fwd": args.batch_fwd, "ppt": args.ppt}
+        args.bwd_kernel = tune.get("bwd_kernel", 0)
+    opts = {"tile": args.tile, "batch": args.batch, "batch_fwd": args.batch_fwd, "ppt": args.ppt,
+            "bwd_kernel": args.bwd_kernel}
 
     run = BatchedStep(rast, torch, R, L, [dev_scene], cams, None, d_rgb, opts)
     head = run.time(args, world, lib, sample_clocks=local, graph=not args.no_graph)
@@ -272,7 +277,7 @@ def run_ours(args, world, rank, local):
                    "pixels_per_step": P, "tex_n": args.tex_n, "mip_level": args.mip, "tex_sh_degree": args.tex_sh,
                    "storage": "f16", "tile": args.tile,
                    "batch_depth": args.batch, "batch_depth_fwd": args.batch_fwd or args.batch,
-                   "pixels_per_thread": args.ppt, "autotune": tune,
+                   "pixels_per_thread": args.ppt, "bwd_kernel": args.bwd_kernel, "autotune": tune,
                    "graph": not args.no_graph, "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{world}"},
         "clocks": head["clocks"], "gpu_launches": int(head["launches"]), "phases_ms": phases,
@@ -415,7 +420,8 @@ def other_tex_n(args, world, rast, torch, R, L, lib, tex_n, sms):
     dev = R.scene_to_device(wl["scenes"][0])
     d = torch.as_tensor(np.concatenate([x.reshape(-1, 3) for x in wl["d_rgb"]]), device="cuda")
     tune = tune_frame(rast, [dev], cams)
-    opts = {"tile": tune["tile"], "batch": tune["batch"], "batch_fwd": tune.get("batch_fwd", 0), "ppt": tune["ppt"]}
+    opts = {"tile": tune["tile"], "batch": tune["batch"], "batch_fwd": tune.get("batch_fwd", 0), "ppt": tune["ppt"],
+            "bwd_kernel": tune.get("bwd_kernel", 0)}
     run = BatchedStep(rast, torch, R, L, [dev], cams, None, d, opts)
     t = run.time(args, world, lib, sample_clocks=torch.cuda.current_device(), graph=not args.no_graph)
     phases, st = run.phase_times(args)
@@ -445,7 +451,8 @@ def train_step(args, world, rast, torch, R, L, lib):
         dev[k] = master[k]
     d = torch.as_tensor(np.concatenate([x.reshape(-1, 3) for x in wl["d_rgb"]]), device="cuda") * 1e-3
     tune = tune_frame(rast, [dev], cams)
-    opts = {"tile": tune["tile"], "batch": tune["batch"], "batch_fwd": tune.get("batch_fwd", 0), "ppt": tune["ppt"]}
+    opts = {"tile": tune["tile"], "batch": tune["batch"], "batch_fwd": tune.get("batch_fwd", 0), "ppt": tune["ppt"],
+            "bwd_kernel": tune.get("bwd_kernel", 0)}
     run = BatchedStep(rast, torch, R, L, [dev], cams, None, d, opts)
     m = {k: torch.zeros_like(master[k]) for k in names}
     v = {k: torch.zeros_like(master[k]) for k in names}
@@ -474,7 +481,8 @@ def multi_scene(args, world, rast, torch, R, L, lib):
     dev = [R.scene_to_device(s) for s in sl]
     d = torch.as_tensor(np.concatenate([x.reshape(-1, 3) for x in wl["d_rgb"]]), device="cuda")
     tune = tune_frame(rast, dev, cams, cam_scene=cs)
-    opts = {"tile": tune["tile"], "batch": tune["batch"], "batch_fwd": tune.get("batch_fwd", 0), "ppt": tune["ppt"]}
+    opts = {"tile": tune["tile"], "batch": tune["batch"], "batch_fwd": tune.get("batch_fwd", 0), "ppt": tune["ppt"],
+            "bwd_kernel": tune.get("bwd_kernel", 0)}
     run = BatchedStep(rast, torch, R, L, dev, cams, cs, d, opts, flags=L.GB_FLAG_PERSISTENT)
     t = run.time(args, world, lib, graph=not args.no_graph)
     batched = {"value": aggregate(P, t["ms"], world)[1], "ms_per_step": t["ms"], "options": opts,
@@ -662,6 +670,7 @@ def e2e(args, wl, rast, R, L, torch, cams, P):
     outs, grads = [], []
     for b in range(2):
         o = rast.forward([dict(d_in[b], **meta)], cams, saved=saved, batch=args.batch, batch_fwd=args.batch_fwd,
+                         bwd_kernel=args.bwd_kernel,
                          tile=args.tile, ppt=args.ppt)
         outs.append(o[:3])
         grads.append(rast.backward(saved, d_drgb[b]))
@@ -689,7 +698,8 @@ def e2e(args, wl, rast, R, L, torch, cams, P):
         comp.wait_event(uploaded[b])
         comp.wait_event(done_out[b])
         rast.forward([dict(d_in[b], **meta)], cams, saved=saved, out=outs[b], flags=L.GB_FLAG_NO_SYNC,
-                     batch=args.batch, batch_fwd=args.batch_fwd, tile=args.tile, ppt=args.ppt, stream=comp)
+                     batch=args.batch, batch_fwd=args.batch_fwd, tile=args.tile, ppt=args.ppt, stream=comp,
+                     bwd_kernel=args.bwd_kernel)
         rast.backward(saved, d_drgb[b], grads=grads[b], stream=comp)
         done_in[b].record(comp)
         computed[b].record(comp)

@@ -163,6 +163,16 @@ typedef struct {
     int32_t batch_depth_fwd; /* the forward's batch depth under the same rules;
                                 0 = batch_depth, or the forward's own automatic
                                 depth when batch_depth is 0 too                */
+    int32_t bwd_kernel;  /* backward render loop: 0 = automatic, 1 = pixel-
+                            parallel (a lane per pixel, gradients reduced across
+                            the warp per splat; pixels_per_thread applies),
+                            2 = splat-parallel (a lane per splat, transmittance
+                            and colour behind each splat by warp prefix scans
+                            over the splats, gradients summed in the lane;
+                            grids of N <= 4 on 8 x 8 or 16 x 16 tiles, else
+                            GB_ERR_UNSUPPORTED; batch depth a multiple of 8 up
+                            to 256).  Automatic is pixel-parallel; the
+                            autotuner times both.                             */
 } gb_options;
 
 /* Counters of the last forward on a saved state (gb_saved_stats). */

@@ -51,7 +51,8 @@ class gb_grads(C.Structure):
 
 class gb_options(C.Structure):
     _fields_ = [("tile_size", C.c_int32), ("batch_depth", C.c_int32), ("flags", C.c_uint32),
-                ("pixels_per_thread", C.c_int32), ("background", C.c_float * 3), ("batch_depth_fwd", C.c_int32)]
+                ("pixels_per_thread", C.c_int32), ("background", C.c_float * 3), ("batch_depth_fwd", C.c_int32),
+                ("bwd_kernel", C.c_int32)]
 
 
 class gb_adam_tensor(C.Structure):

@@ -17,8 +17,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgbill.so")
-SOURCES = ["capi.cu", "preprocess.cu", "sort.cu", "render_fwd.cu", "render_bwd.cu", "render_bwd2.cu", "adam.cu",
-           "mip.cu", "fit2d.cu", "texsh.cu"]
+SOURCES = ["capi.cu", "preprocess.cu", "sort.cu", "render_fwd.cu", "render_bwd.cu", "render_bwd2.cu",
+           "render_bwd_sp.cu", "adam.cu", "mip.cu", "fit2d.cu", "texsh.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

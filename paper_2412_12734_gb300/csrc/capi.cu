@@ -67,6 +67,7 @@ struct gb_saved {
     bool has_forward;
     int64_t n_records, n_pixels, max_k, inst_max;
     int tile_bits, batch_fwd, batch_bwd, ppt;
+    bool bwd_sp;  // the backward runs the splat-parallel loop
     uint32_t flags;
     cudaStream_t stream;
     cudaEvent_t ev[kNumEvents];
@@ -237,6 +238,38 @@ size_t frame_smem(const Frame &f, int batch, bool bwd) {
     for (int g = 0; g < f.n_groups; ++g) m = std::max(m, batch_smem(f.group_N[g], f.group_dtype[g], batch, bwd));
     return m;
 }
+
+// Whether every render group of the frame can take the splat-parallel
+// backward, and its shared memory per block at a batch depth.
+bool frame_sp_ok(const Frame &f) {
+    for (int g = 0; g < f.n_groups; ++g)
+        if (!render_bwd_sp_supported(f.tile, f.group_N[g])) return false;
+    return true;
+}
+size_t frame_sp_smem(const Frame &f, int batch) {
+    size_t m = 0;
+    for (int g = 0; g < f.n_groups; ++g)
+        m = std::max(m, render_bwd_sp_smem(f.tile, f.group_N[g], f.group_dtype[g], batch));
+    return m;
+}
+
+// Automatic batch depth of the splat-parallel backward: its registers leave
+// two resident blocks of 256 threads per SM, so a block may take up to 96 KB
+// of staging; longer batches give each warp longer lists of splats to spread
+// over its lanes.  At most 256, a multiple of 8.
+int default_batch_sp(const Frame &f) {
+    int b = 256;
+    while (b > 8 && frame_sp_smem(f, b) > 96 * 1024) b -= 8;
+    return b;
+}
+
+// The automatic backward loop is the pixel-parallel one: on the 1M-splat,
+// 16-view workload at N = 4 the splat-parallel loop took 63.8 ms at batch depth
+// 176 (68.8 at 128, 78.2 at 88) against 42.7 ms (2-view ncu case: 3.60e9
+// warp instructions at 18 active threads each, against 3.71e9 at 25.6: per
+// pixel only a few splats of a warp's list are blended, so the scans and
+// per-pixel broadcasts serve few lanes).  The autotuner still times it.
+constexpr bool kSplatParallelAuto = false;
 
 __global__ void zero_rec_grad(float *g, const Counters *cnt, int64_t max_n) {
     const int64_t n = std::min<int64_t>(int64_t(cnt->n_visible), max_n) * kRecGrad / 4;
@@ -583,15 +616,29 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
     gb_status r = build_frame(ctx, scenes, n_scenes, cams, n_cams, tile, o.background, f, max_k);
     if (r != GB_OK) return r;
     const int nt = tile * tile;
+    if (o.bwd_kernel < 0 || o.bwd_kernel > 2) return fail(ctx, GB_ERR_INVALID_ARG, "bwd_kernel must be 0, 1 or 2");
+    const bool sp_ok = frame_sp_ok(f);
+    if (o.bwd_kernel == 2 && !sp_ok)
+        return fail(ctx, GB_ERR_UNSUPPORTED, "the splat-parallel backward takes grids of N <= 4 on 8 x 8 or 16 x 16 tiles");
+    // pixels per thread set (1 or 2) asks for the pixel-parallel loop
+    const bool sp = o.bwd_kernel == 2 || (o.bwd_kernel == 0 && o.pixels_per_thread == 0 && sp_ok && kSplatParallelAuto);
     const int bf = forward_batch(o, f, nt);
-    const int bb = o.batch_depth ? o.batch_depth : std::min(default_batch(f, true), nt / ppt);
+    const int bb = o.batch_depth ? o.batch_depth
+                                 : (sp ? default_batch_sp(f) : std::min(default_batch(f, true), nt / ppt));
     if (bf < 8 || bf > nt || (bf & 7)) return fail(ctx, GB_ERR_INVALID_ARG, "forward batch depth %d invalid", bf);
     if (bb < 8 || (bb & 7)) return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d invalid", bb);
-    if (bb > nt / ppt) return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d exceeds the backward's %d threads", bb, nt / ppt);
+    if (sp) {
+        if (bb > 256) return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d above 256 (splat-parallel backward)", bb);
+        if (frame_sp_smem(f, bb) > 200 * 1024)
+            return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d needs too much shared memory", bb);
+    } else {
+        if (bb > nt / ppt)
+            return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d exceeds the backward's %d threads", bb, nt / ppt);
+        if (frame_smem(f, bb, true) > 200 * 1024)
+            return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d needs too much shared memory", bb);
+    }
     if (frame_smem(f, bf, false) > 200 * 1024)
         return fail(ctx, GB_ERR_INVALID_ARG, "forward batch depth %d needs too much shared memory", bf);
-    if (frame_smem(f, bb, true) > 200 * 1024)
-        return fail(ctx, GB_ERR_INVALID_ARG, "batch_depth %d needs too much shared memory", bb);
     const bool nosync = (o.flags & GB_FLAG_NO_SYNC) != 0;
     if (nosync) {
         if (f.n_records > s->cap_rec || f.n_pixels > s->cap_pix || int64_t(f.n_tiles) > s->cap_tiles ||
@@ -680,6 +727,7 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
     s->batch_fwd = bf;
     s->batch_bwd = bb;
     s->ppt = ppt;
+    s->bwd_sp = sp;
     s->flags = o.flags;
     s->stream = st;
     s->has_forward = false;
@@ -814,8 +862,12 @@ gb_status gb_render_backward(gb_context *ctx, gb_saved *s, const float *d_rgb, c
     // the backward's tile counters start from zero at every call (a forward
     // may be followed by several backwards)
     if (persistent) GB_CUDA(ctx, cudaMemsetAsync(s->work + kMaxGroups, 0, kMaxGroups * sizeof(uint32_t), st));
-    GB_CUDA(ctx, launch_render_bwd(f, b, s->batch_bwd, s->ppt, s->use_list ? s->tile_list : nullptr,
-                                   persistent ? s->work + kMaxGroups : nullptr, persistent, st));
+    if (s->bwd_sp)
+        GB_CUDA(ctx, launch_render_bwd_sp(f, b, s->batch_bwd, s->use_list ? s->tile_list : nullptr,
+                                          persistent ? s->work + kMaxGroups : nullptr, persistent, st));
+    else
+        GB_CUDA(ctx, launch_render_bwd(f, b, s->batch_bwd, s->ppt, s->use_list ? s->tile_list : nullptr,
+                                       persistent ? s->work + kMaxGroups : nullptr, persistent, st));
     for (int i = 0; i < n_scenes; ++i)
         if (f.scenes[i].mip && grads[i].d_textures)
             GB_CUDA(ctx, launch_mip_grad(s->mip_grad + s->mip_off[i], f.scenes[i].K, s->mip_ns[i], f.scenes[i].mip,
@@ -1144,7 +1196,9 @@ gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int3
             }
             ++n;
         };
-        // forward + backward over tile, batch depth (both passes) and pixels per thread
+        // forward + backward over tile, batch depth (both passes) and pixels per
+        // thread of the pixel-parallel backward, then the splat-parallel one
+        o.bwd_kernel = 1;
         for (int pi = 1; pi <= 2 && st == GB_OK; ++pi)
         for (int ti = 0; ti < 3 && st == GB_OK; ++ti)
             for (int bi = 0; bi < 8 && st == GB_OK; ++bi) {
@@ -1162,6 +1216,31 @@ gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int3
                     *best = o;
                 }
             }
+        // splat-parallel backward (reported with pixels_per_thread 3): tiles 16
+        // and 8, batch depths up to 256 (the forward at its automatic depth)
+        const int batch_sp[6] = {48, 88, 128, 176, 216, 256};
+        for (int ti = 0; ti < 2 && st == GB_OK; ++ti) {
+            o.tile_size = tile_c[ti];
+            o.pixels_per_thread = 1;
+            o.bwd_kernel = 2;
+            Frame ft = f;
+            ft.tile = o.tile_size;
+            if (!frame_sp_ok(ft)) continue;
+            for (int bi = 0; bi < 6 && st == GB_OK; ++bi) {
+                const int B = batch_sp[bi];
+                if (frame_sp_smem(ft, B) > 160 * 1024) continue;
+                o.batch_depth = B;
+                o.batch_depth_fwd = std::min(default_batch(f, false), o.tile_size * o.tile_size);
+                float t = 0.0f;
+                if ((st = time_candidate(o, true, &t)) != GB_OK) break;
+                report(o.tile_size, B, 3, t);
+                if (t < best_ms) {
+                    best_ms = t;
+                    *best = o;
+                }
+            }
+            o.batch_depth_fwd = 0;
+        }
         // the forward alone at every depth that fits the fastest tile (its time
         // does not depend on the backward's options)
         if (st == GB_OK && best_ms < INFINITY) {

@@ -292,6 +292,11 @@ cudaError_t launch_mip_grad(const float *gc, int64_t K, int ns, int mip, float *
 // ppt = pixels per thread, 1 or 2 (render_bwd.cu, render_bwd2.cu)
 cudaError_t launch_render_bwd(const Frame &f, const RenderBwdBufs &b, int batch, int ppt, const uint32_t *tile_list,
                               uint32_t *work, bool persistent, cudaStream_t s);
+// render_bwd_sp.cu: the splat-parallel backward (grids of N <= 4, tiles 8 and 16)
+bool render_bwd_sp_supported(int tile, int N);
+size_t render_bwd_sp_smem(int tile, int N, int dtype, int batch);
+cudaError_t launch_render_bwd_sp(const Frame &f, const RenderBwdBufs &b, int batch, const uint32_t *tile_list,
+                                 uint32_t *work, bool persistent, cudaStream_t s);
 template <int P>
 cudaError_t launch_render_bwd_p(const Frame &f, const RenderBwdBufs &b, int batch, const uint32_t *tile_list,
                                 uint32_t *work, bool persistent, cudaStream_t s);

@@ -1,7 +1,7 @@
 // Preprocess (forward and backward) of the textured 2D-Gaussian rasterizer.
 //
 // Forward:
-//   1. preprocess_kernel, one thread per (splat, camera) record: FP32 tile
+//   1. preprocess_kernel, one thread per splat looping over its cameras: FP32 tile
 //      rectangle and depth key (culling and rectangles are FP32 decisions; the
 //      operation sequence is fixed and contraction-free, so the (tile, depth)
 //      key list is reproducible bit for bit), and the record's opacity and
@@ -247,30 +247,40 @@ __device__ __forceinline__ float plane_hit_kappa(float t00, float t01, float t10
 }
 
 // --------------------------------------------------------- forward kernel --
+// One thread per splat of scene blockIdx.y, looping over the scene's cameras:
+// the splat's parameters are read once for all its records (coalesced; the
+// SH coefficients stay in L1 across the loop), and each camera's records are
+// written coalesced at rec_off + k.
 __global__ void __launch_bounds__(256, 4) preprocess_kernel(Frame f, uint32_t *depth_key,
                                                          uint32_t *rec_id, uint2 *rect_out, uint2 *pbox,
                                                          Record *rec_out, Counters *cnt) {
-    const int ci = blockIdx.y;
-    const CamDev &cam = f.cams[ci];
-    const SceneDev &sc = f.scenes[cam.scene];
+    const int si = blockIdx.y;
+    const SceneDev &sc = f.scenes[si];
     const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    bool valid = false;
-    if (k < sc.K) {
-        const int64_t r = cam.rec_off + k;
-        float p[3], q[4];
+    const bool live = k < sc.K;
+    float p[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0}, su = 0.0f, sv = 0.0f, o = 0.0f;
+    bool finite = false;
+    if (live) {
         for (int i = 0; i < 3; ++i) p[i] = sc.means[3 * k + i];
         for (int i = 0; i < 4; ++i) q[i] = sc.quats[4 * k + i];
-        const float su = sc.scales[2 * k], sv = sc.scales[2 * k + 1];
-        const float o = sc.opac[k];
-        float zkey;
-        int pr[4];
+        su = sc.scales[2 * k];
+        sv = sc.scales[2 * k + 1];
+        o = sc.opac[k];
         // a splat with a non-finite parameter is culled in every camera and
         // raises error bit 1 (gb_saved_check: GB_ERR_NONFINITE)
-        bool finite = isfinite(su) && isfinite(sv) && isfinite(o);
+        finite = isfinite(su) && isfinite(sv) && isfinite(o);
         for (int i = 0; i < 3; ++i) finite = finite && isfinite(p[i]);
         for (int i = 0; i < 4; ++i) finite = finite && isfinite(q[i]);
         if (!finite) atomicOr(&cnt->error_flags, 2u);
-        valid = finite && key_rect(p, q, su, sv, o, cam, zkey, pr);
+    }
+    const int M = (sc.D + 1) * (sc.D + 1);
+    for (int ci = 0; ci < f.n_cams; ++ci) {
+        const CamDev &cam = f.cams[ci];
+        if (cam.scene != si) continue;  // uniform over the block
+        const int64_t r = cam.rec_off + k;
+        float zkey;
+        int pr[4];
+        bool valid = finite && key_rect(p, q, su, sv, o, cam, zkey, pr);
         // SH colour, d = (p - campos) / |p - campos|; all 16 basis values
         // (registers), coefficients beyond the scene's degree skipped by a
         // uniform predicate.  Non-finite coefficients cull the record too.
@@ -281,7 +291,6 @@ __global__ void __launch_bounds__(256, 4) preprocess_kernel(Frame f, uint32_t *d
             dx *= dn; dy *= dn; dz *= dn;
             float Y[16];
             sh_basis(3, dx, dy, dz, Y);
-            const int M = (sc.D + 1) * (sc.D + 1);
 #pragma unroll
             for (int m = 0; m < 16; ++m)
                 if (m < M)
@@ -292,24 +301,27 @@ __global__ void __launch_bounds__(256, 4) preprocess_kernel(Frame f, uint32_t *d
                 valid = false;
             }
         }
-        if (rec_id) rec_id[r] = uint32_t(r);  // identity values for a sort of every record
-        if (!valid) {
-            depth_key[r] = 0xFFFFFFFFu;
-            rect_out[r] = make_uint2(0u, 0u);
-        } else {
-            depth_key[r] = __float_as_uint(zkey);
-            const int T = f.tile;
-            rect_out[r] = make_uint2(uint32_t(pr[0] / T) | (uint32_t(pr[1] / T) << 16),
-                                     uint32_t(pr[2] / T) | (uint32_t(pr[3] / T) << 16));
-            pbox[r] = make_uint2(uint32_t(pr[0]) | (uint32_t(pr[1]) << 16), uint32_t(pr[2]) | (uint32_t(pr[3]) << 16));
-            // the render record's opacity and SH colour; its homography part
-            // (q0..q2) is built by record_kernel for the visible records only
-            rec_out[r].q3 = make_float4(o, rgb[0], rgb[1], rgb[2]);
+        if (live) {
+            if (rec_id) rec_id[r] = uint32_t(r);  // identity values for a sort of every record
+            if (!valid) {
+                depth_key[r] = 0xFFFFFFFFu;
+                rect_out[r] = make_uint2(0u, 0u);
+            } else {
+                depth_key[r] = __float_as_uint(zkey);
+                const int T = f.tile;
+                rect_out[r] = make_uint2(uint32_t(pr[0] / T) | (uint32_t(pr[1] / T) << 16),
+                                         uint32_t(pr[2] / T) | (uint32_t(pr[3] / T) << 16));
+                pbox[r] = make_uint2(uint32_t(pr[0]) | (uint32_t(pr[1]) << 16),
+                                     uint32_t(pr[2]) | (uint32_t(pr[3]) << 16));
+                // the render record's opacity and SH colour; its homography part
+                // (q0..q2) is built by record_kernel for the visible records only
+                rec_out[r].q3 = make_float4(o, rgb[0], rgb[1], rgb[2]);
+            }
         }
+        // warp-aggregated visible count
+        const unsigned m = __ballot_sync(0xffffffffu, valid);
+        if ((threadIdx.x & 31) == 0 && m) atomicAdd(&cnt->n_visible, uint32_t(__popc(m)));
     }
-    // warp-aggregated visible count
-    const unsigned m = __ballot_sync(0xffffffffu, valid);
-    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&cnt->n_visible, uint32_t(__popc(m)));
 }
 
 // ------------------------------------------------------- record kernel --
@@ -548,7 +560,7 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(Frame f, int si, co
 cudaError_t launch_preprocess(const Frame &f, int64_t max_k, uint32_t *depth_key, uint32_t *rec_id,
                               uint2 *rect, uint2 *pbox, Record *rec, Counters *cnt, cudaStream_t s) {
     if (max_k <= 0) return cudaSuccess;
-    dim3 grid(unsigned(ceil_div(max_k, 256)), unsigned(f.n_cams));
+    dim3 grid(unsigned(ceil_div(max_k, 256)), unsigned(f.n_scenes));
     preprocess_kernel<<<grid, 256, 0, s>>>(f, depth_key, rec_id, rect, pbox, rec, cnt);
     count_launches(1);
     return cudaGetLastError();

@@ -179,7 +179,7 @@ class Rasterizer:
 
     def forward(self, scenes: list, cams: list, cam_scene=None, saved: Saved | None = None,
                 tile: int = 16, batch: int = 0, flags: int = 0, background=None, stream=None,
-                out=None, ppt: int = 1, batch_fwd: int = 0):
+                out=None, ppt: int = 0, batch_fwd: int = 0, bwd_kernel: int = 0):
         """Renders every camera; returns (rgb [P,3], depth [P], alpha [P], saved).
 
         batch is the backward's batch depth (and the forward's unless
@@ -192,6 +192,7 @@ class Rasterizer:
         opt = L.gb_options()
         opt.tile_size, opt.batch_depth, opt.flags, opt.pixels_per_thread = tile, batch, flags, ppt
         opt.batch_depth_fwd = batch_fwd
+        opt.bwd_kernel = bwd_kernel
         if background is not None:
             for i in range(3):
                 opt.background[i] = float(background[i])
@@ -285,9 +286,10 @@ class Rasterizer:
         L.check(lib.gb_autotune(self.ctx, saved.handle, sarr, n_s, carr, n_c, None, reps, C.byref(best),
                                 C.addressof(ms), C.addressof(tiles), C.addressof(batches), C.addressof(ppts), 64,
                                 C.byref(n)), self.ctx)
-        # candidates with ppt 0 time the forward alone at batch depth "batch"
+        # candidates with ppt 0 time the forward alone at batch depth "batch"; ppt 3
+        # marks the splat-parallel backward
         res = {"tile": best.tile_size, "batch": best.batch_depth, "ppt": best.pixels_per_thread,
-               "batch_fwd": best.batch_depth_fwd,
+               "batch_fwd": best.batch_depth_fwd, "bwd_kernel": best.bwd_kernel,
                "candidates": [{"tile": tiles[i], "batch": batches[i], "ppt": ppts[i], "ms": ms[i]}
                               for i in range(min(n.value, 64))]}
         table[key] = res
@@ -422,12 +424,13 @@ class BatchedRenderer:
     """
 
     def __init__(self, rast: Rasterizer, scenes: list, cams: list, cam_scene=None, tile: int = 16,
-                 batch: int = 0, batch_fwd: int = 0, ppt: int = 1, flags: int = 0, background=None,
-                 headroom: float = 1.25):
+                 batch: int = 0, batch_fwd: int = 0, ppt: int = 0, flags: int = 0, background=None,
+                 headroom: float = 1.25, bwd_kernel: int = 0):
         self.rast = rast
         self.scenes, self.cams = list(scenes), list(cams)
         self.cam_scene = list(cam_scene) if cam_scene is not None else [0] * len(self.cams)
-        self.opts = {"tile": tile, "batch": batch, "batch_fwd": batch_fwd, "ppt": ppt, "background": background}
+        self.opts = {"tile": tile, "batch": batch, "batch_fwd": batch_fwd, "ppt": ppt, "background": background,
+                     "bwd_kernel": bwd_kernel}
         self.flags = int(flags) & ~(L.GB_FLAG_NO_SYNC | L.GB_FLAG_TIMING)
         self.P = rast.pixel_count(self.cams)
         self.saved = Saved(rast)

@@ -22,14 +22,14 @@ def split_pixels(flat: np.ndarray, cams) -> list:
 
 
 def gpu_run(scenes_np, cams, cam_scene=None, d_rgb=None, d_depth=None, d_alpha=None, bg=None,
-            keys=False, batch=0, rast=None, tile=16, ppt=1, batch_fwd=0):
+            keys=False, batch=0, rast=None, tile=16, ppt=0, batch_fwd=0, bwd_kernel=0):
     import torch
 
     from paper_2412_12734_gb300 import render as R
     rast = rast or R.Rasterizer(0)
     dev = [R.scene_to_device(s) for s in scenes_np]
     rgb, depth, alpha, saved = rast.forward(dev, cams, cam_scene=cam_scene, background=bg, batch=batch, tile=tile,
-                                            ppt=ppt, batch_fwd=batch_fwd)
+                                            ppt=ppt, batch_fwd=batch_fwd, bwd_kernel=bwd_kernel)
     out = {"rgb": split_pixels(rgb.cpu().numpy(), cams),
            "depth": split_pixels(depth.cpu().numpy(), cams),
            "alpha": split_pixels(alpha.cpu().numpy(), cams),

@@ -78,15 +78,20 @@ def test_plain_100k_gradcheck_64_splats():
         assert abs(num - ana) <= 2e-3 * abs(num) + 1e-4 * scale, (k, num, ana)
 
 
-@pytest.mark.parametrize("tex_n", [4, 8])
-def test_batched_1m_camera0_at_full_size(tex_n):
+@pytest.mark.parametrize("tex_n,kernel,batch,batch_fwd", [(4, 1, 88, 88), (8, 1, 32, 48), (4, 2, 176, 88)])
+def test_batched_1m_camera0_at_full_size(tex_n, kernel, batch, batch_fwd):
+    """Camera 0 of the 16-view workload with all 16 views in the launch, keys
+    bit-exact, image and gradients against the oracle, at the tile size and
+    batch depths the autotuner picks for the bench on this workload (tile 16;
+    backward / forward depth 88 / 88 at N = 4, 32 / 48 at N = 8); kernel 1 / 2:
+    the pixel-parallel / splat-parallel backward (the latter at depth 176)."""
     wl = scenes.workload("batched_1m", tex_n=tex_n)
     sc, cams = wl["scenes"][0], wl["cams"]
     ref = oracle_run(sc, cams[0], prefilter=True)
     rng = np.random.default_rng(tex_n)
     d0 = masked_upstream(ref, rng)
     d_rgb = [d0] + [np.zeros((int(c["height"]), int(c["width"]), 3), np.float32) for c in cams[1:]]
-    gpu = gpu_run([sc], cams, d_rgb=d_rgb, keys=True, tile=16, batch=64)
+    gpu = gpu_run([sc], cams, d_rgb=d_rgb, keys=True, tile=16, batch=batch, batch_fwd=batch_fwd, bwd_kernel=kernel)
     keys, ids, cidx = gpu["keys"]
     k0, i0 = oracle.tile_keys(sc, cams[0], 16, 0)
     assert np.array_equal(keys[cidx == 0], k0)

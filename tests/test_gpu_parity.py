@@ -88,8 +88,14 @@ def test_image_parity(case):
 
 
 @pytest.mark.parametrize("case", list(CASES))
-def test_gradient_parity(case):
+@pytest.mark.parametrize("kernel", ["pixel", "splat"])
+def test_gradient_parity(case, kernel):
+    """Both backward loops: pixel-parallel (a lane per pixel, warp reductions
+    per splat) and splat-parallel (a lane per splat, prefix scans over the
+    splats; grids of N <= 4)."""
     sc, cams = CASES[case]()
+    if kernel == "splat" and int(sc[0]["tex_n"]) > 4:
+        pytest.skip("the splat-parallel backward takes grids of N <= 4")
     rng = np.random.default_rng(11)
     ref = oracle_run(sc[0], cams[0])
     d_rgb = masked_upstream(ref, rng)
@@ -97,7 +103,7 @@ def test_gradient_parity(case):
     d_dep = masked_upstream(ref, rng, 1, 0.3)[..., 0] if use_da else None
     d_alp = masked_upstream(ref, rng, 1)[..., 0] if use_da else None
     gpu = gpu_run(sc, cams, d_rgb=[d_rgb], d_depth=[d_dep] if use_da else None,
-                  d_alpha=[d_alp] if use_da else None)
+                  d_alpha=[d_alp] if use_da else None, **({"ppt": 1} if kernel == "pixel" else {"bwd_kernel": 2}))
     og = oracle.backward(sc[0], cams[0], d_rgb, d_dep, d_alp)
     errs = grad_errors(gpu["grads"][0], og)
     bad = {k: v for k, v in errs.items() if v > 1.0}
