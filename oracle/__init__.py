@@ -50,6 +50,7 @@ class _Scene(C.Structure):
         ("means", C.c_void_p), ("quats", C.c_void_p), ("scales", C.c_void_p),
         ("opacities", C.c_void_p), ("sh", C.c_void_p), ("textures", C.c_void_p),
         ("sh_degree", C.c_int32), ("tex_n", C.c_int32), ("sigma", C.c_double),
+        ("splat_n", C.c_void_p),
     ]
 
 
@@ -125,9 +126,17 @@ def mip_grid_adjoint(d_coarse, level: int):
 class _SceneRef:
     """Holds FP64 copies (exact upcasts of the stored values) alive for a call.
     A scene with ``mip_level`` l > 0 is rendered with its grids box-filtered
-    to N / 2^l (mip_grid)."""
+    to N / 2^l (mip_grid).  A scene with ``splat_tex_n`` [K] renders splat k
+    with the n_k x n_k grid in rows and columns 0..n_k-1 of its N x N block
+    (Alg. 2 with n_k)."""
 
     def __init__(self, scene: dict):
+        self.splat_n = None
+        if scene.get("splat_tex_n") is not None:
+            if int(scene.get("mip_level", 0)) or int(scene.get("tex_sh_degree", 0)):
+                raise ValueError("per-splat grid sizes take no mip level and no per-texel SH")
+            self.splat_n = np.ascontiguousarray(np.asarray(scene["splat_tex_n"]).astype(np.int32))
+            assert self.splat_n.min() >= 1 and self.splat_n.max() <= int(scene["tex_n"])
         self.arrays = {k: _f64(scene[k]) for k in
                        ("means", "quats", "scales", "opacities", "sh", "textures")}
         self.K = int(self.arrays["means"].shape[0])
@@ -144,6 +153,7 @@ class _SceneRef:
         s.sh_degree = self.D
         s.tex_n = self.N
         s.sigma = float(scene.get("sigma", 0.5))
+        s.splat_n = _p(self.splat_n) if self.splat_n is not None else None
         self.struct = s
 
 

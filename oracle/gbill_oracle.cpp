@@ -72,6 +72,9 @@ typedef struct {
     int32_t sh_degree;        /* D in 0..3                                   */
     int32_t tex_n;            /* N >= 1                                      */
     double sigma;             /* grid extent, default 0.5                    */
+    const int32_t *splat_n;   /* [K] or NULL: splat k's grid is n_k x n_k,    */
+                              /* 1 <= n_k <= N, in rows and columns 0..n_k-1 */
+                              /* of its N x N block (Alg. 2 with n_k)         */
 } orc_scene;
 
 typedef struct {
@@ -198,13 +201,16 @@ static Bilin bilin_coords(double u, double v, int N, double sigma) {
     return b;
 }
 
-static void bilinear(double u, double v, int N, double sigma, const double *C, double out[3]) {
+/* C: the grid's texel (i_u, i_v) at C + (i_u * stride + i_v) * 3; stride = N
+   unless the grid is the leading N x N part of a larger block. */
+static void bilinear(double u, double v, int N, double sigma, const double *C, double out[3], int stride = 0) {
+    if (stride == 0) stride = N;
     Bilin b = bilin_coords(u, v, N, sigma);
     if (N == 1) { for (int c = 0; c < 3; ++c) out[c] = C[c]; return; }
-    const double *c00 = C + ((b.iu) * N + b.iv) * 3;
-    const double *c10 = C + ((b.iu + 1) * N + b.iv) * 3;
-    const double *c01 = C + ((b.iu) * N + b.iv + 1) * 3;
-    const double *c11 = C + ((b.iu + 1) * N + b.iv + 1) * 3;
+    const double *c00 = C + ((b.iu) * stride + b.iv) * 3;
+    const double *c10 = C + ((b.iu + 1) * stride + b.iv) * 3;
+    const double *c01 = C + ((b.iu) * stride + b.iv + 1) * 3;
+    const double *c11 = C + ((b.iu + 1) * stride + b.iv + 1) * 3;
     for (int c = 0; c < 3; ++c)
         out[c] = c00[c] * (1 - b.fu) * (1 - b.fv) + c10[c] * b.fu * (1 - b.fv) +
                  c01[c] * (1 - b.fu) * b.fv + c11[c] * b.fu * b.fv;
@@ -212,15 +218,16 @@ static void bilinear(double u, double v, int N, double sigma, const double *C, d
 
 /* Adds the grid adjoint into Chat; returns the uv adjoint in uv_hat. */
 static void adj_bilinear(double u, double v, int N, double sigma, const double *C,
-                         const double chat[3], double *Chat, double uv_hat[2]) {
+                         const double chat[3], double *Chat, double uv_hat[2], int stride = 0) {
+    if (stride == 0) stride = N;
     Bilin b = bilin_coords(u, v, N, sigma);
     if (N == 1) {
         for (int c = 0; c < 3; ++c) Chat[c] += chat[c];
         uv_hat[0] = uv_hat[1] = 0.0;
         return;
     }
-    const int i00 = ((b.iu) * N + b.iv) * 3, i10 = ((b.iu + 1) * N + b.iv) * 3;
-    const int i01 = ((b.iu) * N + b.iv + 1) * 3, i11 = ((b.iu + 1) * N + b.iv + 1) * 3;
+    const int i00 = ((b.iu) * stride + b.iv) * 3, i10 = ((b.iu + 1) * stride + b.iv) * 3;
+    const int i01 = ((b.iu) * stride + b.iv + 1) * 3, i11 = ((b.iu + 1) * stride + b.iv + 1) * 3;
     double fu_hat = 0.0, fv_hat = 0.0;
     for (int c = 0; c < 3; ++c) {
         Chat[i00 + c] += chat[c] * (1 - b.fu) * (1 - b.fv);
@@ -554,16 +561,17 @@ static void pixel_forward(const Ctx &cx, int px, int py, std::vector<Contrib> *c
         const double sg = sc.sigma;
         mg = std::min(mg, std::fabs(std::fabs(e.u) - sg) / sg);
         mg = std::min(mg, std::fabs(std::fabs(e.v) - sg) / sg);
-        if (N > 2) {
-            const double up = (N - 1) * (e.u + sg) / (2 * sg), vp = (N - 1) * (e.v + sg) / (2 * sg);
-            if (up > 0 && up < N - 1) mg = std::min(mg, std::fabs(up - std::round(up)));
-            if (vp > 0 && vp < N - 1) mg = std::min(mg, std::fabs(vp - std::round(vp)));
+        const int nk = sc.splat_n ? sc.splat_n[k] : N;
+        if (nk > 2) {
+            const double up = (nk - 1) * (e.u + sg) / (2 * sg), vp = (nk - 1) * (e.v + sg) / (2 * sg);
+            if (up > 0 && up < nk - 1) mg = std::min(mg, std::fabs(up - std::round(up)));
+            if (vp > 0 && vp < nk - 1) mg = std::min(mg, std::fabs(vp - std::round(vp)));
         }
         Contrib cb;
         cb.k = k;
         cb.e = e;
         cb.T = T;
-        bilinear(e.u, e.v, N, sg, sc.textures + k * N * N * 3, cb.col);
+        bilinear(e.u, e.v, sc.splat_n ? sc.splat_n[k] : N, sg, sc.textures + k * N * N * 3, cb.col, N);
         for (int c = 0; c < 3; ++c) cb.col[c] += pr.rgb_sh[c];
         cb.zi = e.uv_branch ? (pr.T[6] * e.u + pr.T[7] * e.v + pr.T[8]) : pr.T[8];
         const double w = e.alpha * T;
@@ -692,8 +700,8 @@ static void pixel_backward(const Ctx &cx, int px, int py, const std::vector<Cont
         double chat[3] = {w * dC[0], w * dC[1], w * dC[2]};
         for (int ch = 0; ch < 3; ++ch) A.rgb_hat[ch] += chat[ch];
         double uv_hat[2];
-        adj_bilinear(e.u, e.v, N, sc.sigma, sc.textures + c.k * N * N * 3, chat,
-                     tex_hat.data() + c.k * N * N * 3, uv_hat);
+        adj_bilinear(e.u, e.v, sc.splat_n ? sc.splat_n[c.k] : N, sc.sigma, sc.textures + c.k * N * N * 3, chat,
+                     tex_hat.data() + c.k * N * N * 3, uv_hat, N);
         double u_hat = uv_hat[0], v_hat = uv_hat[1];
         /* adjoint of alpha */
         const double inv1ma = 1.0 / (1.0 - a);

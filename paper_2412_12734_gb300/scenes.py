@@ -419,3 +419,20 @@ def with_texel_sh(scene: dict, degree: int, seed: int = 0, std: float = 0.1) -> 
     out["textures"] = round_to(k, scene.get("tex_dtype", "f32"))
     out["tex_sh_degree"] = int(degree)
     return out
+
+
+def with_splat_tex_n(scene: dict, sizes, seed: int = 0, fill: float = 7.0) -> dict:
+    """The scene with a per-splat grid size: splat k gets n_k drawn from
+    ``sizes`` (each <= the scene's tex_n) and keeps the texels in rows and
+    columns 0..n_k-1 of its tex_n x tex_n block; the texels outside are set to
+    ``fill`` (a renderer must never read them)."""
+    rng = np.random.default_rng(seed)
+    N = int(scene["tex_n"])
+    K = int(scene["means"].shape[0])
+    n = rng.choice(np.asarray(sizes, np.int32), K).astype(np.int32)
+    assert n.min() >= 1 and n.max() <= N
+    tex = np.array(scene["textures"], np.float32, copy=True)
+    ii = np.arange(N)
+    outside = (ii[None, :, None] >= n[:, None, None]) | (ii[None, None, :] >= n[:, None, None])
+    tex[outside] = round_to(np.float32(fill), scene.get("tex_dtype", "f32"))
+    return dict(scene, textures=tex, splat_tex_n=n)

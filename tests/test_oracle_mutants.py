@@ -25,6 +25,7 @@ from tests import test_oracle_fit2d as fit
 from tests import test_oracle_mip as mip
 from tests import test_oracle_pins as pins
 from tests import test_oracle_texsh as texsh
+from tests import test_oracle_varn as varn
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "gbill_oracle.cpp")
 
@@ -39,10 +40,14 @@ MUTANTS = {
     "Gaussian exp(-rho)": ("e.G = std::exp(-0.5 * e.rho);", "e.G = std::exp(-e.rho);"),
     "splats blended in input order": ("return a.first < b.first;", "return false;"),
     "splats blended back to front": ("return a.first < b.first;", "return a.first > b.first;"),
-    "texels transposed": ("const double *c10 = C + ((b.iu + 1) * N + b.iv) * 3;\n"
-                          "    const double *c01 = C + ((b.iu) * N + b.iv + 1) * 3;",
-                          "const double *c10 = C + ((b.iu) * N + b.iv + 1) * 3;\n"
-                          "    const double *c01 = C + ((b.iu + 1) * N + b.iv) * 3;"),
+    "texels transposed": ("const double *c10 = C + ((b.iu + 1) * stride + b.iv) * 3;\n"
+                          "    const double *c01 = C + ((b.iu) * stride + b.iv + 1) * 3;",
+                          "const double *c10 = C + ((b.iu) * stride + b.iv + 1) * 3;\n"
+                          "    const double *c01 = C + ((b.iu + 1) * stride + b.iv) * 3;"),
+    "per-splat grid size ignored": ("bilinear(e.u, e.v, sc.splat_n ? sc.splat_n[k] : N, sg,",
+                                    "bilinear(e.u, e.v, N, sg,"),
+    "per-splat grid read at its own width": ("sc.textures + k * N * N * 3, cb.col, N);",
+                                             "sc.textures + k * N * N * 3, cb.col);"),
     "blend weight with the next T": ("const double w = e.alpha * T;", "const double w = e.alpha * tT;"),
     "depth without the tilt terms": ("cb.zi = e.uv_branch ? (pr.T[6] * e.u + pr.T[7] * e.v + pr.T[8]) : pr.T[8];",
                                      "cb.zi = pr.T[8];"),
@@ -126,6 +131,7 @@ PINS = [
     (fd.test_fd_with_background_and_ragged_view, {}),
     (fd.test_fd_all_gradients, {"N": 4, "D": 3}),
     (fd.test_fd_texture_only_heavy_grid, {}),
+    (varn.test_embedded_grids_equal_the_uniform_scene, {}),
 ]
 
 
