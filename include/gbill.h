@@ -136,6 +136,16 @@ typedef struct {
                               /* reach the coefficients and, through d, the      */
                               /* means.  Not combined with mip_level.            */
     int32_t reserved;         /* must be 0                                       */
+    const uint8_t *splat_tex_n; /* [K] or NULL: per-splat grid size n_k in     */
+                              /* 1..tex_n (values outside are clamped to it):  */
+                              /* splat k's n_k x n_k grid is rows and columns  */
+                              /* 0..n_k-1 of its tex_n x tex_n block, sampled  */
+                              /* by Alg. 2 with n_k (the other texels are never */
+                              /* read; their gradient is 0).  Needs tex_n >= 2, */
+                              /* no mip level or per-texel SH, 16 x 16 tiles and */
+                              /* the pixel-parallel backward with one pixel per */
+                              /* thread (else GB_ERR_UNSUPPORTED).  The variable */
+                              /* grid resolution of Sec. 3.3 and 5.             */
 } gb_scene;
 
 /* Gradient outputs of one scene, FP32 device arrays shaped like the inputs.

@@ -41,7 +41,7 @@ class gb_scene(C.Structure):
                 ("sh_degree", C.c_int32), ("sh_dtype", C.c_int32),
                 ("tex_n", C.c_int32), ("tex_dtype", C.c_int32),
                 ("sigma", C.c_float), ("mip_level", C.c_int32), ("tex_sh_degree", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("reserved", C.c_int32), ("splat_tex_n", C.c_void_p)]
 
 
 class gb_grads(C.Structure):

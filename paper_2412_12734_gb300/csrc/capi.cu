@@ -232,18 +232,27 @@ size_t batch_smem(int N, int dtype, int batch, bool bwd) {
     return dtype == GB_F32 ? batch_smem_t<float>(N, batch, bwd) : batch_smem_t<__half>(N, batch, bwd);
 }
 
-// The largest over the frame's render groups (one batch depth serves all).
+// The largest over the frame's render groups (one batch depth serves all);
+// per-splat grid sizes take 4 more bytes a staged splat.
 size_t frame_smem(const Frame &f, int batch, bool bwd) {
     size_t m = 0;
-    for (int g = 0; g < f.n_groups; ++g) m = std::max(m, batch_smem(f.group_N[g], f.group_dtype[g], batch, bwd));
+    for (int g = 0; g < f.n_groups; ++g)
+        m = std::max(m, batch_smem(f.group_N[g], f.group_dtype[g], batch, bwd) +
+                            (f.group_var[g] ? size_t(batch) * 4 : 0));
     return m;
+}
+
+bool frame_has_var(const Frame &f) {
+    for (int g = 0; g < f.n_groups; ++g)
+        if (f.group_var[g]) return true;
+    return false;
 }
 
 // Whether every render group of the frame can take the splat-parallel
 // backward, and its shared memory per block at a batch depth.
 bool frame_sp_ok(const Frame &f) {
     for (int g = 0; g < f.n_groups; ++g)
-        if (!render_bwd_sp_supported(f.tile, f.group_N[g])) return false;
+        if (f.group_var[g] || !render_bwd_sp_supported(f.tile, f.group_N[g])) return false;
     return true;
 }
 size_t frame_sp_smem(const Frame &f, int batch) {
@@ -315,6 +324,9 @@ gb_status build_frame(gb_context *ctx, const gb_scene *scenes, int32_t n_scenes,
                         g.tex_n);
         if (g.num_splats > 0 && (!g.means || !g.quats || !g.scales || !g.opacities || !g.sh || !g.textures))
             return fail(ctx, GB_ERR_INVALID_ARG, "scene %d: null parameter pointer", s);
+        if (g.splat_tex_n && (g.tex_n < 2 || g.mip_level || g.tex_sh_degree))
+            return fail(ctx, GB_ERR_UNSUPPORTED,
+                        "scene %d: per-splat grid sizes need tex_n >= 2 and take no mip level or per-texel SH", s);
         d.K = g.num_splats;
         d.means = g.means;
         d.quats = g.quats;
@@ -329,21 +341,25 @@ gb_status build_frame(gb_context *ctx, const gb_scene *scenes, int32_t n_scenes,
         d.sigma = g.sigma;
         d.mip = g.mip_level;
         d.tex_sh = g.tex_sh_degree;
+        d.splat_n = g.splat_tex_n;
         max_k = std::max(max_k, g.num_splats);
     }
-    // render groups: one per distinct (rendered grid size, tex_dtype) among the scenes
+    // render groups: one per distinct (rendered grid size, tex_dtype, per-splat
+    // sizes or not) among the scenes
     int scene_group[kMaxScenes];
     for (int sidx = 0; sidx < n_scenes; ++sidx) {
         // a scene at a mip level is rendered from its FP32 filtered grid
         const int n_eff = scenes[sidx].tex_n >> scenes[sidx].mip_level;
         const int dt = (scenes[sidx].mip_level || scenes[sidx].tex_sh_degree) ? int(GB_F32) : scenes[sidx].tex_dtype;
+        const int var = scenes[sidx].splat_tex_n ? 1 : 0;
         int g = -1;
         for (int k = 0; k < f.n_groups; ++k)
-            if (f.group_N[k] == n_eff && f.group_dtype[k] == dt) g = k;
+            if (f.group_N[k] == n_eff && f.group_dtype[k] == dt && f.group_var[k] == var) g = k;
         if (g < 0) {
             g = f.n_groups++;
             f.group_N[g] = n_eff;
             f.group_dtype[g] = dt;
+            f.group_var[g] = var;
         }
         scene_group[sidx] = g;
     }
@@ -617,6 +633,9 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *s, const gb_scene *scenes
     if (r != GB_OK) return r;
     const int nt = tile * tile;
     if (o.bwd_kernel < 0 || o.bwd_kernel > 2) return fail(ctx, GB_ERR_INVALID_ARG, "bwd_kernel must be 0, 1 or 2");
+    if (frame_has_var(f) && (tile != 16 || ppt != 1))
+        return fail(ctx, GB_ERR_UNSUPPORTED,
+                    "per-splat grid sizes render on 16 x 16 tiles with one backward pixel per thread");
     const bool sp_ok = frame_sp_ok(f);
     if (o.bwd_kernel == 2 && !sp_ok)
         return fail(ctx, GB_ERR_UNSUPPORTED, "the splat-parallel backward takes grids of N <= 4 on 8 x 8 or 16 x 16 tiles");
@@ -954,6 +973,8 @@ gb_status gb_render_forward_noalloc(gb_context *ctx, const gb_scene *scenes, int
         if (f.scenes[i].mip || f.scenes[i].tex_sh)
             return fail(ctx, GB_ERR_UNSUPPORTED,
                         "the no-allocation forward renders no mip-level or per-texel SH scene");
+    if (frame_has_var(f) && tile != 16)
+        return fail(ctx, GB_ERR_UNSUPPORTED, "per-splat grid sizes render on 16 x 16 tiles");
     if (f.n_records > kNaMaxRecords || f.n_pixels > kNaMaxPixels || int64_t(f.n_tiles) > kNaMaxTiles)
         return fail(ctx, GB_ERR_CAPACITY,
                     "no-allocation forward limits: %lld records (max %lld), %lld pixels (max %lld), %u tiles (max %lld)",
@@ -1204,6 +1225,7 @@ gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int3
             for (int bi = 0; bi < 8 && st == GB_OK; ++bi) {
                 const int T = tile_c[ti], B = batch_c[bi];
                 if (B > T * T / pi) continue;
+                if (frame_has_var(f) && (T != 16 || pi != 1)) continue;
                 if (frame_smem(f, B, false) > 160 * 1024 || frame_smem(f, B, true) > 160 * 1024) continue;
                 o.tile_size = T;
                 o.batch_depth = B;

@@ -13,7 +13,7 @@ namespace gbill {
 
 constexpr int kMaxCams = GBILL_MAX_CAMERAS;
 constexpr int kMaxScenes = GBILL_MAX_SCENES;
-constexpr int kMaxGroups = 16;  // distinct (texture size, storage type) pairs of a frame (5 x 3 possible)
+constexpr int kMaxGroups = 32;  // distinct (texture size, storage type, per-splat size) of a frame (5 x 3 x 2)
 
 // Constants of the method (Sec. 3.1 Eq. 4 with the 3DGS-lineage clamp and
 // cutoffs; the screen-space low-pass of the 2DGS lineage).
@@ -53,6 +53,7 @@ struct SceneDev {
     int32_t mip;                        // mip level (the render reads the filtered grid)
     int32_t tex_sh;                     // per-texel SH degree (the render reads evaluated grids)
     int32_t pad2;
+    const uint8_t *splat_n;             // per-splat grid size (null: every splat N)
     float *g_means, *g_quats, *g_scales, *g_opac, *g_sh, *g_tex;
 };
 
@@ -67,6 +68,7 @@ struct Frame {
     float bg[3];
     float pad2;
     int32_t group_N[kMaxGroups], group_dtype[kMaxGroups];
+    int32_t group_var[kMaxGroups];  // 1: the group's scenes carry per-splat grid sizes
     uint32_t group_off[kMaxGroups], group_count[kMaxGroups];  // segments of the tile list
     CamDev cams[kMaxCams];
     SceneDev scenes[kMaxScenes];

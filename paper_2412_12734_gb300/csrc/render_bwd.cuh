@@ -139,10 +139,12 @@ __device__ __forceinline__ void put(float &slot, float v) {
 // this pair owns are assigned (g[] holds zeros on entry).
 // lo: the splat's RecordLo when its record is flagged for the extended-
 // precision plane hit (the same splat for the whole warp), else null.
-template <int N, typename TexT, bool ACC>
+// VAR: the splat's grid is nk x nk (per-splat grid size; kN = (nk - 1) / (2
+// sigma)) and every texel weight goes to the per-cell pass.
+template <int N, typename TexT, bool ACC, bool VAR = false>
 __device__ __forceinline__ bool pair_adjoint(Pix &px, uint32_t idx, const float4 *rec, const RecordLo *lo,
-                                             const staged_t<TexT> *tex, float sigma, float kN, float g[32], Rem &rem,
-                                             uint32_t &npairs, uint32_t &ncontrib) {
+                                             const staged_t<TexT> *tex, float sigma, float kN, int nk, float g[32],
+                                             Rem &rem, uint32_t &npairs, uint32_t &ncontrib) {
     rem.w00 = rem.w10 = rem.w01 = rem.w11 = 0.0f;
     rem.c0 = rem.c1 = rem.c2 = 0.0f;
     rem.base = 0;
@@ -168,7 +170,7 @@ __device__ __forceinline__ bool pair_adjoint(Pix &px, uint32_t idx, const float4
     ++ncontrib;
     const float iom = fast_rcp(1.0f - alpha);
     const float Ti = px.T * iom;
-    const Cell<N> cell = grid_cell<N>(u, v, sigma, kN);
+    const Cell<N> cell = VAR ? grid_cell_n<N>(u, v, sigma, kN, nk) : grid_cell<N>(u, v, sigma, kN);
     const Quad qd = grid_quad<N, TexT>(tex, cell);
     float col[3];
     grid_colour<N>(qd, cell, col);
@@ -198,7 +200,13 @@ __device__ __forceinline__ bool pair_adjoint(Pix &px, uint32_t idx, const float4
         const float fvh = ch0 * ((qd.c01.x - qd.c00.x) * (1.0f - fu) + (qd.c11.x - qd.c10.x) * fu) +
                           ch1 * ((qd.c01.y - qd.c00.y) * (1.0f - fu) + (qd.c11.y - qd.c10.y) * fu) +
                           ch2 * ((qd.c01.z - qd.c00.z) * (1.0f - fu) + (qd.c11.z - qd.c10.z) * fu);
-        if (N == 2) {
+        if (VAR) {
+            // the grid's size is the splat's own: every weight to the per-cell pass
+            rem.w00 = w00;
+            rem.w10 = w10;
+            rem.w01 = w01;
+            rem.w11 = w11;
+        } else if (N == 2) {
             // every texel of a 2 x 2 grid is a corner: all four weights go to the
             // warp-reduced corner slots
             put<ACC>(g[kCornerSlot + 0], w00 * ch0); put<ACC>(g[kCornerSlot + 1], w00 * ch1); put<ACC>(g[kCornerSlot + 2], w00 * ch2);
@@ -349,7 +357,7 @@ __device__ __forceinline__ void line_window(Rem rem[P], float g[32], int &t0, in
     step = L < 2 ? 1 : N;
 }
 
-template <int TS, int N, typename TexT, int P>
+template <int TS, int N, typename TexT, int P, bool VAR>
 __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b, int batch, uint32_t tile) {
     constexpr int NT = TS * TS / P;
     constexpr int NN = N * N;
@@ -364,6 +372,7 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
     uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_box + batch);
     float *s_g = reinterpret_cast<float *>(s_mask + batch);  // [batch][16]
     float *s_tg = s_g + batch * kRecGrad;                    // [batch][TEXF]
+    int32_t *s_n = reinterpret_cast<int32_t *>(s_tg + batch * TEXF);  // VAR: per-splat grid size
     __shared__ uint32_t s_maxlast;
 
     const int ci = camera_of_tile(f, tile);
@@ -427,8 +436,8 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
         const int bs = max(0, be - batch), nb = be - bs;
         for (int e = threadIdx.x; e < nb * kRecGrad; e += NT) s_g[e] = 0.0f;
         for (int e = threadIdx.x; e < nb * TEXF; e += NT) s_tg[e] = 0.0f;
-        stage_batch<N, NT, TexT, TS, 4 * P>(b.fw, cam, sc, range.x + bs, nb, tx * TS, ty * TS, s_rec, s_tex, s_k,
-                                            s_j, s_box, s_mask, s_fp);
+        stage_batch<N, NT, TexT, TS, 4 * P, false, VAR>(b.fw, cam, sc, range.x + bs, nb, tx * TS, ty * TS, s_rec,
+                                                        s_tex, s_k, s_j, s_box, s_mask, s_fp, s_n);
         __syncthreads();
         // splats at or beyond the warp's last contributor are skipped warp-wide;
         // below it at least one lane of the warp is active
@@ -440,15 +449,17 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
             for (int q = 0; q < 32; ++q) g[q] = 0.0f;
             Rem rem[P];
             const RecordLo *lo = s_rec[4 * i + 1].w < 0.0f ? b.fw.rec_lo + staged_record(cam, s_k[i]) : nullptr;
-            bool act = pair_adjoint<N, TexT, false>(pix[0], uint32_t(bs + i), s_rec + 4 * i, lo, s_tex + i * NN, sigma,
-                                                    kN, g, rem[0], npairs, ncontrib);
+            const int nk = VAR ? s_n[i] : N;
+            const float kNk = VAR ? float(nk - 1) / (2.0f * sigma) : kN;
+            bool act = pair_adjoint<N, TexT, false, VAR>(pix[0], uint32_t(bs + i), s_rec + 4 * i, lo, s_tex + i * NN,
+                                                         sigma, kNk, nk, g, rem[0], npairs, ncontrib);
 #pragma unroll
             for (int p = 1; p < P; ++p)
-                act |= pair_adjoint<N, TexT, true>(pix[p], uint32_t(bs + i), s_rec + 4 * i, lo, s_tex + i * NN, sigma,
-                                                   kN, g, rem[p], npairs, ncontrib);
+                act |= pair_adjoint<N, TexT, true, VAR>(pix[p], uint32_t(bs + i), s_rec + 4 * i, lo, s_tex + i * NN,
+                                                        sigma, kNk, nk, g, rem[p], npairs, ncontrib);
             if (!__any_sync(0xffffffffu, act)) continue;
             int t0 = 0, step = 0;
-            if (N == 4) line_window<N, P>(rem, g, t0, step);
+            if (N == 4 && !VAR) line_window<N, P>(rem, g, t0, step);
             const float tot = warp_reduce_scatter32(g, lane);
             if (tot != 0.0f) {
                 if (lane < kCornerSlot) atomicAdd(s_g + i * kRecGrad + lane, tot);
@@ -456,7 +467,7 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
                     atomicAdd(s_tg + i * TEXF + 3 * (t0 + my_q * step) + my_c, tot);
                 else if (N != 4 && my_corner >= 0) atomicAdd(s_tg + i * TEXF + my_corner_off, tot);
             }
-            if (N > 2) {
+            if (N > 2 || VAR) {
                 // edge / interior texels: lanes sharing a cell touch the same four
                 // texels; each distinct cell is one reduce-scatter and one
                 // conflict-free atomic (a lane's P pixels join the same group
@@ -578,7 +589,7 @@ constexpr int min_blocks() {
     return P == 1 ? 1024 / (TS * TS) : 1280 / (TS * TS);
 }
 
-template <int TS, int N, typename TexT, int P>
+template <int TS, int N, typename TexT, int P, bool VAR>
 __global__ void __launch_bounds__(TS * TS / P, min_blocks<TS, P>())
     render_bwd_kernel(Frame f, RenderBwdBufs b, int batch, TileSched ts) {
     __shared__ uint32_t s_next;
@@ -595,18 +606,18 @@ __global__ void __launch_bounds__(TS * TS / P, min_blocks<TS, P>())
         }
         if (idx >= ts.count) break;
         const uint32_t tile = ts.list ? ts.list[ts.off + idx] : ts.off + idx;
-        bwd_tile<TS, N, TexT, P>(f, b, batch, tile);
+        bwd_tile<TS, N, TexT, P, VAR>(f, b, batch, tile);
     }
 }
 
-template <int TS, int N, typename TexT, int P>
+template <int TS, int N, typename TexT, int P, bool VAR = false>
 cudaError_t launch_t(const Frame &f, const RenderBwdBufs &b, int batch, TileSched ts, bool persistent,
                      cudaStream_t s) {
     constexpr int NT = TS * TS / P;
-    const size_t smem = stage_bytes<N, TexT>(batch, true);
+    const size_t smem = stage_bytes<N, TexT>(batch, true) + (VAR ? size_t(batch) * 4 : 0);
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(render_bwd_kernel<TS, N, TexT, P>,
+        cudaError_t e = cudaFuncSetAttribute(render_bwd_kernel<TS, N, TexT, P, VAR>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
         configured = true;
@@ -619,7 +630,7 @@ cudaError_t launch_t(const Frame &f, const RenderBwdBufs &b, int batch, TileSche
             int dev = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_bwd_kernel<TS, N, TexT, P>, NT, smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_bwd_kernel<TS, N, TexT, P, VAR>, NT, smem);
             smem_seen = smem;
             if (per_sm < 1) per_sm = 1;
         }
@@ -628,7 +639,7 @@ cudaError_t launch_t(const Frame &f, const RenderBwdBufs &b, int batch, TileSche
         ts.work = nullptr;
     }
     if (grid == 0) return cudaSuccess;
-    render_bwd_kernel<TS, N, TexT, P><<<grid, NT, smem, s>>>(f, b, batch, ts);
+    render_bwd_kernel<TS, N, TexT, P, VAR><<<grid, NT, smem, s>>>(f, b, batch, ts);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -646,9 +657,35 @@ cudaError_t launch_n(const Frame &f, const RenderBwdBufs &b, int N, int batch, T
     }
 }
 
+// Per-splat grid sizes: 16 x 16 tiles, one pixel per thread (N is the grid
+// block of the scene).
+template <typename TexT>
+cudaError_t launch_var(const Frame &f, const RenderBwdBufs &b, int N, int batch, TileSched ts, bool persistent,
+                       cudaStream_t s) {
+    switch (N) {
+        case 2: return launch_t<16, 2, TexT, 1, true>(f, b, batch, ts, persistent, s);
+        case 4: return launch_t<16, 4, TexT, 1, true>(f, b, batch, ts, persistent, s);
+        case 8: return launch_t<16, 8, TexT, 1, true>(f, b, batch, ts, persistent, s);
+        case 16: return launch_t<16, 16, TexT, 1, true>(f, b, batch, ts, persistent, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <int TS, int P>
 cudaError_t launch_d(const Frame &f, const RenderBwdBufs &b, int g, int N, int batch, TileSched ts, bool persistent,
                      cudaStream_t s) {
+    if (f.group_var[g]) {
+        if constexpr (P == 1) {
+            if (TS != 16) return cudaErrorInvalidValue;
+            switch (f.group_dtype[g]) {
+                case GB_F16: return launch_var<__half>(f, b, N, batch, ts, persistent, s);
+                case GB_BF16: return launch_var<__nv_bfloat16>(f, b, N, batch, ts, persistent, s);
+                default: return launch_var<float>(f, b, N, batch, ts, persistent, s);
+            }
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
     switch (f.group_dtype[g]) {
         case GB_F16: return launch_n<TS, __half, P>(f, b, N, batch, ts, persistent, s);
         case GB_BF16: return launch_n<TS, __nv_bfloat16, P>(f, b, N, batch, ts, persistent, s);

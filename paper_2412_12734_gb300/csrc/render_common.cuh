@@ -100,12 +100,13 @@ __device__ __forceinline__ bool block_hits(const float4 &q2, uint2 box, const fl
 // Loads the records and colour grids of instances [first, first + nb) of a
 // tile range into shared memory, and for every splat the mask of the tile's
 // 8 x BH warp blocks (row-major, TS/8 per row) that its footprint may touch
-// (block_hits).  Caller synchronizes before and after.
-template <int N, int NT, typename TexT, int TS, int BH, bool WIDE = false>
+// (block_hits); with VAR, the splat's own grid size (1..N) into s_n.  Caller
+// synchronizes before and after.
+template <int N, int NT, typename TexT, int TS, int BH, bool WIDE = false, bool VAR = false>
 __device__ __forceinline__ void stage_batch(const RenderBufs &b, const CamDev &cam, const SceneDev &sc,
                                             uint32_t first, int nb, int tx0, int ty0, float4 *s_rec,
                                             staged_t<TexT, WIDE> *s_tex, int32_t *s_k, uint32_t *s_j,
-                                            uint2 *s_box, uint32_t *s_mask, float4 *s_fp) {
+                                            uint2 *s_box, uint32_t *s_mask, float4 *s_fp, int32_t *s_n = nullptr) {
     constexpr int NN = N * N;
     constexpr int NB = TS * TS / (8 * BH);  // warp blocks per tile: 1 to 32
     static_assert(32 % NB == 0 && NT % 32 == 0, "block masks are gathered within a warp");
@@ -122,6 +123,7 @@ __device__ __forceinline__ void stage_batch(const RenderBufs &b, const CamDev &c
         // camera's block for per-texel SH scenes (evaluated grid per record)
         s_k[t] = int32_t(int64_t(r) - cam.rec_off + cam.tex_row);
         s_j[t] = j;
+        if (VAR) s_n[t] = min(max(int(sc.splat_n[int64_t(r) - cam.rec_off]), 1), N);
         float4 k[3];
         footprint_setup(rp[0], rp[1], rp[3].x, k);
         s_fp[3 * t + 0] = k[0];
@@ -173,6 +175,22 @@ __device__ __forceinline__ Cell<N> grid_cell(float u, float v, float sigma, floa
     const float up = fminf(fmaxf((u + sigma) * kN, 0.0f), float(N - 1));
     const float vp = fminf(fmaxf((v + sigma) * kN, 0.0f), float(N - 1));
     const int iu = min(int(up), N - 2), iv = min(int(vp), N - 2);
+    c.fu = up - float(iu);
+    c.fv = vp - float(iv);
+    c.base = iu * N + iv;
+    return c;
+}
+
+// The same for a splat whose grid is n x n (1 <= n <= N), stored in rows and
+// columns 0..n-1 of its N x N block; kN = (n - 1) / (2 sigma).  For n = 1 the
+// cell is texel 0 with zero fractions (the constant colour).
+template <int N>
+__device__ __forceinline__ Cell<N> grid_cell_n(float u, float v, float sigma, float kN, int n) {
+    Cell<N> c;
+    const float top = float(n - 1);
+    const float up = fminf(fmaxf((u + sigma) * kN, 0.0f), top);
+    const float vp = fminf(fmaxf((v + sigma) * kN, 0.0f), top);
+    const int iu = max(min(int(up), n - 2), 0), iv = max(min(int(vp), n - 2), 0);
     c.fu = up - float(iu);
     c.fv = vp - float(iv);
     c.base = iu * N + iv;

@@ -32,10 +32,11 @@ struct FPix {
 // One (pixel, splat) pair of the front-to-back walk: evaluated by every lane of
 // the warp (a finished pixel's result is dropped), blended only where alpha
 // passes the cutoff and the pixel's transmittance stays above the stop bound.
-template <int N, typename TexT, bool WIDE>
+// VAR: the splat's grid is nk x nk (per-splat grid size), kN = (nk - 1) / (2 sigma).
+template <int N, typename TexT, bool WIDE, bool VAR>
 __device__ __forceinline__ void fwd_pair(FPix &q, const Hit &h, const float4 &q1, const float4 &q3,
                                          const staged_t<TexT, WIDE> *tex, uint32_t idx1, float sigma, float kN,
-                                         uint32_t &npairs, uint32_t &nblend) {
+                                         int nk, uint32_t &npairs, uint32_t &nblend) {
     npairs += q.done ? 0u : 1u;
     const float zz = h.zz;
     const float rz = fast_rcp(zz);
@@ -50,7 +51,7 @@ __device__ __forceinline__ void fwd_pair(FPix &q, const Hit &h, const float4 &q1
     const bool hit = !q.done && zz != 0.0f && alpha >= kAlphaMin;
     q.done = q.done || (hit && tT < kTMin);
     if (hit && !(tT < kTMin)) {
-        const Cell<N> cell = grid_cell<N>(u, v, sigma, kN);
+        const Cell<N> cell = VAR ? grid_cell_n<N>(u, v, sigma, kN, nk) : grid_cell<N>(u, v, sigma, kN);
         float col[3];
         grid_colour<N>(grid_quad<N, TexT, WIDE>(tex, cell), cell, col);
         const float w = alpha * q.T;
@@ -66,7 +67,7 @@ __device__ __forceinline__ void fwd_pair(FPix &q, const Hit &h, const float4 &q1
     }
 }
 
-template <int TS, int N, typename TexT, int P>
+template <int TS, int N, typename TexT, int P, bool VAR>
 __device__ __forceinline__ void fwd_tile(const Frame &f, const RenderBufs &b, int batch, uint32_t tile) {
     constexpr int NT = TS * TS / P;
     constexpr int NN = N * N;
@@ -79,6 +80,7 @@ __device__ __forceinline__ void fwd_tile(const Frame &f, const RenderBufs &b, in
     uint32_t *s_j = reinterpret_cast<uint32_t *>(s_k + batch);
     uint2 *s_box = reinterpret_cast<uint2 *>(s_j + batch);
     uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_box + batch);
+    int32_t *s_n = reinterpret_cast<int32_t *>(s_mask + batch);  // VAR: per-splat grid size
 
     const int ci = camera_of_tile(f, tile);
     const CamDev &cam = f.cams[ci];
@@ -116,26 +118,28 @@ __device__ __forceinline__ void fwd_tile(const Frame &f, const RenderBufs &b, in
     for (int bs = 0; bs < n_inst; bs += batch) {
         if (__syncthreads_count(all_done()) == NT) break;
         const int nb = min(batch, n_inst - bs);
-        stage_batch<N, NT, TexT, TS, 4 * P, WIDE>(b, cam, sc, range.x + bs, nb, tx * TS, ty * TS, s_rec, s_tex, s_k,
-                                                 s_j, s_box, s_mask, s_fp);
+        stage_batch<N, NT, TexT, TS, 4 * P, WIDE, VAR>(b, cam, sc, range.x + bs, nb, tx * TS, ty * TS, s_rec, s_tex,
+                                                      s_k, s_j, s_box, s_mask, s_fp, s_n);
         __syncthreads();
         for (int i = 0; i < nb; ++i) {
             if ((i & 15) == 0 && __all_sync(0xffffffffu, all_done())) break;
             if (!(s_mask[i] & wbit)) continue;
             const float4 q0 = s_rec[4 * i + 0], q1 = s_rec[4 * i + 1], q2 = s_rec[4 * i + 2],
                          q3 = s_rec[4 * i + 3];
+            const int nk = VAR ? s_n[i] : N;
+            const float kNk = VAR ? float(nk - 1) / (2.0f * sigma) : kN;
             if (q1.w < 0.0f) {
                 // flagged record (the same for the whole warp): extended-precision plane hit
                 const RecordLo L = b.rec_lo[staged_record(cam, s_k[i])];
 #pragma unroll
                 for (int p = 0; p < P; ++p)
-                    fwd_pair<N, TexT, WIDE>(pix[p], plane_hit_ext(pix[p].xf, pix[p].yf, q0, q1, q2, L), q1, q3,
-                                            s_tex + i * NN, uint32_t(bs + i + 1), sigma, kN, npairs, nblend);
+                    fwd_pair<N, TexT, WIDE, VAR>(pix[p], plane_hit_ext(pix[p].xf, pix[p].yf, q0, q1, q2, L), q1, q3,
+                                                 s_tex + i * NN, uint32_t(bs + i + 1), sigma, kNk, nk, npairs, nblend);
             } else {
 #pragma unroll
                 for (int p = 0; p < P; ++p)
-                    fwd_pair<N, TexT, WIDE>(pix[p], plane_hit(pix[p].xf, pix[p].yf, q0, q1, q2), q1, q3,
-                                            s_tex + i * NN, uint32_t(bs + i + 1), sigma, kN, npairs, nblend);
+                    fwd_pair<N, TexT, WIDE, VAR>(pix[p], plane_hit(pix[p].xf, pix[p].yf, q0, q1, q2), q1, q3,
+                                                 s_tex + i * NN, uint32_t(bs + i + 1), sigma, kNk, nk, npairs, nblend);
             }
         }
     }
@@ -179,7 +183,7 @@ __host__ __device__ constexpr int fwd_min_blocks() {
     return (N >= 16 ? 1280 : 1536) / (TS * TS);
 }
 
-template <int TS, int N, typename TexT>
+template <int TS, int N, typename TexT, bool VAR>
 __global__ void __launch_bounds__(TS * TS / fwd_ppt<N>(), fwd_min_blocks<TS, N>())
     render_fwd_kernel(Frame f, RenderBufs b, int batch, TileSched ts) {
     __shared__ uint32_t s_next;
@@ -196,17 +200,17 @@ __global__ void __launch_bounds__(TS * TS / fwd_ppt<N>(), fwd_min_blocks<TS, N>(
         }
         if (idx >= ts.count) break;
         const uint32_t tile = ts.list ? ts.list[ts.off + idx] : ts.off + idx;
-        fwd_tile<TS, N, TexT, fwd_ppt<N>()>(f, b, batch, tile);
+        fwd_tile<TS, N, TexT, fwd_ppt<N>(), VAR>(f, b, batch, tile);
     }
 }
 
-template <int TS, int N, typename TexT>
+template <int TS, int N, typename TexT, bool VAR = false>
 cudaError_t launch_t(const Frame &f, const RenderBufs &b, int batch, TileSched ts, bool persistent,
                      cudaStream_t s) {
-    const size_t smem = stage_bytes<N, TexT, (N <= 4)>(batch, false);
+    const size_t smem = stage_bytes<N, TexT, (N <= 4)>(batch, false) + (VAR ? size_t(batch) * 4 : 0);
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(render_fwd_kernel<TS, N, TexT>,
+        cudaError_t e = cudaFuncSetAttribute(render_fwd_kernel<TS, N, TexT, VAR>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
         configured = true;
@@ -219,8 +223,8 @@ cudaError_t launch_t(const Frame &f, const RenderBufs &b, int batch, TileSched t
             int dev = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_fwd_kernel<TS, N, TexT>, TS * TS / fwd_ppt<N>(),
-                                                          smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_fwd_kernel<TS, N, TexT, VAR>,
+                                                          TS * TS / fwd_ppt<N>(), smem);
             smem_seen = smem;
             if (per_sm < 1) per_sm = 1;
         }
@@ -229,7 +233,7 @@ cudaError_t launch_t(const Frame &f, const RenderBufs &b, int batch, TileSched t
         ts.work = nullptr;
     }
     if (grid == 0) return cudaSuccess;
-    render_fwd_kernel<TS, N, TexT><<<grid, TS * TS / fwd_ppt<N>(), smem, s>>>(f, b, batch, ts);
+    render_fwd_kernel<TS, N, TexT, VAR><<<grid, TS * TS / fwd_ppt<N>(), smem, s>>>(f, b, batch, ts);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -247,9 +251,30 @@ cudaError_t launch_n(const Frame &f, const RenderBufs &b, int N, int batch, Tile
     }
 }
 
+// Per-splat grid sizes (16 x 16 tiles): N is the grid block of the scene.
+template <typename TexT>
+cudaError_t launch_var(const Frame &f, const RenderBufs &b, int N, int batch, TileSched ts, bool persistent,
+                       cudaStream_t s) {
+    switch (N) {
+        case 2: return launch_t<16, 2, TexT, true>(f, b, batch, ts, persistent, s);
+        case 4: return launch_t<16, 4, TexT, true>(f, b, batch, ts, persistent, s);
+        case 8: return launch_t<16, 8, TexT, true>(f, b, batch, ts, persistent, s);
+        case 16: return launch_t<16, 16, TexT, true>(f, b, batch, ts, persistent, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <int TS>
 cudaError_t launch_d(const Frame &f, const RenderBufs &b, int g, int N, int batch, TileSched ts, bool persistent,
                      cudaStream_t s) {
+    if (f.group_var[g]) {
+        if (TS != 16) return cudaErrorInvalidValue;
+        switch (f.group_dtype[g]) {
+            case GB_F16: return launch_var<__half>(f, b, N, batch, ts, persistent, s);
+            case GB_BF16: return launch_var<__nv_bfloat16>(f, b, N, batch, ts, persistent, s);
+            default: return launch_var<float>(f, b, N, batch, ts, persistent, s);
+        }
+    }
     switch (f.group_dtype[g]) {
         case GB_F16: return launch_n<TS, __half>(f, b, N, batch, ts, persistent, s);
         case GB_BF16: return launch_n<TS, __nv_bfloat16>(f, b, N, batch, ts, persistent, s);

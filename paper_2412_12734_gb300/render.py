@@ -48,6 +48,8 @@ def scene_to_device(scene: dict, device="cuda") -> dict:
     out["sigma"] = float(scene.get("sigma", 0.5))
     out["mip_level"] = int(scene.get("mip_level", 0))
     out["tex_sh_degree"] = int(scene.get("tex_sh_degree", 0))
+    if scene.get("splat_tex_n") is not None:
+        out["splat_tex_n"] = torch.as_tensor(np.asarray(scene["splat_tex_n"]).astype(np.uint8), device=device)
     return out
 
 
@@ -85,6 +87,12 @@ def scene_struct(sc: dict) -> L.gb_scene:
     s.mip_level = int(sc.get("mip_level", 0))
     s.tex_sh_degree = Dt
     s.reserved = 0
+    sn = sc.get("splat_tex_n")
+    if sn is not None:
+        _check_tensor(sn, "splat_tex_n", (), (torch.uint8,))
+        if sn.shape[0] != K:
+            raise ValueError(f"splat_tex_n: first dimension {sn.shape[0]} != {K}")
+        s.splat_tex_n = sn.data_ptr()
     return s
 
 
