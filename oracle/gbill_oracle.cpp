@@ -41,6 +41,8 @@
  *          explicit depth sort orders splats by (FP32 depth bits, splat id).
  *   R17    optional background added as T_final * bg.
  *   R18    depth output = sum_i z_i alpha_i T_i (not normalised).
+ *   R28    per-splat grid size n_k <= N: splat k's grid is rows and columns
+ *          0..n_k-1 of its N x N block, sampled by Alg. 2 with n_k.
  *
  * Build: g++ -O2 -std=c++17 -ffp-contract=off -fPIC -shared -pthread
  * (-ffp-contract=off keeps the FP32 key formula free of fused multiply-adds.)
