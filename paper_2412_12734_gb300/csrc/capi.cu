@@ -199,12 +199,13 @@ int forward_batch(const gb_options &o, const Frame &f, int nt) {
 // pass's shared-memory budget per block, a multiple of 8, at least 8.  The
 // backward gets 48 KB, so that four blocks (the register limit of its 256
 // threads) stay resident per SM: with FP16 grids staged at 8 bytes a texel
-// that is 88 at N = 4, 32 at N = 8 and 8 at N = 16 (measured on the 1M-splat,
-// 16-view workload: the best of the depths tried at N = 4 and 8; with
-// FP32-width staging N = 8 ran 27 % slower at 40, three blocks per SM, than at
-// 24, and N = 16 at 8 left three blocks per SM: 139 against 165 Mpixel/s).
-// The forward gets 36 KB, so that six blocks (its register limit at 16 x 16
-// tiles) stay resident: 88 at N = 4, 56 at N = 8, 16 at N = 16.
+// that is 184 at N = 4, 72 at N = 8 and 8 at N = 16 (measured on the
+// 1M-splat, 16-view workload: N = 4 at 88 / 128 / 184: 39.9 / 38.7 / 37.8 ms;
+// N = 8 at 32 / 64 / 88: 42.7 / 41.0 / 41.8 ms; with FP32-width staging and
+// shared texel accumulators N = 8 ran 27 % slower at 40, three blocks per SM,
+// than at 24, and N = 16 at 8 left three blocks per SM: 139 against 165
+// Mpixel/s).  The forward gets 36 KB, so that six blocks (its register limit
+// at 16 x 16 tiles) stay resident: 88 at N = 4, 56 at N = 8, 16 at N = 16.
 int default_batch(const Frame &f, bool bwd) {
     const int per = int(frame_smem(f, 1, bwd));
     int b = ((bwd ? 48 : 36) * 1024) / per;
@@ -219,11 +220,11 @@ int default_batch(const Frame &f, bool bwd) {
 template <typename TexT>
 size_t batch_smem_t(int N, int batch, bool bwd) {
     switch (N) {
-        case 1: return bwd ? stage_bytes<1, TexT>(batch, true) : stage_bytes<1, TexT, true>(batch, false);
-        case 2: return bwd ? stage_bytes<2, TexT>(batch, true) : stage_bytes<2, TexT, true>(batch, false);
-        case 4: return bwd ? stage_bytes<4, TexT>(batch, true) : stage_bytes<4, TexT, true>(batch, false);
-        case 8: return stage_bytes<8, TexT>(batch, bwd);
-        default: return stage_bytes<16, TexT>(batch, bwd);
+        case 1: return bwd ? bwd_stage_bytes<1, TexT>(batch) : stage_bytes<1, TexT, true>(batch, false);
+        case 2: return bwd ? bwd_stage_bytes<2, TexT>(batch) : stage_bytes<2, TexT, true>(batch, false);
+        case 4: return bwd ? bwd_stage_bytes<4, TexT>(batch) : stage_bytes<4, TexT, true>(batch, false);
+        case 8: return bwd ? bwd_stage_bytes<8, TexT>(batch) : stage_bytes<8, TexT>(batch, false);
+        default: return bwd ? bwd_stage_bytes<16, TexT>(batch) : stage_bytes<16, TexT>(batch, false);
     }
 }
 
@@ -1183,7 +1184,7 @@ gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int3
         float best_ms = INFINITY;
         int n = 0;
         const int tile_c[3] = {16, 8, 32};
-        const int batch_c[8] = {8, 16, 24, 32, 48, 64, 88, 128};
+        const int batch_c[10] = {8, 16, 24, 32, 48, 64, 88, 128, 176, 256};
         // one untimed run of the candidate (sizes `saved`), then `reps` timed
         // no-sync runs; *t = mean milliseconds
         auto time_candidate = [&](gb_options &c, bool with_bwd, float *t) -> gb_status {
@@ -1222,7 +1223,7 @@ gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int3
         o.bwd_kernel = 1;
         for (int pi = 1; pi <= 2 && st == GB_OK; ++pi)
         for (int ti = 0; ti < 3 && st == GB_OK; ++ti)
-            for (int bi = 0; bi < 8 && st == GB_OK; ++bi) {
+            for (int bi = 0; bi < 10 && st == GB_OK; ++bi) {
                 const int T = tile_c[ti], B = batch_c[bi];
                 if (B > T * T / pi) continue;
                 if (frame_has_var(f) && (T != 16 || pi != 1)) continue;
@@ -1269,7 +1270,7 @@ gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int3
             gb_options c = *best;
             const int T = c.tile_size;
             float best_fwd = INFINITY;
-            for (int bi = 0; bi < 8 && st == GB_OK; ++bi) {
+            for (int bi = 0; bi < 10 && st == GB_OK; ++bi) {
                 const int B = batch_c[bi];
                 if (B > T * T || frame_smem(f, B, false) > 160 * 1024) continue;
                 c.batch_depth_fwd = B;

@@ -21,8 +21,10 @@
 // reduce-scatter; at N >= 8 the four grid corners, the other texel weights
 // reduced per grid cell (one 16-value reduce-scatter per distinct cell of the
 // warp) or, when many cells are hit, added to shared memory directly.  Per
-// batch the per-splat sums reach global memory with one atomic per value per
-// tile.
+// (warp, splat) pair the reduced values go to global memory with one atomic
+// each (record gradients, and texel gradients of grids up to 8 x 8); texel
+// gradients of 16 x 16 grids gather per batch in shared memory and reach
+// global memory with one atomic per value per tile (bwd_tex_shared).
 #pragma once
 
 #include <algorithm>
@@ -448,9 +450,9 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
     uint32_t *s_j = reinterpret_cast<uint32_t *>(s_k + batch);
     uint2 *s_box = reinterpret_cast<uint2 *>(s_j + batch);
     uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_box + batch);
-    float *s_g = reinterpret_cast<float *>(s_mask + batch);  // [batch][16]
-    float *s_tg = s_g + batch * kRecGrad;                    // [batch][TEXF]
-    int32_t *s_n = reinterpret_cast<int32_t *>(s_tg + batch * TEXF);  // VAR: per-splat grid size
+    constexpr bool kTexShared = bwd_tex_shared(N);
+    float *s_tg = reinterpret_cast<float *>(s_mask + batch);  // [batch][TEXF] when kTexShared
+    int32_t *s_n = reinterpret_cast<int32_t *>(s_tg + (kTexShared ? batch * TEXF : 0));  // VAR: per-splat grid size
     __shared__ uint32_t s_maxlast;
 
     const int ci = camera_of_tile(f, tile);
@@ -513,8 +515,8 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
 
     for (int be = max_last; be > 0; be -= batch) {
         const int bs = max(0, be - batch), nb = be - bs;
-        for (int e = threadIdx.x; e < nb * kRecGrad; e += NT) s_g[e] = 0.0f;
-        for (int e = threadIdx.x; e < nb * TEXF; e += NT) s_tg[e] = 0.0f;
+        if (kTexShared)
+            for (int e = threadIdx.x; e < nb * TEXF; e += NT) s_tg[e] = 0.0f;
         stage_batch<N, NT, TexT, TS, 4 * P, false, VAR>(b.fw, cam, sc, range.x + bs, nb, tx * TS, ty * TS, s_rec,
                                                         s_tex, s_k, s_j, s_box, s_mask, s_fp, s_n);
         __syncthreads();
@@ -543,15 +545,23 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
                 if (kind == 5) line_window<N, P>(rem, g, t0, step);
             }
             const float tot = warp_reduce_scatter32(g, lane);
+            // this splat's texel gradients: its rows of the global output (formed
+            // where used, to keep registers free), or its shared accumulator
+            const bool want_tex = kTexShared || g_tex != nullptr;
+            auto gt = [&]() -> float * {
+                return kTexShared ? s_tg + i * TEXF : g_tex + int64_t(s_k[i]) * TEXF;
+            };
             if (tot != 0.0f) {
-                if (lane < kCornerSlot) atomicAdd(s_g + i * kRecGrad + lane, tot);
-                else if (kGrid4) {
-                    if (lane < kCornerSlot + 12)
-                        atomicAdd(s_tg + i * TEXF +
-                                      3 * (kind == 5 ? t0 + my_q * step : grid4_texel(kind, my_q)) + my_c,
-                                  tot);
-                } else if (my_corner >= 0) {
-                    atomicAdd(s_tg + i * TEXF + my_corner_off, tot);
+                if (lane < kCornerSlot) {
+                    atomicAdd(b.rec_grad + (s_j[i] * uint32_t(kRecGrad) + uint32_t(lane)), tot);
+                } else if (want_tex) {
+                    if (kGrid4) {
+                        if (lane < kCornerSlot + 12)
+                            atomicAdd(gt() + 3 * (kind == 5 ? t0 + my_q * step : grid4_texel(kind, my_q)) + my_c,
+                                      tot);
+                    } else if (my_corner >= 0) {
+                        atomicAdd(gt() + my_corner_off, tot);
+                    }
                 }
             }
             if (N > 4 || VAR || (kGrid4 && kind == 5)) {
@@ -568,6 +578,7 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
                     pend[p] = __ballot_sync(0xffffffffu, has[p]);
                     any_pend |= pend[p];
                 }
+                if (!want_tex) any_pend = 0u;
                 int cells = 0;
                 if (N >= 8 && any_pend) {
 #pragma unroll
@@ -577,7 +588,7 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
                     }
                 }
                 if (cells > kGroupCells8) {
-                    float *st = s_tg + i * TEXF;
+                    float *st = gt();
 #pragma unroll
                     for (int p = 0; p < P; ++p) {
                         if (!has[p]) continue;
@@ -637,28 +648,23 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
                         const int k = my_q16 / 3, c = my_q16 - 3 * k;
                         // k: 0 -> (iu, iv), 1 -> (iu+1, iv), 2 -> (iu, iv+1), 3 -> (iu+1, iv+1)
                         const int off = 3 * (key + ((k & 1) ? N : 0) + ((k & 2) ? 1 : 0)) + c;
-                        atomicAdd(s_tg + i * TEXF + off, t);
+                        atomicAdd(gt() + off, t);
                     }
                 }
             }
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < nb * kRecGrad; e += NT) {
-            const float v = s_g[e];
-            if (v != 0.0f) {
-                const int s = e / kRecGrad, q = e - s * kRecGrad;
-                atomicAdd(b.rec_grad + int64_t(s_j[s]) * kRecGrad + q, v);
-            }
-        }
-        if (g_tex)
-            for (int e = threadIdx.x; e < nb * TEXF; e += NT) {
-                const float v = s_tg[e];
-                if (v != 0.0f) {
-                    const int s = e / TEXF, o = e - s * TEXF;
-                    atomicAdd(g_tex + int64_t(s_k[s]) * TEXF + o, v);
+        if (kTexShared) {
+            if (g_tex)
+                for (int e = threadIdx.x; e < nb * TEXF; e += NT) {
+                    const float v = s_tg[e];
+                    if (v != 0.0f) {
+                        const int s = e / TEXF, o = e - s * TEXF;
+                        atomicAdd(g_tex + int64_t(s_k[s]) * TEXF + o, v);
+                    }
                 }
-            }
-        __syncthreads();
+            __syncthreads();
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -701,7 +707,7 @@ template <int TS, int N, typename TexT, int P, bool VAR = false>
 cudaError_t launch_t(const Frame &f, const RenderBwdBufs &b, int batch, TileSched ts, bool persistent,
                      cudaStream_t s) {
     constexpr int NT = TS * TS / P;
-    const size_t smem = stage_bytes<N, TexT>(batch, true) + (VAR ? size_t(batch) * 4 : 0);
+    const size_t smem = bwd_stage_bytes<N, TexT>(batch) + (VAR ? size_t(batch) * 4 : 0);
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(render_bwd_kernel<TS, N, TexT, P, VAR>,

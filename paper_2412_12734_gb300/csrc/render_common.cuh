@@ -17,14 +17,28 @@ template <typename TexT, bool WIDE = false>
 using staged_t = typename std::conditional<WIDE || sizeof(TexT) == 4, float4, uint2>::type;
 
 // Bytes of dynamic shared memory for one staged batch: records, footprints,
-// colour grids, splat indices, pixel rectangles, warp-block masks and (backward)
-// record/grid gradient accumulators.
+// colour grids, splat indices, pixel rectangles, warp-block masks and (with
+// bwd) record/grid gradient accumulators.
 template <int N, typename TexT, bool WIDE = false>
 __host__ __device__ inline size_t stage_bytes(int batch, bool bwd) {
     const int texf = N * N * 3;
     size_t b = size_t(batch) * (64 + 48 + sizeof(staged_t<TexT, WIDE>) * N * N + 20);
     if (bwd) b += size_t(batch) * (4 * kRecGrad + 4 * texf);
     return b;
+}
+
+// Whether the pixel-parallel backward gathers a batch's texel gradients in
+// shared memory (grids of N = 16) rather than adding each reduced value to
+// global memory.  Measured on the 1M-splat, 16-view workload at N = 8: 54.0 ms
+// with the shared accumulators (batch 32, the most that fits four blocks per
+// SM), 41.0 ms adding to global memory (batch 64, in less shared memory).
+__host__ __device__ constexpr bool bwd_tex_shared(int N) { return N >= 16; }
+
+// Staged bytes of one batch of the pixel-parallel backward (render_bwd.cuh):
+// the staging plus, for bwd_tex_shared grids, the texel-gradient accumulators.
+template <int N, typename TexT>
+__host__ __device__ inline size_t bwd_stage_bytes(int batch) {
+    return stage_bytes<N, TexT>(batch, false) + (bwd_tex_shared(N) ? size_t(batch) * 4 * N * N * 3 : 0);
 }
 
 // 1 / x through the SFU (max error 1 ulp; flush-to-zero).

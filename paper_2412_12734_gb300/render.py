@@ -285,14 +285,14 @@ class Rasterizer:
         sarr = (L.gb_scene * n_s)(*[scene_struct(s) for s in scenes])
         carr = (L.gb_camera * n_c)(*[camera_struct(c, cam_scene[i]) for i, c in enumerate(cams)])
         best = L.gb_options()
-        ms = (C.c_float * 64)()
-        tiles = (C.c_int32 * 64)()
-        batches = (C.c_int32 * 64)()
-        ppts = (C.c_int32 * 64)()
+        ms = (C.c_float * 128)()
+        tiles = (C.c_int32 * 128)()
+        batches = (C.c_int32 * 128)()
+        ppts = (C.c_int32 * 128)()
         n = C.c_int32()
         saved = saved or Saved(self)
         L.check(lib.gb_autotune(self.ctx, saved.handle, sarr, n_s, carr, n_c, None, reps, C.byref(best),
-                                C.addressof(ms), C.addressof(tiles), C.addressof(batches), C.addressof(ppts), 64,
+                                C.addressof(ms), C.addressof(tiles), C.addressof(batches), C.addressof(ppts), 128,
                                 C.byref(n)), self.ctx)
         # candidates with ppt 0 time the forward alone at batch depth "batch"; ppt 3
         # marks the splat-parallel backward
