@@ -199,12 +199,10 @@ int forward_batch(const gb_options &o, const Frame &f, int nt) {
 // pass's shared-memory budget per block, a multiple of 8, at least 8.  The
 // backward gets 48 KB, so that four blocks (the register limit of its 256
 // threads) stay resident per SM: with FP16 grids staged at 8 bytes a texel
-// that is 184 at N = 4, 72 at N = 8 and 8 at N = 16 (measured on the
+// that is 184 at N = 4, 72 at N = 8 and 16 at N = 16 (measured on the
 // 1M-splat, 16-view workload: N = 4 at 88 / 128 / 184: 39.9 / 38.7 / 37.8 ms;
-// N = 8 at 32 / 64 / 88: 42.7 / 41.0 / 41.8 ms; with FP32-width staging and
-// shared texel accumulators N = 8 ran 27 % slower at 40, three blocks per SM,
-// than at 24, and N = 16 at 8 left three blocks per SM: 139 against 165
-// Mpixel/s).  The forward gets 36 KB, so that six blocks (its register limit
+// N = 8 at 32 / 64 / 88: 42.7 / 41.0 / 41.8 ms; N = 16 at 16 / 24: 54.1 /
+// 54.2 ms).  The forward gets 36 KB, so that six blocks (its register limit
 // at 16 x 16 tiles) stay resident: 88 at N = 4, 56 at N = 8, 16 at N = 16.
 int default_batch(const Frame &f, bool bwd) {
     const int per = int(frame_smem(f, 1, bwd));

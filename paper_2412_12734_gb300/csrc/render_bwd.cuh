@@ -17,14 +17,15 @@
 // and 12 texel values go through one 32-value warp reduce-scatter: at N = 2 the
 // four texels; at N = 4 the four grid corners or one grid border line when
 // every texel the warp's pixels weight lies there (where the weight of a
-// clamped u or v lands), else all 48 texel channels through a second
-// reduce-scatter; at N >= 8 the four grid corners, the other texel weights
-// reduced per grid cell (one 16-value reduce-scatter per distinct cell of the
-// warp) or, when many cells are hit, added to shared memory directly.  Per
-// (warp, splat) pair the reduced values go to global memory with one atomic
-// each (record gradients, and texel gradients of grids up to 8 x 8); texel
-// gradients of 16 x 16 grids gather per batch in shared memory and reach
-// global memory with one atomic per value per tile (bwd_tex_shared).
+// clamped u or v lands), else the border line holding most of them; at N >= 8
+// the four grid corners.  The other texel weights are reduced per grid cell
+// (one 16-value reduce-scatter per distinct cell of the warp) or, at N >= 8
+// when many cells are hit, added by each lane.  Every reduced value goes to
+// global memory with one atomic per (warp, splat) pair: nothing accumulates in
+// shared memory, which holds only the staged batch.  Measured on the 1M-splat,
+// 16-view workload against per-batch shared accumulators flushed once per
+// tile: 40.5 -> 37.8 ms at N = 4 (batch 88 -> 184 in the same 48 KB), 54.0 ->
+// 41.0 ms at N = 8 (32 -> 64), 76.4 -> 54.1 ms at N = 16 (8 -> 16).
 #pragma once
 
 #include <algorithm>
@@ -450,9 +451,7 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
     uint32_t *s_j = reinterpret_cast<uint32_t *>(s_k + batch);
     uint2 *s_box = reinterpret_cast<uint2 *>(s_j + batch);
     uint32_t *s_mask = reinterpret_cast<uint32_t *>(s_box + batch);
-    constexpr bool kTexShared = bwd_tex_shared(N);
-    float *s_tg = reinterpret_cast<float *>(s_mask + batch);  // [batch][TEXF] when kTexShared
-    int32_t *s_n = reinterpret_cast<int32_t *>(s_tg + (kTexShared ? batch * TEXF : 0));  // VAR: per-splat grid size
+    int32_t *s_n = reinterpret_cast<int32_t *>(s_mask + batch);  // VAR: per-splat grid size
     __shared__ uint32_t s_maxlast;
 
     const int ci = camera_of_tile(f, tile);
@@ -515,8 +514,6 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
 
     for (int be = max_last; be > 0; be -= batch) {
         const int bs = max(0, be - batch), nb = be - bs;
-        if (kTexShared)
-            for (int e = threadIdx.x; e < nb * TEXF; e += NT) s_tg[e] = 0.0f;
         stage_batch<N, NT, TexT, TS, 4 * P, false, VAR>(b.fw, cam, sc, range.x + bs, nb, tx * TS, ty * TS, s_rec,
                                                         s_tex, s_k, s_j, s_box, s_mask, s_fp, s_n);
         __syncthreads();
@@ -545,12 +542,9 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
                 if (kind == 5) line_window<N, P>(rem, g, t0, step);
             }
             const float tot = warp_reduce_scatter32(g, lane);
-            // this splat's texel gradients: its rows of the global output (formed
-            // where used, to keep registers free), or its shared accumulator
-            const bool want_tex = kTexShared || g_tex != nullptr;
-            auto gt = [&]() -> float * {
-                return kTexShared ? s_tg + i * TEXF : g_tex + int64_t(s_k[i]) * TEXF;
-            };
+            // this splat's texel gradients, formed where used (fewer live registers)
+            const bool want_tex = g_tex != nullptr;
+            auto gt = [&]() -> float * { return g_tex + int64_t(s_k[i]) * TEXF; };
             if (tot != 0.0f) {
                 if (lane < kCornerSlot) {
                     atomicAdd(b.rec_grad + (s_j[i] * uint32_t(kRecGrad) + uint32_t(lane)), tot);
@@ -653,18 +647,7 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
                 }
             }
         }
-        __syncthreads();
-        if (kTexShared) {
-            if (g_tex)
-                for (int e = threadIdx.x; e < nb * TEXF; e += NT) {
-                    const float v = s_tg[e];
-                    if (v != 0.0f) {
-                        const int s = e / TEXF, o = e - s * TEXF;
-                        atomicAdd(g_tex + int64_t(s_k[s]) * TEXF + o, v);
-                    }
-                }
-            __syncthreads();
-        }
+        __syncthreads();  // the next batch's staging overwrites this one
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

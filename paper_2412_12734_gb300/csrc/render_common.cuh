@@ -27,18 +27,12 @@ __host__ __device__ inline size_t stage_bytes(int batch, bool bwd) {
     return b;
 }
 
-// Whether the pixel-parallel backward gathers a batch's texel gradients in
-// shared memory (grids of N = 16) rather than adding each reduced value to
-// global memory.  Measured on the 1M-splat, 16-view workload at N = 8: 54.0 ms
-// with the shared accumulators (batch 32, the most that fits four blocks per
-// SM), 41.0 ms adding to global memory (batch 64, in less shared memory).
-__host__ __device__ constexpr bool bwd_tex_shared(int N) { return N >= 16; }
-
-// Staged bytes of one batch of the pixel-parallel backward (render_bwd.cuh):
-// the staging plus, for bwd_tex_shared grids, the texel-gradient accumulators.
+// Staged bytes of one batch of the pixel-parallel backward (render_bwd.cuh),
+// which adds its gradients to global memory and holds no accumulators in
+// shared memory.
 template <int N, typename TexT>
 __host__ __device__ inline size_t bwd_stage_bytes(int batch) {
-    return stage_bytes<N, TexT>(batch, false) + (bwd_tex_shared(N) ? size_t(batch) * 4 * N * N * 3 : 0);
+    return stage_bytes<N, TexT>(batch, false);
 }
 
 // 1 / x through the SFU (max error 1 ulp; flush-to-zero).
