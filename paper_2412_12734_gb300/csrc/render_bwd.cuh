@@ -177,8 +177,24 @@ __device__ __forceinline__ bool pair_adjoint(Pix &px, uint32_t idx, const float4
     const float Ti = px.T * iom;
     const Cell<N> cell = VAR ? grid_cell_n<N>(u, v, sigma, kN, nk) : grid_cell<N>(u, v, sigma, kN);
     const Quad qd = grid_quad<N, TexT>(tex, cell);
-    float col[3];
-    grid_colour<N>(qd, cell, col);
+    // bilinear colour (the forward's lerp order) and its derivatives in f_u
+    // and f_v from the same differences: d col / d f_v = b - a, d col / d f_u
+    // = d10 + f_v (d11 - d10)
+    float col[3], dcu[3], dcv[3];
+    if (N == 1) {
+        grid_colour<N>(qd, cell, col);
+    } else {
+        const float c00[3] = {qd.c00.x, qd.c00.y, qd.c00.z}, c10[3] = {qd.c10.x, qd.c10.y, qd.c10.z};
+        const float c01[3] = {qd.c01.x, qd.c01.y, qd.c01.z}, c11[3] = {qd.c11.x, qd.c11.y, qd.c11.z};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float d10 = c10[k] - c00[k], d11 = c11[k] - c01[k];
+            const float a = fmaf(cell.fu, d10, c00[k]), bb = fmaf(cell.fu, d11, c01[k]);
+            dcv[k] = bb - a;
+            col[k] = fmaf(cell.fv, dcv[k], a);
+            dcu[k] = fmaf(cell.fv, d11 - d10, d10);
+        }
+    }
     col[0] += q3.y;
     col[1] += q3.z;
     col[2] += q3.w;
@@ -199,12 +215,8 @@ __device__ __forceinline__ bool pair_adjoint(Pix &px, uint32_t idx, const float4
         const float w00 = (1.0f - fu) * (1.0f - fv), w10 = fu * (1.0f - fv);
         const float w01 = (1.0f - fu) * fv, w11 = fu * fv;
         // d colour / d f_u and d f_v, dotted with the colour adjoint
-        const float fuh = ch0 * ((qd.c10.x - qd.c00.x) * (1.0f - fv) + (qd.c11.x - qd.c01.x) * fv) +
-                          ch1 * ((qd.c10.y - qd.c00.y) * (1.0f - fv) + (qd.c11.y - qd.c01.y) * fv) +
-                          ch2 * ((qd.c10.z - qd.c00.z) * (1.0f - fv) + (qd.c11.z - qd.c01.z) * fv);
-        const float fvh = ch0 * ((qd.c01.x - qd.c00.x) * (1.0f - fu) + (qd.c11.x - qd.c10.x) * fu) +
-                          ch1 * ((qd.c01.y - qd.c00.y) * (1.0f - fu) + (qd.c11.y - qd.c10.y) * fu) +
-                          ch2 * ((qd.c01.z - qd.c00.z) * (1.0f - fu) + (qd.c11.z - qd.c10.z) * fu);
+        const float fuh = fmaf(ch0, dcu[0], fmaf(ch1, dcu[1], ch2 * dcu[2]));
+        const float fvh = fmaf(ch0, dcv[0], fmaf(ch1, dcv[1], ch2 * dcv[2]));
         if (VAR) {
             // the grid's size is the splat's own: every weight to the per-cell pass
             rem.w00 = w00;
