@@ -17,12 +17,12 @@
 // and 12 texel values go through one 32-value warp reduce-scatter: at N = 2 the
 // four texels; at N = 4 the four grid corners or one grid border line when
 // every texel the warp's pixels weight lies there (where the weight of a
-// clamped u or v lands), else the border line holding most of them; at N >= 8
-// the four grid corners.  The other texel weights are reduced per grid cell
-// (one 16-value reduce-scatter per distinct cell of the warp) or, at N >= 8
-// when many cells are hit, added by each lane.  Every reduced value goes to
-// global memory with one atomic per (warp, splat) pair: nothing accumulates in
-// shared memory, which holds only the staged batch.  Measured on the 1M-splat,
+// clamped u or v lands); at N >= 8 the four grid corners.  The other texel
+// weights are added to global memory by each lane (N = 4 pairs that fit no
+// window; pairs of larger grids that weight more than one cell) or reduced for
+// the one grid cell they weight (a 16-value reduce-scatter).  Every reduced
+// value goes to global memory with one atomic per (warp, splat) pair: nothing
+// accumulates in shared memory, which holds only the staged batch.  Measured on the 1M-splat,
 // 16-view workload against per-batch shared accumulators flushed once per
 // tile: 40.5 -> 37.8 ms at N = 4 (batch 88 -> 184 in the same 48 KB), 54.0 ->
 // 41.0 ms at N = 8 (32 -> 64), 76.4 -> 54.1 ms at N = 16 (8 -> 16).
@@ -101,13 +101,17 @@ __device__ __forceinline__ float warp_reduce_scatter32(float v[32], int lane) {
 // (N-1,N-1).
 constexpr int kCornerSlot = kRecVals;
 static_assert(kCornerSlot + 12 <= 32, "record and corner-texel values share one 32-value reduce-scatter");
-// For N >= 8, above this many distinct edge/interior cells in a (warp, splat)
-// pair the lanes add their texel weights to shared memory directly instead of
-// one reduce-scatter per cell (measured: faster at N = 8, slower at N <= 4;
-// on the 16-view workload the N = 8 / 16 backward took 53.1 / 76.8 ms with
-// 2, 54.1 / 77.0 with 1, 54.7 / 77.2 with 0, 53.4 / 77.6 with 4 and 57.9 /
-// 82.6 with 8).
-constexpr int kGroupCells8 = 2;
+// For N >= 8 (and per-splat grid sizes), above this many distinct edge or
+// interior cells in a (warp, splat) pair the lanes add their texel weights to
+// global memory themselves instead of one 16-value reduce-scatter per cell;
+// N = 4 pairs that fit no corner or line window always do.  Measured on the
+// 16-view workload: N = 8 / 16 backward 39.8 / 52.6 ms at 0, 38.6 / 52.1 at 1,
+// 40.3 / 53.4 at 2; at N = 4 adding directly the lanes of the pairs without a
+// window took 33.5 ms against 37.0 with the border line holding most of their
+// pixels reduced through the window and a per-cell pass for the rest, and
+// adding every texel weight directly (no window at all) 48.6 ms: the lanes of
+// a window pair mostly weight the same few texels, whose atomics serialize.
+constexpr int kDirectCells = 1;
 
 // State of one pixel in the reverse walk.
 struct Pix {
@@ -121,9 +125,9 @@ struct Pix {
 };
 
 // Texel weights of one pixel that the corner slots do not take (N = 4: the
-// four of its cell, routed through a border-line window of the reduce-scatter
-// or the per-cell pass; N >= 8: those off the grid corners), with the colour
-// adjoint they multiply and the cell they belong to.
+// four of its cell, routed through a corner or border-line window of the
+// reduce-scatter or added directly; N >= 8: those off the grid corners), with
+// the colour adjoint they multiply and the cell they belong to.
 struct Rem {
     float w00, w10, w01, w11, c0, c1, c2;
     int base;
@@ -145,7 +149,7 @@ __device__ __forceinline__ void put(float &slot, float v) {
 // lo: the splat's RecordLo when its record is flagged for the extended-
 // precision plane hit (the same splat for the whole warp), else null.
 // VAR: the splat's grid is nk x nk (per-splat grid size; kN = (nk - 1) / (2
-// sigma)) and every texel weight goes to the per-cell pass.
+// sigma)) and every texel weight goes to the cell or direct texel pass.
 template <int N, typename TexT, bool ACC, bool VAR = false>
 __device__ __forceinline__ bool pair_adjoint(Pix &px, uint32_t idx, const float4 *rec, const RecordLo *lo,
                                              const staged_t<TexT> *tex, float sigma, float kN, int nk, float g[32],
@@ -218,7 +222,7 @@ __device__ __forceinline__ bool pair_adjoint(Pix &px, uint32_t idx, const float4
         const float fuh = fmaf(ch0, dcu[0], fmaf(ch1, dcu[1], ch2 * dcu[2]));
         const float fvh = fmaf(ch0, dcv[0], fmaf(ch1, dcv[1], ch2 * dcv[2]));
         if (VAR) {
-            // the grid's size is the splat's own: every weight to the per-cell pass
+            // the grid's size is the splat's own: every weight to the texel pass
             rem.w00 = w00;
             rem.w10 = w10;
             rem.w01 = w01;
@@ -239,7 +243,7 @@ __device__ __forceinline__ bool pair_adjoint(Pix &px, uint32_t idx, const float4
             rem.w11 = w11;
         } else {
             // weights landing on a grid-corner texel go to the warp-reduced
-            // corner slots; the rest (edge and interior texels) to the per-cell pass
+            // corner slots; the rest (edge and interior texels) to the texel pass
             const int iu = cell.base / N, iv = cell.base - iu * N;
             const float wc0 = (iu == 0 && iv == 0) ? w00 : 0.0f;
             const float wc1 = (iu == 0 && iv == N - 2) ? w01 : 0.0f;
@@ -313,11 +317,10 @@ __device__ __forceinline__ bool pair_adjoint(Pix &px, uint32_t idx, const float4
 // weights two neighbours along it), the weights move to slots kCornerSlot ..
 // kCornerSlot + 11 of the 32-value reduce-scatter (window position q, channel
 // c: slot kCornerSlot + 3q + c) and the window kind is returned: 0..3 the
-// lines (texel grid4_texel(kind, q)), 4 the corners.  Otherwise 5, and the
-// border line holding most of the warp's pixels takes the window (line_window)
-// and the per-cell pass the rest.  Measured on a sample of camera 0 of the
-// 1M-splat workload, 77 % of the (warp, splat) pairs fit a corner or line
-// window.
+// lines (texel grid4_texel(kind, q)), 4 the corners.  Otherwise 5: the lanes
+// add their texel weights to global memory themselves.  Measured on a sample
+// of camera 0 of the 1M-splat workload, 77 % of the (warp, splat) pairs fit a
+// corner or line window.
 constexpr unsigned kGrid4Corners = 0x9009u;                          // texels 0, 3, 12, 15
 // border lines i_u = 0, i_u = 3, i_v = 0, i_v = 3
 constexpr unsigned kGrid4Line0 = 0x000fu, kGrid4Line1 = 0xf000u, kGrid4Line2 = 0x1111u, kGrid4Line3 = 0x8888u;
@@ -379,75 +382,6 @@ __device__ __forceinline__ int grid4_window(const Rem rem[P], float g[32]) {
         g[kCornerSlot + 11] = fmaf(w3, r.c2, g[kCornerSlot + 11]);
     }
     return kind;
-}
-
-// Grids of N = 4: texel weights on one border line of the grid go through
-// slots kCornerSlot .. kCornerSlot + 11 of the 32-value reduce-scatter.  The weights of a pixel whose
-// u (v) is clamped to the grid's border lie on the first or last column
-// i_u = 0, N-1 (row i_v = 0, N-1): two texels at cell indices (i, i+1) along
-// it.  The line holding most of the warp's pixels is taken, with a window of
-// four texels from the smallest cell index among them (the whole line at
-// N = 4); the weights of the pixels inside the window move to the slots
-// (window position q, channel c: slot 14 + 3q + c) and leave the per-cell
-// pass.  Returns the texel index of window position 0 and the step between
-// positions (0, 0: no line).  Measured on the 1M-splat, 16-view workload: the
-// backward 44.8 -> 41.3 ms at N = 4; at N = 8 and 16, where four texels cover
-// part of a line, slower than corner slots (55.8 against 54.2 ms, 85.5
-// against 79.6 ms), so larger grids keep those.
-template <int N, int P>
-__device__ __forceinline__ void line_window(Rem rem[P], float g[32], int &t0, int &step) {
-    constexpr int LOG2N = N == 4 ? 2 : N == 8 ? 3 : 4;
-    bool on[P][4];
-    int cnt[4] = {0, 0, 0, 0};
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-        const Rem &r = rem[p];
-        const bool has = r.any();
-        const int iu = r.base >> LOG2N, iv = r.base & (N - 1);
-        on[p][0] = has && iu == 0 && r.w10 == 0.0f && r.w11 == 0.0f;
-        on[p][1] = has && iu == N - 2 && r.w00 == 0.0f && r.w01 == 0.0f;
-        on[p][2] = has && iv == 0 && r.w01 == 0.0f && r.w11 == 0.0f;
-        on[p][3] = has && iv == N - 2 && r.w00 == 0.0f && r.w10 == 0.0f;
-#pragma unroll
-        for (int l = 0; l < 4; ++l) cnt[l] += __popc(__ballot_sync(0xffffffffu, on[p][l]));
-    }
-    int L = 0;
-#pragma unroll
-    for (int l = 1; l < 4; ++l)
-        if (cnt[l] > cnt[L]) L = l;
-    t0 = step = 0;
-    if (cnt[L] == 0) return;
-    // positions along the line: i_v on a column, i_u on a row
-    int pos[P];
-    bool mem[P];
-    int mn = N;
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-        mem[p] = L == 0 ? on[p][0] : L == 1 ? on[p][1] : L == 2 ? on[p][2] : on[p][3];
-        pos[p] = L < 2 ? (rem[p].base & (N - 1)) : (rem[p].base >> LOG2N);
-        if (mem[p]) mn = min(mn, pos[p]);
-    }
-    const int s = min(int(__reduce_min_sync(0xffffffffu, unsigned(mn))), N - 4);
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-        Rem &r = rem[p];
-        if (!(mem[p] && pos[p] <= s + 2)) continue;
-        // the two weights along the line, at window positions rel and rel + 1
-        const float wa = L == 0 ? r.w00 : L == 1 ? r.w10 : L == 2 ? r.w00 : r.w01;
-        const float wb = L == 0 ? r.w01 : L == 1 ? r.w11 : L == 2 ? r.w10 : r.w11;
-        const int rel = pos[p] - s;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float w = q == rel ? wa : (q == rel + 1 ? wb : 0.0f);
-            g[kCornerSlot + 3 * q + 0] = fmaf(w, r.c0, g[kCornerSlot + 3 * q + 0]);
-            g[kCornerSlot + 3 * q + 1] = fmaf(w, r.c1, g[kCornerSlot + 3 * q + 1]);
-            g[kCornerSlot + 3 * q + 2] = fmaf(w, r.c2, g[kCornerSlot + 3 * q + 2]);
-        }
-        r.w00 = r.w10 = r.w01 = r.w11 = 0.0f;
-    }
-    // texel (i_u, i_v) of window position 0, and the index step along the line
-    t0 = L == 0 ? s : L == 1 ? (N - 1) * N + s : L == 2 ? s * N : s * N + N - 1;
-    step = L < 2 ? 1 : N;
 }
 
 template <int TS, int N, typename TexT, int P, bool VAR>
@@ -548,11 +482,7 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
                 act |= pair_adjoint<N, TexT, true, VAR>(pix[p], uint32_t(bs + i), s_rec + 4 * i, lo, s_tex + i * NN,
                                                         sigma, kNk, nk, g, rem[p], npairs, ncontrib);
             if (!__any_sync(0xffffffffu, act)) continue;
-            int kind = 0, t0 = 0, step = 0;
-            if (kGrid4) {
-                kind = grid4_window<P>(rem, g);
-                if (kind == 5) line_window<N, P>(rem, g, t0, step);
-            }
+            const int kind = kGrid4 ? grid4_window<P>(rem, g) : 0;
             const float tot = warp_reduce_scatter32(g, lane);
             // this splat's texel gradients, formed where used (fewer live registers)
             const bool want_tex = g_tex != nullptr;
@@ -562,19 +492,17 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
                     atomicAdd(b.rec_grad + (s_j[i] * uint32_t(kRecGrad) + uint32_t(lane)), tot);
                 } else if (want_tex) {
                     if (kGrid4) {
-                        if (lane < kCornerSlot + 12)
-                            atomicAdd(gt() + 3 * (kind == 5 ? t0 + my_q * step : grid4_texel(kind, my_q)) + my_c,
-                                      tot);
+                        if (lane < kCornerSlot + 12) atomicAdd(gt() + 3 * grid4_texel(kind, my_q) + my_c, tot);
                     } else if (my_corner >= 0) {
                         atomicAdd(gt() + my_corner_off, tot);
                     }
                 }
             }
             if (N > 4 || VAR || (kGrid4 && kind == 5)) {
-                // edge / interior texels: lanes sharing a cell touch the same four
-                // texels; each distinct cell is one reduce-scatter and one
-                // conflict-free atomic (a lane's P pixels join the same group
-                // when they share its cell)
+                // edge / interior texels: added by each lane, or, when the lanes
+                // share one cell (the same four texels), one reduce-scatter and
+                // one atomic per value (a lane's P pixels join the same group when
+                // they share its cell)
                 bool has[P];
                 unsigned pend[P];
                 unsigned any_pend = 0u;
@@ -586,14 +514,14 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
                 }
                 if (!want_tex) any_pend = 0u;
                 int cells = 0;
-                if (N >= 8 && any_pend) {
+                if (any_pend && !kGrid4) {
 #pragma unroll
                     for (int p = 0; p < P; ++p) {
                         const unsigned same = __match_any_sync(0xffffffffu, has[p] ? rem[p].base : -1);
                         cells += __popc(__ballot_sync(0xffffffffu, has[p] && (__ffs(same) - 1) == lane));
                     }
                 }
-                if (cells > kGroupCells8) {
+                if (any_pend && (kGrid4 || cells > kDirectCells)) {
                     float *st = gt();
 #pragma unroll
                     for (int p = 0; p < P; ++p) {

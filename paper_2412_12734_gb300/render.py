@@ -299,7 +299,7 @@ class Rasterizer:
         res = {"tile": best.tile_size, "batch": best.batch_depth, "ppt": best.pixels_per_thread,
                "batch_fwd": best.batch_depth_fwd, "bwd_kernel": best.bwd_kernel,
                "candidates": [{"tile": tiles[i], "batch": batches[i], "ppt": ppts[i], "ms": ms[i]}
-                              for i in range(min(n.value, 64))]}
+                              for i in range(min(n.value, 128))]}
         table[key] = res
         try:
             os.makedirs(os.path.dirname(path), exist_ok=True)
