@@ -200,7 +200,9 @@ typedef struct {
     int64_t pairs_fwd;   /* (pixel, splat) pairs evaluated by the last forward     */
     int64_t pairs_bwd;   /* (pixel, splat) pairs evaluated by the last backward    */
     int64_t blended_fwd;      /* pairs blended by the last forward            */
-    int64_t contributing_bwd; /* pairs with alpha >= 1/255 in the last backward */
+    int64_t contributing_bwd; /* pairs whose adjoints the last backward computed:
+                                 the blended pairs of its forward (0 before a
+                                 backward)                                    */
 } gb_stats;
 
 /* Phases timed under GB_FLAG_TIMING, in the order gb_saved_phase_times

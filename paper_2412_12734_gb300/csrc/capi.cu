@@ -524,7 +524,8 @@ gb_status gb_saved_stats(gb_saved *s, gb_stats *out) {
     out->pairs_fwd = int64_t(s->cnt_host->pairs_fwd);
     out->pairs_bwd = int64_t(s->cnt_host->pairs_bwd);
     out->blended_fwd = int64_t(s->cnt_host->blend_fwd);
-    out->contributing_bwd = int64_t(s->cnt_host->contrib_bwd);
+    // the backward computes the adjoints of exactly the pairs its forward blended
+    out->contributing_bwd = s->cnt_host->pairs_bwd ? int64_t(s->cnt_host->blend_fwd) : 0;
     return GB_OK;
 }
 
@@ -875,7 +876,6 @@ gb_status gb_render_backward(gb_context *ctx, gb_saved *s, const float *d_rgb, c
     b.d_alpha = d_alpha;
     b.rec_grad = s->rec_grad;
     GB_CUDA(ctx, cudaMemsetAsync(&s->cnt->pairs_bwd, 0, sizeof(unsigned long long), st));
-    GB_CUDA(ctx, cudaMemsetAsync(&s->cnt->contrib_bwd, 0, sizeof(unsigned long long), st));
     const bool persistent = (s->flags & GB_FLAG_PERSISTENT) != 0;
     // the backward's tile counters start from zero at every call (a forward
     // may be followed by several backwards)

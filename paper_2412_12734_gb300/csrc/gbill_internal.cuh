@@ -155,7 +155,6 @@ struct Counters {
     unsigned long long pairs_fwd;    // (pixel, splat) pairs evaluated by render fwd
     unsigned long long pairs_bwd;    // ... and by render bwd
     unsigned long long blend_fwd;    // pairs blended by render fwd
-    unsigned long long contrib_bwd;  // pairs with alpha >= 1/255 in render bwd
 };
 
 // Host-side count of kernels launched by the library (see gb_kernel_launches).

@@ -153,14 +153,13 @@ __device__ __forceinline__ void put(float &slot, float v) {
 template <int N, typename TexT, bool ACC, bool VAR = false>
 __device__ __forceinline__ bool pair_adjoint(Pix &px, uint32_t idx, const float4 *rec, const RecordLo *lo,
                                              const staged_t<TexT> *tex, float sigma, float kN, int nk, float g[32],
-                                             Rem &rem, uint32_t &npairs, uint32_t &ncontrib) {
+                                             Rem &rem) {
     rem.w00 = rem.w10 = rem.w01 = rem.w11 = 0.0f;
     rem.c0 = rem.c1 = rem.c2 = 0.0f;
     rem.base = 0;
     // every lane evaluates (lanes past their last splat too, result dropped) so
     // that the only divergent region is the adjoint of the contributing lanes
     const bool live = px.inside && idx < px.last;
-    npairs += live ? 1u : 0u;
     const float4 q0 = rec[0], q1 = rec[1], q2 = rec[2], q3 = rec[3];
     const Hit h = lo ? plane_hit_ext(px.xf, px.yf, q0, q1, q2, *lo) : plane_hit(px.xf, px.yf, q0, q1, q2);
     const float dx = h.dx, dy = h.dy, zz = h.zz;
@@ -176,7 +175,6 @@ __device__ __forceinline__ bool pair_adjoint(Pix &px, uint32_t idx, const float4
     const bool clamped = ar > kAlphaMax;
     const float alpha = clamped ? kAlphaMax : ar;
     if (!(live && zz != 0.0f && alpha >= kAlphaMin)) return false;
-    ++ncontrib;
     const float iom = fast_rcp(1.0f - alpha);
     const float Ti = px.T * iom;
     const Cell<N> cell = VAR ? grid_cell_n<N>(u, v, sigma, kN, nk) : grid_cell<N>(u, v, sigma, kN);
@@ -414,7 +412,13 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
     const float kN = float(N - 1) / (2.0f * sigma);
 
     Pix pix[P];
-    uint32_t mylast = 0, npairs = 0, ncontrib = 0;
+    uint32_t mylast = 0;
+    // evaluated (live) pairs of this warp, counted once per batch into shared
+    // memory: per-pair counters held registers through the event loop
+    // (measured: 1.1 ms of 32.3 on the 16-view workload at N = 4, through the
+    // register cap; a ballot per pair instead cost 0.5 ms more)
+    __shared__ uint32_t s_np[NT / 32];
+    if (lane == 0) s_np[warp] = 0;
     if (threadIdx.x == 0) s_maxlast = 0;
     __syncthreads();
 #pragma unroll
@@ -466,6 +470,20 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
         // splats at or beyond the warp's last contributor are skipped warp-wide;
         // below it at least one lane of the warp is active
         const int i_hi = min(nb, int(wlast) - bs);
+        {
+            // per pixel, the splats of its warp block below its last contributor
+            uint32_t cnt = 0;
+            for (int c = 0; c < i_hi; c += 32) {
+                const unsigned word = __ballot_sync(0xffffffffu, c + lane < i_hi && (s_mask[c + lane] & wbit));
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    const int k = pix[p].inside ? min(int(pix[p].last) - bs, i_hi) - c : 0;
+                    cnt += __popc(k >= 32 ? word : (k <= 0 ? 0u : word & ((1u << k) - 1u)));
+                }
+            }
+            cnt = __reduce_add_sync(0xffffffffu, cnt);
+            if (lane == 0) s_np[warp] += cnt;
+        }
         for (int i = i_hi - 1; i >= 0; --i) {
             if (!(s_mask[i] & wbit)) continue;
             float g[32];
@@ -476,11 +494,11 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
             const int nk = VAR ? s_n[i] : N;
             const float kNk = VAR ? float(nk - 1) / (2.0f * sigma) : kN;
             bool act = pair_adjoint<N, TexT, false, VAR>(pix[0], uint32_t(bs + i), s_rec + 4 * i, lo, s_tex + i * NN,
-                                                         sigma, kNk, nk, g, rem[0], npairs, ncontrib);
+                                                         sigma, kNk, nk, g, rem[0]);
 #pragma unroll
             for (int p = 1; p < P; ++p)
                 act |= pair_adjoint<N, TexT, true, VAR>(pix[p], uint32_t(bs + i), s_rec + 4 * i, lo, s_tex + i * NN,
-                                                        sigma, kNk, nk, g, rem[p], npairs, ncontrib);
+                                                        sigma, kNk, nk, g, rem[p]);
             if (!__any_sync(0xffffffffu, act)) continue;
             const int kind = kGrid4 ? grid4_window<P>(rem, g) : 0;
             const float tot = warp_reduce_scatter32(g, lane);
@@ -589,13 +607,7 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
         }
         __syncthreads();  // the next batch's staging overwrites this one
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
-        ncontrib += __shfl_xor_sync(0xffffffffu, ncontrib, o);
-    }
-    if (lane == 0 && npairs) atomicAdd(&b.fw.cnt->pairs_bwd, (unsigned long long)npairs);
-    if (lane == 0 && ncontrib) atomicAdd(&b.fw.cnt->contrib_bwd, (unsigned long long)ncontrib);
+    if (lane == 0 && s_np[warp]) atomicAdd(&b.fw.cnt->pairs_bwd, (unsigned long long)s_np[warp]);
 }
 
 // Resident blocks per SM the register budget is set for: one pixel per thread

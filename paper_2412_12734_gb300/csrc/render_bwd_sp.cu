@@ -120,7 +120,7 @@ __device__ __forceinline__ void sp_tile(const Frame &f, const RenderBwdBufs &b, 
     __syncthreads();
     const int max_last = int(s_maxlast);
     float *g_tex = sc.g_tex;
-    uint32_t npairs = 0, ncontrib = 0;
+    uint32_t npairs = 0;
 
     for (int be = max_last; be > 0; be -= batch) {
         const int bs = max(0, be - batch), nb = be - bs;
@@ -237,7 +237,6 @@ __device__ __forceinline__ void sp_tile(const Frame &f, const RenderBwdBufs &b, 
                     pSD += a3;
                 }
                 if (!live) continue;
-                ++ncontrib;
                 // adjoints of the pair (as in the pixel-parallel kernel)
                 const float ch0 = w * dC0, ch1 = w * dC1, ch2 = w * dC2;
                 acc[kGRgb + 0] += ch0;
@@ -330,10 +329,8 @@ __device__ __forceinline__ void sp_tile(const Frame &f, const RenderBwdBufs &b, 
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         npairs += __shfl_xor_sync(FULL, npairs, o);
-        ncontrib += __shfl_xor_sync(FULL, ncontrib, o);
     }
     if (lane == 0 && npairs) atomicAdd(&b.fw.cnt->pairs_bwd, (unsigned long long)npairs);
-    if (lane == 0 && ncontrib) atomicAdd(&b.fw.cnt->contrib_bwd, (unsigned long long)ncontrib);
 }
 
 // Registers: two resident blocks of 256 threads per SM (up to 128 a thread).
