@@ -419,6 +419,11 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
     // register cap; a ballot per pair instead cost 0.5 ms more)
     __shared__ uint32_t s_np[NT / 32];
     if (lane == 0) s_np[warp] = 0;
+    // per warp and batch, the bits of the staged splats whose footprint may
+    // touch its block (32 splats a word; a batch holds at most NT splats): the
+    // walk visits only those (measured against testing every staged splat's
+    // mask: 31.2 -> 30.1 ms at N = 4, 38.6 -> 35.5 ms at N = 8)
+    __shared__ uint32_t s_wm[NT / 32][NT / 32];
     if (threadIdx.x == 0) s_maxlast = 0;
     __syncthreads();
 #pragma unroll
@@ -475,6 +480,7 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
             uint32_t cnt = 0;
             for (int c = 0; c < i_hi; c += 32) {
                 const unsigned word = __ballot_sync(0xffffffffu, c + lane < i_hi && (s_mask[c + lane] & wbit));
+                if (lane == 0) s_wm[warp][c >> 5] = word;
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
                     const int k = pix[p].inside ? min(int(pix[p].last) - bs, i_hi) - c : 0;
@@ -484,8 +490,12 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
             cnt = __reduce_add_sync(0xffffffffu, cnt);
             if (lane == 0) s_np[warp] += cnt;
         }
-        for (int i = i_hi - 1; i >= 0; --i) {
-            if (!(s_mask[i] & wbit)) continue;
+        __syncwarp();
+        // back to front over the set bits
+        for (int c = (i_hi - 1) >> 5; c >= 0; --c)
+            for (unsigned wd = s_wm[warp][c]; wd;) {
+            const int i = 32 * c + 31 - __clz(wd);
+            wd &= ~(1u << (i & 31));
             float g[32];
 #pragma unroll
             for (int q = 0; q < 32; ++q) g[q] = 0.0f;
