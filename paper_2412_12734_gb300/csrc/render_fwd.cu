@@ -121,9 +121,21 @@ __device__ __forceinline__ void fwd_tile(const Frame &f, const RenderBufs &b, in
         stage_batch<N, NT, TexT, TS, 4 * P, WIDE, VAR>(b, cam, sc, range.x + bs, nb, tx * TS, ty * TS, s_rec, s_tex,
                                                       s_k, s_j, s_box, s_mask, s_fp, s_n);
         __syncthreads();
-        for (int i = 0; i < nb; ++i) {
-            if ((i & 15) == 0 && __all_sync(0xffffffffu, all_done())) break;
-            if (!(s_mask[i] & wbit)) continue;
+        // the staged splats whose footprint may touch this warp's block, front to
+        // back, 32 at a time from a ballot of their masks (measured against
+        // testing every staged splat: 11.1 -> 9.9 ms at N = 4, 26.0 -> 23.7 ms at
+        // N = 16 on the 16-view workload); the warp stops once all its pixels are
+        // done, checked every 16 splats it evaluates
+        bool stop = false;
+        for (int c = 0; c < nb && !stop; c += 32) {
+            unsigned wd = __ballot_sync(0xffffffffu, c + lane < nb && (s_mask[c + lane] & wbit));
+            for (int ev = 0; wd; ++ev) {
+            if ((ev & 15) == 0 && __all_sync(0xffffffffu, all_done())) {
+                stop = true;
+                break;
+            }
+            const int i = c + __ffs(wd) - 1;
+            wd &= wd - 1u;
             const float4 q0 = s_rec[4 * i + 0], q1 = s_rec[4 * i + 1], q2 = s_rec[4 * i + 2],
                          q3 = s_rec[4 * i + 3];
             const int nk = VAR ? s_n[i] : N;
@@ -140,6 +152,7 @@ __device__ __forceinline__ void fwd_tile(const Frame &f, const RenderBufs &b, in
                 for (int p = 0; p < P; ++p)
                     fwd_pair<N, TexT, WIDE, VAR>(pix[p], plane_hit(pix[p].xf, pix[p].yf, q0, q1, q2), q1, q3,
                                                  s_tex + i * NN, uint32_t(bs + i + 1), sigma, kNk, nk, npairs, nblend);
+            }
             }
         }
     }
