@@ -105,6 +105,20 @@ __device__ __forceinline__ bool block_hits(const float4 &q2, uint2 box, const fl
     return m <= 0.0f;
 }
 
+// A staged texel as FP32 RGB (exact for FP16 / BF16 storage).
+template <typename T>
+__device__ __forceinline__ float4 texel_rgb(const float4 &t, T) {
+    return t;
+}
+__device__ __forceinline__ float4 texel_rgb(const uint2 &t, __half) {
+    const float2 rg = __half22float2(*reinterpret_cast<const __half2 *>(&t.x));
+    return make_float4(rg.x, rg.y, __low2float(*reinterpret_cast<const __half2 *>(&t.y)), 0.0f);
+}
+__device__ __forceinline__ float4 texel_rgb(const uint2 &t, __nv_bfloat16) {
+    const float2 rg = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t.x));
+    return make_float4(rg.x, rg.y, __low2float(*reinterpret_cast<const __nv_bfloat162 *>(&t.y)), 0.0f);
+}
+
 // Loads the records and colour grids of instances [first, first + nb) of a
 // tile range into shared memory, and for every splat the mask of the tile's
 // 8 x BH warp blocks (row-major, TS/8 per row) that its footprint may touch
@@ -151,6 +165,32 @@ __device__ __forceinline__ void stage_batch(const RenderBufs &b, const CamDev &c
         if (e < nb * NB && w == 0) s_mask[s] = (bal >> ((t & 31) & ~(NB - 1))) & kAll;
     }
     const TexT *tex = static_cast<const TexT *>(sc.tex);
+    if constexpr (sizeof(TexT) == 2 && NN % 4 == 0) {
+        if ((reinterpret_cast<uintptr_t>(tex) & 7u) == 0) {
+            // four texels (12 16-bit values, 24 bytes, 8-byte aligned) per step:
+            // three 64-bit loads unpacked in registers
+            constexpr int NQ = NN / 4;
+            const uint2 *raw8 = reinterpret_cast<const uint2 *>(tex);
+            for (int e = t; e < nb * NQ; e += NT) {
+                const int s = e / NQ, o = e - s * NQ;
+                const int64_t g = (int64_t(s_k[s]) * NQ + o) * 3;
+                const uint2 a = raw8[g], b2 = raw8[g + 1], c = raw8[g + 2];
+                // texel q holds values 3q, 3q + 1, 3q + 2 of h0..h11 = (a.x, a.y, b2.x, b2.y, c.x, c.y)
+                const uint2 tx[4] = {make_uint2(a.x, a.y & 0xffffu), make_uint2((a.y >> 16) | (b2.x << 16), b2.x >> 16),
+                                     make_uint2(b2.y, c.x & 0xffffu), make_uint2((c.x >> 16) | (c.y << 16), c.y >> 16)};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if constexpr (sizeof(staged_t<TexT, WIDE>) == 16) {
+                        const float4 f = texel_rgb(tx[q], TexT());
+                        s_tex[4 * e + q] = make_float4(f.x, f.y, f.z, 0.0f);
+                    } else {
+                        s_tex[4 * e + q] = tx[q];
+                    }
+                }
+            }
+            return;
+        }
+    }
     for (int e = t; e < nb * NN; e += NT) {
         const int s = e / NN, o = e - s * NN;
         const int64_t g = (int64_t(s_k[s]) * NN + o) * 3;
@@ -209,20 +249,6 @@ __device__ __forceinline__ Cell<N> grid_cell_n(float u, float v, float sigma, fl
 struct Quad {
     float4 c00, c10, c01, c11;
 };
-
-// A staged texel as FP32 RGB (exact for FP16 / BF16 storage).
-template <typename T>
-__device__ __forceinline__ float4 texel_rgb(const float4 &t, T) {
-    return t;
-}
-__device__ __forceinline__ float4 texel_rgb(const uint2 &t, __half) {
-    const float2 rg = __half22float2(*reinterpret_cast<const __half2 *>(&t.x));
-    return make_float4(rg.x, rg.y, __low2float(*reinterpret_cast<const __half2 *>(&t.y)), 0.0f);
-}
-__device__ __forceinline__ float4 texel_rgb(const uint2 &t, __nv_bfloat16) {
-    const float2 rg = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t.x));
-    return make_float4(rg.x, rg.y, __low2float(*reinterpret_cast<const __nv_bfloat162 *>(&t.y)), 0.0f);
-}
 
 template <int N, typename TexT, bool WIDE = false>
 __device__ __forceinline__ Quad grid_quad(const staged_t<TexT, WIDE> *g, const Cell<N> &c) {
