@@ -191,6 +191,23 @@ __device__ __forceinline__ void stage_batch(const RenderBufs &b, const CamDev &c
             return;
         }
     }
+    if constexpr (sizeof(TexT) == 4 && NN % 4 == 0) {
+        if ((reinterpret_cast<uintptr_t>(tex) & 15u) == 0) {
+            // four FP32 texels (48 bytes, 16-byte aligned) per step: three 128-bit loads
+            constexpr int NQ = NN / 4;
+            const float4 *raw16 = reinterpret_cast<const float4 *>(tex);
+            for (int e = t; e < nb * NQ; e += NT) {
+                const int s = e / NQ, o = e - s * NQ;
+                const int64_t g = (int64_t(s_k[s]) * NQ + o) * 3;
+                const float4 a = raw16[g], b2 = raw16[g + 1], c = raw16[g + 2];
+                s_tex[4 * e + 0] = make_float4(a.x, a.y, a.z, 0.0f);
+                s_tex[4 * e + 1] = make_float4(a.w, b2.x, b2.y, 0.0f);
+                s_tex[4 * e + 2] = make_float4(b2.z, b2.w, c.x, 0.0f);
+                s_tex[4 * e + 3] = make_float4(c.y, c.z, c.w, 0.0f);
+            }
+            return;
+        }
+    }
     for (int e = t; e < nb * NN; e += NT) {
         const int s = e / NN, o = e - s * NN;
         const int64_t g = (int64_t(s_k[s]) * NN + o) * 3;
