@@ -443,9 +443,9 @@ gb_status gb_mse_loss(gb_context *ctx, const float *rgb, const float *target, in
 /* ---------------------------------------------------------------- tuning -- */
 
 /* Autotuner: times forward + backward of this frame for every candidate
- * (tile_size 8, 16 and 32; batch_depth 8, 16, 24, 32, 48, 64, 88, 128, 176,
+ * (tile_size 8, 16 and 32; batch_depth 8, 16, 24, 32, 48, 64, 88, 128, 184,
  * 256 where it fits the tile and the shared-memory budget; pixels_per_thread
- * 1 and 2; the forward at the same depth; the splat-parallel backward where it
+ * 1 and 2; the forward at its automatic depth; the splat-parallel backward where it
  * applies, listed with pixels_per_thread 3), then, at the fastest of those,
  * times the forward alone at every
  * batch_depth_fwd candidate (listed with pixels_per_thread 0 and the forward's

@@ -1182,7 +1182,7 @@ gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int3
         float best_ms = INFINITY;
         int n = 0;
         const int tile_c[3] = {16, 8, 32};
-        const int batch_c[10] = {8, 16, 24, 32, 48, 64, 88, 128, 176, 256};
+        const int batch_c[10] = {8, 16, 24, 32, 48, 64, 88, 128, 184, 256};
         // one untimed run of the candidate (sizes `saved`), then `reps` timed
         // no-sync runs; *t = mean milliseconds
         auto time_candidate = [&](gb_options &c, bool with_bwd, float *t) -> gb_status {
@@ -1216,8 +1216,10 @@ gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int3
             }
             ++n;
         };
-        // forward + backward over tile, batch depth (both passes) and pixels per
-        // thread of the pixel-parallel backward, then the splat-parallel one
+        // forward + backward over tile, the backward's batch depth and pixels per
+        // thread of the pixel-parallel backward (the forward at its automatic
+        // depth, so that the backward's depth is not judged by the forward's
+        // time at the same depth), then the splat-parallel one
         o.bwd_kernel = 1;
         for (int pi = 1; pi <= 2 && st == GB_OK; ++pi)
         for (int ti = 0; ti < 3 && st == GB_OK; ++ti)
@@ -1225,9 +1227,10 @@ gb_status gb_autotune(gb_context *ctx, gb_saved *s, const gb_scene *scenes, int3
                 const int T = tile_c[ti], B = batch_c[bi];
                 if (B > T * T / pi) continue;
                 if (frame_has_var(f) && (T != 16 || pi != 1)) continue;
-                if (frame_smem(f, B, false) > 160 * 1024 || frame_smem(f, B, true) > 160 * 1024) continue;
+                if (frame_smem(f, B, true) > 160 * 1024) continue;
                 o.tile_size = T;
                 o.batch_depth = B;
+                o.batch_depth_fwd = std::min(default_batch(f, false), T * T);
                 o.pixels_per_thread = pi;
                 float t = 0.0f;
                 if ((st = time_candidate(o, true, &t)) != GB_OK) break;
