@@ -165,6 +165,51 @@ __device__ __forceinline__ float load_sh(const SceneDev &s, int64_t i) {
     }
 }
 
+// Calls fn(i, c) for the 48 SH coefficients c (index i = 3 m + channel) of
+// splat k of a degree-3 scene, read with 128-bit loads: six for 16-bit
+// storage, twelve for FP32.  Needs the array 16-byte aligned (sh_vec48).
+// Scalar loads of a thread's coefficients, 96 or 192 bytes apart from its
+// neighbours', touch 32 sectors per load instruction; the vector loads cut
+// the L1 wavefronts of a warp's coefficient reads eightfold.
+template <typename F>
+__device__ __forceinline__ void for_each_sh48(const SceneDev &s, int64_t k, F &&fn) {
+    if (s.sh_dtype == GB_F32) {
+        const float4 *src = reinterpret_cast<const float4 *>(static_cast<const float *>(s.sh) + k * 48);
+#pragma unroll
+        for (int v = 0; v < 12; ++v) {
+            const float4 w = src[v];
+            fn(4 * v + 0, w.x); fn(4 * v + 1, w.y); fn(4 * v + 2, w.z); fn(4 * v + 3, w.w);
+        }
+    } else {
+        const uint4 *src = reinterpret_cast<const uint4 *>(static_cast<const unsigned short *>(s.sh) + k * 48);
+        const bool bf = s.sh_dtype == GB_BF16;
+#pragma unroll
+        for (int v = 0; v < 6; ++v) {
+            const uint4 w = src[v];
+            const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                float lo, hi;
+                if (bf) {
+                    lo = __uint_as_float(u[h] << 16);
+                    hi = __uint_as_float(u[h] & 0xffff0000u);
+                } else {
+                    const float2 t = __half22float2(*reinterpret_cast<const __half2 *>(&u[h]));
+                    lo = t.x;
+                    hi = t.y;
+                }
+                fn(8 * v + 2 * h, lo);
+                fn(8 * v + 2 * h + 1, hi);
+            }
+        }
+    }
+}
+
+// Whether for_each_sh48 serves the scene: degree 3 and a 16-byte aligned array.
+__device__ __forceinline__ bool sh_vec48(const SceneDev &s) {
+    return s.D == 3 && (reinterpret_cast<uintptr_t>(s.sh) & 15u) == 0;
+}
+
 // ------------------------------------------------------ rotation and frame --
 struct Frame3 {
     float tu[3], tv[3];
@@ -291,11 +336,15 @@ __global__ void __launch_bounds__(256, 4) preprocess_kernel(Frame f, uint32_t *d
             dx *= dn; dy *= dn; dz *= dn;
             float Y[16];
             sh_basis(3, dx, dy, dz, Y);
+            if (sh_vec48(sc)) {
+                for_each_sh48(sc, k, [&](int i, float c) { rgb[i % 3] = fmaf(Y[i / 3], c, rgb[i % 3]); });
+            } else {
 #pragma unroll
-            for (int m = 0; m < 16; ++m)
-                if (m < M)
+                for (int m = 0; m < 16; ++m)
+                    if (m < M)
 #pragma unroll
-                    for (int ch = 0; ch < 3; ++ch) rgb[ch] += Y[m] * load_sh(sc, (k * M + m) * 3 + ch);
+                        for (int ch = 0; ch < 3; ++ch) rgb[ch] += Y[m] * load_sh(sc, (k * M + m) * 3 + ch);
+            }
             if (!(isfinite(rgb[0]) && isfinite(rgb[1]) && isfinite(rgb[2]))) {
                 atomicOr(&cnt->error_flags, 2u);
                 valid = false;
@@ -513,13 +562,20 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(Frame f, int si, co
 #pragma unroll
         for (int m = 0; m < M; ++m)
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                g_sh[m][ch] += Y[m] * grgb[ch];
-                const float kc = load_sh(sc, (k * M + m) * 3 + ch) * grgb[ch];
-                gd[0] += kc * Gs[m][0];
-                gd[1] += kc * Gs[m][1];
-                gd[2] += kc * Gs[m][2];
-            }
+            for (int ch = 0; ch < 3; ++ch) g_sh[m][ch] += Y[m] * grgb[ch];
+        auto sh_dir = [&](int i, float c) {
+            const int m = i / 3, ch = i - 3 * m;
+            const float kc = c * grgb[ch];
+            gd[0] += kc * Gs[m][0];
+            gd[1] += kc * Gs[m][1];
+            gd[2] += kc * Gs[m][2];
+        };
+        if (D == 3 && sh_vec48(sc)) {
+            for_each_sh48(sc, k, sh_dir);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 3 * M; ++i) sh_dir(i, load_sh(sc, k * 3 * M + i));
+        }
         const float dd = gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2];
         for (int i = 0; i < 3; ++i) g_p[i] += (gd[i] - d[i] * dd) / dist;
     }
