@@ -604,11 +604,24 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(Frame f, int si, co
     }
     if (sc.g_scales) { sc.g_scales[2 * k] = g_su; sc.g_scales[2 * k + 1] = g_sv; }
     if (sc.g_opac) sc.g_opac[k] = g_o;
-    if (sc.g_sh)
+    if (sc.g_sh) {
+        if (D == 3 && (reinterpret_cast<uintptr_t>(sc.g_sh) & 15u) == 0) {
+            // 48 values, 192 bytes: twelve 128-bit stores (scalar stores 192 bytes
+            // apart from the neighbouring threads' touch 32 sectors each)
+            float4 *dst = reinterpret_cast<float4 *>(sc.g_sh + k * 48);
 #pragma unroll
-        for (int m = 0; m < M; ++m)
+            for (int v = 0; v < 12; ++v) {
+                const int i = 4 * v;
+                dst[v] = make_float4(g_sh[i / 3][i % 3], g_sh[(i + 1) / 3][(i + 1) % 3], g_sh[(i + 2) / 3][(i + 2) % 3],
+                                     g_sh[(i + 3) / 3][(i + 3) % 3]);
+            }
+        } else {
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) sc.g_sh[(k * M + m) * 3 + ch] = g_sh[m][ch];
+            for (int m = 0; m < M; ++m)
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) sc.g_sh[(k * M + m) * 3 + ch] = g_sh[m][ch];
+        }
+    }
 }
 
 }  // namespace
