@@ -59,12 +59,16 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep(
     const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *keys_out, uint32_t *vals_out,
     int64_t max_n, const uint32_t *n_dev, int shift, uint32_t mask, const uint32_t *offs) {
     constexpr int kRadix = 1 << BITS;
-    __shared__ uint32_t wcount[kSortWarps][kRadix];
-    __shared__ uint32_t goff[kRadix];
+    // per-warp digit counts, later the block's keys in local (digit, input) order
+    __shared__ uint32_t wcount[kSortWarps * kRadix > kSortTile ? kSortWarps * kRadix : kSortTile];
+    __shared__ uint32_t s_vals[kSortTile];
+    __shared__ uint32_t goff[kRadix];  // the block's first global position per digit
+    __shared__ uint32_t loc[kRadix];   // the block's first local position per digit
     const uint32_t n = load_n(n_dev, max_n);
     const int64_t blk_base = int64_t(blockIdx.x) * kSortTile;
     if (blk_base >= n) return;  // uniform per block
-    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&wcount[0][0])[i] = 0;
+    const int nblk = int(int64_t(n) - blk_base < int64_t(kSortTile) ? int64_t(n) - blk_base : int64_t(kSortTile));
+    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) wcount[i] = 0;
     for (int i = threadIdx.x; i < kRadix; i += kSortThreads) goff[i] = offs[int64_t(i) * gridDim.x + blockIdx.x];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -82,32 +86,79 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep(
             v_[r] = vals_in[idx];
             const uint32_t d = (k_[r] >> shift) & mask;
             const uint32_t peers = __match_any_sync(am, d);
-            const uint32_t before = wcount[warp][d];
+            const uint32_t before = wcount[warp * kRadix + d];
             rank_[r] = before + __popc(peers & lt);
             __syncwarp(am);
-            if ((peers & lt) == 0) wcount[warp][d] = before + __popc(peers);
+            if ((peers & lt) == 0) wcount[warp * kRadix + d] = before + __popc(peers);
         }
         __syncwarp();
     }
     __syncthreads();
-    // exclusive prefix over warps, per digit
+    // per digit: exclusive prefix over warps (the warp's first slot within the
+    // digit's run) and the digit's block total
     for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
-        uint32_t run = goff[d];
+        uint32_t run = 0;
         for (int w = 0; w < kSortWarps; ++w) {
-            const uint32_t c = wcount[w][d];
-            wcount[w][d] = run;
+            const uint32_t c = wcount[w * kRadix + d];
+            wcount[w * kRadix + d] = run;
             run += c;
+        }
+        loc[d] = run;
+    }
+    __syncthreads();
+    // exclusive prefix over digits of the block totals: each thread sums its
+    // kRadix / kSortThreads consecutive digits, then a warp scan and the warps'
+    // totals
+    {
+        constexpr int PER = kRadix / kSortThreads;
+        static_assert(PER >= 1 && PER * kSortThreads == kRadix, "digits per thread");
+        __shared__ uint32_t wsum[kSortWarps];
+        uint32_t c[PER], tsum = 0;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            c[i] = loc[threadIdx.x * PER + i];
+            tsum += c[i];
+        }
+        uint32_t x = tsum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        uint32_t excl = x - tsum;
+        for (int w = 0; w < warp; ++w) excl += wsum[w];
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            loc[threadIdx.x * PER + i] = excl;
+            excl += c[i];
         }
     }
     __syncthreads();
+    uint32_t lpos[kSortRounds];
 #pragma unroll
-    for (int r = 0; r < kSortRounds; ++r) {
+    for (int r = 0; r < kSortRounds; ++r)
         if (rank_[r] != 0xffffffffu) {
             const uint32_t d = (k_[r] >> shift) & mask;
-            const uint32_t pos = wcount[warp][d] + rank_[r];
-            keys_out[pos] = k_[r];
-            vals_out[pos] = v_[r];
+            lpos[r] = loc[d] + wcount[warp * kRadix + d] + rank_[r];
         }
+    __syncthreads();  // the counts are read; their array now takes the keys
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r)
+        if (rank_[r] != 0xffffffffu) {
+            wcount[lpos[r]] = k_[r];
+            s_vals[lpos[r]] = v_[r];
+        }
+    __syncthreads();
+    // in local order: consecutive threads write consecutive positions of a
+    // digit's run (coalesced)
+    for (int p = threadIdx.x; p < nblk; p += kSortThreads) {
+        const uint32_t k = wcount[p];
+        const uint32_t d = (k >> shift) & mask;
+        const uint32_t pos = goff[d] + uint32_t(p) - loc[d];
+        keys_out[pos] = k;
+        vals_out[pos] = s_vals[p];
     }
 }
 
