@@ -253,6 +253,28 @@ def test_grids_at_an_unaligned_address_render_the_same(tex_n, dtype):
         assert (ga[k] - gb[k]).abs().max().item() <= 1e-5 * max(scale, 1e-12), k
 
 
+@pytest.mark.parametrize("tex_n", [2, 4, 8, 16])
+def test_backward_without_a_texture_gradient_output(tex_n):
+    """The texture-gradient output may be left out (null): the backward skips
+    every texel atomic and gives the other gradients as with it, up to
+    atomic order."""
+    import torch
+
+    from paper_2412_12734_gb300 import render as R
+    sc = scenes.tiny_scene(33, K=30, tex_n=tex_n, spread=0.8, tex_dtype="f16")
+    cams = [scenes.tiny_camera(72, 56)]
+    rast = R.Rasterizer(0)
+    dev = R.scene_to_device(sc)
+    d = torch.randn((72 * 56, 3), device="cuda")
+    saved = rast.forward([dev], cams)[3]
+    full = rast.backward(saved, d)[0]
+    part = {k: torch.empty_like(v) for k, v in full.items() if k != "textures"}
+    rast.backward(saved, d, grads=[part])
+    for k, v in part.items():
+        scale = full[k].abs().max().item()
+        assert (v - full[k]).abs().max().item() <= 1e-5 * max(scale, 1e-12), k
+
+
 @pytest.mark.parametrize("flags", [0, 2])
 def test_second_backward_after_one_forward_gives_the_same_gradients(flags):
     """A forward may be followed by several backwards (other upstream
