@@ -11,8 +11,8 @@ namespace gbill {
 // bytes, alpha unused: one 128-bit shared load); otherwise FP16 and BF16 grids
 // in their storage type as RGB + pad (8 bytes: one 64-bit load, converted
 // exactly to FP32 at use).  The forward stages grids of N <= 4 wide (its
-// shared memory has room, and the lookups skip the conversion); the backward,
-// whose staging also holds gradient accumulators, stages them narrow.
+// shared memory has room, and the lookups skip the conversion); the backward
+// stages them narrow, for deeper batches in the same shared memory.
 template <typename TexT, bool WIDE = false>
 using staged_t = typename std::conditional<WIDE || sizeof(TexT) == 4, float4, uint2>::type;
 
