@@ -253,6 +253,36 @@ def test_grids_at_an_unaligned_address_render_the_same(tex_n, dtype):
         assert (ga[k] - gb[k]).abs().max().item() <= 1e-5 * max(scale, 1e-12), k
 
 
+@pytest.mark.parametrize("dtype", ["f16", "bf16", "f32"])
+def test_sh_at_an_unaligned_address_renders_the_same(dtype):
+    """Degree-3 SH coefficients are read 16 bytes at a time when the array is
+    16-byte aligned, one value at a time otherwise: coefficients stored one
+    element past an aligned address give the same image and gradients up to
+    the rounding order of the colour sum and atomic order."""
+    import torch
+
+    from paper_2412_12734_gb300 import render as R
+    sc = scenes.tiny_scene(34, K=30, tex_n=4, sh_degree=3, spread=0.8, sh_dtype=dtype)
+    cams = [scenes.tiny_camera(72, 56)]
+    rast = R.Rasterizer(0)
+    dev = R.scene_to_device(sc)
+    sh = dev["sh"]
+    buf = torch.empty(sh.numel() + 1, dtype=sh.dtype, device="cuda")
+    buf[1:] = sh.reshape(-1)
+    shifted = dict(dev, sh=buf[1:].view(sh.shape))
+    assert shifted["sh"].data_ptr() % 16 == sh.element_size()
+    d = torch.randn((72 * 56, 3), device="cuda")
+    a = rast.forward([dev], cams)
+    ga = rast.backward(a[3], d)[0]
+    b = rast.forward([shifted], cams)
+    gb = rast.backward(b[3], d)[0]
+    for x, y in zip(a[:3], b[:3]):
+        assert (x - y).abs().max().item() <= 1e-6
+    for k in ga:
+        scale = ga[k].abs().max().item()
+        assert (ga[k] - gb[k]).abs().max().item() <= 1e-5 * max(scale, 1e-12), k
+
+
 @pytest.mark.parametrize("tex_n", [2, 4, 8, 16])
 def test_backward_without_a_texture_gradient_output(tex_n):
     """The texture-gradient output may be left out (null): the backward skips
