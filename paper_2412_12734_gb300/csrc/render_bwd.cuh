@@ -20,7 +20,9 @@
 // clamped u or v lands); at N >= 8 the four grid corners.  The other texel
 // weights are added to global memory by each lane (N = 4 pairs that fit no
 // window; pairs of larger grids that weight more than one cell) or reduced for
-// the one grid cell they weight (a 16-value reduce-scatter).  Every reduced
+// the one grid cell they weight (a 16-value reduce-scatter); at N = 4 a pair
+// with few contributing lanes skips the reduce-scatter altogether
+// (kFewLanes4).  Every reduced
 // value goes to global memory with one atomic per (warp, splat) pair: nothing
 // accumulates in shared memory, which holds only the staged batch.  Measured on the 1M-splat,
 // 16-view workload against per-batch shared accumulators flushed once per
@@ -112,6 +114,14 @@ static_assert(kCornerSlot + 12 <= 32, "record and corner-texel values share one 
 // adding every texel weight directly (no window at all) 48.6 ms: the lanes of
 // a window pair mostly weight the same few texels, whose atomics serialize.
 constexpr int kDirectCells = 1;
+
+// At N = 4 a (warp, splat) pair with at most this many contributing lanes
+// skips the window and the reduce-scatter: each of those lanes adds its own
+// record values and texel weights to global memory.  Measured on the 16-view
+// workload (render_bwd at N = 4): 29.55 ms without, 29.03 / 28.72 / 28.53 /
+// 28.57 / 28.82 / 31.19 ms at 4 / 6 / 8 / 10 / 12 / 16 lanes; at N = 8 every
+// threshold from 1 to 4 was slower (35.6-35.8 against 34.4 ms).
+constexpr int kFewLanes4 = 8;
 
 // State of one pixel in the reverse walk.
 struct Pix {
@@ -510,6 +520,34 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
                 act |= pair_adjoint<N, TexT, true, VAR>(pix[p], uint32_t(bs + i), s_rec + 4 * i, lo, s_tex + i * NN,
                                                         sigma, kNk, nk, g, rem[p]);
             if (!__any_sync(0xffffffffu, act)) continue;
+            if (kGrid4 && P == 1 && __popc(__ballot_sync(0xffffffffu, act)) <= kFewLanes4) {
+                // few contributing lanes: each adds its own values
+                if (act) {
+                    float *rg = b.rec_grad + int64_t(s_j[i]) * kRecGrad;
+#pragma unroll
+                    for (int q = 0; q < kRecVals; ++q)
+                        if (g[q] != 0.0f) atomicAdd(rg + q, g[q]);
+                    if (g_tex) {
+                        const Rem &r = rem[0];
+                        float *t = g_tex + int64_t(s_k[i]) * TEXF + 3 * r.base;
+                        if (r.w00 != 0.0f) {
+                            atomicAdd(t + 0, r.w00 * r.c0); atomicAdd(t + 1, r.w00 * r.c1); atomicAdd(t + 2, r.w00 * r.c2);
+                        }
+                        if (r.w10 != 0.0f) {
+                            atomicAdd(t + 3 * N + 0, r.w10 * r.c0); atomicAdd(t + 3 * N + 1, r.w10 * r.c1);
+                            atomicAdd(t + 3 * N + 2, r.w10 * r.c2);
+                        }
+                        if (r.w01 != 0.0f) {
+                            atomicAdd(t + 3, r.w01 * r.c0); atomicAdd(t + 4, r.w01 * r.c1); atomicAdd(t + 5, r.w01 * r.c2);
+                        }
+                        if (r.w11 != 0.0f) {
+                            atomicAdd(t + 3 * N + 3, r.w11 * r.c0); atomicAdd(t + 3 * N + 4, r.w11 * r.c1);
+                            atomicAdd(t + 3 * N + 5, r.w11 * r.c2);
+                        }
+                    }
+                }
+                continue;
+            }
             const int kind = kGrid4 ? grid4_window<P>(rem, g) : 0;
             const float tot = warp_reduce_scatter32(g, lane);
             // this splat's texel gradients, formed where used (fewer live registers)
