@@ -107,12 +107,13 @@ static_assert(kCornerSlot + 12 <= 32, "record and corner-texel values share one 
 // interior cells in a (warp, splat) pair the lanes add their texel weights to
 // global memory themselves instead of one 16-value reduce-scatter per cell;
 // N = 4 pairs that fit no corner or line window always do.  Measured on the
-// 16-view workload: N = 8 / 16 backward 36.0 / 44.2 ms at 0, 34.5 / 43.5 at 1,
-// 35.6 / 44.3 at 2, 37.3 / 45.6 at 3; at N = 4 adding directly the lanes of the pairs without a
-// window took 33.5 ms against 37.0 with the border line holding most of their
-// pixels reduced through the window and a per-cell pass for the rest, and
-// adding every texel weight directly (no window at all) 48.6 ms: the lanes of
-// a window pair mostly weight the same few texels, whose atomics serialize.
+// 16-view workload: N = 8 / 16 backward 36.0 / 44.2 ms at 0, 34.5 / 43.5 at
+// 1, 35.6 / 44.3 at 2, 37.3 / 45.6 at 3; at N = 4 adding directly the lanes
+// of the pairs without a window took 33.5 ms against 37.0 with the border
+// line holding most of their pixels reduced through the window and a per-cell
+// pass for the rest, and adding every texel weight directly (no window at all)
+// 48.6 ms: the lanes of a window pair mostly weight the same few texels, whose
+// atomics serialize.
 constexpr int kDirectCells = 1;
 
 // At N = 4 a (warp, splat) pair with at most this many contributing lanes
