@@ -534,7 +534,7 @@ def launches_per_step(lib, step):
 # differ, or a configuration not captured, reports traffic null.
 TRAFFIC = {
     "render_bwd": {"files": ("render_bwd.cuh", "render_common.cuh", "render_bwd.cu", "render_bwd2.cu"),
-                   "sha256_16": "19271934f21afd87", "keys": ("workload", "tex_n", "tile", "batch", "ppt"),
+                   "sha256_16": "fa8633142f80a770", "keys": ("workload", "tex_n", "tile", "batch", "ppt"),
                    "measured": [({"workload": "batched_1m", "tex_n": 4, "tile": 16, "batch": 184, "ppt": 1},
                                  3.5810e9 + 0.9574e9)]},
     "render_fwd": {"files": ("render_fwd.cu", "render_common.cuh"),

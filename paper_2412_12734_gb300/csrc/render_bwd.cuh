@@ -22,12 +22,12 @@
 // window; pairs of larger grids that weight more than one cell) or reduced for
 // the one grid cell they weight (a 16-value reduce-scatter); at N = 4 a pair
 // with few contributing lanes skips the reduce-scatter altogether
-// (kFewLanes4).  Every reduced
-// value goes to global memory with one atomic per (warp, splat) pair: nothing
-// accumulates in shared memory, which holds only the staged batch.  Measured on the 1M-splat,
-// 16-view workload against per-batch shared accumulators flushed once per
-// tile: 40.5 -> 37.8 ms at N = 4 (batch 88 -> 184 in the same 48 KB), 54.0 ->
-// 41.0 ms at N = 8 (32 -> 64), 76.4 -> 54.1 ms at N = 16 (8 -> 16).
+// (kFewLanes4).  Every reduced value goes to global memory with one atomic per
+// (warp, splat) pair: nothing accumulates in shared memory, which holds only
+// the staged batch.  Measured on the 1M-splat, 16-view workload against
+// per-batch shared accumulators flushed once per tile: 40.5 -> 37.8 ms at
+// N = 4 (batch 88 -> 184 in the same 48 KB), 54.0 -> 41.0 ms at N = 8 (32 ->
+// 64), 76.4 -> 54.1 ms at N = 16 (8 -> 16).
 #pragma once
 
 #include <algorithm>
