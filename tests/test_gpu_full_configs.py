@@ -78,12 +78,12 @@ def test_plain_100k_gradcheck_64_splats():
         assert abs(num - ana) <= 2e-3 * abs(num) + 1e-4 * scale, (k, num, ana)
 
 
-@pytest.mark.parametrize("tex_n,kernel,batch,batch_fwd", [(4, 1, 88, 88), (8, 1, 32, 48), (4, 2, 176, 88)])
+@pytest.mark.parametrize("tex_n,kernel,batch,batch_fwd", [(4, 1, 184, 88), (8, 1, 64, 48), (4, 2, 176, 88)])
 def test_batched_1m_camera0_at_full_size(tex_n, kernel, batch, batch_fwd):
     """Camera 0 of the 16-view workload with all 16 views in the launch, keys
     bit-exact, image and gradients against the oracle, at the tile size and
     batch depths the autotuner picks for the bench on this workload (tile 16;
-    backward / forward depth 88 / 88 at N = 4, 32 / 48 at N = 8); kernel 1 / 2:
+    backward / forward depth 184 / 88 at N = 4, 64 / 48 at N = 8); kernel 1 / 2:
     the pixel-parallel / splat-parallel backward (the latter at depth 176)."""
     wl = scenes.workload("batched_1m", tex_n=tex_n)
     sc, cams = wl["scenes"][0], wl["cams"]
