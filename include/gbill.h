@@ -259,7 +259,10 @@ gb_status gb_saved_destroy(gb_saved *saved);
 /* Pre-sizes a saved state so that GB_FLAG_NO_SYNC forwards (e.g. inside a CUDA
  * graph capture) never allocate: `records` = sum over cameras of the scene's
  * splat count, `instances` = (tile, splat) pairs, `pixels` and `tiles` over
- * all cameras.  Synchronizes the device. */
+ * all cameras.  Synchronizes the device.  A forward recorded on the state
+ * stays valid: buffers that grow keep their contents, so its backward may
+ * follow the reserve.  Growing moves the buffers, so a CUDA graph captured
+ * on the state before the reserve must be captured again. */
 gb_status gb_saved_reserve(gb_saved *saved, int64_t records, int64_t instances, int64_t pixels,
                            int64_t tiles);
 

@@ -108,66 +108,92 @@ cudaError_t alloc_t(T **p, int64_t n) {
     return alloc(reinterpret_cast<void **>(p), size_t(std::max<int64_t>(n, 1)) * sizeof(T));
 }
 
-gb_status reserve_records(gb_saved *s, int64_t n) {
+// Grows *p, which holds old_n elements, to n elements.  With keep, the first
+// old_n elements move to the new allocation (a recorded forward stays valid
+// across gb_saved_reserve); without, the contents are dropped.  The device is
+// idle when it is called.
+template <typename T>
+cudaError_t grow_t(T **p, int64_t old_n, int64_t n, bool keep) {
+    if (!keep || !*p || old_n <= 0) return alloc_t(p, n);
+    T *q = nullptr;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&q), std::max<size_t>(size_t(std::max<int64_t>(n, 1)) * sizeof(T), 16));
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpy(q, *p, size_t(std::min(old_n, n)) * sizeof(T), cudaMemcpyDeviceToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(q);
+        return e;
+    }
+    e = cudaFree(*p);
+    *p = q;
+    return e;
+}
+
+// The reserve_* functions grow one group of saved-state buffers to at least n
+// elements.  keep: the buffers hold a recorded forward that a backward may
+// still read (gb_saved_reserve between a forward and its backward), so their
+// contents move with them; a forward sizing its own buffers drops them.
+gb_status reserve_records(gb_saved *s, int64_t n, bool keep = false) {
     if (n <= s->cap_rec) return GB_OK;
     gb_context *ctx = s->ctx;
     GB_CUDA(ctx, cudaDeviceSynchronize());
-    const int64_t c = n + n / 8 + 1024;
-    GB_CUDA(ctx, alloc_t(&s->rec, c));
-    GB_CUDA(ctx, alloc_t(&s->rec_lo, c));
-    GB_CUDA(ctx, alloc_t(&s->depth_key, c));
-    GB_CUDA(ctx, alloc_t(&s->keys_tmp, c));
-    GB_CUDA(ctx, alloc_t(&s->vals_tmp, c));
-    GB_CUDA(ctx, alloc_t(&s->dkeys_sorted, c));
-    GB_CUDA(ctx, alloc_t(&s->perm, c));
-    GB_CUDA(ctx, alloc_t(&s->offsets, c));
-    GB_CUDA(ctx, alloc_t(&s->rect, c));
-    GB_CUDA(ctx, alloc_t(&s->pbox, c));
-    GB_CUDA(ctx, alloc_t(&s->inv, c));
-    GB_CUDA(ctx, alloc_t(&s->rec_grad, c * kRecGrad));
+    const int64_t c = n + n / 8 + 1024, o = s->cap_rec;
+    GB_CUDA(ctx, grow_t(&s->rec, o, c, keep));
+    GB_CUDA(ctx, grow_t(&s->rec_lo, o, c, keep));
+    GB_CUDA(ctx, grow_t(&s->depth_key, o, c, keep));
+    GB_CUDA(ctx, grow_t(&s->keys_tmp, o, c, keep));
+    GB_CUDA(ctx, grow_t(&s->vals_tmp, o, c, keep));
+    GB_CUDA(ctx, grow_t(&s->dkeys_sorted, o, c, keep));
+    GB_CUDA(ctx, grow_t(&s->perm, o, c, keep));
+    GB_CUDA(ctx, grow_t(&s->offsets, o, c, keep));
+    GB_CUDA(ctx, grow_t(&s->rect, o, c, keep));
+    GB_CUDA(ctx, grow_t(&s->pbox, o, c, keep));
+    GB_CUDA(ctx, grow_t(&s->inv, o, c, keep));
+    GB_CUDA(ctx, grow_t(&s->rec_grad, o * kRecGrad, c * kRecGrad, keep));
     s->cap_rec = c;
     return GB_OK;
 }
 
-gb_status reserve_instances(gb_saved *s, int64_t n) {
+gb_status reserve_instances(gb_saved *s, int64_t n, bool keep = false) {
     if (n <= s->cap_inst) return GB_OK;
     gb_context *ctx = s->ctx;
     if (n >= int64_t(0xF0000000u))
         return fail(ctx, GB_ERR_CAPACITY, "%lld (tile, splat) instances exceed the 32-bit index range",
                     (long long)n);
     GB_CUDA(ctx, cudaDeviceSynchronize());
-    const int64_t c = std::min<int64_t>(n + n / 4 + 4096, int64_t(0xF0000000u));
-    GB_CUDA(ctx, alloc_t(&s->inst_tile, c));
-    GB_CUDA(ctx, alloc_t(&s->inst_val, c));
-    GB_CUDA(ctx, alloc_t(&s->inst_tile_tmp, c));
-    GB_CUDA(ctx, alloc_t(&s->inst_val_tmp, c));
-    GB_CUDA(ctx, alloc_t(&s->tiles_sorted, c));
-    GB_CUDA(ctx, alloc_t(&s->vals_sorted, c));
+    const int64_t c = std::min<int64_t>(n + n / 4 + 4096, int64_t(0xF0000000u)), o = s->cap_inst;
+    GB_CUDA(ctx, grow_t(&s->inst_tile, o, c, keep));
+    GB_CUDA(ctx, grow_t(&s->inst_val, o, c, keep));
+    GB_CUDA(ctx, grow_t(&s->inst_tile_tmp, o, c, keep));
+    GB_CUDA(ctx, grow_t(&s->inst_val_tmp, o, c, keep));
+    GB_CUDA(ctx, grow_t(&s->tiles_sorted, o, c, keep));
+    GB_CUDA(ctx, grow_t(&s->vals_sorted, o, c, keep));
     s->cap_inst = c;
     return GB_OK;
 }
 
-gb_status reserve_pixels(gb_saved *s, int64_t n) {
+gb_status reserve_pixels(gb_saved *s, int64_t n, bool keep = false) {
     if (n <= s->cap_pix) return GB_OK;
     gb_context *ctx = s->ctx;
     GB_CUDA(ctx, cudaDeviceSynchronize());
-    GB_CUDA(ctx, alloc_t(&s->t_final, n));
-    GB_CUDA(ctx, alloc_t(&s->last, n));
+    const int64_t o = s->cap_pix;
+    GB_CUDA(ctx, grow_t(&s->t_final, o, n, keep));
+    GB_CUDA(ctx, grow_t(&s->last, o, n, keep));
     s->cap_pix = n;
     return GB_OK;
 }
 
-gb_status reserve_tiles(gb_saved *s, int64_t n) {
+gb_status reserve_tiles(gb_saved *s, int64_t n, bool keep = false) {
     if (n <= s->cap_tiles) return GB_OK;
     gb_context *ctx = s->ctx;
     GB_CUDA(ctx, cudaDeviceSynchronize());
-    GB_CUDA(ctx, alloc_t(&s->ranges, n));
-    GB_CUDA(ctx, alloc_t(&s->tl_keys, n));
-    GB_CUDA(ctx, alloc_t(&s->tl_vals, n));
-    GB_CUDA(ctx, alloc_t(&s->tl_keys_tmp, n));
-    GB_CUDA(ctx, alloc_t(&s->tl_vals_tmp, n));
-    GB_CUDA(ctx, alloc_t(&s->tl_keys_out, n));
-    GB_CUDA(ctx, alloc_t(&s->tile_list, n));
+    const int64_t o = s->cap_tiles;
+    GB_CUDA(ctx, grow_t(&s->ranges, o, n, keep));
+    GB_CUDA(ctx, grow_t(&s->tl_keys, o, n, keep));
+    GB_CUDA(ctx, grow_t(&s->tl_vals, o, n, keep));
+    GB_CUDA(ctx, grow_t(&s->tl_keys_tmp, o, n, keep));
+    GB_CUDA(ctx, grow_t(&s->tl_vals_tmp, o, n, keep));
+    GB_CUDA(ctx, grow_t(&s->tl_keys_out, o, n, keep));
+    GB_CUDA(ctx, grow_t(&s->tile_list, o, n, keep));
     if (!s->work) GB_CUDA(ctx, alloc_t(&s->work, 2 * kMaxGroups));
     s->cap_tiles = n;
     return GB_OK;
@@ -500,10 +526,12 @@ gb_status gb_saved_reserve(gb_saved *s, int64_t records, int64_t instances, int6
     if (!s || records < 0 || instances < 0 || pixels < 0 || tiles < 0)
         return fail(s ? s->ctx : nullptr, GB_ERR_INVALID_ARG, "bad reserve arguments");
     gb_status st;
-    if ((st = reserve_records(s, records)) != GB_OK) return st;
-    if ((st = reserve_instances(s, instances)) != GB_OK) return st;
-    if ((st = reserve_pixels(s, pixels)) != GB_OK) return st;
-    if ((st = reserve_tiles(s, tiles)) != GB_OK) return st;
+    // a recorded forward stays valid: a backward may follow the reserve
+    const bool keep = s->has_forward;
+    if ((st = reserve_records(s, records, keep)) != GB_OK) return st;
+    if ((st = reserve_instances(s, instances, keep)) != GB_OK) return st;
+    if ((st = reserve_pixels(s, pixels, keep)) != GB_OK) return st;
+    if ((st = reserve_tiles(s, tiles, keep)) != GB_OK) return st;
     if ((st = reserve_scratch(s)) != GB_OK) return st;
     GB_CUDA(s->ctx, cudaDeviceSynchronize());
     return GB_OK;

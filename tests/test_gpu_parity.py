@@ -326,6 +326,35 @@ def test_second_backward_after_one_forward_gives_the_same_gradients(flags):
         assert (g1[k] - ref[k]).abs().max().item() <= 1e-5 * scale, k
         assert (g2[k] - ref[k]).abs().max().item() <= 1e-5 * scale, k
 
+@pytest.mark.parametrize("flags", [0, 2])
+def test_reserve_between_forward_and_backward_keeps_the_forward(flags):
+    """A reserve that grows every buffer group (records, instances, pixels,
+    tiles) between a synchronizing forward and its backward moves the recorded
+    forward with the buffers: the backward equals the same forward's backward
+    without the reserve (flag 2: persistent blocks, which also read the tile
+    list)."""
+    import torch
+
+    from paper_2412_12734_gb300 import render as R
+    sc, cams = CASES["dense_many_tiles"]()
+    rast = R.Rasterizer(0)
+    dev = [R.scene_to_device(s) for s in sc]
+    P = rast.pixel_count(cams)
+    d = torch.randn((P, 3), device="cuda")
+    ref = rast.backward(rast.forward(dev, cams, flags=flags)[3], d)[0]
+    saved = rast.forward(dev, cams, flags=flags)[3]
+    st = saved.stats()
+    saved.reserve(4 * st["records"] + 4096, 4 * st["capacity"], 4 * P, 4 * st["tiles"])
+    after = saved.stats()
+    assert after["capacity"] > st["capacity"]
+    assert after["instances"] == st["instances"]
+    g = rast.backward(saved, d)[0]
+    torch.cuda.synchronize()
+    for k in ref:
+        scale = ref[k].abs().max().item()
+        assert (g[k] - ref[k]).abs().max().item() <= 1e-5 * max(scale, 1e-12), k
+
+
 def test_graph_replay_with_new_parameters_matches_eager():
     """A no-sync forward and backward captured in a CUDA graph, replayed after
     the splat parameters were overwritten in place (other centres and sizes:
