@@ -118,11 +118,30 @@ constexpr int kDirectCells = 1;
 
 // At N = 4 a (warp, splat) pair with at most this many contributing lanes
 // skips the window and the reduce-scatter: each of those lanes adds its own
-// record values and texel weights to global memory.  Measured on the 16-view
-// workload (render_bwd at N = 4): 29.55 ms without, 29.03 / 28.72 / 28.53 /
-// 28.57 / 28.82 / 31.19 ms at 4 / 6 / 8 / 10 / 12 / 16 lanes; at N = 8 every
-// threshold from 1 to 4 was slower (35.6-35.8 against 34.4 ms).
-constexpr int kFewLanes4 = 8;
+// record values (four 128-bit reductions) and texel weights (a 64-bit and a
+// 32-bit reduction per texel) to global memory.  Measured on the 16-view
+// workload (render_bwd at N = 4): 29.55 ms without; with scalar reductions
+// 29.03 / 28.53 / 28.82 / 31.19 ms at 4 / 8 / 12 / 16 lanes; with the record
+// values as 128-bit reductions 26.50 ms at 8, 25.42 / 25.49 / 26.14 / 67.3 ms
+// at 16 / 20 / 24 / 32 lanes (every pair direct: the lanes' reductions to the
+// same texels serialize), and 25.06 ms at 16 with the texels' 64-bit pairs.
+// At N = 8 every threshold from 1 to 4 was slower (35.6-35.8 against 34.4 ms
+// with scalar reductions).
+constexpr int kFewLanes4 = 16;
+
+// Adds w (c0, c1, c2) to the RGB texel at t: one 64-bit and one 32-bit
+// reduction (t is 4-byte aligned; the pair goes where it is 8-byte aligned).
+// Used where few lanes add texels (at N >= 8, in the direct texel pass of many
+// lanes, three 32-bit reductions measured faster: 34.4 against 34.9 ms).
+__device__ __forceinline__ void add_texel(float *t, float w, float c0, float c1, float c2) {
+    if ((reinterpret_cast<uintptr_t>(t) & 7u) == 0) {
+        atomicAdd(reinterpret_cast<float2 *>(t), make_float2(w * c0, w * c1));
+        atomicAdd(t + 2, w * c2);
+    } else {
+        atomicAdd(t, w * c0);
+        atomicAdd(reinterpret_cast<float2 *>(t + 1), make_float2(w * c1, w * c2));
+    }
+}
 
 // State of one pixel in the reverse walk.
 struct Pix {
@@ -524,27 +543,18 @@ __device__ __forceinline__ void bwd_tile(const Frame &f, const RenderBwdBufs &b,
             if (kGrid4 && P == 1 && __popc(__ballot_sync(0xffffffffu, act)) <= kFewLanes4) {
                 // few contributing lanes: each adds its own values
                 if (act) {
-                    float *rg = b.rec_grad + int64_t(s_j[i]) * kRecGrad;
+                    // the record's 16 slots are 64-byte aligned (rows of the gradient array)
+                    float4 *rg = reinterpret_cast<float4 *>(b.rec_grad + int64_t(s_j[i]) * kRecGrad);
 #pragma unroll
-                    for (int q = 0; q < kRecVals; ++q)
-                        if (g[q] != 0.0f) atomicAdd(rg + q, g[q]);
+                    for (int q = 0; q < kRecVals / 4; ++q)
+                        atomicAdd(rg + q, make_float4(g[4 * q], g[4 * q + 1], g[4 * q + 2], g[4 * q + 3]));
                     if (g_tex) {
                         const Rem &r = rem[0];
                         float *t = g_tex + int64_t(s_k[i]) * TEXF + 3 * r.base;
-                        if (r.w00 != 0.0f) {
-                            atomicAdd(t + 0, r.w00 * r.c0); atomicAdd(t + 1, r.w00 * r.c1); atomicAdd(t + 2, r.w00 * r.c2);
-                        }
-                        if (r.w10 != 0.0f) {
-                            atomicAdd(t + 3 * N + 0, r.w10 * r.c0); atomicAdd(t + 3 * N + 1, r.w10 * r.c1);
-                            atomicAdd(t + 3 * N + 2, r.w10 * r.c2);
-                        }
-                        if (r.w01 != 0.0f) {
-                            atomicAdd(t + 3, r.w01 * r.c0); atomicAdd(t + 4, r.w01 * r.c1); atomicAdd(t + 5, r.w01 * r.c2);
-                        }
-                        if (r.w11 != 0.0f) {
-                            atomicAdd(t + 3 * N + 3, r.w11 * r.c0); atomicAdd(t + 3 * N + 4, r.w11 * r.c1);
-                            atomicAdd(t + 3 * N + 5, r.w11 * r.c2);
-                        }
+                        if (r.w00 != 0.0f) add_texel(t, r.w00, r.c0, r.c1, r.c2);
+                        if (r.w10 != 0.0f) add_texel(t + 3 * N, r.w10, r.c0, r.c1, r.c2);
+                        if (r.w01 != 0.0f) add_texel(t + 3, r.w01, r.c0, r.c1, r.c2);
+                        if (r.w11 != 0.0f) add_texel(t + 3 * N + 3, r.w11, r.c0, r.c1, r.c2);
                     }
                 }
                 continue;
