@@ -238,6 +238,26 @@ def test_faint_splat_below_the_alpha_cutoff_is_culled():
     np.testing.assert_allclose(oracle.render(sc, cam)["alpha"][24, 32], float(np.float32(0.004)), rtol=1e-12)
 
 
+def test_empty_and_behind_camera_scenes_render_the_background():
+    """No splat in front of the camera (K = 0, or every centre behind it):
+    every pixel keeps T = 1, so the image is the background (Alg. 1 with an
+    empty list), alpha and depth are zero, and every gradient is zero."""
+    cam = scenes.tiny_camera(24, 16)
+    bg = np.array([0.2, 0.5, 0.7])
+    empty = scenes.subset(scenes.tiny_scene(1, K=3), np.arange(0))
+    behind = scenes.tiny_scene(2, K=4)
+    behind["means"][:, 2] = -6.0  # the camera sits at z = -4 looking along +z
+    rng = np.random.default_rng(3)
+    for sc in (empty, behind):
+        r = oracle.render(sc, cam, bg=bg)
+        assert np.array_equal(r["rgb"], np.broadcast_to(bg, r["rgb"].shape))
+        assert np.all(r["alpha"] == 0.0) and np.all(r["depth"] == 0.0)
+        assert np.all(r["t_final"] == 1.0) and np.all(r["n_contrib"] == 0)
+        g = oracle.backward(sc, cam, rng.standard_normal((16, 24, 3)), bg=bg)
+        for k, v in g.items():
+            assert v.shape[0] == sc["means"].shape[0] and np.all(v == 0.0), k
+
+
 def test_fronto_parallel_uv_and_colour_closed_form():
     """Fronto-parallel splat: u = (x_c - c_x) d / (f s_u), v likewise; alpha =
     o exp(-(u^2+v^2)/2) on the uv branch; colour from an affine grid."""
