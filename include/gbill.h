@@ -346,7 +346,9 @@ gb_status gb_render_forward(gb_context *ctx, gb_saved *saved, const gb_scene *sc
  *   grads   host array [n_scenes] of gb_grads (device pointers), overwritten
  *           with the gradient summed over each scene's cameras.
  * The scene parameter arrays passed to the forward must be unchanged.
- * Enqueued on `stream`, never synchronizes. */
+ * Enqueued on `stream`, never synchronizes.  It reads what the forward wrote
+ * into `saved`: use the forward's stream, or order `stream` after it (an
+ * event), as for any dependent CUDA work. */
 gb_status gb_render_backward(gb_context *ctx, gb_saved *saved, const float *d_rgb,
                              const float *d_depth, const float *d_alpha, const gb_grads *grads,
                              int32_t n_scenes, void *stream);
