@@ -94,6 +94,7 @@ MUTANTS = {
     # FP32 tile rectangles (keys)
     "key depth from the wrong coordinate": ("*z_out = P2;", "*z_out = P0;"),
     "opacity cull threshold 1/64": ("if (!(o >= 1.0f / 255.0f)) return 0;", "if (!(o >= 1.0f / 64.0f)) return 0;"),
+    "near-plane cull dropped": ("if (!(P2 > near_plane)) return 0;", "if (false) return 0;"),
     "rectangle radius too small": ("static const float kRhoMaxF = 11.0825270903f;",
                                    "static const float kRhoMaxF = 9.0f;"),
     "rectangle low bound rounded down": ("const float fx0 = std::fmax(std::ceil(lox - 0.5f), 0.0f);",
@@ -114,6 +115,7 @@ PINS = [
     (pins.test_single_splat_at_pixel_centre, {"N": 4, "o": 0.995}),
     (pins.test_single_splat_at_pixel_centre, {"N": 4, "o": 0.01}),
     (pins.test_faint_splat_below_the_alpha_cutoff_is_culled, {}),
+    (pins.test_empty_and_behind_camera_scenes_render_the_background, {}),
     (pins.test_fronto_parallel_uv_and_colour_closed_form, {}),
     (pins.test_lowpass_branch_closed_form, {}),
     (pins.test_tilted_splat_ray_plane_intersection, {}),
