@@ -332,13 +332,14 @@ class _RenderFn(torch.autograd.Function):
         ctx.rast = rast
         ctx.keep = sc  # parameters must stay alive and unchanged until backward
         ctx.dtypes = (sh.dtype, textures.dtype)
+        ctx.n_pix = rgb.shape[0]
         return rgb, depth, alpha
 
     @staticmethod
     def backward(ctx, d_rgb, d_depth, d_alpha):
         d_rgb = d_rgb.contiguous().float() if d_rgb is not None else None
-        if d_rgb is None:
-            d_rgb = torch.zeros_like(ctx.keep["means"][:0])
+        if d_rgb is None:  # only without materialised gradients: the library needs [P, 3]
+            d_rgb = torch.zeros((ctx.n_pix, 3), device=ctx.keep["means"].device)
         d_depth = d_depth.contiguous().float() if d_depth is not None else None
         d_alpha = d_alpha.contiguous().float() if d_alpha is not None else None
         g = ctx.rast.backward(ctx.saved_handle, d_rgb, d_depth, d_alpha)[0]
