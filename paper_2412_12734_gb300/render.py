@@ -64,6 +64,25 @@ def _check_tensor(t: torch.Tensor, name: str, shape_tail, dtypes=(torch.float32,
         raise ValueError(f"{name}: shape {tuple(t.shape)} does not end in {shape_tail}")
 
 
+def _check_buffer(t: torch.Tensor, name: str, numel: int):
+    """A buffer the library reads or writes through a plain pointer (an
+    output, an upstream gradient or a gradient output): CUDA, float32,
+    contiguous and exactly ``numel`` elements, which the C ABI cannot check."""
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float32 tensor")
+    if t.numel() != numel:
+        raise ValueError(f"{name}: {t.numel()} elements, expected {numel}")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+
+
+def grad_shapes(K: int, D: int, N: int, Mt: int) -> dict:
+    """Shape of each gradient output of a scene of K splats, SH degree D,
+    N x N grids and Mt SH coefficients per texel (0: RGB texels)."""
+    return {"means": (K, 3), "quats": (K, 4), "scales": (K, 2), "opacities": (K,), "sh": (K, (D + 1) ** 2, 3),
+            "textures": (K, N, N, 3) if Mt == 0 else (K, N, N, Mt, 3)}
+
+
 def scene_struct(sc: dict) -> L.gb_scene:
     K = int(sc["means"].shape[0])
     D, N = int(sc["sh_degree"]), int(sc["tex_n"])
@@ -106,6 +125,7 @@ class Saved:
         self.handle = h
         self.n_scenes = 0
         self.shapes = []
+        self.n_pix = None
 
     def reserve(self, records: int, instances: int, pixels: int, tiles: int):
         L.check(L.load().gb_saved_reserve(self.handle, records, instances, pixels, tiles), self.rast.ctx)
@@ -212,8 +232,14 @@ class Rasterizer:
             alpha = torch.empty(P, device=dev)
         else:
             rgb, depth, alpha = out
+            _check_buffer(rgb, "rgb", 3 * P)
+            if depth is not None:
+                _check_buffer(depth, "depth", P)
+            if alpha is not None:
+                _check_buffer(alpha, "alpha", P)
         if saved is None:
             saved = Saved(self)
+        saved.n_pix = P
         saved.n_scenes = n_s
         saved.shapes = [(int(s["means"].shape[0]), int(s["sh_degree"]), int(s["tex_n"]),
                          (int(s.get("tex_sh_degree", 0)) + 1) ** 2 if int(s.get("tex_sh_degree", 0)) else 0)
@@ -231,22 +257,25 @@ class Rasterizer:
         lib = L.load()
         dev = d_rgb.device
         if grads is None:
-            grads = []
-            for K, D, N, Mt in saved.shapes:
-                grads.append({
-                    "means": torch.empty((K, 3), device=dev), "quats": torch.empty((K, 4), device=dev),
-                    "scales": torch.empty((K, 2), device=dev), "opacities": torch.empty(K, device=dev),
-                    "sh": torch.empty((K, (D + 1) ** 2, 3), device=dev),
-                    "textures": torch.empty((K, N, N, 3) if Mt == 0 else (K, N, N, Mt, 3), device=dev),
-                })
+            grads = [{k: torch.empty(shape, device=dev) for k, shape in grad_shapes(*sh).items()}
+                     for sh in saved.shapes]
+        if len(grads) != saved.n_scenes:
+            raise ValueError(f"grads: {len(grads)} entries for {saved.n_scenes} scenes")
         garr = (L.gb_grads * len(grads))()
         for i, g in enumerate(grads):
+            want = grad_shapes(*saved.shapes[i])
             for k in PARAMS:
                 t = g.get(k)
+                if t is not None:
+                    _check_buffer(t, f"grads[{i}][{k!r}]", int(np.prod(want[k])))
                 setattr(garr[i], "d_" + k, t.data_ptr() if t is not None else None)
-        for t, name in ((d_rgb, "d_rgb"), (d_depth, "d_depth"), (d_alpha, "d_alpha")):
-            if t is not None and (not t.is_contiguous() or t.dtype != torch.float32):
-                raise ValueError(f"{name} must be contiguous float32")
+        n_pix = saved.n_pix
+        for t, name, m in ((d_rgb, "d_rgb", 3), (d_depth, "d_depth", 1), (d_alpha, "d_alpha", 1)):
+            if t is not None:
+                if n_pix is not None:
+                    _check_buffer(t, name, m * n_pix)
+                elif not t.is_contiguous() or t.dtype != torch.float32:
+                    raise ValueError(f"{name} must be contiguous float32")
         s = stream if stream is not None else torch.cuda.current_stream(dev)
         st = lib.gb_render_backward(self.ctx, saved.handle, d_rgb.data_ptr(),
                                     d_depth.data_ptr() if d_depth is not None else None,
